@@ -1,0 +1,163 @@
+"""Alg. 2 (fast Fourier-space sum) restated step by step, plain FP64 (oracle; test use only).
+
+Given the plan's (m, P, cs, cw, rc) for a box [0, L)^3, with h = L/m and the
+window half-width alpha = P h / 2 (Sec. 6.3, eq. alpha and the relation alpha = P L/(2m)):
+
+1. spread   a_l = sum_j rho_j phitilde(x_j - h l)                       (Alg. 2 step 1, eq. spread_def)
+            phi^{cw}(y) = prod_i psi^{cw}(y_i/alpha)/psi^{cw}(0) on [-alpha, alpha]^3
+            Each particle touches the P grid points l0..l0+P-1 per axis,
+            l0 = ceil(x/h - P/2) (the points with x - h l in (-alpha, alpha]);
+            indices are taken mod m (periodisation).
+2. FFT      ahat_k = sum_l a_l e^{+2 pi i k.l/m}                          (Alg. 2 step 2)
+3. scale    bhat_k = S(k) ahat_k,  S(0) = 0,
+            S(k) = (1/V) Mhat(k) / [phihat(k)/h^3]^2                      (Alg. 2 step 3, eq. diag_scale)
+            phihat(k)/h^3 = prod_i (1/h) int phi_1d(y) e^{-i w_i y} dy,  w_i = 2 pi k_i/L.
+            The factor h^-3 converts the continuous transform of Sec. 4.3 into the
+            coefficient seen by an unnormalised m^3-point DFT (Poisson summation with
+            c_k = phihat/V of eq. fcoeffs, times m^3); Alg. 2 as printed leaves it implicit.
+            S(k) = 0 also for |k| > m/2 (the cube corners of I_m): Prop. 1 bounds the
+            split error by the modes outside this ball, and deconvolving the corners,
+            where phihat ~ psi(1)^3, amplifies FFT rounding by ~exp(3 c_w - c_s)
+            (``ball=False`` keeps the full cube for comparison).
+4. IFFT     b_l = sum_k bhat_k e^{-2 pi i k.l/m}                          (Alg. 2 step 4)
+5. interp   phi_i^far = sum_l b_l phitilde(x_i - h l)                     (Alg. 2 step 5)
+            grad phi_i^far = sum_l b_l grad phitilde(x_i - h l)           (Remark 'force', eq. force)
+            d/dy_j phi = (1/alpha) psi'(y_j/alpha) prod_{i != j} psi(y_i/alpha) / psi(0)^3
+
+psi is evaluated exactly from its Legendre series (no polynomial fits), the
+FFTs are NumPy's complex FFTs, and k runs over I_m = {-m/2, ..., m/2-1}.
+
+Parity status: pinned (tests/test_oracle_alg2.py) against the converged Ewald sum
+of ``exact`` (its difference is the method's own error, compared with the error
+models of Sec. 5) and by a single-charge DFT identity.
+"""
+import numpy as np
+
+from .pswf import PSWF
+from .split import PSWFSplit
+from .exact import wrap, realspace
+
+
+class Alg2:
+    def __init__(self, L, m, P, cs, cw, rc, ball=True):
+        self.ball = bool(ball)
+        self.L, self.m, self.P = float(L), int(m), int(P)
+        self.cs, self.cw, self.rc = float(cs), float(cw), float(rc)
+        self.h = self.L / self.m
+        self.alpha = self.P * self.h / 2.0
+        self.win = PSWF(self.cw)
+        self.split = PSWFSplit(self.cs, self.rc)
+
+    # -- window ------------------------------------------------------------------
+    def _stencil(self, x):
+        """Per-axis grid indices (n,3,P) and window arguments s = (x - h l)/alpha."""
+        t = x / self.h
+        l0 = np.ceil(t - self.P / 2.0)
+        a = np.arange(self.P, dtype=np.float64)
+        l = l0[:, :, None] + a[None, None, :]
+        s = (x[:, :, None] - self.h * l) / self.alpha
+        idx = np.mod(l.astype(np.int64), self.m)
+        return idx, s
+
+    def window_1d(self, s):
+        return self.win.psi(s) / self.win.psi0
+
+    def dwindow_1d(self, s):
+        return self.win.dpsi(s) / (self.win.psi0 * self.alpha)
+
+    # -- Alg. 2 steps -----------------------------------------------------------
+    def spread(self, x, rho, chunk=4096):
+        x = wrap(x, self.L)
+        m, P = self.m, self.P
+        a = np.zeros(m ** 3)
+        for s0 in range(0, len(x), chunk):
+            idx, s = self._stencil(x[s0:s0 + chunk])
+            w = self.window_1d(s)
+            r = np.asarray(rho[s0:s0 + chunk], dtype=np.float64)
+            vals = (r[:, None, None, None] * w[:, 0, :, None, None]
+                    * w[:, 1, None, :, None] * w[:, 2, None, None, :])
+            flat = (idx[:, 0, :, None, None] * m + idx[:, 1, None, :, None]) * m + idx[:, 2, None, None, :]
+            a += np.bincount(flat.ravel(), weights=vals.ravel(), minlength=m ** 3)
+        return a.reshape(m, m, m)
+
+    def kgrid(self):
+        return np.fft.fftfreq(self.m) * self.m           # index -> k in I_m
+
+    def scaling(self):
+        """S(k) on the full m^3 index grid (S(0) = 0)."""
+        m, L = self.m, self.L
+        k = self.kgrid()
+        # window transform per axis, divided by h: (1/h) int_{-alpha}^{alpha} psi(y/alpha)/psi(0) cos(w y) dy
+        w = 2.0 * np.pi * k / L
+        ph1 = self.alpha * self.win.cos_transform(w * self.alpha) / (self.win.psi0 * self.h)
+        KX, KY, KZ = np.meshgrid(k, k, k, indexing='ij')
+        k2 = (KX ** 2 + KY ** 2 + KZ ** 2)
+        S = np.zeros(k2.shape)
+        nz = k2 > 0
+        uk, inv = np.unique(k2[nz], return_inverse=True)
+        Mh = self.split.Mhat_k2(uk, L)[inv]
+        den = (ph1[:, None, None] * ph1[None, :, None] * ph1[None, None, :]) ** 2
+        S[nz] = Mh / (L ** 3) / den[nz]
+        if self.ball:
+            S[4 * k2 > m * m] = 0.0
+        return S
+
+    def fft(self, a):
+        return np.fft.ifftn(a) * a.size                  # e^{+2 pi i k.l/m}, unnormalised
+
+    def ifft(self, bh):
+        return np.fft.fftn(bh)                           # e^{-2 pi i k.l/m}, unnormalised
+
+    def interp(self, x, b, chunk=4096):
+        x = wrap(x, self.L)
+        m = self.m
+        bf = b.ravel()
+        phi = np.zeros(len(x))
+        grad = np.zeros((len(x), 3))
+        for s0 in range(0, len(x), chunk):
+            idx, s = self._stencil(x[s0:s0 + chunk])
+            w = self.window_1d(s)
+            dw = self.dwindow_1d(s)
+            flat = (idx[:, 0, :, None, None] * m + idx[:, 1, None, :, None]) * m + idx[:, 2, None, None, :]
+            G = bf[flat]                                  # (c, P, P, P)
+            # contract the z axis, then y, then x (plain tensor contractions)
+            Gz = np.einsum('nabc,nc->nab', G, w[:, 2])
+            Gdz = np.einsum('nabc,nc->nab', G, dw[:, 2])
+            Gzy = np.einsum('nab,nb->na', Gz, w[:, 1])
+            Gzdy = np.einsum('nab,nb->na', Gz, dw[:, 1])
+            Gdzy = np.einsum('nab,nb->na', Gdz, w[:, 1])
+            sl = slice(s0, s0 + chunk)
+            phi[sl] = np.einsum('na,na->n', Gzy, w[:, 0])
+            grad[sl, 0] = np.einsum('na,na->n', Gzy, dw[:, 0])
+            grad[sl, 1] = np.einsum('na,na->n', Gzdy, w[:, 0])
+            grad[sl, 2] = np.einsum('na,na->n', Gdzy, w[:, 0])
+        return phi, grad
+
+    def far(self, x, rho, stages=False, targets=None):
+        a = self.spread(x, rho)
+        ah = self.fft(a)
+        bh = self.scaling() * ah
+        b = np.real(self.ifft(bh))
+        xt = x if targets is None else np.asarray(x)[targets]
+        phi, grad = self.interp(xt, b)
+        if stages:
+            return phi, grad, {"a": a, "ahat": ah, "bhat": bh, "b": b}
+        return phi, grad
+
+    def total(self, x, rho, stages=False, targets=None):
+        """phi, grad phi, E, F of the fast method (far + local + self) on CPU."""
+        rho = np.asarray(rho, dtype=np.float64)
+        out = self.far(x, rho, stages=stages, targets=targets)
+        pf, gf = out[0], out[1]
+        pl, gl = realspace(x, rho, self.L, self.split, self.rc, targets=targets)
+        if targets is not None:
+            r = rho[targets]
+        else:
+            r = rho
+        phi = pl + pf - self.split.self_coeff() * r
+        grad = gl + gf
+        F = -r[:, None] * grad
+        E = 0.5 * float(np.dot(rho, phi)) if targets is None else None
+        if stages:
+            return phi, grad, E, F, out[2]
+        return phi, grad, E, F

@@ -1,0 +1,161 @@
+"""Converged triply periodic Ewald sums, plain FP64 (oracle; test use only).
+
+The potential at x_i (Sec. 3.1, eqs. potential2 / Ewald decomposition):
+  phi_i = phi_i^local + phi_i^far + phi_i^self
+  phi_i^local = sum_{r in Z^3} sum_j' rho_j R(|x_i - x_j + L r|)          (real space)
+  phi_i^far   = (1/V) sum_{k != 0} Mhat(k) Re[rhohat(k) e^{-2 pi i k.x_i/L}],
+                rhohat(k) = sum_j rho_j e^{+2 pi i k.x_j/L}                 (Alg. 1, eq. Fsum)
+  phi_i^self  = -lim_{r->0} M(r) rho_i
+  E = 1/2 sum_i rho_i phi_i,   F_i = -rho_i grad phi_i                    (Remark after eq. Ewald)
+The k-sum runs over the whole sphere |k| <= K (not truncated to I_m); the
+caller picks K so that the omitted tail is below the test tolerance.  The prime
+omits (j = i, r = 0).
+
+``lattice_shell_sum`` is the brute-force replica sum of 1/r over cubic shells
+|r|_inf <= N, used to pin the Ewald result on tiny neutral systems.
+
+Parity status: pinned (tests/test_oracle_exact.py) by split independence
+(two PSWF cutoffs and the Gaussian split agree), the NaCl Madelung constant,
+brute-force lattice sums, translation invariance, the scaling law of
+eq. phinondim and sum_i F_i = 0.
+"""
+import numpy as np
+
+
+def wrap(x, L):
+    """Map positions into the periodic box [0, L)^3."""
+    x = np.mod(np.asarray(x, dtype=np.float64), L)
+    return np.where(x >= L, x - L, x)
+
+
+def realspace(x, rho, L, split, rcut, targets=None, chunk=64):
+    """phi^local and grad phi^local at the targets (all particles by default).
+
+    Sums every periodic image within ``rcut`` of the target.
+    """
+    x = wrap(x, L)
+    rho = np.asarray(rho, dtype=np.float64)
+    tgt = np.arange(len(x)) if targets is None else np.asarray(targets)
+    if rcut <= 0.5 * L:
+        # any image other than the minimum one is at least L/2 away
+        shifts = np.zeros((1, 3))
+    else:
+        nimg = int(np.ceil(rcut / L))
+        rng = np.arange(-nimg, nimg + 1)
+        shifts = np.array([(a, b, c) for a in rng for b in rng for c in rng], dtype=np.float64) * L
+    phi = np.zeros(len(tgt))
+    grad = np.zeros((len(tgt), 3))
+    for s in range(0, len(tgt), chunk):
+        ti = tgt[s:s + chunk]
+        d0 = x[ti, None, :] - x[None, :, :]
+        d0 -= L * np.round(d0 / L)               # minimum image, then explicit shells
+        for sh in shifts:
+            d = d0 + sh
+            r = np.sqrt(np.sum(d * d, axis=-1))
+            mask = r < rcut
+            self_pair = (ti[:, None] == np.arange(len(x))[None, :]) & (r < 1e-300)
+            mask &= ~self_pair
+            if not mask.any():
+                continue
+            rs = np.where(mask, r, 1.0)
+            Rv = np.where(mask, split.R(rs), 0.0)
+            dRv = np.where(mask, split.dR(rs), 0.0)
+            phi[s:s + chunk] += Rv @ rho
+            coef = dRv / rs * rho[None, :]
+            grad[s:s + chunk] += np.einsum('tn,tnd->td', coef, d)
+    return phi, grad
+
+
+def structure_factor(x, rho, L, K):
+    """rhohat(k) = sum_j rho_j exp(+2 pi i k.x_j / L) on the cube |k_i| <= K."""
+    x = wrap(x, L)
+    kr = np.arange(-K, K + 1)
+    E = np.exp(2j * np.pi * x[:, :, None] * kr[None, None, :] / L)   # (n, 3, 2K+1)
+    Ex, Ey, Ez = E[:, 0, :], E[:, 1, :], E[:, 2, :]
+    rh = np.empty((2 * K + 1,) * 3, dtype=np.complex128)
+    for ix in range(2 * K + 1):
+        A = (np.asarray(rho) * Ex[:, ix])[:, None] * Ey
+        rh[ix] = A.T @ Ez
+    return rh
+
+
+def kspace(x, rho, L, split, K, targets=None):
+    """phi^far and grad phi^far from the direct Fourier sum over 0 < |k| <= K."""
+    x = wrap(x, L)
+    V = L ** 3
+    kr = np.arange(-K, K + 1)
+    KX, KY, KZ = np.meshgrid(kr, kr, kr, indexing='ij')
+    k2 = KX ** 2 + KY ** 2 + KZ ** 2
+    mask = (k2 > 0) & (k2 <= K * K)
+    Mh = np.zeros(k2.shape)
+    uk, inv = np.unique(k2[mask], return_inverse=True)
+    Mh[mask] = split.Mhat_k2(uk.astype(np.float64), L)[inv]
+    C = Mh * structure_factor(x, rho, L, K) / V        # (1/V) Mhat rhohat
+    tgt = np.arange(len(x)) if targets is None else np.asarray(targets)
+    xt = x[tgt]
+    E = np.exp(-2j * np.pi * xt[:, :, None] * kr[None, None, :] / L)   # e^{-2 pi i k.x/L}
+    Ex, Ey, Ez = E[:, 0, :], E[:, 1, :], E[:, 2, :]
+    fac = -2j * np.pi * kr / L
+    phi = np.zeros(len(tgt))
+    grad = np.zeros((len(tgt), 3))
+    for ix in range(2 * K + 1):
+        B = Ex[:, ix][:, None] * Ey                     # (t, ky)
+        T = B @ C[ix]                                   # (t, kz): sum over ky
+        Ty = (B * fac[None, :]) @ C[ix]
+        phi += np.real(np.sum(T * Ez, axis=1))
+        grad[:, 0] += np.real(fac[ix] * np.sum(T * Ez, axis=1))
+        grad[:, 1] += np.real(np.sum(Ty * Ez, axis=1))
+        grad[:, 2] += np.real(np.sum(T * Ez * fac[None, :], axis=1))
+    return phi, grad
+
+
+def ewald(x, rho, L, split, K, rcut, targets=None):
+    """Total phi, grad phi, energy (only when all particles are targets) and forces."""
+    rho = np.asarray(rho, dtype=np.float64)
+    pl, gl = realspace(x, rho, L, split, rcut, targets)
+    pf, gf = kspace(x, rho, L, split, K, targets)
+    tgt = np.arange(len(rho)) if targets is None else np.asarray(targets)
+    phi = pl + pf - split.self_coeff() * rho[tgt]
+    grad = gl + gf
+    F = -rho[tgt, None] * grad
+    E = 0.5 * float(np.dot(rho, phi)) if targets is None else None
+    return phi, grad, E, F
+
+
+def pswf_exact(x, rho, L, cs=34.0, rc_frac=0.5, kfac=1.25, targets=None):
+    """O-exact with the oracle's own PSWF split (cs ~ 34, rc = rc_frac L)."""
+    from .split import PSWFSplit
+    rc = rc_frac * L
+    K = int(np.ceil(kfac * cs * L / (2.0 * np.pi * rc)))
+    return ewald(x, rho, L, PSWFSplit(cs, rc), K, rc, targets)
+
+
+def gaussian_exact(x, rho, L, xi=6.0, targets=None):
+    """Classical erfc Ewald: real space cut at L/2, sigma = L/(2 xi), k-range to e^{-...} < 1e-17."""
+    from .split import GaussianSplit
+    sigma = L / (2.0 * xi)
+    # exp(-sigma^2 w^2 / 4) < 1e-17  <=>  w > 2 sqrt(17 ln 10)/sigma
+    wmax = 2.0 * np.sqrt(17.0 * np.log(10.0)) / sigma
+    K = int(np.ceil(wmax * L / (2.0 * np.pi)))
+    return ewald(x, rho, L, GaussianSplit(sigma), K, 0.5 * L, targets)
+
+
+def lattice_shell_sum(x, rho, L, N):
+    """Brute force: phi_i and grad phi_i summed over whole replicas |r|_inf <= N (self excluded)."""
+    x = np.asarray(x, dtype=np.float64)
+    rho = np.asarray(rho, dtype=np.float64)
+    n = len(x)
+    rng = np.arange(-N, N + 1, dtype=np.float64)
+    R = np.stack(np.meshgrid(rng, rng, rng, indexing='ij'), axis=-1).reshape(-1, 3) * L
+    phi = np.zeros(n)
+    grad = np.zeros((n, 3))
+    for i in range(n):
+        for j in range(n):
+            d = x[i] - x[j] + R                      # (nimg, 3)
+            r2 = np.sum(d * d, axis=1)
+            if i == j:
+                r2 = np.where(r2 == 0.0, np.inf, r2)
+            r = np.sqrt(r2)
+            phi[i] += rho[j] * np.sum(1.0 / r)
+            grad[i] -= rho[j] * np.sum(d / (r ** 3)[:, None], axis=0)
+    return phi, grad

@@ -1,0 +1,111 @@
+"""Pins of the oracle's converged Ewald sum (Sec. 3.1) against facts independent of the split."""
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from oracle import exact
+from paper_2602_16591_gb300.workloads import nacl_lattice, uniform_neutral
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b))
+
+
+@pytest.fixture(scope="module")
+def small_system():
+    x, rho, L = uniform_neutral(40, L=1.0, seed=3, dist="normal")
+    return x, rho, L
+
+
+def test_split_independence(small_system):
+    """The total does not depend on the split: two PSWF cutoffs and the Gaussian split agree."""
+    x, rho, L = small_system
+    a = exact.pswf_exact(x, rho, L, cs=34.0, rc_frac=0.5)
+    b = exact.pswf_exact(x, rho, L, cs=34.0, rc_frac=0.3)
+    g = exact.gaussian_exact(x, rho, L, xi=6.0)
+    for o in (b, g):
+        assert _rel(o[0], a[0]) <= 1e-13
+        assert _rel(o[3], a[3]) <= 1e-12
+        assert abs(o[2] - a[2]) <= 1e-12 * abs(a[2])
+
+
+def test_split_independence_detects_wrong_self_term(small_system):
+    """A plausible mistake (self term with lambda_0 dropped) is caught by the same comparison."""
+    x, rho, L = small_system
+    from oracle.split import PSWFSplit
+    sp = PSWFSplit(34.0, 0.5)
+    phi, _, _, _ = exact.pswf_exact(x, rho, L)
+    bad = phi + sp.self_coeff() * rho - 2.0 / 0.5 * rho
+    g = exact.gaussian_exact(x, rho, L)
+    assert _rel(bad, g[0]) > 1e-3
+
+
+def test_nacl_madelung():
+    M = float(read_golden("nacl_madelung.txt")[0][1])
+    x, q, L = nacl_lattice(cells=4, L=1.0)
+    phi, grad, E, F = exact.pswf_exact(x, q, L)
+    d = L / 8.0
+    assert np.allclose(phi, -q * M / d, rtol=1e-12, atol=0)
+    assert abs(E - (-len(q) * M / (2 * d))) <= 1e-11 * abs(E)
+    assert np.max(np.abs(F)) <= 1e-11 * M / d ** 2
+
+
+def _extrapolate(vals, Ns, powers=(2, 3, 4)):
+    """Least-squares fit v(N) = v_inf + sum_p a_p N^-p over the shell sums; returns v_inf."""
+    A = np.array([[1.0] + [float(N) ** -p for p in powers] for N in Ns])
+    V = np.array([np.ravel(v) for v in vals])
+    return np.linalg.lstsq(A, V, rcond=None)[0][0].reshape(np.shape(vals[0]))
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_bruteforce_lattice_sum(seed):
+    """Dipole-free neutral cells: the cubic-shell replica sum of 1/r converges to the
+    Ewald potential plus the constant (2 pi/(3V)) sum_j rho_j |x_j - c|^2 (a derivation
+    of this library; no gradient), so phi, forces and energy are pinned together."""
+    rng = np.random.default_rng(seed)
+    c = np.full(3, 0.5)
+    a = rng.uniform(-0.3, 0.3, (2, 3))
+    x = np.array([c + a[0], c - a[0], c + a[1], c - a[1]])
+    rho = np.array([1.0, 1.0, -1.0, -1.0])
+    ref = exact.pswf_exact(x, rho, 1.0)
+    Ns = (8, 12, 16, 24, 32)
+    sums = [exact.lattice_shell_sum(x, rho, 1.0, N) for N in Ns]
+    const = 2 * np.pi / 3.0 * np.sum(rho * np.sum((x - c) ** 2, axis=1))
+    phi = _extrapolate([s[0] for s in sums], Ns) + const
+    grad = _extrapolate([s[1] for s in sums], Ns)
+    assert np.max(np.abs(phi - ref[0])) <= 1e-7 * np.max(np.abs(ref[0]))
+    assert np.max(np.abs(grad - ref[1])) <= 1e-7 * np.max(np.abs(ref[1]))
+
+
+def test_translation_invariance(small_system):
+    x, rho, L = small_system
+    a = exact.pswf_exact(x, rho, L)
+    b = exact.pswf_exact(np.mod(x + np.array([0.31, -0.72, 0.45]), L), rho, L)
+    assert _rel(b[0], a[0]) <= 1e-13 and _rel(b[3], a[3]) <= 1e-12
+
+
+def test_scaling_law(small_system):
+    """eq. phinondim: phi(s x; s L) = phi(x; L)/s, forces scale as 1/s^2."""
+    x, rho, L = small_system
+    s = 3.7
+    a = exact.pswf_exact(x, rho, L)
+    b = exact.pswf_exact(s * x, rho, s * L)
+    assert _rel(b[0], a[0] / s) <= 1e-13
+    assert _rel(b[3], a[3] / s ** 2) <= 1e-12
+
+
+def test_forces_sum_to_zero(small_system):
+    x, rho, L = small_system
+    _, _, _, F = exact.pswf_exact(x, rho, L)
+    assert np.max(np.abs(F.sum(axis=0))) <= 1e-12 * np.max(np.abs(F)) * len(rho)
+
+
+def test_rms_potential_matches_kappa():
+    """RMS(phi) ~ sqrt(kappa) ||rho|| / L for uniform neutral charges (the relative-tol reading)."""
+    from oracle.params import KAPPA
+    r = []
+    for seed in range(3):
+        x, rho, L = uniform_neutral(600, seed=seed)
+        phi = exact.pswf_exact(x, rho, L)[0]
+        r.append(np.sqrt(np.mean(phi ** 2)) / np.linalg.norm(rho))
+    assert abs(np.mean(r) / np.sqrt(KAPPA) - 1.0) < 0.15
