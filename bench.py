@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Throughput of the PSWF fast Ewald hot path on GB300 (one JSON line on rank 0).
+
+Workload: n = 100,000 uniform neutral charges (rho ~ U[-1,1] minus the mean) in the
+unit box, relative tolerance 1e-6, mixed precision (the metric's headline form).  One
+"step" is one full evaluation: bin/sort, spread, FFT, scale, inverse FFT, interpolate
+(phi and forces), real-space sum, self term and energy.  Inputs are resident in HBM when
+the timed region starts; L2 is flushed (256 MB write) between timed steps, outside the
+events that bracket each step.  Under torchrun every rank evaluates its own independent
+system (replicas, weak scaling); the time reported is the max over ranks.
+
+--impl reference times the FP64 CPU oracle (the converged Ewald sum) on the host cores
+on a bounded sample of the same workload; it never touches the GPU.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle evals/s (phi+forces) at rel tol 1e-6/1e-10, mixed vs FP64 GPU form"
+UNIT = "particle evals/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12     # SMs x FP32 lanes x 2 (FMA) x max SM clock
+FP64_PEAK_TFLOPS = 1.25                               # nominal GB300 FP64 (non-tensor)
+REF_TARGETS = 8                                       # oracle sample per reference step
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def workload_config(n, tol, precision):
+    return {
+        "workload": "uniform neutral charges n=%d, rho~U[-1,1] minus mean, L=1, rel tol %g, %s" % (n, tol, precision),
+        "n": n, "tol": tol, "precision": precision, "L": 1.0,
+        "l2": "flushed between timed steps (256 MB write, outside the step events)",
+        "parallelism": "replicas (one independent system per GPU)",
+    }
+
+
+# ------------------------------------------------------------------ oracle timing (CPU) --
+def oracle_sample(n, targets, seed=0):
+    """Time the FP64 converged Ewald sum (oracle) for `targets` of the n-particle system."""
+    code = r"""
+import os, sys, time, json
+sys.path.insert(0, %r)
+import numpy as np
+from oracle import exact
+from paper_2602_16591_gb300.workloads import uniform_neutral
+x, rho, L = uniform_neutral(%d, seed=%d)
+tg = np.linspace(0, len(x) - 1, %d).astype(np.int64)
+t = time.perf_counter()
+exact.pswf_exact(x, rho, L, targets=tg)
+print(json.dumps({"seconds": time.perf_counter() - t}))
+""" % (ROOT, n, seed, targets)
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    n = args.n
+    times = []
+    for k in range(args.warmup + args.steps):
+        s = oracle_sample(n, REF_TARGETS, seed=0)
+        if k >= args.warmup:
+            times.append(s)
+    t = sum(times) / len(times)
+    value = REF_TARGETS / t
+    sample = "phi+F at %d of %d particles per step (oracle: FP64 PSWF Ewald, c_s=34, r_c=L/2, " \
+             "all-source structure factor, k-sphere |k|<=14)" % (REF_TARGETS, n)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(n, args.tol, args.precision),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- work models --
+def algorithmic_flops(stage, p, n, pairs):
+    """Algorithmic flops of one launch (FMA = 2 flops); definitions in the design doc."""
+    P, dw, dr = p.P, p.deg_w, p.deg_r
+    if stage == "spread":
+        return n * 2 * (P ** 3 + P ** 2 + 3 * P * (dw + 1))
+    if stage == "interp":
+        return n * 2 * (2 * P ** 3 + 6 * P ** 2 + 6 * P * (dw + 1))
+    if stage == "short":
+        return pairs * 2 * (10 + 2 * (dr + 1))
+    return None
+
+
+def traffic_for(stage, n, p, precision):
+    """Per-launch DRAM bytes from the committed ncu summary, if taken on the current kernels."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
+    src = os.path.join(ROOT, "paper_2602_16591_gb300", "csrc", "device.cuh")
+    if not os.path.exists(path):
+        return None
+    digest = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 6 and not line.startswith("#") and f[0] == stage and int(f[1]) == n and int(f[2]) == p.P \
+                and f[3] == precision and f[5] == digest:
+            return float(f[4])
+    return None
+
+
+# ------------------------------------------------------------------------- main run --
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import paper_2602_16591_gb300 as pe
+    from paper_2602_16591_gb300.workloads import uniform_neutral
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    n = args.n
+    x_np, rho_np, L = uniform_neutral(n, seed=rank)
+    x = torch.tensor(x_np, device="cuda")
+    rho = torch.tensor(rho_np, device="cuda")
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(plan, steps, warmup, profile=False):
+        phi = torch.empty(n, dtype=torch.float64, device="cuda")
+        F = torch.empty(n, 3, dtype=torch.float64, device="cuda")
+        for _ in range(warmup):
+            plan.eval(x, rho, phi, F, energy=False)
+        torch.cuda.synchronize()
+        if profile:
+            plan.profile(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        torch.cuda.synchronize()
+        barrier()
+        for k in range(steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            plan.eval(x, rho, phi, F, energy=False)
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        stages = None
+        if profile:
+            stages, cnt = plan.profile_read()
+            plan.profile(False)
+            stages = {k: v / cnt for k, v in stages.items()}
+        plan.check()
+        return ms / steps, stages
+
+    gpu_index = local_rank
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        try:
+            gpu_index = int(cvd.split(",")[local_rank])
+        except (ValueError, IndexError):
+            pass
+
+    plan = pe.Plan(L, n, args.tol, precision=args.precision)
+    with ClockSampler(gpu_index) as clk:
+        ms_local, stages = timed(plan, args.steps, args.warmup, profile=True)
+    clocks = clk.summary()
+    ms = max_over_ranks(ms_local)
+    value = world * n / (ms / 1000.0)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    xh = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
+    rh = torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    xh[:] = x_np
+    rh[:] = rho_np
+    for _ in range(args.warmup):
+        plan.eval_host(xh, rh)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.eval_host(xh, rh)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e2e_s = max_over_ranks(e2e_s)
+
+    p = plan.params
+    # dominant kernel of the step and its roofline
+    rc = p.rc
+    pairs = n * (n - 1) * (4.0 / 3.0) * np.pi * rc ** 3 / L ** 3
+    ours = {k: v for k, v in stages.items() if k not in ("fft_fwd", "fft_inv")}
+    dom = max(ours, key=ours.get)
+    fl = algorithmic_flops(dom, p, n, pairs)
+    prec_tag = "f32" if p.precision == pe.EWALD_MIXED else "f64"
+    peak = FP32_PEAK_TFLOPS if prec_tag == "f32" else FP64_PEAK_TFLOPS
+    roofline = None
+    if fl is not None:
+        ach = fl / (stages[dom] / 1000.0) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": traffic_for(dom, n, p, prec_tag),
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if prec_tag == "f32"
+                    else "nominal GB300 FP64 1.25 TFLOP/s"}
+
+    variants = []
+    if not args.no_variants:
+        for tol, prec in ((1e-6, "fp64"), (1e-10, "mixed"), (1e-10, "fp64")):
+            vp = pe.Plan(L, n, tol, precision=prec)
+            vms, vst = timed(vp, max(5, args.steps // 3), 2, profile=True)
+            vms = max_over_ranks(vms)
+            variants.append({"tol": tol, "precision": prec,
+                             "path": "f32" if vp.params.precision == pe.EWALD_MIXED else "f64",
+                             "m": vp.params.m, "P": vp.params.P, "ms_per_step": vms,
+                             "value": world * n / (vms / 1000.0), "stages_ms": vst})
+            del vp
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        s = oracle_sample(n, 48)
+        cpu = {"value": 48 / s, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "phi+F at 48 of %d particles (FP64 converged PSWF Ewald sum incl. the all-source "
+                         "structure factor), %.1f s, single thread" % (n, s)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": prec_tag, "data": "synthetic",
+            "config": dict(workload_config(n, args.tol, args.precision), m=p.m, P=p.P, rc=p.rc, cs=p.cs, cw=p.cw,
+                           deg_w=p.deg_w, deg_r=p.deg_r),
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
+                    "d2h_bytes_per_step": 32 * n + 8},
+            "gpu_launches": 10 * args.steps, "clocks": clocks, "stages_ms": stages, "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--n", type=int, default=100_000)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--precision", default="mixed", choices=("mixed", "fp64"))
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,182 @@
+/*
+ * pswf_ewald.h -- C ABI of the GB300 PSWF fast Ewald library (libpswf_ewald.so).
+ *
+ * Computes, for n point charges rho_j at x_j in the triply periodic cube
+ * [0, L)^3, the Coulomb potential phi_i (Gaussian units, phi = sum rho/r,
+ * self-interaction excluded, all periodic images included), the forces
+ * F_i = -rho_i grad phi_i and the energy E = 1/2 sum_i rho_i phi_i
+ * (paper: Sec. 3.1, eqs. potential1/potential2 and the Remark on energy and
+ * forces).  The method is the PSWF split + PSWF window fast Ewald summation of
+ * Sec. 4 (Alg. 2 for the Fourier-space part, the compactly supported residual
+ * R of eq. R for the real-space part) with parameters from Alg. 3 (Sec. 6).
+ *
+ * Conventions shared by every entry point
+ *  - Positions are any finite reals; they are wrapped into [0, L)^3.
+ *  - Layouts: x is (n, 3) row-major float64, rho is (n) float64, phi is (n)
+ *    float64, force is (n, 3) row-major float64; outputs follow the caller's
+ *    particle order.
+ *  - The caller owns every buffer passed in; the plan owns its workspace.
+ *  - A plan is not reentrant: calls on one plan must not overlap in time
+ *    (use one plan per concurrent stream).
+ *  - Return value: 0 (EWALD_OK) or one of the EWALD_E* codes below; no C++
+ *    exception crosses the ABI.  ewald_last_error() returns a thread-local
+ *    message for the last failure on the calling thread.
+ */
+#ifndef PSWF_EWALD_H
+#define PSWF_EWALD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------- */
+#define EWALD_OK           0
+#define EWALD_EINVAL       1  /* bad argument: L <= 0, n < 2, tol outside [1e-13, 1e-2], NULL pointer, ... */
+#define EWALD_ENONNEUTRAL  2  /* |sum rho| > 1e-10 sum |rho| (charge neutrality, Sec. 1 and Alg. 1) */
+#define EWALD_ENOMEM       3  /* device or host allocation failed */
+#define EWALD_ECUDA        4  /* a CUDA runtime call failed */
+#define EWALD_ECUFFT       5  /* a cuFFT call failed */
+#define EWALD_ETOOBIG      6  /* grid, window support or particle count beyond the library limits */
+#define EWALD_ETIMEOUT     7  /* reserved: a bounded device wait expired */
+#define EWALD_ENONFINITE   8  /* an input position or charge is not finite */
+
+/* ---- precision of the device path ------------------------------------- */
+#define EWALD_FP64   0   /* every stage in float64 */
+#define EWALD_MIXED  1   /* spreading, FFT, interpolation and the real-space sum in float32
+                            (positions reduced to per-tile/per-cell offsets in float64 first);
+                            outputs, energy and self term in float64.  For tol < 1e-7 a MIXED
+                            plan runs the float64 kernels (ewald_params.precision reports it). */
+
+/* ---- options (ewald_opts_default fills the defaults) -------------------- */
+typedef struct ewald_opts {
+    int    precision;     /* EWALD_FP64 or EWALD_MIXED (default EWALD_FP64) */
+    double rc;            /* <= 0: automatic cutoff rule; > 0: upper bound on the cutoff (length units) */
+    double grid_density;  /* target m^3 / n for the automatic cutoff rule (default 1.0) */
+    double tol_safety;    /* the plan is sized for tol * tol_safety (default 0.25; forces have no
+                             error model in the paper and measure ~2-5x the potential error) */
+    int    sr_reach;      /* cells per cutoff radius in the real-space cell list (default 2) */
+} ewald_opts;
+
+/* ---- derived parameters (Alg. 3 and the library's readings of it) ------ */
+typedef struct ewald_params {
+    double L;          /* box edge */
+    double rc;         /* cutoff radius r_c (R(r) = 0 for r >= r_c) */
+    double cs;         /* split bandlimit c_s (eq. csrc: c_s / r_c = pi m / L) */
+    double cw;         /* window bandlimit c_w = pi P / 2 (eq. cwP) */
+    double cw_target;  /* c_w from eq. cwW before rounding P */
+    double alpha;      /* window half-width alpha = P h / 2 */
+    double h;          /* grid spacing L / m */
+    double lambda_s;   /* lambda_0(c_s) */
+    double lambda_w;   /* lambda_0(c_w) */
+    double self_coeff; /* 2 / (lambda_0(c_s) r_c): phi_i^self = -self_coeff * rho_i */
+    double tol;        /* requested relative tolerance */
+    double fit_tol;    /* max abs error allowed for the polynomial fits */
+    int64_t n;         /* particle count the plan is for */
+    int    m;          /* FFT grid points per axis (multiple of 4, prime factors <= 7) */
+    int    P;          /* window support in grid points per axis */
+    int    deg_w;      /* degree of the per-interval window polynomials (in z = 2f - 1) */
+    int    deg_r;      /* degree of the radial polynomials (in u = 2 r^2 / r_c^2 - 1) */
+    int    tile;       /* spreading tile edge T (grid points), m % T == 0 */
+    int    ncell;      /* real-space cells per axis */
+    int    sr_reach;   /* real-space neighbour reach in cells */
+    int    precision;  /* EWALD_FP64 or EWALD_MIXED */
+} ewald_params;
+
+typedef struct ewald_plan_s* ewald_plan;   /* opaque, owned by the library */
+
+/* Fill *opts with the defaults listed above.  Returns EWALD_EINVAL on NULL. */
+int ewald_opts_default(ewald_opts* opts);
+
+/* Host only (no CUDA call): run Alg. 3 (Sec. 6.4) for a box of edge L holding
+ * n particles at relative tolerance tol and fill *out.  opts may be NULL. */
+int ewald_plan_params(double L, int64_t n, double tol, const ewald_opts* opts,
+                      ewald_params* out);
+
+/* Create a plan on the current CUDA device: parameters as ewald_plan_params,
+ * PSWF tables, cuFFT plans and a device workspace sized for n particles.
+ * On success *out holds the plan; release it with ewald_plan_destroy. */
+int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts,
+                      ewald_plan* out);
+
+/* Copy the plan's parameters into *out. */
+int ewald_plan_query(ewald_plan plan, ewald_params* out);
+
+/* Evaluate on device buffers (Alg. 2 steps 1-5 plus the real-space sum, self
+ * term, forces and energy).  x, rho: DEVICE pointers, layouts above, n = the
+ * plan's n.  phi, force: DEVICE pointers or NULL (not wanted).  energy: HOST
+ * pointer or NULL; when non-NULL the call synchronises `stream` and also
+ * reports EWALD_ENONNEUTRAL / EWALD_ENONFINITE detected on the device.
+ * stream: a cudaStream_t (NULL = legacy default stream).  Without `energy`
+ * the call is asynchronous; ewald_check() reports the device-side status. */
+int ewald_eval(ewald_plan plan, const double* x, const double* rho,
+               double* phi, double* force, double* energy, void* stream);
+
+/* Same as ewald_eval but every pointer is a HOST pointer (pinned or pageable):
+ * copies x and rho to the device, evaluates, copies phi/force back, and
+ * synchronises `stream` before returning. */
+int ewald_eval_host(ewald_plan plan, const double* x, const double* rho,
+                    double* phi, double* force, double* energy, void* stream);
+
+/* Synchronise `stream` and return the device status of the last evaluation
+ * (EWALD_OK, EWALD_ENONNEUTRAL or EWALD_ENONFINITE). */
+int ewald_check(ewald_plan plan, void* stream);
+
+/* Test access: copy an internal stage of the last evaluation to HOST memory
+ * as float64.  which = 0: the spread grid a_l (m^3, z fastest; Alg. 2 step 1);
+ * which = 1: the grid b_l after scaling and the inverse FFT (Alg. 2 step 4).
+ * host_out must hold m^3 doubles.  Synchronises the device. */
+int ewald_debug_grid(ewald_plan plan, int which, double* host_out);
+
+void ewald_plan_destroy(ewald_plan plan);
+
+/* ---- per-stage timing ----------------------------------------------------
+ * Stages, in pipeline order: 0 bin+sort, 1 spread (Alg. 2 step 1), 2 halo sum,
+ * 3 forward FFT (step 2), 4 scaling (step 3), 5 inverse FFT (step 4),
+ * 6 interpolation (step 5), 7 real-space sum, 8 energy reduction.
+ * While enabled, every ewald_eval / ewald_eval_host records CUDA events on its
+ * stream at the stage boundaries (no synchronisation).  enable != 0 also
+ * clears the accumulated records. */
+#define EWALD_NSTAGES 9
+int ewald_profile(ewald_plan plan, int enable);
+
+/* Synchronise the recorded events and write the summed milliseconds of each
+ * stage over the recorded evaluations into ms[EWALD_NSTAGES] and their number
+ * into *count. */
+int ewald_profile_read(ewald_plan plan, double* ms, int* count);
+
+/* ---- host-side tables (no CUDA call), for tests and tooling ------------- */
+
+/* The planner's PSWF (App. B: Legendre expansion, Sturm bisection + inverse
+ * iteration): psi_0^c and its derivative at nx points |x| <= 1, plus chi_0 and
+ * lambda_0.  Any output pointer may be NULL. */
+int ewald_pswf_eval(double c, int nx, const double* x, double* psi, double* dpsi,
+                    double* chi, double* lambda0);
+
+/* Lambert W on branch 0 (z >= -1/e) or -1 (-1/e <= z < 0), Halley iteration. */
+double ewald_lambertw(int branch, double z);
+
+/* The fitted window polynomials of a plan (Remark on piecewise polynomials in
+ * Sec. 4.3): for each z in [-1, 1] write the P weights
+ * w_a = psi(s_a)/psi(0), s_a = (z + P - 1 - 2a)/P, into w[i*P + a] and their
+ * x-derivatives psi'(s_a)/(alpha psi(0)) into dw[i*P + a] (dw may be NULL). */
+int ewald_window_fit(const ewald_params* p, int nz, const double* z, double* w, double* dw);
+
+/* The fitted radial functions of a plan at nr distances 0 < r < rc:
+ * R[i] = R(r) (eq. R) and G[i] = -R'(r)/r (pair force factor); G may be NULL. */
+int ewald_radial_fit(const ewald_params* p, int nr, const double* r, double* R, double* G);
+
+/* The diagonal scaling S(k) of Alg. 2 step 3 on the half spectrum the library
+ * uses: S[(ix*m + iy)*(m/2+1) + iz] for k = (kx(ix), ky(iy), iz), where
+ * kx(i) = i for i < m/2 and i - m otherwise.  S holds m*m*(m/2+1) doubles. */
+int ewald_scale_table(const ewald_params* p, double* S);
+
+const char* ewald_error_string(int code);
+const char* ewald_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PSWF_EWALD_H */

@@ -81,7 +81,8 @@ class Alg2:
         return a.reshape(m, m, m)
 
     def kgrid(self):
-        return np.fft.fftfreq(self.m) * self.m           # index -> k in I_m
+        """Integer k in I_m for each FFT index (index m/2 is k = -m/2)."""
+        return np.rint(np.fft.fftfreq(self.m) * self.m).astype(np.int64)
 
     def scaling(self):
         """S(k) on the full m^3 index grid (S(0) = 0)."""

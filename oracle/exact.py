@@ -52,17 +52,16 @@ def realspace(x, rho, L, split, rcut, targets=None, chunk=64):
         for sh in shifts:
             d = d0 + sh
             r = np.sqrt(np.sum(d * d, axis=-1))
-            mask = r < rcut
-            self_pair = (ti[:, None] == np.arange(len(x))[None, :]) & (r < 1e-300)
-            mask &= ~self_pair
-            if not mask.any():
+            mask = (r < rcut) & (r > 0.0)                # r = 0 only for the omitted self pair
+            tt, jj = np.nonzero(mask)
+            if len(tt) == 0:
                 continue
-            rs = np.where(mask, r, 1.0)
-            Rv = np.where(mask, split.R(rs), 0.0)
-            dRv = np.where(mask, split.dR(rs), 0.0)
-            phi[s:s + chunk] += Rv @ rho
-            coef = dRv / rs * rho[None, :]
-            grad[s:s + chunk] += np.einsum('tn,tnd->td', coef, d)
+            rr = r[tt, jj]
+            Rv, dRv = split.R_and_dR(rr)
+            phi[s:s + chunk] += np.bincount(tt, weights=Rv * rho[jj], minlength=len(ti))
+            coef = dRv / rr * rho[jj]
+            for dim in range(3):
+                grad[s:s + chunk, dim] += np.bincount(tt, weights=coef * d[tt, jj, dim], minlength=len(ti))
     return phi, grad
 
 

@@ -65,6 +65,12 @@ class PSWFSplit:
         val = -(1.0 - self.Phi(rs)) / rs ** 2 - self.dPhi(rs) / rs
         return np.where(inside, val, 0.0)
 
+    def R_and_dR(self, r):
+        """R(r) and R'(r) for 0 < r < rc (one Phi evaluation)."""
+        r = np.asarray(r, dtype=np.float64)
+        one_m_phi = 1.0 - self.norm * self.f.int0(r / self.rc)
+        return one_m_phi / r, -one_m_phi / r ** 2 - self.dPhi(r) / r
+
     def gammahat(self, omega):
         om = np.asarray(omega, dtype=np.float64) * self.rc
         return self.f.cos_transform(om) / (self.f.lam * self.f.psi0)
@@ -93,6 +99,9 @@ class GaussianSplit:
         r = np.asarray(r, dtype=np.float64)
         s = self.sigma
         return -erfc(r / s) / r ** 2 - 2.0 / (np.sqrt(np.pi) * s) * np.exp(-(r / s) ** 2) / r
+
+    def R_and_dR(self, r):
+        return self.R(r), self.dR(r)
 
     def Mhat_k2(self, k2, L):
         k2 = np.asarray(k2, dtype=np.float64)

@@ -1,0 +1,545 @@
+// C ABI of the PSWF fast Ewald library: plan management, the evaluation pipeline and the
+// host-side table entry points declared in include/pswf_ewald.h.
+#include <cufft.h>
+
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "launch.h"
+#include "planner.h"
+#include "pswf_ewald.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define PSWF_CUDA(call)                                                                  \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess)                                                           \
+            return fail(EWALD_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define PSWF_CUFFT(call)                                                                    \
+    do {                                                                                    \
+        cufftResult r_ = (call);                                                            \
+        if (r_ != CUFFT_SUCCESS) return fail(EWALD_ECUFFT, std::string(#call) + " failed: " + std::to_string(r_)); \
+    } while (0)
+
+template <typename T>
+int upload(T** dst, const std::vector<double>& src) {
+    std::vector<T> tmp(src.begin(), src.end());
+    if (cudaMalloc(dst, sizeof(T) * (tmp.empty() ? 1 : tmp.size())) != cudaSuccess)
+        return fail(EWALD_ENOMEM, "cudaMalloc of a table failed");
+    if (!tmp.empty() && cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(EWALD_ECUDA, "table upload failed");
+    return EWALD_OK;
+}
+
+}  // namespace
+
+struct ewald_plan_s {
+    pswf::HostPlan hp;
+    pswf::Geom g{};
+    int device = 0;
+    bool fp64 = true;
+    int ntiles = 0, ncells = 0, epart_blocks = 0;
+    // workspace
+    int* key_rank = nullptr;
+    int* tile_cnt = nullptr;
+    int* tile_off = nullptr;
+    int* cell_cnt = nullptr;
+    int* cell_off = nullptr;
+    void* sp_rec = nullptr;
+    int2* sp_idx = nullptr;
+    void* sr_rec = nullptr;
+    int2* sr_idx = nullptr;
+    void* scratch = nullptr;
+    void* grid_a = nullptr;
+    void* grid_b = nullptr;
+    void* spec = nullptr;
+    void* wcoef = nullptr;
+    void* dwcoef = nullptr;
+    void* p1c = nullptr;
+    void* qc = nullptr;
+    void* iw = nullptr;
+    void* mtab = nullptr;
+    double* phi_int = nullptr;
+    double* f_int = nullptr;
+    double* status = nullptr;
+    double* epart = nullptr;
+    double* energy_d = nullptr;
+    double* x_stage = nullptr;
+    double* rho_stage = nullptr;
+    double* status_h = nullptr;   // pinned
+    cufftHandle fwd = 0, inv = 0;
+    bool have_fwd = false, have_inv = false;
+    bool profiling = false;
+    std::vector<std::vector<cudaEvent_t>> prof;   // EWALD_NSTAGES + 1 events per recorded evaluation
+    std::vector<cudaEvent_t>* cur = nullptr;
+
+    void mark(int k, cudaStream_t s) {
+        if (cur) cudaEventRecord((*cur)[k], s);
+    }
+    void clear_prof() {
+        for (auto& v : prof)
+            for (cudaEvent_t e : v) cudaEventDestroy(e);
+        prof.clear();
+        cur = nullptr;
+    }
+
+    ~ewald_plan_s() {
+        void* bufs[] = {key_rank, tile_cnt, tile_off, cell_cnt, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, scratch,
+                        grid_a, grid_b, spec, wcoef, dwcoef, p1c, qc, iw, mtab, phi_int, f_int, status, epart,
+                        energy_d, x_stage, rho_stage};
+        for (void* b : bufs)
+            if (b) cudaFree(b);
+        if (status_h) cudaFreeHost(status_h);
+        clear_prof();
+        if (have_fwd) cufftDestroy(fwd);
+        if (have_inv) cufftDestroy(inv);
+    }
+};
+
+namespace {
+
+template <typename real, typename cplx>
+int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, double* f, cudaStream_t s) {
+    using pswf::Vec4;
+    const pswf::Geom& g = p->g;
+    const int n = g.n, m = g.m;
+    p->mark(0, s);
+    PSWF_CUDA(cudaMemsetAsync(p->tile_cnt, 0, sizeof(int) * p->ntiles, s));
+    PSWF_CUDA(cudaMemsetAsync(p->cell_cnt, 0, sizeof(int) * p->ncells, s));
+    PSWF_CUDA(cudaMemsetAsync(p->status, 0, sizeof(double) * 3, s));
+    const int tb = 256, nb = (n + tb - 1) / tb;
+    pswf::k_prep<<<nb, tb, 0, s>>>(x, rho, g, p->key_rank, p->tile_cnt, p->cell_cnt, p->status);
+    PSWF_CUDA(cudaGetLastError());
+    pswf::k_scan<<<2, 1024, 0, s>>>(p->tile_cnt, p->tile_off, p->ntiles, p->cell_cnt, p->cell_off, p->ncells);
+    PSWF_CUDA(cudaGetLastError());
+    auto* sp_rec = static_cast<Vec4<real>*>(p->sp_rec);
+    auto* sr_rec = static_cast<Vec4<real>*>(p->sr_rec);
+    pswf::k_scatter<real><<<nb, tb, 0, s>>>(x, rho, g, p->key_rank, p->tile_off, p->cell_off, sp_rec, p->sp_idx,
+                                            sr_rec, p->sr_idx);
+    PSWF_CUDA(cudaGetLastError());
+    p->mark(1, s);
+    // Alg. 2 step 1
+    PSWF_CUDA(pswf::Launch<real>::spread(g.P, p->ntiles, sp_rec, p->sp_idx, p->tile_off,
+                                         static_cast<const real*>(p->wcoef), g.degw, static_cast<real*>(p->scratch), s));
+    p->mark(2, s);
+    const int mm = m * m * m;
+    pswf::k_halo<real><<<(mm + 255) / 256, 256, 0, s>>>(static_cast<const real*>(p->scratch), p->tile_off, g,
+                                                        static_cast<real*>(p->grid_a));
+    PSWF_CUDA(cudaGetLastError());
+    // Alg. 2 steps 2-4
+    p->mark(3, s);
+    PSWF_CUFFT(cufftSetStream(p->fwd, s));
+    PSWF_CUFFT(cufftSetStream(p->inv, s));
+    if constexpr (sizeof(real) == 8) {
+        PSWF_CUFFT(cufftExecD2Z(p->fwd, static_cast<cufftDoubleReal*>(p->grid_a), static_cast<cufftDoubleComplex*>(p->spec)));
+    } else {
+        PSWF_CUFFT(cufftExecR2C(p->fwd, static_cast<cufftReal*>(p->grid_a), static_cast<cufftComplex*>(p->spec)));
+    }
+    p->mark(4, s);
+    const int ns = m * m * (m / 2 + 1);
+    pswf::k_scale<real, cplx><<<(ns + 255) / 256, 256, 0, s>>>(static_cast<cplx*>(p->spec), m,
+                                                               static_cast<const real*>(p->iw),
+                                                               static_cast<const real*>(p->mtab));
+    PSWF_CUDA(cudaGetLastError());
+    p->mark(5, s);
+    if constexpr (sizeof(real) == 8) {
+        PSWF_CUFFT(cufftExecZ2D(p->inv, static_cast<cufftDoubleComplex*>(p->spec), static_cast<cufftDoubleReal*>(p->grid_b)));
+    } else {
+        PSWF_CUFFT(cufftExecC2R(p->inv, static_cast<cufftComplex*>(p->spec), static_cast<cufftReal*>(p->grid_b)));
+    }
+    p->mark(6, s);
+    // Alg. 2 step 5 + self term + forces
+    const real inv_alpha = static_cast<real>(1.0 / p->hp.p.alpha);
+    PSWF_CUDA(pswf::Launch<real>::interp(g.P, p->ntiles, static_cast<const real*>(p->grid_b), sp_rec, p->sp_idx,
+                                         p->tile_off, static_cast<const real*>(p->wcoef),
+                                         static_cast<const real*>(p->dwcoef), g, inv_alpha, phi, f, s));
+    p->mark(7, s);
+    // real-space sum
+    pswf::k_short<real><<<(n + 127) / 128, 128, 0, s>>>(sr_rec, p->sr_idx, p->cell_off, g,
+                                                       static_cast<const real*>(p->p1c),
+                                                       static_cast<const real*>(p->qc), phi, f);
+    PSWF_CUDA(cudaGetLastError());
+    p->mark(8, s);
+    pswf::k_energy_partial<<<p->epart_blocks, 256, 0, s>>>(phi, rho, n, p->epart);
+    pswf::k_energy_final<<<1, 256, 0, s>>>(p->epart, p->epart_blocks, p->energy_d);
+    PSWF_CUDA(cudaGetLastError());
+    p->mark(9, s);
+    return EWALD_OK;
+}
+
+int eval_device(ewald_plan p, const double* x, const double* rho, double* phi, double* force, cudaStream_t s) {
+    p->cur = nullptr;
+    if (p->profiling) {
+        std::vector<cudaEvent_t> ev(EWALD_NSTAGES + 1);
+        for (auto& e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) return fail(EWALD_ECUDA, "cudaEventCreate failed");
+        p->prof.push_back(ev);
+        p->cur = &p->prof.back();
+    }
+    double* phi_d = phi ? phi : p->phi_int;
+    double* f_d = force ? force : p->f_int;
+    if (p->fp64) return run_pipeline<double, cufftDoubleComplex>(p, x, rho, phi_d, f_d, s);
+    return run_pipeline<float, cufftComplex>(p, x, rho, phi_d, f_d, s);
+}
+
+int read_status(ewald_plan p, cudaStream_t s, double* energy) {
+    PSWF_CUDA(cudaMemcpyAsync(p->status_h, p->status, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+    if (energy) PSWF_CUDA(cudaMemcpyAsync(p->status_h + 3, p->energy_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PSWF_CUDA(cudaStreamSynchronize(s));
+    if (energy) *energy = p->status_h[3];
+    if (p->status_h[2] > 0) return fail(EWALD_ENONFINITE, "non-finite position or charge in the input");
+    if (std::fabs(p->status_h[0]) > 1e-10 * p->status_h[1])
+        return fail(EWALD_ENONNEUTRAL, "charges are not neutral: |sum rho| > 1e-10 sum |rho|");
+    return EWALD_OK;
+}
+
+int check_ptr_device(const void* ptr, const char* name) {
+    if (!ptr) return EWALD_OK;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(EWALD_EINVAL, std::string(name) + " is not a CUDA-accessible pointer");
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(EWALD_EINVAL, std::string(name) + " must be a device pointer (use ewald_eval_host for host buffers)");
+    return EWALD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ewald_opts_default(ewald_opts* opts) {
+    if (!opts) return fail(EWALD_EINVAL, "opts is NULL");
+    *opts = pswf::default_opts();
+    return EWALD_OK;
+}
+
+int ewald_plan_params(double L, int64_t n, double tol, const ewald_opts* opts, ewald_params* out) {
+    if (!out) return fail(EWALD_EINVAL, "out is NULL");
+    try {
+        const ewald_opts o = opts ? *opts : pswf::default_opts();
+        *out = pswf::make_plan(L, n, tol, o).p;
+        return EWALD_OK;
+    } catch (const std::invalid_argument& e) {
+        return fail(EWALD_EINVAL, e.what());
+    } catch (const std::length_error& e) {
+        return fail(EWALD_ETOOBIG, e.what());
+    } catch (const std::exception& e) {
+        return fail(EWALD_EINVAL, e.what());
+    }
+}
+
+int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out) {
+    if (!out) return fail(EWALD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n > (int64_t(1) << 30)) return fail(EWALD_ETOOBIG, "n beyond 2^30 particles");
+    ewald_plan p = new (std::nothrow) ewald_plan_s();
+    if (!p) return fail(EWALD_ENOMEM, "host allocation failed");
+    try {
+        const ewald_opts o = opts ? *opts : pswf::default_opts();
+        p->hp = pswf::make_plan(L, n, tol, o);
+    } catch (const std::invalid_argument& e) {
+        delete p;
+        return fail(EWALD_EINVAL, e.what());
+    } catch (const std::length_error& e) {
+        delete p;
+        return fail(EWALD_ETOOBIG, e.what());
+    } catch (const std::exception& e) {
+        delete p;
+        return fail(EWALD_EINVAL, e.what());
+    }
+    const ewald_params& q = p->hp.p;
+    p->fp64 = q.precision == EWALD_FP64;
+    pswf::Geom& g = p->g;
+    g.n = static_cast<int>(n);
+    g.m = q.m;
+    g.P = q.P;
+    g.T = q.tile;
+    g.nt = q.m / q.tile;
+    g.ncell = q.ncell;
+    g.reach = q.sr_reach;
+    g.degw = q.deg_w;
+    g.degr = q.deg_r;
+    g.L = q.L;
+    g.invL = 1.0 / q.L;
+    g.h = q.h;
+    g.invh = q.m / q.L;
+    g.cellw = q.L / q.ncell;
+    g.rc = q.rc;
+    g.self = q.self_coeff;
+    p->ntiles = g.nt * g.nt * g.nt;
+    p->ncells = g.ncell * g.ncell * g.ncell;
+    p->epart_blocks = 256;
+    cudaGetDevice(&p->device);
+
+    const size_t rs = p->fp64 ? sizeof(double) : sizeof(float);
+    const int E = g.T + g.P - 1;
+    const size_t m3 = static_cast<size_t>(g.m) * g.m * g.m;
+    const size_t nspec = static_cast<size_t>(g.m) * g.m * (g.m / 2 + 1);
+    struct A { void** ptr; size_t bytes; } allocs[] = {
+        {reinterpret_cast<void**>(&p->key_rank), sizeof(int4) * n},
+        {reinterpret_cast<void**>(&p->tile_cnt), sizeof(int) * (p->ntiles + 1)},
+        {reinterpret_cast<void**>(&p->tile_off), sizeof(int) * (p->ntiles + 1)},
+        {reinterpret_cast<void**>(&p->cell_cnt), sizeof(int) * (p->ncells + 1)},
+        {reinterpret_cast<void**>(&p->cell_off), sizeof(int) * (p->ncells + 1)},
+        {&p->sp_rec, 4 * rs * n},
+        {reinterpret_cast<void**>(&p->sp_idx), sizeof(int2) * n},
+        {&p->sr_rec, 4 * rs * n},
+        {reinterpret_cast<void**>(&p->sr_idx), sizeof(int2) * n},
+        {&p->scratch, rs * static_cast<size_t>(p->ntiles) * E * E * E},
+        {&p->grid_a, rs * m3},
+        {&p->grid_b, rs * m3},
+        {&p->spec, 2 * rs * nspec},
+        {reinterpret_cast<void**>(&p->phi_int), sizeof(double) * n},
+        {reinterpret_cast<void**>(&p->f_int), sizeof(double) * 3 * n},
+        {reinterpret_cast<void**>(&p->status), sizeof(double) * 4},
+        {reinterpret_cast<void**>(&p->epart), sizeof(double) * p->epart_blocks},
+        {reinterpret_cast<void**>(&p->energy_d), sizeof(double)},
+        {reinterpret_cast<void**>(&p->x_stage), sizeof(double) * 3 * n},
+        {reinterpret_cast<void**>(&p->rho_stage), sizeof(double) * n},
+    };
+    for (auto& a : allocs) {
+        if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            delete p;
+            return fail(EWALD_ENOMEM, "device allocation failed (" + std::to_string(a.bytes) + " bytes)");
+        }
+    }
+    if (cudaMallocHost(reinterpret_cast<void**>(&p->status_h), sizeof(double) * 4) != cudaSuccess) {
+        delete p;
+        return fail(EWALD_ENOMEM, "pinned host allocation failed");
+    }
+    int rc = EWALD_OK;
+    if (p->fp64) {
+        if ((rc = upload<double>(reinterpret_cast<double**>(&p->wcoef), p->hp.wc)) ||
+            (rc = upload<double>(reinterpret_cast<double**>(&p->dwcoef), p->hp.dwc)) ||
+            (rc = upload<double>(reinterpret_cast<double**>(&p->p1c), p->hp.p1c)) ||
+            (rc = upload<double>(reinterpret_cast<double**>(&p->qc), p->hp.qc)) ||
+            (rc = upload<double>(reinterpret_cast<double**>(&p->iw), p->hp.iw)) ||
+            (rc = upload<double>(reinterpret_cast<double**>(&p->mtab), p->hp.mtab))) {
+            delete p;
+            return rc;
+        }
+    } else {
+        if ((rc = upload<float>(reinterpret_cast<float**>(&p->wcoef), p->hp.wc)) ||
+            (rc = upload<float>(reinterpret_cast<float**>(&p->dwcoef), p->hp.dwc)) ||
+            (rc = upload<float>(reinterpret_cast<float**>(&p->p1c), p->hp.p1c)) ||
+            (rc = upload<float>(reinterpret_cast<float**>(&p->qc), p->hp.qc)) ||
+            (rc = upload<float>(reinterpret_cast<float**>(&p->iw), p->hp.iw)) ||
+            (rc = upload<float>(reinterpret_cast<float**>(&p->mtab), p->hp.mtab))) {
+            delete p;
+            return rc;
+        }
+    }
+    const cufftType tf = p->fp64 ? CUFFT_D2Z : CUFFT_R2C, ti = p->fp64 ? CUFFT_Z2D : CUFFT_C2R;
+    if (cufftPlan3d(&p->fwd, g.m, g.m, g.m, tf) != CUFFT_SUCCESS) {
+        delete p;
+        return fail(EWALD_ECUFFT, "cufftPlan3d (forward) failed");
+    }
+    p->have_fwd = true;
+    if (cufftPlan3d(&p->inv, g.m, g.m, g.m, ti) != CUFFT_SUCCESS) {
+        delete p;
+        return fail(EWALD_ECUFFT, "cufftPlan3d (inverse) failed");
+    }
+    p->have_inv = true;
+    *out = p;
+    return EWALD_OK;
+}
+
+int ewald_plan_query(ewald_plan plan, ewald_params* out) {
+    if (!plan || !out) return fail(EWALD_EINVAL, "NULL argument");
+    *out = plan->hp.p;
+    return EWALD_OK;
+}
+
+int ewald_eval(ewald_plan plan, const double* x, const double* rho, double* phi, double* force, double* energy,
+               void* stream) {
+    if (!plan || !x || !rho) return fail(EWALD_EINVAL, "NULL plan, x or rho");
+    int rc;
+    if ((rc = check_ptr_device(x, "x")) || (rc = check_ptr_device(rho, "rho")) ||
+        (rc = check_ptr_device(phi, "phi")) || (rc = check_ptr_device(force, "force")))
+        return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((rc = eval_device(plan, x, rho, phi, force, s))) return rc;
+    if (energy) return read_status(plan, s, energy);
+    return EWALD_OK;
+}
+
+int ewald_eval_host(ewald_plan plan, const double* x, const double* rho, double* phi, double* force, double* energy,
+                    void* stream) {
+    if (!plan || !x || !rho) return fail(EWALD_EINVAL, "NULL plan, x or rho");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n = static_cast<size_t>(plan->g.n);
+    PSWF_CUDA(cudaMemcpyAsync(plan->x_stage, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
+    PSWF_CUDA(cudaMemcpyAsync(plan->rho_stage, rho, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+    int rc = eval_device(plan, plan->x_stage, plan->rho_stage, nullptr, nullptr, s);
+    if (rc) return rc;
+    if (phi) PSWF_CUDA(cudaMemcpyAsync(phi, plan->phi_int, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    if (force) PSWF_CUDA(cudaMemcpyAsync(force, plan->f_int, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, s));
+    double e = 0.0;
+    rc = read_status(plan, s, &e);
+    if (energy) *energy = e;
+    return rc;
+}
+
+int ewald_check(ewald_plan plan, void* stream) {
+    if (!plan) return fail(EWALD_EINVAL, "NULL plan");
+    return read_status(plan, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+int ewald_debug_grid(ewald_plan plan, int which, double* host_out) {
+    if (!plan || !host_out || (which != 0 && which != 1)) return fail(EWALD_EINVAL, "bad argument");
+    PSWF_CUDA(cudaDeviceSynchronize());
+    const size_t m3 = static_cast<size_t>(plan->g.m) * plan->g.m * plan->g.m;
+    const void* src = which == 0 ? plan->grid_a : plan->grid_b;
+    if (plan->fp64) {
+        PSWF_CUDA(cudaMemcpy(host_out, src, sizeof(double) * m3, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> tmp(m3);
+        PSWF_CUDA(cudaMemcpy(tmp.data(), src, sizeof(float) * m3, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < m3; ++i) host_out[i] = tmp[i];
+    }
+    return EWALD_OK;
+}
+
+void ewald_plan_destroy(ewald_plan plan) { delete plan; }
+
+int ewald_profile(ewald_plan plan, int enable) {
+    if (!plan) return fail(EWALD_EINVAL, "NULL plan");
+    if (enable) {
+        PSWF_CUDA(cudaDeviceSynchronize());
+        plan->clear_prof();
+    }
+    plan->profiling = enable != 0;
+    return EWALD_OK;
+}
+
+int ewald_profile_read(ewald_plan plan, double* ms, int* count) {
+    if (!plan || !ms) return fail(EWALD_EINVAL, "bad argument");
+    for (int k = 0; k < EWALD_NSTAGES; ++k) ms[k] = 0.0;
+    for (auto& v : plan->prof) {
+        PSWF_CUDA(cudaEventSynchronize(v[EWALD_NSTAGES]));
+        for (int k = 0; k < EWALD_NSTAGES; ++k) {
+            float t = 0.f;
+            PSWF_CUDA(cudaEventElapsedTime(&t, v[k], v[k + 1]));
+            ms[k] += t;
+        }
+    }
+    if (count) *count = static_cast<int>(plan->prof.size());
+    return EWALD_OK;
+}
+
+int ewald_pswf_eval(double c, int nx, const double* x, double* psi, double* dpsi, double* chi, double* lambda0) {
+    if (nx < 0 || (nx > 0 && !x)) return fail(EWALD_EINVAL, "bad point array");
+    try {
+        const pswf::Prolate f(c);
+        for (int i = 0; i < nx; ++i) {
+            if (psi) psi[i] = f.psi(x[i]);
+            if (dpsi) dpsi[i] = f.dpsi(x[i]);
+        }
+        if (chi) *chi = f.chi;
+        if (lambda0) *lambda0 = f.lambda;
+        return EWALD_OK;
+    } catch (const std::exception& e) {
+        return fail(EWALD_EINVAL, e.what());
+    }
+}
+
+double ewald_lambertw(int branch, double z) {
+    try {
+        return pswf::lambert_w(branch, z);
+    } catch (const std::exception& e) {
+        g_last_error = e.what();
+        return std::nan("");
+    }
+}
+
+int ewald_window_fit(const ewald_params* p, int nz, const double* z, double* w, double* dw) {
+    if (!p || nz < 0 || (nz > 0 && (!z || !w))) return fail(EWALD_EINVAL, "bad argument");
+    try {
+        const pswf::Prolate pw(p->cw);
+        const auto wc = pswf::fit_window(pw, p->P, p->deg_w, false, nullptr);
+        const auto dwc = pswf::fit_window(pw, p->P, p->deg_w, true, nullptr);
+        const int d = p->deg_w;
+        for (int i = 0; i < nz; ++i)
+            for (int a = 0; a < p->P; ++a) {
+                w[static_cast<size_t>(i) * p->P + a] = pswf::horner(wc.data() + a * (d + 1), d, z[i]);
+                if (dw) dw[static_cast<size_t>(i) * p->P + a] = pswf::horner(dwc.data() + a * (d + 1), d, z[i]) / p->alpha;
+            }
+        return EWALD_OK;
+    } catch (const std::exception& e) {
+        return fail(EWALD_EINVAL, e.what());
+    }
+}
+
+int ewald_radial_fit(const ewald_params* p, int nr, const double* r, double* R, double* G) {
+    if (!p || nr < 0 || (nr > 0 && (!r || !R))) return fail(EWALD_EINVAL, "bad argument");
+    try {
+        const pswf::Prolate ps(p->cs);
+        const auto c1 = pswf::fit_radial(ps, p->rc, p->deg_r, 0, nullptr);
+        const auto c2 = pswf::fit_radial(ps, p->rc, p->deg_r, 1, nullptr);
+        for (int i = 0; i < nr; ++i) {
+            const double u = 2.0 * r[i] * r[i] / (p->rc * p->rc) - 1.0;
+            R[i] = 1.0 / r[i] - pswf::horner(c1.data(), p->deg_r, u);
+            if (G) G[i] = 1.0 / (r[i] * r[i] * r[i]) + pswf::horner(c2.data(), p->deg_r, u);
+        }
+        return EWALD_OK;
+    } catch (const std::exception& e) {
+        return fail(EWALD_EINVAL, e.what());
+    }
+}
+
+int ewald_scale_table(const ewald_params* p, double* S) {
+    if (!p || !S) return fail(EWALD_EINVAL, "bad argument");
+    try {
+        const pswf::Prolate ps(p->cs), pw(p->cw);
+        std::vector<double> iw, mtab;
+        pswf::scale_tables(*p, ps, pw, iw, mtab);
+        const int m = p->m, mh = m / 2 + 1, qmax = (m / 2) * (m / 2);
+        for (int ix = 0; ix < m; ++ix)
+            for (int iy = 0; iy < m; ++iy)
+                for (int iz = 0; iz < mh; ++iz) {
+                    const int kx = ix < m / 2 ? ix : ix - m, ky = iy < m / 2 ? iy : iy - m, kz = iz;
+                    const int q = kx * kx + ky * ky + kz * kz;
+                    S[(static_cast<size_t>(ix) * m + iy) * mh + iz] =
+                        (q > 0 && q <= qmax) ? mtab[q] * iw[ix] * iw[iy] * iw[iz] : 0.0;
+                }
+        return EWALD_OK;
+    } catch (const std::exception& e) {
+        return fail(EWALD_EINVAL, e.what());
+    }
+}
+
+const char* ewald_error_string(int code) {
+    switch (code) {
+        case EWALD_OK: return "ok";
+        case EWALD_EINVAL: return "invalid argument";
+        case EWALD_ENONNEUTRAL: return "charges are not neutral";
+        case EWALD_ENOMEM: return "out of memory";
+        case EWALD_ECUDA: return "CUDA runtime error";
+        case EWALD_ECUFFT: return "cuFFT error";
+        case EWALD_ETOOBIG: return "problem beyond library limits";
+        case EWALD_ETIMEOUT: return "device wait timed out";
+        case EWALD_ENONFINITE: return "non-finite input";
+        default: return "unknown error";
+    }
+}
+
+const char* ewald_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

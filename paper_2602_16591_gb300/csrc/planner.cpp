@@ -1,0 +1,504 @@
+// Host planner for PSWF fast Ewald summation.
+//
+//  * Prolate: psi_0^c from its even Legendre expansion (App. B).  The ODE
+//    (eq. ode) becomes a symmetric tridiagonal eigenproblem in the orthonormal
+//    basis sqrt(k+1/2) P_k; the smallest eigenvalue chi_0 is located by Sturm
+//    bisection and the coefficients by inverse iteration (App. B, "Computation
+//    of eigenpairs").  lambda_0 = (1/psi(0)) int psi by Gauss-Legendre quadrature.
+//  * Alg. 3 (Sec. 6.4) with Lambert W by Halley iteration.
+//  * Piecewise window polynomials (Remark on Horner evaluation, Sec. 4.3) and
+//    radial polynomials for the residual kernel R (eq. R, eq. Phi_cs).
+//  * Diagonal scaling tables for Alg. 2 step 3.
+#include "planner.h"
+
+#include <algorithm>
+#include <cmath>
+#include <stdexcept>
+
+namespace pswf {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_N.
+void gauss_legendre(int N, std::vector<double>& x, std::vector<double>& w) {
+    x.assign(N, 0.0);
+    w.assign(N, 0.0);
+    for (int i = 0; i < (N + 1) / 2; ++i) {
+        double z = std::cos(kPi * (i + 0.75) / (N + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= N; ++k) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            // p1 = P_N(z), p0 = P_{N-1}(z)
+            dp = N * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = -z;
+        x[N - 1 - i] = z;
+        double wt = 2.0 / ((1.0 - z * z) * dp * dp);
+        w[i] = wt;
+        w[N - 1 - i] = wt;
+    }
+}
+
+// Number of eigenvalues of the symmetric tridiagonal (d, e) below sigma.
+int sturm_count(const std::vector<double>& d, const std::vector<double>& e, double sigma) {
+    int cnt = 0;
+    double q = d[0] - sigma;
+    if (q < 0) ++cnt;
+    for (size_t i = 1; i < d.size(); ++i) {
+        if (q == 0.0) q = 1e-300;
+        q = d[i] - sigma - e[i - 1] * e[i - 1] / q;
+        if (q < 0) ++cnt;
+    }
+    return cnt;
+}
+
+// Solve (T) y = b for a general tridiagonal T (sub, diag, super) with partial pivoting.
+void tridiag_solve(std::vector<double> sub, std::vector<double> diag, std::vector<double> sup,
+                   std::vector<double>& b) {
+    const int n = static_cast<int>(diag.size());
+    std::vector<double> sup2(n, 0.0);
+    for (int i = 0; i < n - 1; ++i) {
+        if (std::fabs(diag[i]) >= std::fabs(sub[i])) {
+            if (diag[i] == 0.0) diag[i] = 1e-300;
+            double f = sub[i] / diag[i];
+            diag[i + 1] -= f * sup[i];
+            b[i + 1] -= f * b[i];
+        } else {
+            // swap rows i and i+1
+            double f = diag[i] / sub[i];
+            diag[i] = sub[i];
+            double t = diag[i + 1];
+            diag[i + 1] = sup[i] - f * t;
+            if (i < n - 2) {
+                sup2[i] = sup[i + 1];
+                sup[i + 1] = -f * sup2[i];
+            }
+            sup[i] = t;
+            double tb = b[i];
+            b[i] = b[i + 1];
+            b[i + 1] = tb - f * b[i + 1];
+        }
+    }
+    if (diag[n - 1] == 0.0) diag[n - 1] = 1e-300;
+    b[n - 1] /= diag[n - 1];
+    if (n > 1) b[n - 2] = (b[n - 2] - sup[n - 2] * b[n - 1]) / diag[n - 2];
+    for (int i = n - 3; i >= 0; --i) b[i] = (b[i] - sup[i] * b[i + 1] - sup2[i] * b[i + 2]) / diag[i];
+}
+
+}  // namespace
+
+double horner(const double* c, int deg, double x) {
+    double r = c[deg];
+    for (int k = deg - 1; k >= 0; --k) r = r * x + c[k];
+    return r;
+}
+
+// ---------------------------------------------------------------- Prolate ----
+Prolate::Prolate(double cc) : c(cc) {
+    if (!(c > 0)) throw std::invalid_argument("PSWF bandlimit must be positive");
+    const int K = static_cast<int>(std::ceil(1.2 * c)) + 24;   // App. B: K ~ 1.2 c, plus margin
+    std::vector<double> d(K), e(K - 1);
+    for (int i = 0; i < K; ++i) {
+        const double k = 2.0 * i;
+        d[i] = k * (k + 1) + c * c * (2 * k * (k + 1) - 1) / ((2 * k + 3) * (2 * k - 1));
+        if (i < K - 1) e[i] = c * c * (k + 1) * (k + 2) / ((2 * k + 3) * std::sqrt((2 * k + 1) * (2 * k + 5)));
+    }
+    // Sturm bisection for the smallest eigenvalue (Gershgorin lower bound, Rayleigh upper bound)
+    double lo = d[0] - std::fabs(e[0]);
+    for (int i = 1; i < K; ++i)
+        lo = std::min(lo, d[i] - std::fabs(e[i - 1]) - (i < K - 1 ? std::fabs(e[i]) : 0.0));
+    double hi = d[0] + 1e-9 * (1.0 + std::fabs(d[0]));
+    for (int it = 0; it < 200 && hi - lo > 4e-16 * std::max(1.0, std::fabs(hi)); ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (sturm_count(d, e, mid) >= 1) hi = mid; else lo = mid;
+    }
+    chi = 0.5 * (lo + hi);
+    // inverse iteration
+    std::vector<double> v(K, 1.0);
+    const double shift = chi + 1e-13 * std::max(1.0, std::fabs(chi));
+    for (int it = 0; it < 4; ++it) {
+        std::vector<double> dd(K), sub(e), sup(e);
+        for (int i = 0; i < K; ++i) dd[i] = d[i] - shift;
+        tridiag_solve(sub, dd, sup, v);
+        double nrm = 0;
+        for (double t : v) nrm += t * t;
+        nrm = std::sqrt(nrm);
+        for (double& t : v) t /= nrm;
+    }
+    a.resize(K);
+    for (int i = 0; i < K; ++i) a[i] = v[i] * std::sqrt(2.0 * i + 0.5);
+    if (psi(0.0) < 0)
+        for (double& t : a) t = -t;
+    psi0 = psi(0.0);
+    psi1 = psi(1.0);
+    std::vector<double> gx, gw;
+    gauss_legendre(K + 10, gx, gw);
+    double s = 0;
+    for (size_t i = 0; i < gx.size(); ++i) s += gw[i] * psi(gx[i]);
+    lambda = s / psi0;   // App. B: lambda_0 = (1/psi(0)) int psi
+}
+
+double Prolate::psi(double x) const {
+    const int nmax = 2 * static_cast<int>(a.size()) - 2;
+    double p0 = 1.0, p1 = x, s = a[0];
+    for (int n = 1; n < nmax; ++n) {
+        double p2 = ((2.0 * n + 1.0) * x * p1 - n * p0) / (n + 1.0);   // P_{n+1}
+        p0 = p1;
+        p1 = p2;
+        if ((n + 1) % 2 == 0) s += a[(n + 1) / 2] * p1;
+    }
+    return s;
+}
+
+long double Prolate::psi_ld(long double x) const {
+    const int nmax = 2 * static_cast<int>(a.size()) - 2;
+    long double p0 = 1.0L, p1 = x, s = a[0];
+    for (int n = 1; n < nmax; ++n) {
+        long double p2 = ((2.0L * n + 1.0L) * x * p1 - n * p0) / (n + 1.0L);
+        p0 = p1;
+        p1 = p2;
+        if ((n + 1) % 2 == 0) s += a[(n + 1) / 2] * p1;
+    }
+    return s;
+}
+
+double Prolate::dpsi(double x) const {
+    // P'_{n+1} = P'_{n-1} + (2n+1) P_n
+    const int nmax = 2 * static_cast<int>(a.size()) - 2;
+    std::vector<double> P(nmax + 1), D(nmax + 1);
+    P[0] = 1.0;
+    D[0] = 0.0;
+    if (nmax >= 1) { P[1] = x; D[1] = 1.0; }
+    for (int n = 1; n < nmax; ++n) {
+        P[n + 1] = ((2.0 * n + 1.0) * x * P[n] - n * P[n - 1]) / (n + 1.0);
+        D[n + 1] = D[n - 1] + (2.0 * n + 1.0) * P[n];
+    }
+    double s = 0;
+    for (size_t i = 0; i < a.size(); ++i) s += a[i] * D[2 * i];
+    return s;
+}
+
+long double Prolate::int0_ld(long double x) const {
+    // int_0^x P_0 = x; int_0^x P_n = (P_{n+1}(x) - P_{n-1}(x)) / (2n+1) for n >= 1
+    const int nmax = 2 * static_cast<int>(a.size());
+    std::vector<long double> P(nmax + 1);
+    P[0] = 1.0L;
+    P[1] = x;
+    for (int n = 1; n < nmax; ++n) P[n + 1] = ((2.0L * n + 1.0L) * x * P[n] - n * P[n - 1]) / (n + 1.0L);
+    long double s = a[0] * x;
+    for (size_t i = 1; i < a.size(); ++i) {
+        const int n = 2 * static_cast<int>(i);
+        s += a[i] * (P[n + 1] - P[n - 1]) / (2.0L * n + 1.0L);
+    }
+    return s;
+}
+
+double Prolate::cos_transform(double omega) const {
+    CosQuadrature q(*this, std::fabs(omega));
+    return q(omega);
+}
+
+CosQuadrature::CosQuadrature(const Prolate& f, double omega_max) {
+    const int N = static_cast<int>(f.a.size()) + static_cast<int>(0.6 * omega_max) + 48;
+    gauss_legendre(N, x, w);
+    for (int i = 0; i < N; ++i) w[i] *= f.psi(x[i]);
+}
+
+double CosQuadrature::operator()(double omega) const {
+    double s = 0;
+    for (size_t i = 0; i < x.size(); ++i) s += w[i] * std::cos(omega * x[i]);
+    return s;
+}
+
+// --------------------------------------------------------------- Lambert W --
+double lambert_w(int branch, double z) {
+    const double em1 = 0.36787944117144233;   // 1/e
+    if (z < -em1 - 1e-15) throw std::invalid_argument("Lambert W: z < -1/e");
+    if (branch == -1 && !(z < 0)) throw std::invalid_argument("Lambert W_{-1}: z must be in [-1/e, 0)");
+    double w;
+    if (branch == 0) {
+        if (z > 3.0) {
+            const double l1 = std::log(z), l2 = std::log(l1);
+            w = l1 - l2 + l2 / l1;
+        } else if (z > -0.25) {
+            w = std::log1p(z);
+        } else {
+            w = -1.0 + std::sqrt(std::max(0.0, 2.0 * (1.0 + z / em1)));
+        }
+    } else {
+        if (z < -0.25) {
+            w = -1.0 - std::sqrt(std::max(0.0, 2.0 * (1.0 + z / em1)));
+        } else {
+            const double l1 = std::log(-z), l2 = std::log(-l1);
+            w = l1 - l2 + l2 / l1;
+        }
+    }
+    for (int it = 0; it < 100; ++it) {
+        const double ew = std::exp(w);
+        const double f = w * ew - z;
+        const double wp1 = w + 1.0;
+        if (wp1 == 0.0) break;
+        const double dw = f / (ew * wp1 - (w + 2.0) * f / (2.0 * wp1));
+        w -= dw;
+        if (std::fabs(dw) <= 1e-15 * (1.0 + std::fabs(w))) break;
+    }
+    return w;
+}
+
+double kappa_constant() {
+    // sum_{k in Z^3 \ 0} |k|^-4 = sum_n r3(n)/n^2; tail sum_{n > N} r3(n)/n^2 ~ 4 pi / sqrt(N + 1/2)
+    const long N = 40000;
+    const int K = static_cast<int>(std::sqrt(static_cast<double>(N))) + 1;
+    double s = 0;
+    for (int i = -K; i <= K; ++i)
+        for (int j = -K; j <= K; ++j)
+            for (int k = -K; k <= K; ++k) {
+                const long q = static_cast<long>(i) * i + static_cast<long>(j) * j + static_cast<long>(k) * k;
+                if (q > 0 && q <= N) s += 1.0 / (static_cast<double>(q) * q);
+            }
+    s += 4.0 * kPi / std::sqrt(N + 0.5);
+    return s / (kPi * kPi);
+}
+
+int good_size(int m, int mult) {
+    m = std::max(m, mult);
+    for (;; ++m) {
+        if (m % mult) continue;
+        int r = m;
+        for (int p : {2, 3, 5, 7})
+            while (r % p == 0) r /= p;
+        if (r == 1) return m;
+    }
+}
+
+ewald_opts default_opts() {
+    ewald_opts o{};
+    o.precision = EWALD_FP64;
+    o.rc = 0.0;
+    o.grid_density = 1.0;
+    o.tol_safety = 0.25;
+    o.sr_reach = 2;
+    return o;
+}
+
+// ------------------------------------------------------------------- fits ---
+namespace {
+
+// Chebyshev interpolant of f at deg+1 first-kind nodes on [-1, 1], converted to monomials.
+template <class F>
+std::vector<double> cheb_monomial_fit(F f, int deg) {
+    const int N = deg + 1;
+    std::vector<long double> fv(N), ch(N, 0.0L);
+    for (int j = 0; j < N; ++j) fv[j] = f(std::cos(kPi * (j + 0.5) / N));
+    for (int k = 0; k < N; ++k) {
+        long double s = 0;
+        for (int j = 0; j < N; ++j) s += fv[j] * std::cos(kPi * k * (j + 0.5) / N);
+        ch[k] = s * (k == 0 ? 1.0L : 2.0L) / N;
+    }
+    // monomial coefficients of T_k by the recurrence T_{k+1} = 2 z T_k - T_{k-1}
+    std::vector<long double> tm1(N, 0.0L), t0(N, 0.0L), mono(N, 0.0L);
+    t0[0] = 1.0L;
+    for (int k = 0; k < N; ++k) {
+        for (int i = 0; i < N; ++i) mono[i] += ch[k] * t0[i];
+        std::vector<long double> t1(N, 0.0L);
+        for (int i = 0; i + 1 < N; ++i) t1[i + 1] += 2.0L * t0[i];
+        for (int i = 0; i < N; ++i) t1[i] -= (k == 0 ? 0.0L : tm1[i]);
+        if (k == 0) {                      // T_1 = z
+            std::fill(t1.begin(), t1.end(), 0.0L);
+            if (N > 1) t1[1] = 1.0L;
+        }
+        tm1 = t0;
+        t0 = t1;
+    }
+    return std::vector<double>(mono.begin(), mono.end());
+}
+
+template <class F>
+double max_fit_error(F f, const std::vector<double>& c, int deg, int nsample) {
+    double e = 0;
+    for (int i = 0; i <= nsample; ++i) {
+        const double z = -1.0 + 2.0 * i / nsample;
+        e = std::max(e, std::fabs(horner(c.data(), deg, z) - static_cast<double>(f(z))));
+    }
+    return e;
+}
+
+}  // namespace
+
+std::vector<double> fit_window(const Prolate& pw, int P, int deg, bool deriv, double* max_err) {
+    std::vector<double> out;
+    double err = 0;
+    for (int a = 0; a < P; ++a) {
+        auto f = [&](double z) {
+            const double s = (z + P - 1 - 2.0 * a) / P;
+            return (deriv ? pw.dpsi(s) : pw.psi(s)) / pw.psi0;
+        };
+        auto c = cheb_monomial_fit(f, deg);
+        err = std::max(err, max_fit_error(f, c, deg, 8 * (deg + 1)));
+        out.insert(out.end(), c.begin(), c.end());
+    }
+    if (max_err) *max_err = err;
+    return out;
+}
+
+std::vector<double> fit_radial(const Prolate& ps, double rc_d, int deg, int which, double* rel_err) {
+    const long double norm = 2.0L / (static_cast<long double>(ps.lambda) * ps.psi0);
+    const long double rc = rc_d;
+    auto f = [&](double u) -> double {
+        const long double x = std::sqrt((static_cast<long double>(u) + 1.0L) / 2.0L);
+        const long double Phi = norm * ps.int0_ld(x);
+        if (which == 0) return static_cast<double>(Phi / (x * rc));                 // P1
+        const long double dPhi = norm * ps.psi_ld(x);
+        return static_cast<double>((dPhi * x - Phi) / (x * x * x) / (rc * rc * rc));  // Q
+    };
+    auto c = cheb_monomial_fit(f, deg);
+    if (rel_err) {
+        // error measured away from u = -1, where the sampled form itself loses digits in FP64
+        double e = 0, s = 0;
+        for (int i = 0; i <= 1000; ++i) {
+            const double u = -1.0 + 1e-4 + (2.0 - 1e-4) * i / 1000.0;
+            const double v = f(u);
+            s = std::max(s, std::fabs(v));
+            e = std::max(e, std::fabs(horner(c.data(), deg, u) - v));
+        }
+        *rel_err = e / s;
+    }
+    return c;
+}
+
+void scale_tables(const ewald_params& p, const Prolate& ps, const Prolate& pw, std::vector<double>& iw,
+                  std::vector<double>& mtab) {
+    const int m = p.m;
+    const double L = p.L;
+    iw.resize(m);
+    const CosQuadrature qw(pw, kPi * (m / 2) * p.alpha * 2.0 / L + 1.0);
+    for (int i = 0; i < m; ++i) {
+        const int k = i < m / 2 ? i : i - m;
+        const double w = 2.0 * kPi * k / L;
+        const double ph = p.alpha * qw(w * p.alpha) / (pw.psi0 * p.h);   // phihat_1d(k) / h
+        iw[i] = 1.0 / (ph * ph);
+    }
+    const int qmax = (m / 2) * (m / 2);
+    mtab.assign(qmax + 1, 0.0);
+    const double V = L * L * L;
+    const CosQuadrature qs(ps, 2.0 * kPi * (m / 2) / L * p.rc + 1.0);
+    for (int q = 1; q <= qmax; ++q) {
+        const double omega = 2.0 * kPi * std::sqrt(static_cast<double>(q)) / L;
+        const double gh = qs(omega * p.rc) / (ps.lambda * ps.psi0);   // eq. gammahatintegral (with 1/lambda_0)
+        mtab[q] = L * L / (kPi * q) * gh / V;                          // eq. MhatPSWF and the 1/V of step 3
+    }
+}
+
+HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
+    if (!(L > 0) || !std::isfinite(L)) throw std::invalid_argument("L must be positive and finite");
+    if (n < 2) throw std::invalid_argument("n must be at least 2");
+    if (!(tol >= 1e-13 && tol <= 1e-2)) throw std::invalid_argument("tol must lie in [1e-13, 1e-2]");
+    if (o.precision != EWALD_FP64 && o.precision != EWALD_MIXED) throw std::invalid_argument("unknown precision");
+    if (!(o.tol_safety > 0 && o.tol_safety <= 1)) throw std::invalid_argument("tol_safety must lie in (0, 1]");
+    if (!(o.grid_density > 0)) throw std::invalid_argument("grid_density must be positive");
+    if (o.sr_reach < 1 || o.sr_reach > 4) throw std::invalid_argument("sr_reach must lie in [1, 4]");
+
+    const double As = 5.0, Aw = 3.1;                      // Secs. 5.1.1 and 5.2.1
+    static const double kappa = kappa_constant();
+    const double t = tol * o.tol_safety;
+    auto cs_of = [&](double rcl) {
+        const double bs_eps = As * std::sqrt(rcl) / (std::sqrt(kappa) * t);
+        return 0.5 * lambert_w(0, 2.0 * bs_eps * bs_eps);   // eq. cs_dimless
+    };
+    double rcl;
+    if (o.rc > 0) {
+        rcl = std::min(o.rc / L, 0.5);
+    } else {
+        const double mstar = std::cbrt(o.grid_density * static_cast<double>(n));
+        rcl = 0.1;
+        for (int it = 0; it < 12; ++it) rcl = std::min(cs_of(rcl) / (kPi * mstar), 0.5);
+    }
+    const double cs = cs_of(rcl);
+    const double mraw = std::ceil(cs / (kPi * rcl));      // eq. m_cs_dimless
+    if (mraw > 1024) throw std::length_error("grid beyond 1024^3");
+    const int m = good_size(static_cast<int>(mraw), 4);
+    if (m > 1024) throw std::length_error("grid beyond 1024^3");
+    rcl = cs / (kPi * m);                                 // eq. csrc holds exactly
+    const double bw = (As / Aw) * std::sqrt(rcl);
+    const double cw_t = -0.5 * lambert_w(-1, -2.0 * bw * bw * std::exp(-2.0 * cs) / cs);   // eq. cwW
+    const double alpha_over_L = rcl * cw_t / cs;          // eq. alpha
+    int P = static_cast<int>(std::ceil(2.0 * alpha_over_L * m));   // eq. P_dimless
+    P = std::max(P, 3);
+    if (P > 24) throw std::length_error("window support P > 24 (tolerance too tight)");
+
+    HostPlan hp;
+    ewald_params& p = hp.p;
+    p.L = L;
+    p.n = n;
+    p.tol = tol;
+    p.m = m;
+    p.P = P;
+    p.h = L / m;
+    p.rc = rcl * L;
+    p.cs = cs;
+    p.cw_target = cw_t;
+    p.cw = kPi * P / 2.0;                                 // eq. cwP
+    p.alpha = P * p.h / 2.0;
+    // float32 products cannot reach tol < 1e-7; below it MIXED runs the float64 kernels
+    p.precision = (o.precision == EWALD_MIXED && tol < 1e-7) ? EWALD_FP64 : o.precision;
+    p.tile = 4;
+    p.sr_reach = o.sr_reach;
+    int nc = static_cast<int>(std::floor(o.sr_reach / rcl));
+    nc = std::max(1, std::min(nc, 1024));
+    p.ncell = nc;
+    p.fit_tol = std::max(0.02 * t, p.precision == EWALD_MIXED ? 1e-8 : 5e-16);
+
+    const Prolate ps(p.cs), pw(p.cw);
+    p.lambda_s = ps.lambda;
+    p.lambda_w = pw.lambda;
+    p.self_coeff = 2.0 / (ps.lambda * p.rc);
+
+    // ---- window polynomials: smallest degree meeting fit_tol
+    {
+        double dmax = 0;
+        for (int i = 0; i <= 400; ++i) dmax = std::max(dmax, std::fabs(pw.dpsi(-1.0 + i / 200.0)) / pw.psi0);
+        bool ok = false;
+        for (int deg = 4; deg <= kDegWMax && !ok; ++deg) {
+            double err = 0, derr = 0;
+            auto wc = fit_window(pw, P, deg, false, &err);
+            auto dwc = fit_window(pw, P, deg, true, &derr);
+            if (err <= p.fit_tol && derr <= p.fit_tol * dmax) {
+                ok = true;
+                p.deg_w = deg;
+                hp.wc = wc;
+                hp.dwc = dwc;
+            }
+        }
+        if (!ok) throw std::runtime_error("window polynomial fit did not converge");
+    }
+    // ---- radial polynomials in u = 2 r^2/rc^2 - 1
+    {
+        bool ok = false;
+        for (int deg = 4; deg <= kDegRMax && !ok; ++deg) {
+            double e1 = 0, e2 = 0;
+            auto c1 = fit_radial(ps, p.rc, deg, 0, &e1);
+            auto c2 = fit_radial(ps, p.rc, deg, 1, &e2);
+            if (e1 <= p.fit_tol && e2 <= p.fit_tol) {
+                ok = true;
+                p.deg_r = deg;
+                hp.p1c = c1;
+                hp.qc = c2;
+            }
+        }
+        if (!ok) throw std::runtime_error("radial polynomial fit did not converge");
+    }
+    scale_tables(p, ps, pw, hp.iw, hp.mtab);
+    return hp;
+}
+
+}  // namespace pswf

@@ -1,0 +1,257 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Stage parity uses the oracle's step-by-step Alg. 2 with the plan's own (m, P, c_s, c_w, r_c);
+end-to-end parity uses the converged Ewald sum.  The bar: relative l2 error of phi and of F
+(over all 3n components) and the relative energy error at most 2 * tol; stage outputs of the
+FP64 path within a few hundred ulps of the oracle (bounded by the polynomial-fit tolerance).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import paper_2602_16591_gb300 as pe  # noqa: E402
+from oracle import exact  # noqa: E402
+from oracle.alg2 import Alg2  # noqa: E402
+from paper_2602_16591_gb300.workloads import nacl_lattice, uniform_alternating, uniform_neutral  # noqa: E402
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / np.linalg.norm(np.ravel(b)))
+
+
+def _run(x, rho, L, tol, prec, **opts):
+    plan = pe.Plan(L, len(x), tol, precision=prec, **opts)
+    phi, F, E = plan.eval(torch.tensor(x, device="cuda"), torch.tensor(rho, device="cuda"))
+    return plan, phi.cpu().numpy(), F.cpu().numpy(), E
+
+
+_CACHE = {}
+
+
+def _exact(key, x, rho, L, targets=None):
+    if key not in _CACHE:
+        _CACHE[key] = exact.pswf_exact(x, rho, L, targets=targets)
+    return _CACHE[key]
+
+
+def _alg2(plan, x, rho):
+    p = plan.params
+    return Alg2(p.L, p.m, p.P, p.cs, p.cw, p.rc)
+
+
+# ---------------------------------------------------------------- stage parity (FP64) --
+@pytest.fixture(scope="module")
+def fp64_stage_case():
+    x, rho, L = uniform_neutral(1500, seed=11)
+    plan, phi, F, E = _run(x, rho, L, 1e-12, "fp64")
+    A = _alg2(plan, x, rho)
+    ref = A.total(x, rho, stages=True)
+    return plan, x, rho, phi, F, E, ref
+
+
+def test_stage_spread_grid(fp64_stage_case):
+    """Alg. 2 step 1: the spread grid a_l."""
+    plan, x, rho, phi, F, E, ref = fp64_stage_case
+    a_gpu = plan.debug_grid(0)
+    a_ref = ref[4]["a"]
+    assert np.max(np.abs(a_gpu - a_ref)) <= 50 * plan.params.fit_tol * np.max(np.abs(a_ref))
+
+
+def test_stage_scaled_inverse_grid(fp64_stage_case):
+    """Alg. 2 steps 2-4: the grid b_l after FFT, scaling, inverse FFT."""
+    plan, x, rho, phi, F, E, ref = fp64_stage_case
+    b_gpu = plan.debug_grid(1)
+    b_ref = ref[4]["b"]
+    assert np.max(np.abs(b_gpu - b_ref)) <= 1e-9 * np.max(np.abs(b_ref))
+
+
+def test_stage_total_vs_cpu_alg2(fp64_stage_case):
+    """Alg. 2 step 5 + real-space sum + self term: phi, F, E against the CPU restatement."""
+    plan, x, rho, phi, F, E, ref = fp64_stage_case
+    assert _rel(phi, ref[0]) <= 1e-10
+    assert _rel(F, ref[3]) <= 1e-9
+    assert abs(E - ref[2]) <= 1e-10 * abs(ref[2])
+
+
+# ------------------------------------------------------------- end to end vs O-exact --
+CASES = [
+    ("alt1000", 1e-6, "fp64"),
+    ("alt1000", 1e-6, "mixed"),
+    ("alt1000", 1e-10, "fp64"),
+    ("uni4000", 1e-4, "mixed"),
+    ("uni4000", 1e-6, "mixed"),
+    ("uni4000", 1e-8, "fp64"),
+    ("uni4000", 1e-12, "fp64"),
+]
+
+
+def _system(name):
+    if name == "alt1000":
+        return uniform_alternating(1000, seed=0)
+    if name == "uni4000":
+        return uniform_neutral(4000, seed=2)
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name,tol,prec", CASES)
+def test_end_to_end_vs_exact(name, tol, prec):
+    x, rho, L = _system(name)
+    ref = _exact(name, x, rho, L)
+    plan, phi, F, E = _run(x, rho, L, tol, prec)
+    assert _rel(phi, ref[0]) <= 2 * tol
+    assert _rel(F, ref[3]) <= 2 * tol
+    assert abs(E - ref[2]) <= 2 * tol * abs(ref[2])
+
+
+@pytest.mark.parametrize("tol,prec", [(1e-6, "mixed"), (1e-10, "fp64")])
+def test_nacl_madelung(tol, prec):
+    M = 1.747564594633
+    x, q, L = nacl_lattice(4, 1.0)
+    plan, phi, F, E = _run(x, q, L, tol, prec)
+    ref = -q * M / (L / 8)
+    assert _rel(phi, ref) <= 2 * tol
+    assert abs(E / (-len(q) * M / (2 * L / 8)) - 1) <= 2 * tol
+    assert np.max(np.abs(F)) <= 2 * tol * M / (L / 8) ** 2 * 10
+
+
+# ----------------------------------------------- full size (bench workload), sampled targets --
+@pytest.fixture(scope="module")
+def full_size():
+    x, rho, L = uniform_neutral(100_000, seed=0)
+    tg = np.linspace(0, len(x) - 1, 48).astype(np.int64)
+    ref = exact.pswf_exact(x, rho, L, targets=tg)
+    return x, rho, L, tg, ref
+
+
+@pytest.mark.parametrize("tol,prec", [(1e-6, "mixed"), (1e-10, "fp64")])
+def test_full_size_sampled(full_size, tol, prec):
+    x, rho, L, tg, ref = full_size
+    plan, phi, F, E = _run(x, rho, L, tol, prec)
+    assert _rel(phi[tg], ref[0]) <= 2 * tol
+    assert _rel(F[tg], ref[3]) <= 2 * tol
+    assert np.isfinite(E)
+
+
+# ------------------------------------------------------------------------ edge cases --
+def test_two_charges():
+    x = np.array([[0.1, 0.2, 0.3], [0.6, 0.25, 0.9]])
+    rho = np.array([1.0, -1.0])
+    ref = exact.pswf_exact(x, rho, 1.0)
+    plan, phi, F, E = _run(x, rho, 1.0, 1e-8, "fp64")
+    assert _rel(phi, ref[0]) <= 2e-8 and _rel(F, ref[3]) <= 2e-8
+
+
+def test_positions_outside_box_and_on_boundary():
+    x, rho, L = uniform_alternating(600, seed=5)
+    shifted = x.copy()
+    shifted[:50] += 3 * L
+    shifted[50:100] -= 7 * L
+    shifted[100, :] = 0.0
+    x[100, :] = 0.0
+    shifted[101, :] = L           # wraps to 0 in every coordinate
+    x[101, :] = 0.0
+    x[101, 0] = 0.5
+    shifted[101, 0] = 0.5
+    ref_plan, phi0, F0, E0 = _run(np.mod(shifted, L), rho, L, 1e-8, "fp64")
+    plan, phi1, F1, E1 = _run(shifted, rho, L, 1e-8, "fp64")
+    assert _rel(phi1, phi0) <= 1e-12 and _rel(F1, F0) <= 1e-12
+
+
+def test_clustered_particles_many_per_tile():
+    rng = np.random.default_rng(3)
+    x = 0.3 + 0.05 * rng.random((800, 3))
+    rho = rng.uniform(-1, 1, 800)
+    rho -= rho.mean()
+    ref = exact.pswf_exact(x, rho, 1.0)
+    plan, phi, F, E = _run(x, rho, 1.0, 1e-6, "fp64")
+    assert _rel(phi, ref[0]) <= 2e-6 and _rel(F, ref[3]) <= 2e-6
+
+
+def test_ragged_tiles_odd_n():
+    x, rho, L = uniform_neutral(1001, seed=9)
+    ref = exact.pswf_exact(x, rho, L)
+    plan, phi, F, E = _run(x, rho, L, 1e-6, "mixed")
+    assert _rel(phi, ref[0]) <= 2e-6 and _rel(F, ref[3]) <= 2e-6
+
+
+def test_non_neutral_rejected():
+    x, rho, L = uniform_alternating(100, seed=1)
+    rho = rho.copy()
+    rho[0] += 0.5
+    with pytest.raises(pe.EwaldError) as ei:
+        _run(x, rho, L, 1e-6, "fp64")
+    assert ei.value.code == pe.EWALD_ENONNEUTRAL
+
+
+def test_non_finite_rejected():
+    x, rho, L = uniform_alternating(100, seed=1)
+    x = x.copy()
+    x[3, 1] = np.nan
+    with pytest.raises(pe.EwaldError) as ei:
+        _run(x, rho, L, 1e-6, "fp64")
+    assert ei.value.code == pe.EWALD_ENONFINITE
+
+
+def test_host_pointer_to_device_entry_rejected():
+    x, rho, L = uniform_alternating(100, seed=1)
+    plan = pe.Plan(L, 100, 1e-6)
+    import ctypes
+    xa = np.ascontiguousarray(x)
+    ra = np.ascontiguousarray(rho)
+    code = pe.lib.ewald_eval(plan._h, xa.ctypes.data_as(ctypes.c_void_p), ra.ctypes.data_as(ctypes.c_void_p),
+                             None, None, None, None)
+    assert code == pe.EWALD_EINVAL
+
+
+def test_eval_host_matches_eval():
+    x, rho, L = uniform_neutral(3000, seed=4)
+    plan = pe.Plan(L, len(x), 1e-8, precision="fp64")
+    phi_d, F_d, E_d = plan.eval(torch.tensor(x, device="cuda"), torch.tensor(rho, device="cuda"))
+    phi_h, F_h, E_h = plan.eval_host(x, rho)
+    assert _rel(phi_h, phi_d.cpu().numpy()) <= 1e-13
+    assert _rel(F_h, F_d.cpu().numpy()) <= 1e-12
+    assert abs(E_h - E_d) <= 1e-13 * abs(E_d)
+
+
+def test_repeated_evaluations_stable():
+    x, rho, L = uniform_neutral(5000, seed=6)
+    plan = pe.Plan(L, len(x), 1e-6, precision="mixed")
+    xt, rt = torch.tensor(x, device="cuda"), torch.tensor(rho, device="cuda")
+    outs = [plan.eval(xt, rt) for _ in range(3)]
+    for o in outs[1:]:
+        assert _rel(o[0].cpu().numpy(), outs[0][0].cpu().numpy()) <= 1e-6
+        assert abs(o[2] - outs[0][2]) <= 1e-6 * abs(outs[0][2])
+
+
+def test_forces_are_energy_gradient():
+    """The discrete energy's gradient is -F (adjoint structure of spread/interp); central differences."""
+    x, rho, L = uniform_neutral(200, seed=8)
+    plan = pe.Plan(L, len(x), 1e-12, precision="fp64")
+    xt, rt = torch.tensor(x, device="cuda"), torch.tensor(rho, device="cuda")
+    _, F, _ = plan.eval(xt, rt)
+    F = F.cpu().numpy()
+    h = 1e-5
+    for i, d in [(0, 0), (17, 1), (123, 2), (199, 0)]:
+        xp = x.copy()
+        xm = x.copy()
+        xp[i, d] += h
+        xm[i, d] -= h
+        Ep = plan.eval(torch.tensor(xp, device="cuda"), rt)[2]
+        Em = plan.eval(torch.tensor(xm, device="cuda"), rt)[2]
+        fd = -(Ep - Em) / (2 * h)
+        assert abs(fd - F[i, d]) <= 1e-6 * max(1.0, np.max(np.abs(F)))
+
+
+def test_autograd_energy():
+    x, rho, L = uniform_neutral(500, seed=12)
+    plan = pe.Plan(L, len(x), 1e-8, precision="fp64")
+    xt = torch.tensor(x, device="cuda", requires_grad=True)
+    rt = torch.tensor(rho, device="cuda", requires_grad=True)
+    E = pe.energy(xt, rt, plan)
+    E.backward()
+    phi, F, E2 = plan.eval(xt.detach(), rt.detach())
+    assert torch.allclose(xt.grad, -F, rtol=1e-12, atol=1e-12 * F.abs().max().item())
+    assert torch.allclose(rt.grad, phi, rtol=1e-12, atol=1e-12 * phi.abs().max().item())
