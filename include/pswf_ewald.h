@@ -169,7 +169,8 @@ int ewald_radial_fit(const ewald_params* p, int nr, const double* r, double* R, 
 
 /* The diagonal scaling S(k) of Alg. 2 step 3 on the half spectrum the library
  * uses: S[(ix*m + iy)*(m/2+1) + iz] for k = (kx(ix), ky(iy), iz), where
- * kx(i) = i for i < m/2 and i - m otherwise.  S holds m*m*(m/2+1) doubles. */
+ * kx(i) = i for i < m/2 and i - m otherwise; S = 0 outside the open ball
+ * 0 < |k| < m/2.  S holds m*m*(m/2+1) doubles. */
 int ewald_scale_table(const ewald_params* p, double* S);
 
 const char* ewald_error_string(int code);

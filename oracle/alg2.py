@@ -15,10 +15,11 @@ window half-width alpha = P h / 2 (Sec. 6.3, eq. alpha and the relation alpha = 
             The factor h^-3 converts the continuous transform of Sec. 4.3 into the
             coefficient seen by an unnormalised m^3-point DFT (Poisson summation with
             c_k = phihat/V of eq. fcoeffs, times m^3); Alg. 2 as printed leaves it implicit.
-            S(k) = 0 also for |k| > m/2 (the cube corners of I_m): Prop. 1 bounds the
-            split error by the modes outside this ball, and deconvolving the corners,
-            where phihat ~ psi(1)^3, amplifies FFT rounding by ~exp(3 c_w - c_s)
-            (``ball=False`` keeps the full cube for comparison).
+            S(k) = 0 also for |k| >= m/2 (the cube corners of I_m and the sphere
+            |k| = m/2 itself, which holds the Nyquist axis modes): Prop. 1 bounds the
+            split error by the modes outside this ball, and deconvolving where
+            phihat ~ psi(1)^3 (corners) or ~psi(1) (Nyquist) amplifies rounding by up to
+            ~exp(3 c_w - c_s) (``ball=False`` keeps the full cube for comparison).
 4. IFFT     b_l = sum_k bhat_k e^{-2 pi i k.l/m}                          (Alg. 2 step 4)
 5. interp   phi_i^far = sum_l b_l phitilde(x_i - h l)                     (Alg. 2 step 5)
             grad phi_i^far = sum_l b_l grad phitilde(x_i - h l)           (Remark 'force', eq. force)
@@ -100,7 +101,7 @@ class Alg2:
         den = (ph1[:, None, None] * ph1[None, :, None] * ph1[None, None, :]) ** 2
         S[nz] = Mh / (L ** 3) / den[nz]
         if self.ball:
-            S[4 * k2 > m * m] = 0.0
+            S[4 * k2 >= m * m] = 0.0
         return S
 
     def fft(self, a):

@@ -63,6 +63,7 @@ struct ewald_plan_s {
     int2* sp_idx = nullptr;
     void* sr_rec = nullptr;
     int2* sr_idx = nullptr;
+    void* sr_lo = nullptr;   // float32 plans: float-float residue of the local coordinates
     void* scratch = nullptr;
     void* grid_a = nullptr;
     void* grid_b = nullptr;
@@ -98,7 +99,7 @@ struct ewald_plan_s {
     }
 
     ~ewald_plan_s() {
-        void* bufs[] = {key_rank, tile_cnt, tile_off, cell_cnt, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, scratch,
+        void* bufs[] = {key_rank, tile_cnt, tile_off, cell_cnt, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, sr_lo, scratch,
                         grid_a, grid_b, spec, wcoef, dwcoef, p1c, qc, iw, mtab, phi_int, f_int, status, epart,
                         energy_d, x_stage, rho_stage};
         for (void* b : bufs)
@@ -128,8 +129,9 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     PSWF_CUDA(cudaGetLastError());
     auto* sp_rec = static_cast<Vec4<real>*>(p->sp_rec);
     auto* sr_rec = static_cast<Vec4<real>*>(p->sr_rec);
+    auto* sr_lo = static_cast<Vec4<real>*>(p->sr_lo);
     pswf::k_scatter<real><<<nb, tb, 0, s>>>(x, rho, g, p->key_rank, p->tile_off, p->cell_off, sp_rec, p->sp_idx,
-                                            sr_rec, p->sr_idx);
+                                            sr_rec, p->sr_idx, sr_lo);
     PSWF_CUDA(cudaGetLastError());
     p->mark(1, s);
     // Alg. 2 step 1
@@ -169,7 +171,7 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
                                          static_cast<const real*>(p->dwcoef), g, inv_alpha, phi, f, s));
     p->mark(7, s);
     // real-space sum
-    pswf::k_short<real><<<(n + 127) / 128, 128, 0, s>>>(sr_rec, p->sr_idx, p->cell_off, g,
+    pswf::k_short<real><<<(n + 127) / 128, 128, 0, s>>>(sr_rec, p->sr_idx, sr_lo, p->cell_off, g,
                                                        static_cast<const real*>(p->p1c),
                                                        static_cast<const real*>(p->qc), phi, f);
     PSWF_CUDA(cudaGetLastError());
@@ -319,6 +321,11 @@ int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, e
             delete p;
             return fail(EWALD_ENOMEM, "device allocation failed (" + std::to_string(a.bytes) + " bytes)");
         }
+    }
+    if (!p->fp64 && cudaMalloc(&p->sr_lo, 4 * sizeof(float) * n) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return fail(EWALD_ENOMEM, "device allocation failed (real-space residues)");
     }
     if (cudaMallocHost(reinterpret_cast<void**>(&p->status_h), sizeof(double) * 4) != cudaSuccess) {
         delete p;
@@ -517,7 +524,7 @@ int ewald_scale_table(const ewald_params* p, double* S) {
                     const int kx = ix < m / 2 ? ix : ix - m, ky = iy < m / 2 ? iy : iy - m, kz = iz;
                     const int q = kx * kx + ky * ky + kz * kz;
                     S[(static_cast<size_t>(ix) * m + iy) * mh + iz] =
-                        (q > 0 && q <= qmax) ? mtab[q] * iw[ix] * iw[iy] * iw[iz] : 0.0;
+                        (q > 0 && q < qmax) ? mtab[q] * iw[ix] * iw[iy] * iw[iz] : 0.0;
                 }
         return EWALD_OK;
     } catch (const std::exception& e) {

@@ -172,7 +172,8 @@ template <typename real>
 __global__ void k_scatter(const double* __restrict__ x, const double* __restrict__ rho, Geom g,
                           const int* __restrict__ key_rank, const int* __restrict__ tile_off,
                           const int* __restrict__ cell_off, Vec4<real>* __restrict__ sp_rec,
-                          int2* __restrict__ sp_idx, Vec4<real>* __restrict__ sr_rec, int2* __restrict__ sr_idx) {
+                          int2* __restrict__ sp_idx, Vec4<real>* __restrict__ sr_rec, int2* __restrict__ sr_idx,
+                          Vec4<real>* __restrict__ sr_lo) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     const Located r = locate(x + 3 * static_cast<size_t>(i), g);
@@ -196,6 +197,14 @@ __global__ void k_scatter(const double* __restrict__ x, const double* __restrict
     b.w = static_cast<real>(q);
     sr_rec[pc] = b;
     sr_idx[pc] = make_int2(cell_of(r, g), i);
+    if (sr_lo) {   // float32 records carry the rounding residue (float-float local coordinates)
+        Vec4<real> c;
+        c.x = static_cast<real>(r.loc[0] - static_cast<double>(b.x));
+        c.y = static_cast<real>(r.loc[1] - static_cast<double>(b.y));
+        c.z = static_cast<real>(r.loc[2] - static_cast<double>(b.z));
+        c.w = real(0);
+        sr_lo[pc] = c;
+    }
 }
 
 // P window weights at one coordinate z by Horner (coefficients c[a*(deg+1) + k], monomials in z).
@@ -332,7 +341,7 @@ __global__ void k_scale(cplx* __restrict__ spec, int m, const real* __restrict__
     const int q = kx * kx + ky * ky + kz * kz;
     const int qmax = (m / 2) * (m / 2);
     real s = real(0);
-    if (q > 0 && q <= qmax) s = mtab[q] * iw[ix] * iw[iy] * iw[iz];
+    if (q > 0 && q < qmax) s = mtab[q] * iw[ix] * iw[iy] * iw[iz];   // open ball |k| < m/2
     cplx v = spec[id];
     v.x *= s;
     v.y *= s;
@@ -447,6 +456,10 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
 // ---- real-space sum of R over the cell list (Sec. 3.1.1) -----------------------------------------
 // One thread per target in cell order; neighbour cells within `reach` whose box distance is below
 // rc.  R(r) = 1/r - P1(u), -R'(r)/r = 1/r^3 + Q(u), u = 2 r^2/rc^2 - 1 (host-fitted polynomials).
+// In float32 the pair displacement is formed in float-float: positions are (hi, lo) pairs relative
+// to their cell, the neighbour-cell shift o is split the same way, and d = x_i - (x_j + o) is
+// evaluated as (hi_i - (hi_j + o_hi)) + ((lo_i - o_lo) - lo_j): for close pairs across a cell face
+// hi_j + o_hi cancels exactly, so d keeps full relative precision.
 template <typename real>
 __device__ __forceinline__ real rsqrt_r(real v);
 template <> __device__ __forceinline__ float rsqrt_r<float>(float v) { return rsqrtf(v); }
@@ -454,8 +467,8 @@ template <> __device__ __forceinline__ double rsqrt_r<double>(double v) { return
 
 template <typename real>
 __global__ void __launch_bounds__(128) k_short(const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
-                                               const int* __restrict__ cell_off, Geom g,
-                                               const real* __restrict__ p1c, const real* __restrict__ qc,
+                                               const Vec4<real>* __restrict__ lo, const int* __restrict__ cell_off,
+                                               Geom g, const real* __restrict__ p1c, const real* __restrict__ qc,
                                                double* __restrict__ phi_out, double* __restrict__ f_out) {
     __shared__ real sp[64], sq[64];
     const int degr = g.degr;
@@ -468,30 +481,42 @@ __global__ void __launch_bounds__(128) k_short(const Vec4<real>* __restrict__ re
     if (i >= g.n) return;
     const int nc = g.ncell, R = g.reach;
     const Vec4<real> me = rec[i];
+    const Vec4<real> mlo = lo ? lo[i] : Vec4<real>{real(0), real(0), real(0), real(0)};
     const int2 id = idx[i];
     const int cz = id.x % nc, cy = (id.x / nc) % nc, cx = id.x / (nc * nc);
-    const real cw = static_cast<real>(g.cellw);
     const real rc2 = static_cast<real>(g.rc * g.rc);
     const real two_over_rc2 = static_cast<real>(2.0 / (g.rc * g.rc));
     const double cw2 = g.cellw * g.cellw, rcsq = g.rc * g.rc;
     real ph = 0, fx = 0, fy = 0, fz = 0;
     for (int dx = -R; dx <= R; ++dx) {
         const int bx = abs(dx) > 0 ? abs(dx) - 1 : 0;
+        const double odx = dx * g.cellw;
+        const real ohx = static_cast<real>(odx), olx = static_cast<real>(odx - static_cast<double>(ohx));
         for (int dy = -R; dy <= R; ++dy) {
             const int by = abs(dy) > 0 ? abs(dy) - 1 : 0;
+            const double ody = dy * g.cellw;
+            const real ohy = static_cast<real>(ody), oly = static_cast<real>(ody - static_cast<double>(ohy));
             for (int dz = -R; dz <= R; ++dz) {
                 const int bz = abs(dz) > 0 ? abs(dz) - 1 : 0;
                 if ((bx * bx + by * by + bz * bz) * cw2 >= rcsq) continue;
+                const double odz = dz * g.cellw;
+                const real ohz = static_cast<real>(odz), olz = static_cast<real>(odz - static_cast<double>(ohz));
                 int nx = (cx + dx) % nc, ny = (cy + dy) % nc, nz = (cz + dz) % nc;
                 nx += nx < 0 ? nc : 0;
                 ny += ny < 0 ? nc : 0;
                 nz += nz < 0 ? nc : 0;
                 const int cell = (nx * nc + ny) * nc + nz;
                 const int b = cell_off[cell], e = cell_off[cell + 1];
-                const real ox = me.x - dx * cw, oy = me.y - dy * cw, oz = me.z - dz * cw;
+                const real lx = mlo.x - olx, ly = mlo.y - oly, lz = mlo.z - olz;
                 for (int j = b; j < e; ++j) {
                     const Vec4<real> s = rec[j];
-                    const real ddx = ox - s.x, ddy = oy - s.y, ddz = oz - s.z;
+                    real ddx = me.x - (s.x + ohx), ddy = me.y - (s.y + ohy), ddz = me.z - (s.z + ohz);
+                    if (lo) {
+                        const Vec4<real> t = lo[j];
+                        ddx += lx - t.x;
+                        ddy += ly - t.y;
+                        ddz += lz - t.z;
+                    }
                     const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
                     if (r2 < rc2 && r2 > real(0)) {
                         const real u = fma(r2, two_over_rc2, real(-1));

@@ -41,7 +41,7 @@ struct HostPlan {
     std::vector<double> wc, dwc;    // dwc fits psi'(s)/psi(0) (the 1/alpha is applied on the device)
     // radial polynomials in u = 2 r^2/rc^2 - 1: R(r) = 1/r - P1(u), -R'(r)/r = 1/r^3 + Q(u)
     std::vector<double> p1c, qc;
-    // scaling: S(k) = mtab[|k|^2] * iw[kx] * iw[ky] * iw[kz] for |k|^2 <= (m/2)^2, else 0
+    // scaling: S(k) = mtab[|k|^2] * iw[kx] * iw[ky] * iw[kz] for 0 < |k|^2 < (m/2)^2, else 0
     std::vector<double> iw;         // indexed by grid index 0..m-1
     std::vector<double> mtab;       // indexed by |k|^2 = 0..(m/2)^2, mtab[0] = 0
 };
