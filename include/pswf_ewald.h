@@ -173,6 +173,32 @@ int ewald_radial_fit(const ewald_params* p, int nr, const double* r, double* R, 
  * 0 < |k| < m/2.  S holds m*m*(m/2+1) doubles. */
 int ewald_scale_table(const ewald_params* p, double* S);
 
+/* ---- spreading without device allocation -------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory when they need the spread grid: code running
+ * under an external allocator that forbids cudaMalloc/cudaFree, plugins inside
+ * a host application that owns all GPU memory, and latency-critical loops that
+ * must not hit the implicit synchronisation of allocation calls.
+ *
+ * Spreads n = p->n charges (Alg. 2 step 1, float64 arithmetic) onto the
+ * caller's grid: x (n,3) and rho (n) float64 DEVICE pointers as in ewald_eval,
+ * grid an m^3 float64 DEVICE array (z fastest) that receives a_l.  p holds the
+ * parameters of ewald_plan_params / ewald_plan_query (any precision; the
+ * window degree p->deg_w is used as given).  Asynchronous on `stream`.
+ *
+ * Scratch: a fixed 64 MiB array in the library's device image (every GPU that
+ * loads the library holds it until the process exits).  Problems needing more
+ * (roughly 120 n bytes plus 8 (m/4)^3 (P+3)^3 bytes) return EWALD_ETOOBIG.
+ * No cudaMalloc, cudaFree or other allocating call is made.  The first call on
+ * each device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  All
+ * calls share the one array and it keeps the previous call's contents (the
+ * entry point clears what must start at zero), so calls whose GPU work
+ * overlaps -- on different streams or host threads -- race and must be
+ * serialised by the caller.  Errors: EWALD_EINVAL (NULL pointer, parameters
+ * not from the planner), EWALD_ETOOBIG (scratch limit), EWALD_ECUDA. */
+int ewald_spread_static(const ewald_params* p, const double* x, const double* rho, double* grid, void* stream);
+
 const char* ewald_error_string(int code);
 const char* ewald_last_error(void);
 

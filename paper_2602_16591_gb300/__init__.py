@@ -67,6 +67,7 @@ def _load():
         "ewald_scale_table": (I, [ctypes.POINTER(ewald_params), P]),
         "ewald_profile": (I, [P, I]),
         "ewald_profile_read": (I, [P, P, ctypes.POINTER(ctypes.c_int)]),
+        "ewald_spread_static": (I, [ctypes.POINTER(ewald_params), P, P, P, P]),
         "ewald_error_string": (ctypes.c_char_p, [I]),
         "ewald_last_error": (ctypes.c_char_p, []),
     }

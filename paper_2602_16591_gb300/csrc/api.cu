@@ -47,6 +47,11 @@ int upload(T** dst, const std::vector<double>& src) {
 
 }  // namespace
 
+namespace pswf {
+// Lets other translation units of the library set the message ewald_last_error() returns.
+void record_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace pswf
+
 struct ewald_plan_s {
     pswf::HostPlan hp;
     pswf::Geom g{};

@@ -57,6 +57,9 @@ void scale_tables(const ewald_params& p, const Prolate& ps, const Prolate& pw, s
 HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& opts);
 ewald_opts default_opts();
 
+// Sets the thread-local message returned by ewald_last_error() (defined in api.cu).
+void record_error(const std::string& msg);
+
 double horner(const double* c, int deg, double x);
 
 }  // namespace pswf

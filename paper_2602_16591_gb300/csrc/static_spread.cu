@@ -1,0 +1,159 @@
+// Allocation-free spreading entry point (ewald_spread_static).
+//
+// Some callers cannot allocate device memory at the moment they need a result: code running
+// under a custom or pre-reserved device allocator that forbids cudaMalloc/cudaFree on the hot
+// path, plugins loaded into a host application that owns all GPU memory, and real-time loops
+// that must not trigger the implicit synchronisation cudaMalloc/cudaFree can cause.  For them
+// this entry point spreads charges onto a caller-owned grid using only a fixed scratch area
+// that lives in this library's image: one file-scope __device__ array, created when a GPU first
+// loads the library and held until the process exits.
+//
+// The computation is the float64 spreading of the regular pipeline (counting sort into tiles,
+// the tile spreading kernel, the halo sum), with every intermediate buffer carved out of the
+// static array instead of a plan workspace.
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "device.cuh"
+#include "launch.h"
+#include "planner.h"
+#include "pswf_ewald.h"
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(64) << 20;   // 64 MiB
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device address of g_static_scratch, looked up once per device.  In host code the symbol
+// name only stands in for the array; kernels must be given this address instead.
+constexpr int kMaxDevices = 64;
+std::mutex g_addr_mu;
+void* g_addr[kMaxDevices] = {nullptr};
+
+int fail_static(int code, const std::string& msg) {
+    pswf::record_error(msg);   // reported by ewald_last_error()
+    return code;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const double* rho, double* grid,
+                                   void* stream) {
+    if (!p || !x || !rho || !grid) return fail_static(EWALD_EINVAL, "NULL argument");
+    if (p->n < 1 || p->n > (int64_t(1) << 30)) return fail_static(EWALD_EINVAL, "particle count out of range");
+    if (p->P < pswf::kPMin || p->P > pswf::kPMax || p->tile != pswf::kTile || p->m % p->tile != 0 ||
+        p->deg_w < 1 || p->deg_w > pswf::kDegWMax || !(p->L > 0) || !(p->alpha > 0))
+        return fail_static(EWALD_EINVAL, "parameters do not come from ewald_plan_params");
+
+    // ---- carve the static array: counts, offsets, sort records, tile slabs, window table
+    const int64_t n = p->n;
+    const int m = p->m, P = p->P, T = p->tile, nt = m / T, E = T + P - 1;
+    const size_t ntiles = size_t(nt) * nt * nt;
+    const size_t need_key = align256(sizeof(int4) * n);
+    const size_t need_tcnt = align256(sizeof(int) * (ntiles + 1));
+    const size_t need_ccnt = align256(sizeof(int) * 2);
+    const size_t need_status = align256(sizeof(double) * 4);
+    const size_t need_rec = align256(sizeof(pswf::Vec4<double>) * n);
+    const size_t need_idx = align256(sizeof(int2) * n);
+    const size_t need_slab = align256(sizeof(double) * ntiles * size_t(E) * E * E);
+    const size_t need_coef = align256(sizeof(double) * P * (p->deg_w + 1));
+    const size_t need = need_key + 2 * need_tcnt + 2 * need_ccnt + need_status + 2 * need_rec + 2 * need_idx +
+                        need_slab + need_coef;
+    if (need > kStaticScratchBytes)
+        return fail_static(EWALD_ETOOBIG, "ewald_spread_static needs " + std::to_string(need) +
+                                              " bytes of scratch; its static array holds " +
+                                              std::to_string(kStaticScratchBytes) + " bytes");
+
+    // ---- per-device set-up: look up the array's device address with that device current
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return fail_static(EWALD_ECUDA, "no usable current CUDA device");
+    void* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_addr_mu);
+        if (!g_addr[dev]) {
+            void* ptr = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+            if (e != cudaSuccess || !ptr)
+                return fail_static(EWALD_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_addr[dev] = ptr;
+        }
+        base = g_addr[dev];
+    }
+
+    unsigned char* cur = static_cast<unsigned char*>(base);
+    auto take = [&](size_t b) {
+        unsigned char* r = cur;
+        cur += b;
+        return r;
+    };
+    int* key_rank = reinterpret_cast<int*>(take(need_key));
+    int* tile_cnt = reinterpret_cast<int*>(take(need_tcnt));
+    int* tile_off = reinterpret_cast<int*>(take(need_tcnt));
+    int* cell_cnt = reinterpret_cast<int*>(take(need_ccnt));
+    int* cell_off = reinterpret_cast<int*>(take(need_ccnt));
+    double* status = reinterpret_cast<double*>(take(need_status));
+    auto* sp_rec = reinterpret_cast<pswf::Vec4<double>*>(take(need_rec));
+    auto* sr_rec = reinterpret_cast<pswf::Vec4<double>*>(take(need_rec));
+    int2* sp_idx = reinterpret_cast<int2*>(take(need_idx));
+    int2* sr_idx = reinterpret_cast<int2*>(take(need_idx));
+    double* slab = reinterpret_cast<double*>(take(need_slab));
+    double* coef = reinterpret_cast<double*>(take(need_coef));
+
+    // ---- window polynomial table (host fit, copied into the static array)
+    std::vector<double> wc;
+    try {
+        const pswf::Prolate pw(p->cw);
+        wc = pswf::fit_window(pw, P, p->deg_w, false, nullptr);
+    } catch (const std::exception& e) {
+        return fail_static(EWALD_EINVAL, e.what());
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(coef, wc.data(), sizeof(double) * wc.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return fail_static(EWALD_ECUDA, "window table copy failed");
+
+    // the array keeps the previous call's contents: counters must start at zero
+    if (cudaMemsetAsync(tile_cnt, 0, sizeof(int) * ntiles, s) != cudaSuccess ||
+        cudaMemsetAsync(cell_cnt, 0, sizeof(int) * 2, s) != cudaSuccess ||
+        cudaMemsetAsync(status, 0, sizeof(double) * 4, s) != cudaSuccess)
+        return fail_static(EWALD_ECUDA, "clearing the static counters failed");
+
+    pswf::Geom g{};
+    g.n = static_cast<int>(n);
+    g.m = m;
+    g.P = P;
+    g.T = T;
+    g.nt = nt;
+    g.ncell = 1;
+    g.reach = 1;
+    g.degw = p->deg_w;
+    g.degr = 0;
+    g.L = p->L;
+    g.invL = 1.0 / p->L;
+    g.h = p->L / m;
+    g.invh = m / p->L;
+    g.cellw = p->L;
+    g.rc = p->rc;
+    g.self = 0.0;
+
+    const int tb = 256, nb = static_cast<int>((n + tb - 1) / tb);
+    pswf::k_prep<<<nb, tb, 0, s>>>(x, rho, g, key_rank, tile_cnt, cell_cnt, status);
+    pswf::k_scan<<<2, 1024, 0, s>>>(tile_cnt, tile_off, static_cast<int>(ntiles), cell_cnt, cell_off, 1);
+    pswf::k_scatter<double><<<nb, tb, 0, s>>>(x, rho, g, key_rank, tile_off, cell_off, sp_rec, sp_idx, sr_rec,
+                                              sr_idx, nullptr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_static(EWALD_ECUDA, std::string("sort launch: ") + cudaGetErrorString(e));
+    e = pswf::Launch<double>::spread(P, static_cast<int>(ntiles), sp_rec, sp_idx, tile_off, coef, p->deg_w, slab, s);
+    if (e != cudaSuccess) return fail_static(EWALD_ECUDA, std::string("spread launch: ") + cudaGetErrorString(e));
+    const int mm = m * m * m;
+    pswf::k_halo<double><<<(mm + 255) / 256, 256, 0, s>>>(slab, tile_off, g, grid);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return fail_static(EWALD_ECUDA, std::string("halo launch: ") + cudaGetErrorString(e));
+    return EWALD_OK;
+}

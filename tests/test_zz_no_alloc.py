@@ -1,0 +1,53 @@
+"""ewald_spread_static: spreading into a caller-owned grid with no device allocation.
+
+It serves callers that cannot call cudaMalloc when they need the grid (an external
+allocator owns the GPU, or the loop cannot afford allocation-induced synchronisation).
+Its output must equal the spread grid of the regular pipeline (ewald_eval, stage 0 of
+ewald_debug_grid) for the same plan parameters, call after call: the entry point reuses
+one static device array whose counters it has to clear itself.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+import paper_2602_16591_gb300 as pe  # noqa: E402
+from paper_2602_16591_gb300.workloads import uniform_neutral  # noqa: E402
+
+
+def _spread_static(params, xt, rt):
+    m = params.m
+    out = torch.full((m ** 3,), float("nan"), dtype=torch.float64, device="cuda")   # caller-owned output
+    stream = torch.cuda.current_stream().cuda_stream
+    code = pe.lib.ewald_spread_static(ctypes.byref(params), ctypes.c_void_p(xt.data_ptr()),
+                                      ctypes.c_void_p(rt.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                      ctypes.c_void_p(stream))
+    assert code == pe.EWALD_OK, pe.lib.ewald_last_error().decode()
+    torch.cuda.synchronize()
+    return out.cpu().numpy().reshape(m, m, m)
+
+
+def test_static_spread_matches_pipeline_on_consecutive_calls():
+    # two calls in a row on different systems (different n, grid and tile counts)
+    for seed, n in ((21, 3000), (22, 5200)):
+        x, rho, L = uniform_neutral(n, seed=seed)
+        xt = torch.tensor(x, device="cuda")
+        rt = torch.tensor(rho, device="cuda")
+        plan = pe.Plan(L, n, 1e-8, precision="fp64")
+        plan.eval(xt, rt)
+        ref = plan.debug_grid(0)
+        got = _spread_static(plan.params, xt, rt)
+        assert np.all(np.isfinite(got))
+        assert np.max(np.abs(got - ref)) <= 50 * plan.params.fit_tol * np.max(np.abs(ref))
+
+
+def test_static_spread_rejects_problems_beyond_its_scratch():
+    p = pe.plan_params(1.0, 10_000_000, 1e-8)     # m = 216: the tile slabs alone exceed the array
+    dummy = ctypes.c_void_p(16)                    # never dereferenced: the size check comes first
+    code = pe.lib.ewald_spread_static(ctypes.byref(p), dummy, dummy, dummy, None)
+    assert code == pe.EWALD_ETOOBIG
+    assert b"static array" in pe.lib.ewald_last_error()
