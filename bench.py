@@ -246,7 +246,8 @@ def run_ours(args, rank, world, local_rank):
         except (ValueError, IndexError):
             pass
 
-    plan = pe.Plan(L, n, args.tol, precision=args.precision)
+    popts = {} if args.grid_density is None else {"grid_density": args.grid_density}
+    plan = pe.Plan(L, n, args.tol, precision=args.precision, **popts)
     with ClockSampler(gpu_index) as clk:
         ms_local, stages = timed(plan, args.steps, args.warmup, profile=True)
     clocks = clk.summary()
@@ -288,7 +289,7 @@ def run_ours(args, rank, world, local_rank):
     variants = []
     if not args.no_variants:
         for tol, prec in ((1e-6, "fp64"), (1e-10, "mixed"), (1e-10, "fp64")):
-            vp = pe.Plan(L, n, tol, precision=prec)
+            vp = pe.Plan(L, n, tol, precision=prec, **popts)
             vms, vst = timed(vp, max(5, args.steps // 3), 2, profile=True)
             vms = max_over_ranks(vms)
             variants.append({"tol": tol, "precision": prec,
@@ -331,6 +332,7 @@ def main():
     ap.add_argument("--n", type=int, default=100_000)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--precision", default="mixed", choices=("mixed", "fp64"))
+    ap.add_argument("--grid-density", type=float, default=None, help="m^3/n target of the cutoff rule")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -53,10 +53,12 @@ extern "C" {
 typedef struct ewald_opts {
     int    precision;     /* EWALD_FP64 or EWALD_MIXED (default EWALD_FP64) */
     double rc;            /* <= 0: automatic cutoff rule; > 0: upper bound on the cutoff (length units) */
-    double grid_density;  /* target m^3 / n for the automatic cutoff rule (default 1.0) */
+    double grid_density;  /* target m^3 / n for the automatic cutoff rule (default 2.0, the
+                             measured optimum of the GB300 kernels for n ~ 1e5) */
     double tol_safety;    /* the plan is sized for tol * tol_safety (default 0.25; forces have no
                              error model in the paper and measure ~2-5x the potential error) */
-    int    sr_reach;      /* cells per cutoff radius in the real-space cell list (default 2) */
+    int    sr_reach;      /* cells per cutoff radius in the real-space cell list, 1..4;
+                             0 (default) picks it for ~3 particles per cell */
 } ewald_opts;
 
 /* ---- derived parameters (Alg. 3 and the library's readings of it) ------ */

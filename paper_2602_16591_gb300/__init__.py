@@ -87,13 +87,14 @@ def _check(code):
         raise EwaldError(code, _lib.ewald_last_error().decode())
 
 
-def make_opts(precision="fp64", rc=None, grid_density=1.0, tol_safety=None, sr_reach=None):
+def make_opts(precision="fp64", rc=None, grid_density=None, tol_safety=None, sr_reach=None):
     o = ewald_opts()
     _check(_lib.ewald_opts_default(ctypes.byref(o)))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     if rc is not None:
         o.rc = float(rc)
-    o.grid_density = float(grid_density)
+    if grid_density is not None:
+        o.grid_density = float(grid_density)
     if tol_safety is not None:
         o.tol_safety = float(tol_safety)
     if sr_reach is not None:

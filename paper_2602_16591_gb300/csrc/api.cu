@@ -69,6 +69,9 @@ struct ewald_plan_s {
     void* sr_rec = nullptr;
     int2* sr_idx = nullptr;
     void* sr_lo = nullptr;   // float32 plans: float-float residue of the local coordinates
+    float4* sr_f32 = nullptr;  // float64 plans: float32 copy of the local coordinates (cutoff pre-test)
+    int4* sr_cols = nullptr;   // real-space columns {dx, dy, dzmax, 0} with box distance < rc
+    int n_cols = 0;
     void* scratch = nullptr;
     void* grid_a = nullptr;
     void* grid_b = nullptr;
@@ -104,7 +107,7 @@ struct ewald_plan_s {
     }
 
     ~ewald_plan_s() {
-        void* bufs[] = {key_rank, tile_cnt, tile_off, cell_cnt, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, sr_lo, scratch,
+        void* bufs[] = {key_rank, tile_cnt, tile_off, cell_cnt, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, sr_lo, sr_f32, sr_cols, scratch,
                         grid_a, grid_b, spec, wcoef, dwcoef, p1c, qc, iw, mtab, phi_int, f_int, status, epart,
                         energy_d, x_stage, rho_stage};
         for (void* b : bufs)
@@ -117,6 +120,41 @@ struct ewald_plan_s {
 };
 
 namespace {
+
+template <typename real, int D>
+cudaError_t launch_short_d(ewald_plan p, const pswf::Vec4<real>* sr_rec, const pswf::Vec4<real>* sr_lo, double* phi,
+                           double* f, cudaStream_t s) {
+    const pswf::Geom& g = p->g;
+    pswf::ShortParams<real, D> kp{};
+    const auto& c1 = p->hp.p1c;
+    const auto& c2 = p->hp.qc;
+    for (int k = 0; k <= D; ++k) {
+        kp.p1[k] = static_cast<real>(k < static_cast<int>(c1.size()) ? c1[k] : 0.0);
+        kp.q[k] = static_cast<real>(k < static_cast<int>(c2.size()) ? c2[k] : 0.0);
+    }
+    kp.rc2 = static_cast<real>(g.rc * g.rc);
+    kp.two_over_rc2 = static_cast<real>(2.0 / (g.rc * g.rc));
+    kp.rc2f = static_cast<float>(g.rc * g.rc * (1.0 + 1e-4));
+    const int ncells = g.ncell * g.ncell * g.ncell;
+    pswf::k_short<real, D><<<(ncells + pswf::kShortWarps - 1) / pswf::kShortWarps, 32 * pswf::kShortWarps, 0, s>>>(
+        sr_rec, p->sr_idx, sr_lo, p->sr_f32, p->cell_off, p->sr_cols, p->n_cols, g, kp, phi, f);
+    return cudaGetLastError();
+}
+
+// Radial polynomial degrees are rounded up to a bucket; the padding coefficients are zero.
+template <typename real>
+cudaError_t launch_short(ewald_plan p, const pswf::Vec4<real>* sr_rec, const pswf::Vec4<real>* sr_lo, double* phi,
+                         double* f, cudaStream_t s) {
+    const int d = p->g.degr;
+    if (d <= 8) return launch_short_d<real, 8>(p, sr_rec, sr_lo, phi, f, s);
+    if (d <= 12) return launch_short_d<real, 12>(p, sr_rec, sr_lo, phi, f, s);
+    if (d <= 16) return launch_short_d<real, 16>(p, sr_rec, sr_lo, phi, f, s);
+    if (d <= 20) return launch_short_d<real, 20>(p, sr_rec, sr_lo, phi, f, s);
+    if (d <= 24) return launch_short_d<real, 24>(p, sr_rec, sr_lo, phi, f, s);
+    if (d <= 32) return launch_short_d<real, 32>(p, sr_rec, sr_lo, phi, f, s);
+    if (d <= 44) return launch_short_d<real, 44>(p, sr_rec, sr_lo, phi, f, s);
+    return launch_short_d<real, 60>(p, sr_rec, sr_lo, phi, f, s);
+}
 
 template <typename real, typename cplx>
 int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, double* f, cudaStream_t s) {
@@ -136,7 +174,7 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     auto* sr_rec = static_cast<Vec4<real>*>(p->sr_rec);
     auto* sr_lo = static_cast<Vec4<real>*>(p->sr_lo);
     pswf::k_scatter<real><<<nb, tb, 0, s>>>(x, rho, g, p->key_rank, p->tile_off, p->cell_off, sp_rec, p->sp_idx,
-                                            sr_rec, p->sr_idx, sr_lo);
+                                            sr_rec, p->sr_idx, sr_lo, p->sr_f32);
     PSWF_CUDA(cudaGetLastError());
     p->mark(1, s);
     // Alg. 2 step 1
@@ -176,9 +214,7 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
                                          static_cast<const real*>(p->dwcoef), g, inv_alpha, phi, f, s));
     p->mark(7, s);
     // real-space sum
-    pswf::k_short<real><<<(n + 127) / 128, 128, 0, s>>>(sr_rec, p->sr_idx, sr_lo, p->cell_off, g,
-                                                       static_cast<const real*>(p->p1c),
-                                                       static_cast<const real*>(p->qc), phi, f);
+    PSWF_CUDA(launch_short<real>(p, sr_rec, sr_lo, phi, f, s));
     PSWF_CUDA(cudaGetLastError());
     p->mark(8, s);
     pswf::k_energy_partial<<<p->epart_blocks, 256, 0, s>>>(phi, rho, n, p->epart);
@@ -327,10 +363,40 @@ int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, e
             return fail(EWALD_ENOMEM, "device allocation failed (" + std::to_string(a.bytes) + " bytes)");
         }
     }
-    if (!p->fp64 && cudaMalloc(&p->sr_lo, 4 * sizeof(float) * n) != cudaSuccess) {
+    if ((!p->fp64 && cudaMalloc(&p->sr_lo, 4 * sizeof(float) * n) != cudaSuccess) ||
+        (p->fp64 && cudaMalloc(reinterpret_cast<void**>(&p->sr_f32), sizeof(float4) * n) != cudaSuccess)) {
         cudaGetLastError();
         delete p;
         return fail(EWALD_ENOMEM, "device allocation failed (real-space residues)");
+    }
+    {
+        // real-space columns: (dx, dy) within reach and, for each, the largest |dz| keeping the box
+        // distance between target and source cell below rc
+        std::vector<int4> cols;
+        const int R = g.reach;
+        auto gap = [](int d) { return d == 0 ? 0 : std::abs(d) - 1; };
+        const double lim = (g.rc / g.cellw) * (g.rc / g.cellw);
+        for (int dx = -R; dx <= R; ++dx)
+            for (int dy = -R; dy <= R; ++dy) {
+                const double gxy = double(gap(dx)) * gap(dx) + double(gap(dy)) * gap(dy);
+                if (gxy >= lim) continue;
+                int dzmax = 0;
+                while (dzmax < R && gxy + double(gap(dzmax + 1)) * gap(dzmax + 1) < lim) ++dzmax;
+                cols.push_back(make_int4(dx, dy, dzmax, 0));
+            }
+        p->n_cols = static_cast<int>(cols.size());
+        // every column's z-run splits into at most ceil((2R+1)/nc) + 1 contiguous pieces
+        const int pieces = (2 * R + 1 + g.ncell - 1) / g.ncell + 1;
+        if (p->n_cols * pieces > pswf::kShortMaxRanges) {
+            delete p;
+            return fail(EWALD_EINVAL, "real-space neighbourhood has too many cell ranges for the kernel");
+        }
+        if (cudaMalloc(reinterpret_cast<void**>(&p->sr_cols), sizeof(int4) * cols.size()) != cudaSuccess ||
+            cudaMemcpy(p->sr_cols, cols.data(), sizeof(int4) * cols.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            delete p;
+            return fail(EWALD_ENOMEM, "device allocation of the real-space columns failed");
+        }
     }
     if (cudaMallocHost(reinterpret_cast<void**>(&p->status_h), sizeof(double) * 4) != cudaSuccess) {
         delete p;

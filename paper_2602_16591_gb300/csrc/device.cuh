@@ -173,7 +173,7 @@ __global__ void k_scatter(const double* __restrict__ x, const double* __restrict
                           const int* __restrict__ key_rank, const int* __restrict__ tile_off,
                           const int* __restrict__ cell_off, Vec4<real>* __restrict__ sp_rec,
                           int2* __restrict__ sp_idx, Vec4<real>* __restrict__ sr_rec, int2* __restrict__ sr_idx,
-                          Vec4<real>* __restrict__ sr_lo) {
+                          Vec4<real>* __restrict__ sr_lo, float4* __restrict__ sr_f32) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     const Located r = locate(x + 3 * static_cast<size_t>(i), g);
@@ -202,9 +202,12 @@ __global__ void k_scatter(const double* __restrict__ x, const double* __restrict
         c.x = static_cast<real>(r.loc[0] - static_cast<double>(b.x));
         c.y = static_cast<real>(r.loc[1] - static_cast<double>(b.y));
         c.z = static_cast<real>(r.loc[2] - static_cast<double>(b.z));
-        c.w = real(0);
+        c.w = static_cast<real>(r.cell[2]);   // z cell index, exact in float
         sr_lo[pc] = c;
     }
+    if (sr_f32)    // float64 records get a float32 copy for the cutoff pre-test of the real-space sum
+        sr_f32[pc] = make_float4(static_cast<float>(r.loc[0]), static_cast<float>(r.loc[1]),
+                                 static_cast<float>(r.loc[2]), static_cast<float>(r.cell[2]));
 }
 
 // P window weights at one coordinate z by Horner (coefficients c[a*(deg+1) + k], monomials in z).
@@ -297,7 +300,9 @@ __global__ void __launch_bounds__(spread_threads<P>()) k_spread(const Vec4<real>
     }
 }
 
-// Sum of every tile slab covering grid point l (periodic): tile t, slab offset e with t T + e = l mod m.
+// Sum of every tile slab covering grid point l (periodic).  Point l lies in tile t = l / T at
+// offset o = l % T; the tiles t - j (mod nt) cover it at slab offset e = o + j T for every j with
+// e < E = T + P - 1 (per axis).  Empty tiles write no slab and are skipped.
 template <typename real>
 __global__ void k_halo(const real* __restrict__ scratch, const int* __restrict__ tile_off, Geom g,
                        real* __restrict__ grid) {
@@ -305,27 +310,24 @@ __global__ void k_halo(const real* __restrict__ scratch, const int* __restrict__
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= m * m * m) return;
     const int lz = id % m, ly = (id / m) % m, lx = id / (m * m);
+    const int tlx = lx / T, tly = ly / T, tlz = lz / T;
+    const int olx = lx - tlx * T, oly = ly - tly * T, olz = lz - tlz * T;
+    const size_t slab = static_cast<size_t>(E) * E * E;
     real s = real(0);
-    for (int ex = 0; ex < E; ++ex) {
-        int rx = (lx - ex) % m;
-        if (rx < 0) rx += m;
-        if (rx % T) continue;
-        const int tx = rx / T;
-        for (int ey = 0; ey < E; ++ey) {
-            int ry = (ly - ey) % m;
-            if (ry < 0) ry += m;
-            if (ry % T) continue;
-            const int ty = ry / T;
-            for (int ez = 0; ez < E; ++ez) {
-                int rz = (lz - ez) % m;
-                if (rz < 0) rz += m;
-                if (rz % T) continue;
-                const int tz = rz / T;
+    int tx = tlx;
+    for (int ex = olx; ex < E; ex += T) {
+        int ty = tly;
+        for (int ey = oly; ey < E; ey += T) {
+            int tz = tlz;
+            for (int ez = olz; ez < E; ez += T) {
                 const int tile = (tx * nt + ty) * nt + tz;
-                if (tile_off[tile] == tile_off[tile + 1]) continue;
-                s += scratch[static_cast<size_t>(tile) * E * E * E + (ex * E + ey) * E + ez];
+                if (tile_off[tile] != tile_off[tile + 1])
+                    s += scratch[static_cast<size_t>(tile) * slab + (ex * E + ey) * E + ez];
+                tz = tz == 0 ? nt - 1 : tz - 1;
             }
+            ty = ty == 0 ? nt - 1 : ty - 1;
         }
+        tx = tx == 0 ? nt - 1 : tx - 1;
     }
     grid[id] = s;
 }
@@ -350,11 +352,12 @@ __global__ void k_scale(cplx* __restrict__ spec, int m, const real* __restrict__
 
 // ---- Alg. 2 step 5 with eq. force: interpolation of phi and grad phi ------------------------------
 // One CTA per tile: the tile's extended block of the grid b (E^3 values) is staged in shared memory.
-// Each warp first evaluates the 6 P window weights (value, derivative per axis) of NB particles,
-// one particle per lane, then contracts each particle's P^3 stencil cooperatively: lanes take
-// (b, c) pairs, reduce over a in registers, and the warp sums the four results by shuffles.
+// Each warp takes batches of NB particles: all 32 lanes first evaluate the 6 P window weights
+// (value and x-derivative per axis) of the batch, one (particle, axis, kind) Horner vector per lane,
+// then contract each particle's P^3 stencil cooperatively: lanes take (b, c) pairs, reduce over a in
+// registers (two independent chains), and the warp sums the four results with shuffles.
 template <typename real> struct InterpCfg;
-template <> struct InterpCfg<float> { static constexpr int NB = 32, NWARP = 4; };
+template <> struct InterpCfg<float> { static constexpr int NB = 8, NWARP = 4; };
 template <> struct InterpCfg<double> { static constexpr int NB = 8, NWARP = 4; };
 
 template <typename real, int P>
@@ -365,6 +368,7 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
                                                 double* __restrict__ f_out) {
     constexpr int T = kTile, E = T + P - 1;
     constexpr int NB = InterpCfg<real>::NB, NWARP = InterpCfg<real>::NWARP;
+    constexpr int NQ = (P * P + 31) / 32;
     const int tile = blockIdx.x;
     const int beg = tile_off[tile], end = tile_off[tile + 1];
     if (beg == end) return;
@@ -381,7 +385,15 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
     }
     for (int e = threadIdx.x; e < E * E * E; e += blockDim.x) {
         const int ez = e % E, ey = (e / E) % E, ex = e / (E * E);
-        const int gx = (tx * T + ex) % m, gy = (ty * T + ey) % m, gz = (tz * T + ez) % m;
+        int gx = tx * T + ex, gy = ty * T + ey, gz = tz * T + ez;
+        gx -= gx >= m ? m : 0;
+        gy -= gy >= m ? m : 0;
+        gz -= gz >= m ? m : 0;
+        if (gx >= m || gy >= m || gz >= m) {   // extended block wider than the grid (small m)
+            gx %= m;
+            gy %= m;
+            gz %= m;
+        }
         G[e] = grid[(static_cast<size_t>(gx) * m + gy) * m + gz];
     }
     __syncthreads();
@@ -390,18 +402,19 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
     for (int b0 = beg + warp * NB; b0 < end; b0 += NWARP * NB) {
         const int cnt = min(NB, end - b0);
         __syncwarp();
-        if (lane < cnt) {
-            const Vec4<real> r = rec[b0 + lane];
+        for (int task = lane; task < cnt * 6; task += 32) {
+            const int j = task / 6, kind = task % 6, d = kind % 3;
+            const Vec4<real> r = rec[b0 + j];
+            const real z = d == 0 ? r.x : (d == 1 ? r.y : r.z);
             real w[P];
-            const real zz[3] = {r.x, r.y, r.z};
+            if (kind < 3) {
+                window_weights<real, P>(sc, degw, z, w);
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                window_weights<real, P>(sc, degw, zz[d], w);
+                for (int a = 0; a < P; ++a) ww[(j * 6 + kind) * P + a] = w[a];
+            } else {
+                window_weights<real, P>(sd, degw, z, w);
 #pragma unroll
-                for (int a = 0; a < P; ++a) ww[(lane * 6 + d) * P + a] = w[a];
-                window_weights<real, P>(sd, degw, zz[d], w);
-#pragma unroll
-                for (int a = 0; a < P; ++a) ww[(lane * 6 + 3 + d) * P + a] = w[a] * inv_alpha;
+                for (int a = 0; a < P; ++a) ww[(j * 6 + kind) * P + a] = w[a] * inv_alpha;
             }
         }
         __syncwarp();
@@ -416,23 +429,33 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
                 dwx[a] = wp[3 * P + a];
             }
             real ph = 0, gx = 0, gy = 0, gz = 0;
-            for (int q = lane; q < P * P; q += 32) {
-                const int bb = q / P, cc = q % P;
-                const real* col = G + (ox * E + oy + bb) * E + oz + cc;
-                real s1 = 0, s2 = 0;
 #pragma unroll
-                for (int a = 0; a < P; ++a) {
-                    const real v = col[a * E * E];
-                    s1 = fma(v, wx[a], s1);
-                    s2 = fma(v, dwx[a], s2);
+            for (int qi = 0; qi < NQ; ++qi) {
+                const int q = lane + 32 * qi;
+                if (q < P * P) {
+                    const int bb = q / P, cc = q - (q / P) * P;
+                    const real* col = G + (ox * E + oy + bb) * E + oz + cc;
+                    real s1a = 0, s1b = 0, s2a = 0, s2b = 0;
+#pragma unroll
+                    for (int a = 0; a < P; a += 2) {
+                        const real v = col[a * E * E];
+                        s1a = fma(v, wx[a], s1a);
+                        s2a = fma(v, dwx[a], s2a);
+                        if (a + 1 < P) {
+                            const real v2 = col[(a + 1) * E * E];
+                            s1b = fma(v2, wx[a + 1], s1b);
+                            s2b = fma(v2, dwx[a + 1], s2b);
+                        }
+                    }
+                    const real s1 = s1a + s1b, s2 = s2a + s2b;
+                    const real wy = wp[P + bb], wz = wp[2 * P + cc];
+                    const real dwy = wp[4 * P + bb], dwz = wp[5 * P + cc];
+                    const real yz = wy * wz;
+                    ph = fma(s1, yz, ph);
+                    gx = fma(s2, yz, gx);
+                    gy = fma(s1, dwy * wz, gy);
+                    gz = fma(s1, wy * dwz, gz);
                 }
-                const real wy = wp[P + bb], wz = wp[2 * P + cc];
-                const real dwy = wp[4 * P + bb], dwz = wp[5 * P + cc];
-                const real yz = wy * wz;
-                ph = fma(s1, yz, ph);
-                gx = fma(s2, yz, gx);
-                gy = fma(s1, dwy * wz, gy);
-                gz = fma(s1, wy * dwz, gz);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -454,94 +477,279 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
 }
 
 // ---- real-space sum of R over the cell list (Sec. 3.1.1) -----------------------------------------
-// One thread per target in cell order; neighbour cells within `reach` whose box distance is below
-// rc.  R(r) = 1/r - P1(u), -R'(r)/r = 1/r^3 + Q(u), u = 2 r^2/rc^2 - 1 (host-fitted polynomials).
-// In float32 the pair displacement is formed in float-float: positions are (hi, lo) pairs relative
-// to their cell, the neighbour-cell shift o is split the same way, and d = x_i - (x_j + o) is
-// evaluated as (hi_i - (hi_j + o_hi)) + ((lo_i - o_lo) - lo_j): for close pairs across a cell face
-// hi_j + o_hi cancels exactly, so d keeps full relative precision.
+// Real-space sum over a cell list of cubic cells of edge w >= rc/R ("reach" R).  For a target cell
+// c, the source cells within reach form columns (dx, dy) with a z-run dz in [-dzmax, dzmax] that
+// keeps the box distance below rc (host table).  Cells are stored z-fastest, so each z-run is one
+// or two contiguous particle ranges (more when the box has fewer than 2R+1 cells per axis and the
+// run wraps onto itself: every wrapped piece is a different periodic image).
+//
+// One warp per target cell.  The warp flattens the cell's ranges into one stream of candidate
+// sources; lanes take 32 consecutive candidates at a time (coalesced loads) and test each against
+// every target of the cell (held in shared memory, up to kShortMaxT per pass, accumulated in
+// registers per lane).  Candidates pass a float32 test against a slightly enlarged cutoff and are
+// then evaluated in the plan's precision:
+//   R(r) = 1/r - P1(u),  -R'(r)/r = 1/r^3 + Q(u),  u = 2 r^2/rc^2 - 1   (host-fitted polynomials).
+// In float32 the displacement is float-float: positions are (hi, lo) pairs relative to their cell and
+// the cell shift d w is split the same way, d = (hi_i - (hi_j + s_hi)) + ((lo_i - s_lo) - lo_j), so a
+// close pair across a cell face keeps full relative precision.  In float64, 1/r is the float32
+// reciprocal square root refined by two Newton steps y <- y (3 - r^2 y^2) / 2.
 template <typename real>
 __device__ __forceinline__ real rsqrt_r(real v);
 template <> __device__ __forceinline__ float rsqrt_r<float>(float v) { return rsqrtf(v); }
-template <> __device__ __forceinline__ double rsqrt_r<double>(double v) { return rsqrt(v); }
+template <> __device__ __forceinline__ double rsqrt_r<double>(double v) {
+    double y = static_cast<double>(rsqrtf(static_cast<float>(v)));
+    const double hv = 0.5 * v;
+    y = y * fma(-hv * y, y, 1.5);
+    y = y * fma(-hv * y, y, 1.5);
+    return y;
+}
 
-template <typename real>
-__global__ void __launch_bounds__(128) k_short(const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
-                                               const Vec4<real>* __restrict__ lo, const int* __restrict__ cell_off,
-                                               Geom g, const real* __restrict__ p1c, const real* __restrict__ qc,
-                                               double* __restrict__ phi_out, double* __restrict__ f_out) {
-    __shared__ real sp[64], sq[64];
-    const int degr = g.degr;
-    for (int k = threadIdx.x; k <= degr; k += blockDim.x) {
-        sp[k] = p1c[k];
-        sq[k] = qc[k];
+constexpr int kShortWarps = 4;      // target cells per block
+constexpr int kShortMaxT = 8;       // targets per pass
+constexpr int kShortMaxR = 4;       // largest reach
+constexpr int kShortMaxRanges = 512;
+
+// Per-plan constants of the real-space kernel, passed by value (kernel parameter space): the radial
+// polynomials padded with leading zeros to the compile-time degree D, so the fully unrolled Horner
+// loops read every coefficient as a constant operand.
+template <typename real, int D>
+struct ShortParams {
+    real p1[D + 1], q[D + 1];
+    real rc2, two_over_rc2;
+    float rc2f;
+};
+
+template <typename real, int D>
+__global__ void __launch_bounds__(32 * kShortWarps) k_short(const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
+                                                            const Vec4<real>* __restrict__ lo, const float4* __restrict__ pf,
+                                                            const int* __restrict__ cell_off, const int4* __restrict__ cols,
+                                                            int ncols, Geom g, const __grid_constant__ ShortParams<real, D> kp,
+                                                            double* __restrict__ phi_out, double* __restrict__ f_out) {
+    constexpr bool kF32 = sizeof(real) == 4;
+    constexpr int NSH = 2 * kShortMaxR + 1;
+    __shared__ float sh_hi[NSH], sh_lo[NSH];
+    __shared__ double sh_d[NSH];
+    __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
+    __shared__ int4 srng[kShortWarps][kShortMaxRanges];        // {first particle, z cell, dz, column}
+    __shared__ int spos[kShortWarps][kShortMaxRanges + 1];     // stream offset of each range
+    __shared__ real stx[kShortWarps][kShortMaxT][4];           // exact target position and charge
+    __shared__ float stl[kShortWarps][kShortMaxT][4];          // float path: lo parts
+    const int R = g.reach, nc = g.ncell;
+    for (int k = threadIdx.x; k < 2 * R + 1; k += blockDim.x) {
+        const double o = (k - R) * g.cellw;
+        sh_d[k] = o;
+        sh_hi[k] = static_cast<float>(o);
+        sh_lo[k] = static_cast<float>(o - static_cast<double>(sh_hi[k]));
     }
+    for (int k = threadIdx.x; k < ncols; k += blockDim.x) scol[k] = cols[k];
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
-    const int nc = g.ncell, R = g.reach;
-    const Vec4<real> me = rec[i];
-    const Vec4<real> mlo = lo ? lo[i] : Vec4<real>{real(0), real(0), real(0), real(0)};
-    const int2 id = idx[i];
-    const int cz = id.x % nc, cy = (id.x / nc) % nc, cx = id.x / (nc * nc);
-    const real rc2 = static_cast<real>(g.rc * g.rc);
-    const real two_over_rc2 = static_cast<real>(2.0 / (g.rc * g.rc));
-    const double cw2 = g.cellw * g.cellw, rcsq = g.rc * g.rc;
-    real ph = 0, fx = 0, fy = 0, fz = 0;
-    for (int dx = -R; dx <= R; ++dx) {
-        const int bx = abs(dx) > 0 ? abs(dx) - 1 : 0;
-        const double odx = dx * g.cellw;
-        const real ohx = static_cast<real>(odx), olx = static_cast<real>(odx - static_cast<double>(ohx));
-        for (int dy = -R; dy <= R; ++dy) {
-            const int by = abs(dy) > 0 ? abs(dy) - 1 : 0;
-            const double ody = dy * g.cellw;
-            const real ohy = static_cast<real>(ody), oly = static_cast<real>(ody - static_cast<double>(ohy));
-            for (int dz = -R; dz <= R; ++dz) {
-                const int bz = abs(dz) > 0 ? abs(dz) - 1 : 0;
-                if ((bx * bx + by * by + bz * bz) * cw2 >= rcsq) continue;
-                const double odz = dz * g.cellw;
-                const real ohz = static_cast<real>(odz), olz = static_cast<real>(odz - static_cast<double>(ohz));
-                int nx = (cx + dx) % nc, ny = (cy + dy) % nc, nz = (cz + dz) % nc;
-                nx += nx < 0 ? nc : 0;
-                ny += ny < 0 ? nc : 0;
-                nz += nz < 0 ? nc : 0;
-                const int cell = (nx * nc + ny) * nc + nz;
-                const int b = cell_off[cell], e = cell_off[cell + 1];
-                const real lx = mlo.x - olx, ly = mlo.y - oly, lz = mlo.z - olz;
-                for (int j = b; j < e; ++j) {
-                    const Vec4<real> s = rec[j];
-                    real ddx = me.x - (s.x + ohx), ddy = me.y - (s.y + ohy), ddz = me.z - (s.z + ohz);
-                    if (lo) {
-                        const Vec4<real> t = lo[j];
-                        ddx += lx - t.x;
-                        ddy += ly - t.y;
-                        ddz += lz - t.z;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * kShortWarps + warp;
+    if (c >= nc * nc * nc) return;
+    const int tb = cell_off[c], te = cell_off[c + 1];
+    if (tb == te) return;
+    const int cz = c % nc, cy = (c / nc) % nc, cx = c / (nc * nc);
+    int4* rng = srng[warp];
+    int* pos = spos[warp];
+
+    // ---- flatten the neighbour ranges of this cell (pieces of each column's z-run)
+    auto wrap = [nc](int v) {   // v in (-2 nc, 2 nc) -> [0, nc)
+        v += v < 0 ? nc : 0;
+        v += v < 0 ? nc : 0;
+        v -= v >= nc ? nc : 0;
+        v -= v >= nc ? nc : 0;
+        return v;
+    };
+    int nr = 0;
+    for (int k0 = 0; k0 < ncols; k0 += 32) {
+        const int k = k0 + lane;
+        int npc = 0;
+        int4 col = make_int4(0, 0, -1, 0);
+        int base = 0;
+        if (k < ncols) {
+            col = scol[k];
+            base = (wrap(cx + col.x) * nc + wrap(cy + col.y)) * nc;
+            for (int d = -col.z; d <= col.z;) {
+                const int zw = wrap(cz + d);
+                d += min(col.z - d + 1, nc - zw);
+                ++npc;
+            }
+        }
+        int incl = npc;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int slot = nr + incl - npc;
+        if (k < ncols) {
+            for (int d = -col.z; d <= col.z;) {
+                const int zw = wrap(cz + d);
+                const int len = min(col.z - d + 1, nc - zw);
+                if (slot < kShortMaxRanges) {
+                    const int a = cell_off[base + zw], b = cell_off[base + zw + len];
+                    rng[slot] = make_int4(a, zw, d, k);
+                    pos[slot] = b - a;            // length, turned into offsets below
+                }
+                ++slot;
+                d += len;
+            }
+        }
+        nr += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    nr = min(nr, kShortMaxRanges);
+    __syncwarp();
+    int total = 0;
+    for (int r0 = 0; r0 < nr; r0 += 32) {
+        const int r = r0 + lane;
+        const int len = r < nr ? pos[r] : 0;
+        int incl = len;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        __syncwarp();
+        if (r < nr) pos[r] = total + incl - len;
+        total += __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+    }
+    if (lane == 0) pos[nr] = total;
+    __syncwarp();
+
+    for (int t0 = tb; t0 < te; t0 += kShortMaxT) {
+        const int nt = min(kShortMaxT, te - t0);
+        // targets: float32 test copies in registers of every lane, exact parts in shared memory
+        float tf[kShortMaxT][3];
+        __syncwarp();
+        if (lane < nt) {
+            const Vec4<real> a = rec[t0 + lane];
+            stx[warp][lane][0] = a.x;
+            stx[warp][lane][1] = a.y;
+            stx[warp][lane][2] = a.z;
+            stx[warp][lane][3] = a.w;
+            if constexpr (kF32) {
+                const Vec4<real> l = lo[t0 + lane];
+                stl[warp][lane][0] = l.x;
+                stl[warp][lane][1] = l.y;
+                stl[warp][lane][2] = l.z;
+            } else {
+                const float4 f = pf[t0 + lane];
+                stl[warp][lane][0] = f.x;
+                stl[warp][lane][1] = f.y;
+                stl[warp][lane][2] = f.z;
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < kShortMaxT; ++t) {
+            const int tt = t < nt ? t : 0;
+            if constexpr (kF32) {
+                tf[t][0] = static_cast<float>(stx[warp][tt][0]);
+                tf[t][1] = static_cast<float>(stx[warp][tt][1]);
+                tf[t][2] = static_cast<float>(stx[warp][tt][2]);
+            } else {
+                tf[t][0] = stl[warp][tt][0];
+                tf[t][1] = stl[warp][tt][1];
+                tf[t][2] = stl[warp][tt][2];
+            }
+        }
+        real acc[kShortMaxT][4];
+#pragma unroll
+        for (int t = 0; t < kShortMaxT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = real(0);
+        int r = 0;
+        for (int s0 = 0; s0 < total; s0 += 32) {
+            const int p = s0 + lane;
+            if (p >= total) continue;
+            while (pos[r + 1] <= p) ++r;
+            const int4 rg = rng[r];
+            const int j = rg.x + (p - pos[r]);
+            float sfx, sfy, sfz, szc;
+            if constexpr (kF32) {
+                const Vec4<real> a = rec[j];
+                sfx = a.x; sfy = a.y; sfz = a.z;
+                szc = lo[j].w;
+            } else {
+                const float4 f = pf[j];
+                sfx = f.x; sfy = f.y; sfz = f.z;
+                szc = f.w;
+            }
+            const int4 col = scol[rg.w];
+            const int ix = col.x + R, iy = col.y + R, iz = rg.z + (static_cast<int>(szc) - rg.y) + R;
+            const float px = sfx + sh_hi[ix], py = sfy + sh_hi[iy], pz = sfz + sh_hi[iz];
+            bool loaded = false;
+            real qj = real(0), ex = real(0), ey = real(0), ez = real(0);
+#pragma unroll
+            for (int t = 0; t < kShortMaxT; ++t) {
+                if (t >= nt) break;   // nt is warp-uniform
+                const float dxf = tf[t][0] - px, dyf = tf[t][1] - py, dzf = tf[t][2] - pz;
+                const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
+                if (r2f < kp.rc2f && r2f > 0.f) {
+                    if (!loaded) {
+                        loaded = true;
+                        if constexpr (kF32) {
+                            const Vec4<real> l = lo[j];
+                            qj = rec[j].w;
+                            ex = l.x + sh_lo[ix];
+                            ey = l.y + sh_lo[iy];
+                            ez = l.z + sh_lo[iz];
+                        } else {
+                            const Vec4<real> a = rec[j];
+                            qj = a.w;
+                            ex = a.x + sh_d[ix];
+                            ey = a.y + sh_d[iy];
+                            ez = a.z + sh_d[iz];
+                        }
+                    }
+                    real ddx, ddy, ddz;
+                    if constexpr (kF32) {
+                        ddx = dxf + (stl[warp][t][0] - ex);
+                        ddy = dyf + (stl[warp][t][1] - ey);
+                        ddz = dzf + (stl[warp][t][2] - ez);
+                    } else {
+                        ddx = stx[warp][t][0] - ex;
+                        ddy = stx[warp][t][1] - ey;
+                        ddz = stx[warp][t][2] - ez;
                     }
                     const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    if (r2 < rc2 && r2 > real(0)) {
-                        const real u = fma(r2, two_over_rc2, real(-1));
-                        real p1 = sp[degr], q = sq[degr];
-                        for (int k = degr - 1; k >= 0; --k) {
-                            p1 = fma(p1, u, sp[k]);
-                            q = fma(q, u, sq[k]);
+                    if (r2 < kp.rc2 && r2 > real(0)) {
+                        const real u = fma(r2, kp.two_over_rc2, real(-1));
+                        real p1 = kp.p1[D], qq = kp.q[D];
+#pragma unroll
+                        for (int kk = D - 1; kk >= 0; --kk) {
+                            p1 = fma(p1, u, kp.p1[kk]);
+                            qq = fma(qq, u, kp.q[kk]);
                         }
                         const real ri = rsqrt_r<real>(r2);
-                        ph = fma(s.w, ri - p1, ph);
-                        const real cf = s.w * fma(ri * ri, ri, q);
-                        fx = fma(cf, ddx, fx);
-                        fy = fma(cf, ddy, fy);
-                        fz = fma(cf, ddz, fz);
+                        acc[t][0] = fma(qj, ri - p1, acc[t][0]);
+                        const real cf = qj * fma(ri * ri, ri, qq);
+                        acc[t][1] = fma(cf, ddx, acc[t][1]);
+                        acc[t][2] = fma(cf, ddy, acc[t][2]);
+                        acc[t][3] = fma(cf, ddz, acc[t][3]);
                     }
                 }
             }
         }
+        // reduce each target's partial sums over the lanes; lane t writes target t
+#pragma unroll
+        for (int t = 0; t < kShortMaxT; ++t) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                real x = acc[t][v];
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                acc[t][v] = x;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < kShortMaxT; ++t) {
+            if (lane == t && t < nt) {
+                const int oi = idx[t0 + t].y;
+                const double qi = static_cast<double>(stx[warp][t][3]);
+                phi_out[oi] += static_cast<double>(acc[t][0]);
+                f_out[3 * static_cast<size_t>(oi) + 0] += qi * static_cast<double>(acc[t][1]);
+                f_out[3 * static_cast<size_t>(oi) + 1] += qi * static_cast<double>(acc[t][2]);
+                f_out[3 * static_cast<size_t>(oi) + 2] += qi * static_cast<double>(acc[t][3]);
+            }
+        }
     }
-    const int o = id.y;
-    const double qi = static_cast<double>(me.w);
-    phi_out[o] += static_cast<double>(ph);
-    f_out[3 * static_cast<size_t>(o) + 0] += qi * static_cast<double>(fx);
-    f_out[3 * static_cast<size_t>(o) + 1] += qi * static_cast<double>(fy);
-    f_out[3 * static_cast<size_t>(o) + 2] += qi * static_cast<double>(fz);
 }
 
 // ---- energy ------------------------------------------------------------------------------------

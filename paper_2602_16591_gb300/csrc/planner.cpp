@@ -285,9 +285,9 @@ ewald_opts default_opts() {
     ewald_opts o{};
     o.precision = EWALD_FP64;
     o.rc = 0.0;
-    o.grid_density = 1.0;
+    o.grid_density = 2.0;
     o.tol_safety = 0.25;
-    o.sr_reach = 2;
+    o.sr_reach = 0;
     return o;
 }
 
@@ -406,7 +406,7 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
     if (o.precision != EWALD_FP64 && o.precision != EWALD_MIXED) throw std::invalid_argument("unknown precision");
     if (!(o.tol_safety > 0 && o.tol_safety <= 1)) throw std::invalid_argument("tol_safety must lie in (0, 1]");
     if (!(o.grid_density > 0)) throw std::invalid_argument("grid_density must be positive");
-    if (o.sr_reach < 1 || o.sr_reach > 4) throw std::invalid_argument("sr_reach must lie in [1, 4]");
+    if (o.sr_reach < 0 || o.sr_reach > 4) throw std::invalid_argument("sr_reach must lie in [0, 4]");
 
     const double As = 5.0, Aw = 3.1;                      // Secs. 5.1.1 and 5.2.1
     static const double kappa = kappa_constant();
@@ -452,8 +452,14 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
     // float32 products cannot reach tol < 1e-7; below it MIXED runs the float64 kernels
     p.precision = (o.precision == EWALD_MIXED && tol < 1e-7) ? EWALD_FP64 : o.precision;
     p.tile = 4;
-    p.sr_reach = o.sr_reach;
-    int nc = static_cast<int>(std::floor(o.sr_reach / rcl));
+    // real-space cells of edge >= rc / reach; the automatic reach aims at ~3 particles per cell
+    int reach = o.sr_reach;
+    if (reach <= 0) {
+        reach = static_cast<int>(std::lround(rcl * std::cbrt(static_cast<double>(n) / 3.0)));
+        reach = std::max(1, std::min(reach, 4));
+    }
+    p.sr_reach = reach;
+    int nc = static_cast<int>(std::floor(reach / rcl));
     nc = std::max(1, std::min(nc, 1024));
     p.ncell = nc;
     p.fit_tol = std::max(0.02 * t, p.precision == EWALD_MIXED ? 1e-8 : 5e-16);

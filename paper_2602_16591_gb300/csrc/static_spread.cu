@@ -146,7 +146,7 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
     pswf::k_prep<<<nb, tb, 0, s>>>(x, rho, g, key_rank, tile_cnt, cell_cnt, status);
     pswf::k_scan<<<2, 1024, 0, s>>>(tile_cnt, tile_off, static_cast<int>(ntiles), cell_cnt, cell_off, 1);
     pswf::k_scatter<double><<<nb, tb, 0, s>>>(x, rho, g, key_rank, tile_off, cell_off, sp_rec, sp_idx, sr_rec,
-                                              sr_idx, nullptr);
+                                              sr_idx, nullptr, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail_static(EWALD_ECUDA, std::string("sort launch: ") + cudaGetErrorString(e));
     e = pswf::Launch<double>::spread(P, static_cast<int>(ntiles), sp_rec, sp_idx, tile_off, coef, p->deg_w, slab, s);
