@@ -92,12 +92,18 @@ struct ewald_plan_s {
     double* status_h = nullptr;   // pinned
     cufftHandle fwd = 0, inv = 0;
     bool have_fwd = false, have_inv = false;
+    // the real-space sum runs on its own stream, concurrently with spread -> FFT -> interpolation
+    // (Alg. 2 on a high-priority stream so its short kernels are not starved by the real-space blocks)
+    cudaStream_t s_short = nullptr, s_alg2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
+    double* phi_sr = nullptr;   // real-space potential and forces, merged by k_combine_energy
+    double* f_sr = nullptr;
     bool profiling = false;
-    std::vector<std::vector<cudaEvent_t>> prof;   // EWALD_NSTAGES + 1 events per recorded evaluation
+    std::vector<std::vector<cudaEvent_t>> prof;   // begin/end event of every stage per recorded evaluation
     std::vector<cudaEvent_t>* cur = nullptr;
 
-    void mark(int k, cudaStream_t s) {
-        if (cur) cudaEventRecord((*cur)[k], s);
+    void mark(int k, bool end, cudaStream_t s) {
+        if (cur) cudaEventRecord((*cur)[2 * k + (end ? 1 : 0)], s);
     }
     void clear_prof() {
         for (auto& v : prof)
@@ -114,6 +120,13 @@ struct ewald_plan_s {
             if (b) cudaFree(b);
         if (status_h) cudaFreeHost(status_h);
         clear_prof();
+        if (phi_sr) cudaFree(phi_sr);
+        if (f_sr) cudaFree(f_sr);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (ev_join2) cudaEventDestroy(ev_join2);
+        if (s_short) cudaStreamDestroy(s_short);
+        if (s_alg2) cudaStreamDestroy(s_alg2);
         if (have_fwd) cufftDestroy(fwd);
         if (have_inv) cufftDestroy(inv);
     }
@@ -161,7 +174,7 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     using pswf::Vec4;
     const pswf::Geom& g = p->g;
     const int n = g.n, m = g.m;
-    p->mark(0, s);
+    p->mark(0, false, s);
     PSWF_CUDA(cudaMemsetAsync(p->tile_cnt, 0, sizeof(int) * p->ntiles, s));
     PSWF_CUDA(cudaMemsetAsync(p->cell_cnt, 0, sizeof(int) * p->ncells, s));
     PSWF_CUDA(cudaMemsetAsync(p->status, 0, sizeof(double) * 3, s));
@@ -176,17 +189,31 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     pswf::k_scatter<real><<<nb, tb, 0, s>>>(x, rho, g, p->key_rank, p->tile_off, p->cell_off, sp_rec, p->sp_idx,
                                             sr_rec, p->sr_idx, sr_lo, p->sr_f32);
     PSWF_CUDA(cudaGetLastError());
-    p->mark(1, s);
+    p->mark(0, true, s);
+    // real-space sum on the second stream, concurrent with Alg. 2
+    PSWF_CUDA(cudaEventRecord(p->ev_fork, s));
+    PSWF_CUDA(cudaStreamWaitEvent(p->s_short, p->ev_fork, 0));
+    p->mark(7, false, p->s_short);
+    PSWF_CUDA(launch_short<real>(p, sr_rec, sr_lo, p->phi_sr, p->f_sr, p->s_short));
+    p->mark(7, true, p->s_short);
+    PSWF_CUDA(cudaEventRecord(p->ev_join, p->s_short));
+    // Alg. 2 on the high-priority stream
+    const cudaStream_t caller = s;
+    PSWF_CUDA(cudaStreamWaitEvent(p->s_alg2, p->ev_fork, 0));
+    s = p->s_alg2;
     // Alg. 2 step 1
+    p->mark(1, false, s);
     PSWF_CUDA(pswf::Launch<real>::spread(g.P, p->ntiles, sp_rec, p->sp_idx, p->tile_off,
                                          static_cast<const real*>(p->wcoef), g.degw, static_cast<real*>(p->scratch), s));
-    p->mark(2, s);
+    p->mark(1, true, s);
+    p->mark(2, false, s);
     const int mm = m * m * m;
     pswf::k_halo<real><<<(mm + 255) / 256, 256, 0, s>>>(static_cast<const real*>(p->scratch), p->tile_off, g,
                                                         static_cast<real*>(p->grid_a));
     PSWF_CUDA(cudaGetLastError());
     // Alg. 2 steps 2-4
-    p->mark(3, s);
+    p->mark(2, true, s);
+    p->mark(3, false, s);
     PSWF_CUFFT(cufftSetStream(p->fwd, s));
     PSWF_CUFFT(cufftSetStream(p->inv, s));
     if constexpr (sizeof(real) == 8) {
@@ -194,40 +221,45 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     } else {
         PSWF_CUFFT(cufftExecR2C(p->fwd, static_cast<cufftReal*>(p->grid_a), static_cast<cufftComplex*>(p->spec)));
     }
-    p->mark(4, s);
+    p->mark(3, true, s);
+    p->mark(4, false, s);
     const int ns = m * m * (m / 2 + 1);
     pswf::k_scale<real, cplx><<<(ns + 255) / 256, 256, 0, s>>>(static_cast<cplx*>(p->spec), m,
                                                                static_cast<const real*>(p->iw),
                                                                static_cast<const real*>(p->mtab));
     PSWF_CUDA(cudaGetLastError());
-    p->mark(5, s);
+    p->mark(4, true, s);
+    p->mark(5, false, s);
     if constexpr (sizeof(real) == 8) {
         PSWF_CUFFT(cufftExecZ2D(p->inv, static_cast<cufftDoubleComplex*>(p->spec), static_cast<cufftDoubleReal*>(p->grid_b)));
     } else {
         PSWF_CUFFT(cufftExecC2R(p->inv, static_cast<cufftComplex*>(p->spec), static_cast<cufftReal*>(p->grid_b)));
     }
-    p->mark(6, s);
+    p->mark(5, true, s);
+    p->mark(6, false, s);
     // Alg. 2 step 5 + self term + forces
     const real inv_alpha = static_cast<real>(1.0 / p->hp.p.alpha);
     PSWF_CUDA(pswf::Launch<real>::interp(g.P, p->ntiles, static_cast<const real*>(p->grid_b), sp_rec, p->sp_idx,
                                          p->tile_off, static_cast<const real*>(p->wcoef),
                                          static_cast<const real*>(p->dwcoef), g, inv_alpha, phi, f, s));
-    p->mark(7, s);
-    // real-space sum
-    PSWF_CUDA(launch_short<real>(p, sr_rec, sr_lo, phi, f, s));
-    PSWF_CUDA(cudaGetLastError());
-    p->mark(8, s);
-    pswf::k_energy_partial<<<p->epart_blocks, 256, 0, s>>>(phi, rho, n, p->epart);
+    p->mark(6, true, s);
+    // join both branches on the caller's stream, merge the real-space sum into phi and F, energy
+    PSWF_CUDA(cudaEventRecord(p->ev_join2, s));
+    s = caller;
+    PSWF_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
+    PSWF_CUDA(cudaStreamWaitEvent(s, p->ev_join2, 0));
+    p->mark(8, false, s);
+    pswf::k_combine_energy<<<p->epart_blocks, 256, 0, s>>>(phi, f, p->phi_sr, p->f_sr, rho, n, p->epart);
     pswf::k_energy_final<<<1, 256, 0, s>>>(p->epart, p->epart_blocks, p->energy_d);
     PSWF_CUDA(cudaGetLastError());
-    p->mark(9, s);
+    p->mark(8, true, s);
     return EWALD_OK;
 }
 
 int eval_device(ewald_plan p, const double* x, const double* rho, double* phi, double* force, cudaStream_t s) {
     p->cur = nullptr;
     if (p->profiling) {
-        std::vector<cudaEvent_t> ev(EWALD_NSTAGES + 1);
+        std::vector<cudaEvent_t> ev(2 * EWALD_NSTAGES);
         for (auto& e : ev)
             if (cudaEventCreate(&e) != cudaSuccess) return fail(EWALD_ECUDA, "cudaEventCreate failed");
         p->prof.push_back(ev);
@@ -354,6 +386,8 @@ int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, e
         {reinterpret_cast<void**>(&p->epart), sizeof(double) * p->epart_blocks},
         {reinterpret_cast<void**>(&p->energy_d), sizeof(double)},
         {reinterpret_cast<void**>(&p->x_stage), sizeof(double) * 3 * n},
+        {reinterpret_cast<void**>(&p->phi_sr), sizeof(double) * n},
+        {reinterpret_cast<void**>(&p->f_sr), sizeof(double) * 3 * n},
         {reinterpret_cast<void**>(&p->rho_stage), sizeof(double) * n},
     };
     for (auto& a : allocs) {
@@ -397,6 +431,17 @@ int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, e
             delete p;
             return fail(EWALD_ENOMEM, "device allocation of the real-space columns failed");
         }
+    }
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (cudaStreamCreateWithPriority(&p->s_short, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&p->s_alg2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        return fail(EWALD_ECUDA, "stream/event creation failed");
     }
     if (cudaMallocHost(reinterpret_cast<void**>(&p->status_h), sizeof(double) * 4) != cudaSuccess) {
         delete p;
@@ -511,10 +556,10 @@ int ewald_profile_read(ewald_plan plan, double* ms, int* count) {
     if (!plan || !ms) return fail(EWALD_EINVAL, "bad argument");
     for (int k = 0; k < EWALD_NSTAGES; ++k) ms[k] = 0.0;
     for (auto& v : plan->prof) {
-        PSWF_CUDA(cudaEventSynchronize(v[EWALD_NSTAGES]));
         for (int k = 0; k < EWALD_NSTAGES; ++k) {
+            PSWF_CUDA(cudaEventSynchronize(v[2 * k + 1]));
             float t = 0.f;
-            PSWF_CUDA(cudaEventElapsedTime(&t, v[k], v[k + 1]));
+            PSWF_CUDA(cudaEventElapsedTime(&t, v[2 * k], v[2 * k + 1]));
             ms[k] += t;
         }
     }

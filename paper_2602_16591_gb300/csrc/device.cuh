@@ -10,8 +10,9 @@
 //   k_scale    Alg. 2 step 3: b_k = S(k) a_k with S from host tables
 //   cuFFT C2R  Alg. 2 step 4
 //   k_interp   Alg. 2 step 5 and eq. force: phi^far, grad phi^far; writes phi - self, F
-//   k_short    real-space sum of the residual R (eq. R) over the cell list, adds to phi, F
-//   k_energy   E = 1/2 sum rho phi (Remark on energy), deterministic two-pass reduction
+//   k_short    real-space sum of the residual R (eq. R) over the cell list (second stream, concurrent
+//              with spread..interp), into separate phi/F buffers
+//   k_combine_energy  phi += phi_sr, F += F_sr, E = 1/2 sum rho phi (Remark on energy), two-pass reduction
 #pragma once
 
 #include <cstdint>
@@ -743,22 +744,30 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short(const Vec4<real>* __
             if (lane == t && t < nt) {
                 const int oi = idx[t0 + t].y;
                 const double qi = static_cast<double>(stx[warp][t][3]);
-                phi_out[oi] += static_cast<double>(acc[t][0]);
-                f_out[3 * static_cast<size_t>(oi) + 0] += qi * static_cast<double>(acc[t][1]);
-                f_out[3 * static_cast<size_t>(oi) + 1] += qi * static_cast<double>(acc[t][2]);
-                f_out[3 * static_cast<size_t>(oi) + 2] += qi * static_cast<double>(acc[t][3]);
+                phi_out[oi] = static_cast<double>(acc[t][0]);
+                f_out[3 * static_cast<size_t>(oi) + 0] = qi * static_cast<double>(acc[t][1]);
+                f_out[3 * static_cast<size_t>(oi) + 1] = qi * static_cast<double>(acc[t][2]);
+                f_out[3 * static_cast<size_t>(oi) + 2] = qi * static_cast<double>(acc[t][3]);
             }
         }
     }
 }
 
 // ---- energy ------------------------------------------------------------------------------------
-static __global__ void k_energy_partial(const double* __restrict__ phi, const double* __restrict__ rho, int n,
-                                 double* __restrict__ part) {
+// phi += phi_sr, F += F_sr (the real-space sum computed on the second stream), and per-block partial
+// sums of rho phi for the energy.
+static __global__ void k_combine_energy(double* __restrict__ phi, double* __restrict__ f,
+                                        const double* __restrict__ phi_sr, const double* __restrict__ f_sr,
+                                        const double* __restrict__ rho, int n, double* __restrict__ part) {
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double q = rho[i];
-        s += (isfinite(q) ? q : 0.0) * phi[i];
+        const double p = phi[i] + phi_sr[i];
+        phi[i] = p;
+        f[3 * static_cast<size_t>(i) + 0] += f_sr[3 * static_cast<size_t>(i) + 0];
+        f[3 * static_cast<size_t>(i) + 1] += f_sr[3 * static_cast<size_t>(i) + 1];
+        f[3 * static_cast<size_t>(i) + 2] += f_sr[3 * static_cast<size_t>(i) + 2];
+        s += (isfinite(q) ? q : 0.0) * p;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     __shared__ double red[32];
