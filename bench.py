@@ -179,6 +179,22 @@ def traffic_for(stage, n, p, precision):
     return None
 
 
+# ---------------------------------------------------------------------- multi-rank --
+def max_over_ranks(value, dist=None, device="cuda"):
+    """Max of a host float over all ranks (replica timing); identity without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_value(n_per_rank, world, ms_max):
+    """Whole-job throughput: every rank evaluates n_per_rank particles per step."""
+    return world * n_per_rank / (ms_max / 1000.0)
+
+
 # ------------------------------------------------------------------------- main run --
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -197,12 +213,8 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def reduce_max(v):
+        return max_over_ranks(v, dist, "cuda")
 
     n = args.n
     x_np, rho_np, L = uniform_neutral(n, seed=rank)
@@ -251,8 +263,8 @@ def run_ours(args, rank, world, local_rank):
     with ClockSampler(gpu_index) as clk:
         ms_local, stages = timed(plan, args.steps, args.warmup, profile=True)
     clocks = clk.summary()
-    ms = max_over_ranks(ms_local)
-    value = world * n / (ms / 1000.0)
+    ms = reduce_max(ms_local)
+    value = aggregate_value(n, world, ms)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     xh = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
@@ -267,7 +279,7 @@ def run_ours(args, rank, world, local_rank):
     for _ in range(args.steps):
         plan.eval_host(xh, rh)
     e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e_s = max_over_ranks(e2e_s)
+    e2e_s = reduce_max(e2e_s)
 
     p = plan.params
     # dominant kernel of the step and its roofline
@@ -291,7 +303,7 @@ def run_ours(args, rank, world, local_rank):
         for tol, prec in ((1e-6, "fp64"), (1e-10, "mixed"), (1e-10, "fp64")):
             vp = pe.Plan(L, n, tol, precision=prec, **popts)
             vms, vst = timed(vp, max(5, args.steps // 3), 2, profile=True)
-            vms = max_over_ranks(vms)
+            vms = reduce_max(vms)
             variants.append({"tol": tol, "precision": prec,
                              "path": "f32" if vp.params.precision == pe.EWALD_MIXED else "f64",
                              "m": vp.params.m, "P": vp.params.P, "ms_per_step": vms,

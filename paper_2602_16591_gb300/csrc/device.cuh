@@ -419,6 +419,7 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
             }
         }
         __syncwarp();
+        real mph = 0, mgx = 0, mgy = 0, mgz = 0;   // lane j keeps particle j's results
         for (int j = 0; j < cnt; ++j) {
             const int2 id = idx[b0 + j];
             const int ox = id.x & 0xff, oy = (id.x >> 8) & 0xff, oz = (id.x >> 16) & 0xff;
@@ -465,14 +466,22 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
                 gy += __shfl_xor_sync(0xffffffffu, gy, o);
                 gz += __shfl_xor_sync(0xffffffffu, gz, o);
             }
-            if (lane == 0) {
-                const int i = id.y;
-                const double q = static_cast<double>(rec[b0 + j].w);
-                phi_out[i] = static_cast<double>(ph) - g.self * q;
-                f_out[3 * static_cast<size_t>(i) + 0] = -q * static_cast<double>(gx);
-                f_out[3 * static_cast<size_t>(i) + 1] = -q * static_cast<double>(gy);
-                f_out[3 * static_cast<size_t>(i) + 2] = -q * static_cast<double>(gz);
+            if (lane == j) {
+                mph = ph;
+                mgx = gx;
+                mgy = gy;
+                mgz = gz;
             }
+        }
+        // float64 outputs written lane-parallel: one float64 instruction stream per batch, not per
+        // particle (float64 issue is ~1/64 of float32 on this GPU)
+        if (lane < cnt) {
+            const int i = idx[b0 + lane].y;
+            const double q = static_cast<double>(rec[b0 + lane].w);
+            phi_out[i] = static_cast<double>(mph) - g.self * q;
+            f_out[3 * static_cast<size_t>(i) + 0] = -q * static_cast<double>(mgx);
+            f_out[3 * static_cast<size_t>(i) + 1] = -q * static_cast<double>(mgy);
+            f_out[3 * static_cast<size_t>(i) + 2] = -q * static_cast<double>(mgz);
         }
     }
 }
@@ -739,16 +748,23 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short(const Vec4<real>* __
                 acc[t][v] = x;
             }
         }
+        real mine[4] = {real(0), real(0), real(0), real(0)};
 #pragma unroll
         for (int t = 0; t < kShortMaxT; ++t) {
-            if (lane == t && t < nt) {
-                const int oi = idx[t0 + t].y;
-                const double qi = static_cast<double>(stx[warp][t][3]);
-                phi_out[oi] = static_cast<double>(acc[t][0]);
-                f_out[3 * static_cast<size_t>(oi) + 0] = qi * static_cast<double>(acc[t][1]);
-                f_out[3 * static_cast<size_t>(oi) + 1] = qi * static_cast<double>(acc[t][2]);
-                f_out[3 * static_cast<size_t>(oi) + 2] = qi * static_cast<double>(acc[t][3]);
+            if (lane == t) {
+                mine[0] = acc[t][0];
+                mine[1] = acc[t][1];
+                mine[2] = acc[t][2];
+                mine[3] = acc[t][3];
             }
+        }
+        if (lane < nt) {   // float64 conversions once per pass, lane-parallel
+            const int oi = idx[t0 + lane].y;
+            const double qi = static_cast<double>(stx[warp][lane][3]);
+            phi_out[oi] = static_cast<double>(mine[0]);
+            f_out[3 * static_cast<size_t>(oi) + 0] = qi * static_cast<double>(mine[1]);
+            f_out[3 * static_cast<size_t>(oi) + 1] = qi * static_cast<double>(mine[2]);
+            f_out[3 * static_cast<size_t>(oi) + 2] = qi * static_cast<double>(mine[3]);
         }
     }
 }
