@@ -53,7 +53,7 @@ extern "C" {
 typedef struct ewald_opts {
     int    precision;     /* EWALD_FP64 or EWALD_MIXED (default EWALD_FP64) */
     double rc;            /* <= 0: automatic cutoff rule; > 0: upper bound on the cutoff (length units) */
-    double grid_density;  /* target m^3 / n for the automatic cutoff rule (default 2.0, the
+    double grid_density;  /* target m^3 / n for the automatic cutoff rule (default 3.0, the
                              measured optimum of the GB300 kernels for n ~ 1e5) */
     double tol_safety;    /* the plan is sized for tol * tol_safety (default 0.25; forces have no
                              error model in the paper and measure ~2-5x the potential error) */

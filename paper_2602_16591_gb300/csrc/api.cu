@@ -355,6 +355,7 @@ int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, e
     g.h = q.h;
     g.invh = q.m / q.L;
     g.cellw = q.L / q.ncell;
+    g.invcellw = q.ncell / q.L;
     g.rc = q.rc;
     g.self = q.self_coeff;
     p->ntiles = g.nt * g.nt * g.nt;

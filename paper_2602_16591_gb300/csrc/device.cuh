@@ -25,7 +25,7 @@ template <typename real> struct alignas(4 * sizeof(real)) Vec4 { real x, y, z, w
 // Geometry and sizes shared by the kernels of one plan (passed by value).
 struct Geom {
     int n, m, P, T, nt, ncell, reach, degw, degr;
-    double L, invL, h, invh, cellw, rc, self;
+    double L, invL, h, invh, cellw, invcellw, rc, self;
 };
 
 constexpr int kTile = 4;   // spreading tile edge (grid points); m is a multiple of it
@@ -56,7 +56,7 @@ __device__ inline Located locate(const double* xp, const Geom& g) {
         int lw = l0 % g.m;
         if (lw < 0) lw += g.m;
         r.lw[d] = lw;
-        int c = static_cast<int>(w / g.cellw);
+        int c = static_cast<int>(w * g.invcellw);   // no float64 division: multiply, then clamp
         c = c < 0 ? 0 : (c >= g.ncell ? g.ncell - 1 : c);
         r.cell[d] = c;
         r.loc[d] = w - c * g.cellw;
@@ -517,7 +517,7 @@ template <> __device__ __forceinline__ double rsqrt_r<double>(double v) {
 constexpr int kShortWarps = 4;      // target cells per block
 constexpr int kShortMaxT = 8;       // targets per pass
 constexpr int kShortMaxR = 4;       // largest reach
-constexpr int kShortMaxRanges = 512;
+constexpr int kShortMaxRanges = 256;   // >= 81 columns x 3 pieces (nc >= 2R since rc <= L/2)
 
 // Per-plan constants of the real-space kernel, passed by value (kernel parameter space): the radial
 // polynomials padded with leading zeros to the compile-time degree D, so the fully unrolled Horner

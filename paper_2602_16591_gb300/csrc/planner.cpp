@@ -285,7 +285,7 @@ ewald_opts default_opts() {
     ewald_opts o{};
     o.precision = EWALD_FP64;
     o.rc = 0.0;
-    o.grid_density = 2.0;
+    o.grid_density = 3.0;
     o.tol_safety = 0.25;
     o.sr_reach = 0;
     return o;

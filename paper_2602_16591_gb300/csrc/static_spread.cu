@@ -139,6 +139,7 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
     g.h = p->L / m;
     g.invh = m / p->L;
     g.cellw = p->L;
+    g.invcellw = 1.0 / p->L;
     g.rc = p->rc;
     g.self = 0.0;
 

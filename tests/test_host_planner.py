@@ -66,7 +66,7 @@ CFGS = [(1.0, 1000, 1e-6), (1.0, 512, 1e-6), (1.0, 100_000, 1e-4), (1.0, 100_000
 @pytest.mark.parametrize("L,n,tol", CFGS)
 def test_plan_params_match_oracle_alg3(L, n, tol):
     p = pe.plan_params(L, n, tol)
-    q = oparams.plan(L, n, tol, tol_safety=0.25, grid_density=2.0)
+    q = oparams.plan(L, n, tol, tol_safety=0.25, grid_density=3.0)
     assert (p.m, p.P) == (q["m"], q["P"])
     for k in ("rc", "cs", "cw", "alpha", "h"):
         assert abs(getattr(p, k) / q[k] - 1) <= 1e-11, k
