@@ -59,6 +59,7 @@ typedef struct ewald_opts {
                              error model in the paper and measure ~2-5x the potential error) */
     int    sr_reach;      /* cells per cutoff radius in the real-space cell list, 1..4;
                              0 (default) picks it for ~3 particles per cell */
+    int    window_extra;  /* window support added to the Alg. 3 value of P (default 0) */
 } ewald_opts;
 
 /* ---- derived parameters (Alg. 3 and the library's readings of it) ------ */

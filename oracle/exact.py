@@ -65,16 +65,21 @@ def realspace(x, rho, L, split, rcut, targets=None, chunk=64):
     return phi, grad
 
 
-def structure_factor(x, rho, L, K):
-    """rhohat(k) = sum_j rho_j exp(+2 pi i k.x_j / L) on the cube |k_i| <= K."""
+def structure_factor(x, rho, L, K, chunk=250_000):
+    """rhohat(k) = sum_j rho_j exp(+2 pi i k.x_j / L) on the cube |k_i| <= K.
+
+    The sum over j is accumulated over blocks of particles (memory only)."""
     x = wrap(x, L)
+    rho = np.asarray(rho, dtype=np.float64)
     kr = np.arange(-K, K + 1)
-    E = np.exp(2j * np.pi * x[:, :, None] * kr[None, None, :] / L)   # (n, 3, 2K+1)
-    Ex, Ey, Ez = E[:, 0, :], E[:, 1, :], E[:, 2, :]
-    rh = np.empty((2 * K + 1,) * 3, dtype=np.complex128)
-    for ix in range(2 * K + 1):
-        A = (np.asarray(rho) * Ex[:, ix])[:, None] * Ey
-        rh[ix] = A.T @ Ez
+    rh = np.zeros((2 * K + 1,) * 3, dtype=np.complex128)
+    for s0 in range(0, len(x), chunk):
+        xs, rs = x[s0:s0 + chunk], rho[s0:s0 + chunk]
+        E = np.exp(2j * np.pi * xs[:, :, None] * kr[None, None, :] / L)   # (c, 3, 2K+1)
+        Ex, Ey, Ez = E[:, 0, :], E[:, 1, :], E[:, 2, :]
+        for ix in range(2 * K + 1):
+            A = (rs * Ex[:, ix])[:, None] * Ey
+            rh[ix] += A.T @ Ez
     return rh
 
 

@@ -17,6 +17,9 @@ Steps of Alg. 3 with the readings the library uses (all recorded in the design doc):
 * alpha = rc c_w/c_s, P = ceil(2 alpha m/L) (eqs. alpha, P_dimless); with the rc
   above this equals ceil(2 c_w/pi).  The window is instantiated with
   c_w := pi P/2 and alpha := P h/2 (eq. cwP), so c_s/rc = c_w/alpha (eq. bandwidth).
+* Forces (no model in the paper): measured relative force errors are ~m/10 times the
+  potential errors, so the potential target tol*tol_safety is multiplied by
+  min(1, 10/m0), m0 = c_s/(pi rc/L) before rounding, and rc re-derived.
 
 Parity status: pinned in tests/test_oracle_params.py (Lambert-W identities,
 balance equation eq. cwcs_model_dimless, kappa against a direct lattice sum).
@@ -73,13 +76,21 @@ def cw_of(cs, rc_over_L):
 def plan(L, n, tol, grid_density=1.0, rc=None, tol_safety=1.0):
     """Alg. 3 with the readings above; returns a dict of plan parameters."""
     t = tol * tol_safety
-    if rc is None:
-        mstar = (grid_density * n) ** (1.0 / 3.0)
-        rcl = 0.1
-        for _ in range(12):
-            rcl = min(cs_of(rcl, t) / (math.pi * mstar), 0.5)
-    else:
-        rcl = min(rc / L, 0.5)
+
+    def cutoff(t):
+        if rc is None:
+            mstar = (grid_density * n) ** (1.0 / 3.0)
+            r = 0.1
+            for _ in range(12):
+                r = min(cs_of(r, t) / (math.pi * mstar), 0.5)
+            return r
+        return min(rc / L, 0.5)
+
+    rcl = cutoff(t)
+    m0 = cs_of(rcl, t) / (math.pi * rcl)
+    if m0 > 10.0:
+        t *= 10.0 / m0
+        rcl = cutoff(t)
     cs = cs_of(rcl, t)
     m = good_size(math.ceil(cs / (math.pi * rcl)))
     rcl = cs / (math.pi * m)

@@ -24,7 +24,7 @@ PRECISIONS = {"fp64": EWALD_FP64, "mixed": EWALD_MIXED}
 
 class ewald_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rc", ctypes.c_double), ("grid_density", ctypes.c_double),
-                ("tol_safety", ctypes.c_double), ("sr_reach", ctypes.c_int)]
+                ("tol_safety", ctypes.c_double), ("sr_reach", ctypes.c_int), ("window_extra", ctypes.c_int)]
 
 
 class ewald_params(ctypes.Structure):
@@ -87,7 +87,7 @@ def _check(code):
         raise EwaldError(code, _lib.ewald_last_error().decode())
 
 
-def make_opts(precision="fp64", rc=None, grid_density=None, tol_safety=None, sr_reach=None):
+def make_opts(precision="fp64", rc=None, grid_density=None, tol_safety=None, sr_reach=None, window_extra=None):
     o = ewald_opts()
     _check(_lib.ewald_opts_default(ctypes.byref(o)))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -99,6 +99,8 @@ def make_opts(precision="fp64", rc=None, grid_density=None, tol_safety=None, sr_
         o.tol_safety = float(tol_safety)
     if sr_reach is not None:
         o.sr_reach = int(sr_reach)
+    if window_extra is not None:
+        o.window_extra = int(window_extra)
     return o
 
 

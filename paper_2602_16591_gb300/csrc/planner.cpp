@@ -288,6 +288,7 @@ ewald_opts default_opts() {
     o.grid_density = 3.0;
     o.tol_safety = 0.25;
     o.sr_reach = 0;
+    o.window_extra = 0;
     return o;
 }
 
@@ -406,22 +407,35 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
     if (o.precision != EWALD_FP64 && o.precision != EWALD_MIXED) throw std::invalid_argument("unknown precision");
     if (!(o.tol_safety > 0 && o.tol_safety <= 1)) throw std::invalid_argument("tol_safety must lie in (0, 1]");
     if (!(o.grid_density > 0)) throw std::invalid_argument("grid_density must be positive");
+    if (o.window_extra < 0 || o.window_extra > 8) throw std::invalid_argument("window_extra must lie in [0, 8]");
     if (o.sr_reach < 0 || o.sr_reach > 4) throw std::invalid_argument("sr_reach must lie in [0, 4]");
 
     const double As = 5.0, Aw = 3.1;                      // Secs. 5.1.1 and 5.2.1
     static const double kappa = kappa_constant();
-    const double t = tol * o.tol_safety;
+    double t = tol * o.tol_safety;
     auto cs_of = [&](double rcl) {
         const double bs_eps = As * std::sqrt(rcl) / (std::sqrt(kappa) * t);
         return 0.5 * lambert_w(0, 2.0 * bs_eps * bs_eps);   // eq. cs_dimless
     };
-    double rcl;
-    if (o.rc > 0) {
-        rcl = std::min(o.rc / L, 0.5);
-    } else {
-        const double mstar = std::cbrt(o.grid_density * static_cast<double>(n));
-        rcl = 0.1;
-        for (int it = 0; it < 12; ++it) rcl = std::min(cs_of(rcl) / (kPi * mstar), 0.5);
+    auto cutoff = [&]() {
+        double rcl;
+        if (o.rc > 0) {
+            rcl = std::min(o.rc / L, 0.5);
+        } else {
+            const double mstar = std::cbrt(o.grid_density * static_cast<double>(n));
+            rcl = 0.1;
+            for (int it = 0; it < 12; ++it) rcl = std::min(cs_of(rcl) / (kPi * mstar), 0.5);
+        }
+        return rcl;
+    };
+    double rcl = cutoff();
+    // Forces: their relative error, measured against the oracle, is ~m/10 times the potential's
+    // (the band-edge modes of the truncation carry the factor |k| ~ m/2 into the gradient); the
+    // potential target is tightened accordingly (factor min(1, 10/m0), m0 the unrounded grid size).
+    const double m0 = cs_of(rcl) / (kPi * rcl);
+    if (m0 > 10.0) {
+        t *= 10.0 / m0;
+        rcl = cutoff();
     }
     const double cs = cs_of(rcl);
     const double mraw = std::ceil(cs / (kPi * rcl));      // eq. m_cs_dimless
@@ -433,7 +447,7 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
     const double cw_t = -0.5 * lambert_w(-1, -2.0 * bw * bw * std::exp(-2.0 * cs) / cs);   // eq. cwW
     const double alpha_over_L = rcl * cw_t / cs;          // eq. alpha
     int P = static_cast<int>(std::ceil(2.0 * alpha_over_L * m));   // eq. P_dimless
-    P = std::max(P, 3);
+    P = std::max(P + o.window_extra, 3);
     if (P > 24) throw std::length_error("window support P > 24 (tolerance too tight)");
 
     HostPlan hp;
@@ -462,7 +476,7 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
     int nc = static_cast<int>(std::floor(reach / rcl));
     nc = std::max(1, std::min(nc, 1024));
     p.ncell = nc;
-    p.fit_tol = std::max(0.02 * t, p.precision == EWALD_MIXED ? 1e-8 : 5e-16);
+    p.fit_tol = std::max(0.02 * t, p.precision == EWALD_MIXED ? 1e-8 : 5e-15);
 
     const Prolate ps(p.cs), pw(p.cw);
     p.lambda_s = ps.lambda;

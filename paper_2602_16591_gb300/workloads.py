@@ -63,8 +63,8 @@ def water_box(n_mol=33_000, density=33.4, seed=0, min_dist=0.12):
 
     O at -0.8476, two H at +0.4238, O-H 0.1 nm, HOH 109.47 deg; O sites drawn
     without replacement from a cubic lattice with jitter, orientations uniform.
-    Orientations whose intermolecular H/O sites come closer than ``min_dist`` to
-    an already placed site are redrawn (a coarse cell check).
+    Orientations of molecules with an intermolecular site pair closer than
+    ``min_dist`` are redrawn (periodic k-d tree query) until none is left.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     L = (n_mol / density) ** (1.0 / 3.0)
@@ -88,24 +88,20 @@ def water_box(n_mol=33_000, density=33.4, seed=0, min_dist=0.12):
             np.stack([2 * (xq * zq - yq * w), 2 * (yq * zq + xq * w), 1 - 2 * (xq * xq + yq * yq)], -1),
         ], 1)
 
+    from scipy.spatial import cKDTree
+
     Rm = rand_rot(n_mol)
     pos = O[:, None, :] + np.einsum('mij,sj->msi', Rm, body)
-    # redraw orientations that clash with other molecules (bounded retries)
-    for _ in range(20):
+    # redraw the orientations of molecules with an intermolecular site pair closer than min_dist
+    for _ in range(200):
         flat = np.mod(pos.reshape(-1, 3), L)
-        cell = np.floor(flat / min_dist).astype(np.int64)
-        nc = int(np.floor(L / min_dist))
-        cell = np.minimum(cell, nc - 1)
-        key = (cell[:, 0] * nc + cell[:, 1]) * nc + cell[:, 2]
-        mol = np.repeat(np.arange(n_mol), 3)
-        order = np.argsort(key, kind='stable')
-        ks, ms = key[order], mol[order]
-        clash = np.zeros(n_mol, dtype=bool)
-        same = (ks[1:] == ks[:-1]) & (ms[1:] != ms[:-1])
-        clash[ms[1:][same]] = True
-        if not clash.any():
+        pairs = cKDTree(flat, boxsize=L).query_pairs(min_dist, output_type='ndarray')
+        mol = np.arange(3 * n_mol) // 3
+        if len(pairs):
+            pairs = pairs[mol[pairs[:, 0]] != mol[pairs[:, 1]]]
+        if len(pairs) == 0:
             break
-        idx = np.nonzero(clash)[0]
+        idx = np.unique(mol[pairs.ravel()])
         Rm[idx] = rand_rot(len(idx))
         pos[idx] = O[idx, None, :] + np.einsum('mij,sj->msi', Rm[idx], body)
     x = np.mod(pos.reshape(-1, 3), L)
