@@ -288,24 +288,24 @@ def run_ours(args, rank, world, local_rank):
     ours = {k: v for k, v in stages.items() if k not in ("fft_fwd", "fft_inv")}
     dom = max(ours, key=ours.get)
     fl = algorithmic_flops(dom, p, n, pairs)
-    prec_tag = "f32" if p.precision == pe.EWALD_MIXED else "f64"
-    peak = FP32_PEAK_TFLOPS if prec_tag == "f32" else FP64_PEAK_TFLOPS
+    prec_tag = pe.PATH_NAMES[p.precision]
+    peak = FP64_PEAK_TFLOPS if prec_tag == "f64" else FP32_PEAK_TFLOPS
     roofline = None
     if fl is not None:
         ach = fl / (stages[dom] / 1000.0) / 1e12
         roofline = {"bound": "alu", "kernel": dom, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": traffic_for(dom, n, p, prec_tag),
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz" if prec_tag == "f32"
-                    else "nominal GB300 FP64 1.25 TFLOP/s"}
+                    "peak_source": "nominal GB300 FP64 1.25 TFLOP/s" if prec_tag == "f64"
+                    else "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
     variants = []
     if not args.no_variants:
-        for tol, prec in ((1e-6, "fp64"), (1e-10, "mixed"), (1e-10, "fp64")):
+        for tol, prec in ((1e-6, "fp64"), (1e-8, "mixed"), (1e-10, "mixed"), (1e-10, "fp64"), (1e-12, "mixed")):
             vp = pe.Plan(L, n, tol, precision=prec, **popts)
             vms, vst = timed(vp, max(5, args.steps // 3), 2, profile=True)
             vms = reduce_max(vms)
             variants.append({"tol": tol, "precision": prec,
-                             "path": "f32" if vp.params.precision == pe.EWALD_MIXED else "f64",
+                             "path": pe.PATH_NAMES[vp.params.precision],
                              "m": vp.params.m, "P": vp.params.P, "ms_per_step": vms,
                              "value": world * n / (vms / 1000.0), "stages_ms": vst})
             del vp
@@ -343,7 +343,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--n", type=int, default=100_000)
     ap.add_argument("--tol", type=float, default=1e-6)
-    ap.add_argument("--precision", default="mixed", choices=("mixed", "fp64"))
+    ap.add_argument("--precision", default="mixed", choices=("mixed", "fp64", "floatfloat"))
     ap.add_argument("--grid-density", type=float, default=None, help="m^3/n target of the cutoff rule")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

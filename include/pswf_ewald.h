@@ -47,11 +47,18 @@ extern "C" {
 #define EWALD_MIXED  1   /* spreading, FFT, interpolation and the real-space sum in float32
                             (positions reduced to per-tile/per-cell offsets in float64 first);
                             outputs, energy and self term in float64.  For tol < 1e-7 a MIXED
-                            plan runs the float64 kernels (ewald_params.precision reports it). */
+                            plan runs the EWALD_FLOATFLOAT kernels instead (float32 products
+                            cannot reach it); ewald_params.precision reports the path taken. */
+#define EWALD_FLOATFLOAT 2 /* spreading, interpolation and the real-space sum in float-float
+                            arithmetic (unevaluated sums of two float32, ~48 bits, on the float32
+                            pipes); grid, FFT and scaling in float64; outputs in float64.
+                            Accuracy of the float64 path down to tol ~1e-12 at a fraction of its
+                            cost on GPUs with reduced float64 throughput.  Positions, charges and
+                            L must lie in the float32 exponent range. */
 
 /* ---- options (ewald_opts_default fills the defaults) -------------------- */
 typedef struct ewald_opts {
-    int    precision;     /* EWALD_FP64 or EWALD_MIXED (default EWALD_FP64) */
+    int    precision;     /* EWALD_FP64, EWALD_MIXED or EWALD_FLOATFLOAT (default EWALD_FP64) */
     double rc;            /* <= 0: automatic cutoff rule; > 0: upper bound on the cutoff (length units) */
     double grid_density;  /* target m^3 / n for the automatic cutoff rule (default 3.0, the
                              measured optimum of the GB300 kernels for n ~ 1e5) */
@@ -84,7 +91,7 @@ typedef struct ewald_params {
     int    tile;       /* spreading tile edge T (grid points), m % T == 0 */
     int    ncell;      /* real-space cells per axis */
     int    sr_reach;   /* real-space neighbour reach in cells */
-    int    precision;  /* EWALD_FP64 or EWALD_MIXED */
+    int    precision;  /* path the plan runs: EWALD_FP64, EWALD_MIXED or EWALD_FLOATFLOAT */
 } ewald_params;
 
 typedef struct ewald_plan_s* ewald_plan;   /* opaque, owned by the library */

@@ -18,8 +18,9 @@ LIB_PATH = os.path.join(_HERE, "libpswf_ewald.so")
 
 EWALD_OK, EWALD_EINVAL, EWALD_ENONNEUTRAL, EWALD_ENOMEM = 0, 1, 2, 3
 EWALD_ECUDA, EWALD_ECUFFT, EWALD_ETOOBIG, EWALD_ETIMEOUT, EWALD_ENONFINITE = 4, 5, 6, 7, 8
-EWALD_FP64, EWALD_MIXED = 0, 1
-PRECISIONS = {"fp64": EWALD_FP64, "mixed": EWALD_MIXED}
+EWALD_FP64, EWALD_MIXED, EWALD_FLOATFLOAT = 0, 1, 2
+PRECISIONS = {"fp64": EWALD_FP64, "mixed": EWALD_MIXED, "floatfloat": EWALD_FLOATFLOAT}
+PATH_NAMES = {EWALD_FP64: "f64", EWALD_MIXED: "f32", EWALD_FLOATFLOAT: "ff"}
 
 
 class ewald_opts(ctypes.Structure):
@@ -164,7 +165,8 @@ def scale_table(params):
 class Plan:
     """A PSWF Ewald plan on the current CUDA device (C ABI: ewald_plan_create).
 
-    ``precision`` is "fp64" or "mixed"; other keywords are the ewald_opts fields.
+    ``precision`` is "fp64", "mixed" or "floatfloat" ("mixed" below tol 1e-7 runs the float-float
+    kernels; ``params.precision`` reports the path); other keywords are the ewald_opts fields.
     """
 
     def __init__(self, L, n, tol, precision="fp64", **opts):

@@ -2,6 +2,7 @@
 // host-side table entry points declared in include/pswf_ewald.h.
 #include <cufft.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <stdexcept>
@@ -45,6 +46,41 @@ int upload(T** dst, const std::vector<double>& src) {
     return EWALD_OK;
 }
 
+// Float-float table: the high parts of every coefficient followed by the low parts.
+int upload_ff(float** dst, const std::vector<double>& src) {
+    std::vector<float> tmp(2 * src.size());
+    for (size_t i = 0; i < src.size(); ++i) {
+        tmp[i] = static_cast<float>(src[i]);
+        tmp[src.size() + i] = static_cast<float>(src[i] - static_cast<double>(tmp[i]));
+    }
+    if (cudaMalloc(dst, sizeof(float) * (tmp.empty() ? 1 : tmp.size())) != cudaSuccess)
+        return fail(EWALD_ENOMEM, "cudaMalloc of a table failed");
+    if (!tmp.empty() && cudaMemcpy(*dst, tmp.data(), sizeof(float) * tmp.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(EWALD_ECUDA, "table upload failed");
+    return EWALD_OK;
+}
+
+// Smallest kf in [1, deg_w] such that a float32 Horner pass over the window terms k >= kf errs by at
+// most a quarter of the fit tolerance: 2^-23 (deg_w - kf + 1) max_a sum_{k >= kf} |c_ak| (|z| <= 1),
+// for the window (scale 1) and its derivative (scale max |psi'| / psi(0)).
+int ff_split_index(const pswf::HostPlan& hp) {
+    const int P = hp.p.P, d = hp.p.deg_w;
+    double dscale = 0;
+    for (int a = 0; a < P; ++a) dscale = std::max(dscale, std::fabs(hp.dwc[a * (d + 1)]));
+    auto tail_ok = [&](const std::vector<double>& c, int kf, double scale) {
+        double mx = 0;
+        for (int a = 0; a < P; ++a) {
+            double t = 0;
+            for (int k = kf; k <= d; ++k) t += std::fabs(c[a * (d + 1) + k]);
+            mx = std::max(mx, t);
+        }
+        return std::ldexp(mx * (d - kf + 1), -23) <= 0.25 * hp.p.fit_tol * scale;
+    };
+    for (int kf = 1; kf <= d; ++kf)
+        if (tail_ok(hp.wc, kf, 1.0) && tail_ok(hp.dwc, kf, std::max(dscale, 1.0))) return kf;
+    return d;
+}
+
 }  // namespace
 
 namespace pswf {
@@ -56,7 +92,9 @@ struct ewald_plan_s {
     pswf::HostPlan hp;
     pswf::Geom g{};
     int device = 0;
-    bool fp64 = true;
+    bool fp64 = true;   // grid, FFT and scaling in float64 (EWALD_FP64 and EWALD_FLOATFLOAT plans)
+    bool ff = false;    // float-float particle kernels (EWALD_FLOATFLOAT)
+    int ff_kf = 1;      // window polynomial terms k >= ff_kf are summed in float32 (float-float plans)
     int ntiles = 0, ncells = 0, epart_blocks = 0;
     // workspace
     int* key_rank = nullptr;
@@ -70,6 +108,8 @@ struct ewald_plan_s {
     int2* sr_idx = nullptr;
     void* sr_lo = nullptr;   // float32 plans: float-float residue of the local coordinates
     float4* sr_f32 = nullptr;  // float64 plans: float32 copy of the local coordinates (cutoff pre-test)
+    int* sr_cz = nullptr;      // float-float plans: z cell index of every cell-sorted record
+    void* grid_ff = nullptr;   // float-float plans: the interpolation grid as {hi, lo} float pairs
     int4* sr_cols = nullptr;   // real-space columns {dx, dy, dzmax, 0} with box distance < rc
     int n_cols = 0;
     void* scratch = nullptr;
@@ -113,7 +153,7 @@ struct ewald_plan_s {
     }
 
     ~ewald_plan_s() {
-        void* bufs[] = {key_rank, tile_cnt, tile_off, cell_cnt, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, sr_lo, sr_f32, sr_cols, scratch,
+        void* bufs[] = {key_rank, tile_cnt, tile_off, cell_cnt, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, sr_lo, sr_f32, sr_cz, grid_ff, sr_cols, scratch,
                         grid_a, grid_b, spec, wcoef, dwcoef, p1c, qc, iw, mtab, phi_int, f_int, status, epart,
                         energy_d, x_stage, rho_stage};
         for (void* b : bufs)
@@ -256,6 +296,81 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     return EWALD_OK;
 }
 
+// Float-float plans: same stages and streams as run_pipeline; particle kernels from LaunchFF, float64
+// grid, cuFFT D2Z/Z2D and k_scale.
+int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* phi, double* f, cudaStream_t s) {
+    using pswf::LaunchFF;
+    const pswf::Geom& g = p->g;
+    const int n = g.n, m = g.m;
+    const size_t nn = static_cast<size_t>(n);
+    p->mark(0, false, s);
+    PSWF_CUDA(cudaMemsetAsync(p->tile_cnt, 0, sizeof(int) * p->ntiles, s));
+    PSWF_CUDA(cudaMemsetAsync(p->cell_cnt, 0, sizeof(int) * p->ncells, s));
+    PSWF_CUDA(cudaMemsetAsync(p->status, 0, sizeof(double) * 3, s));
+    const int tb = 256, nb = (n + tb - 1) / tb;
+    pswf::k_prep<<<nb, tb, 0, s>>>(x, rho, g, p->key_rank, p->tile_cnt, p->cell_cnt, p->status);
+    PSWF_CUDA(cudaGetLastError());
+    pswf::k_scan<<<2, 1024, 0, s>>>(p->tile_cnt, p->tile_off, p->ntiles, p->cell_cnt, p->cell_off, p->ncells);
+    PSWF_CUDA(cudaGetLastError());
+    auto* sp_h = static_cast<float4*>(p->sp_rec);
+    auto* sp_l = sp_h + nn;
+    auto* sr_h = static_cast<float4*>(p->sr_rec);
+    auto* sr_l = sr_h + nn;
+    PSWF_CUDA(LaunchFF::scatter(x, rho, g, p->key_rank, p->tile_off, p->cell_off, sp_h, sp_l, p->sp_idx, sr_h, sr_l,
+                                p->sr_idx, p->sr_cz, s));
+    p->mark(0, true, s);
+    PSWF_CUDA(cudaEventRecord(p->ev_fork, s));
+    PSWF_CUDA(cudaStreamWaitEvent(p->s_short, p->ev_fork, 0));
+    p->mark(7, false, p->s_short);
+    PSWF_CUDA(LaunchFF::short_range(g, sr_h, sr_l, p->sr_idx, p->sr_cz, p->cell_off, p->sr_cols, p->n_cols,
+                                    p->hp.p1c.data(), p->hp.qc.data(), p->phi_sr, p->f_sr, p->s_short));
+    p->mark(7, true, p->s_short);
+    PSWF_CUDA(cudaEventRecord(p->ev_join, p->s_short));
+    const cudaStream_t caller = s;
+    PSWF_CUDA(cudaStreamWaitEvent(p->s_alg2, p->ev_fork, 0));
+    s = p->s_alg2;
+    const auto* wc = static_cast<const float*>(p->wcoef);
+    const auto* dwc = static_cast<const float*>(p->dwcoef);
+    p->mark(1, false, s);
+    PSWF_CUDA(LaunchFF::spread(p->ntiles, g, sp_h, sp_l, p->sp_idx, p->tile_off, wc, p->ff_kf,
+                               static_cast<float2*>(p->scratch), s));
+    p->mark(1, true, s);
+    p->mark(2, false, s);
+    PSWF_CUDA(LaunchFF::halo(static_cast<const float2*>(p->scratch), p->tile_off, g, static_cast<double*>(p->grid_a), s));
+    p->mark(2, true, s);
+    p->mark(3, false, s);
+    PSWF_CUFFT(cufftSetStream(p->fwd, s));
+    PSWF_CUFFT(cufftSetStream(p->inv, s));
+    PSWF_CUFFT(cufftExecD2Z(p->fwd, static_cast<cufftDoubleReal*>(p->grid_a), static_cast<cufftDoubleComplex*>(p->spec)));
+    p->mark(3, true, s);
+    p->mark(4, false, s);
+    const int ns = m * m * (m / 2 + 1);
+    pswf::k_scale<double, cufftDoubleComplex><<<(ns + 255) / 256, 256, 0, s>>>(
+        static_cast<cufftDoubleComplex*>(p->spec), m, static_cast<const double*>(p->iw),
+        static_cast<const double*>(p->mtab));
+    PSWF_CUDA(cudaGetLastError());
+    p->mark(4, true, s);
+    p->mark(5, false, s);
+    PSWF_CUFFT(cufftExecZ2D(p->inv, static_cast<cufftDoubleComplex*>(p->spec), static_cast<cufftDoubleReal*>(p->grid_b)));
+    const size_t m3 = static_cast<size_t>(m) * m * m;
+    PSWF_CUDA(LaunchFF::to_ff(static_cast<const double*>(p->grid_b), m3, static_cast<float2*>(p->grid_ff), s));
+    p->mark(5, true, s);
+    p->mark(6, false, s);
+    PSWF_CUDA(LaunchFF::interp(p->ntiles, g, static_cast<const float2*>(p->grid_ff), sp_h, sp_l, p->sp_idx,
+                               p->tile_off, wc, dwc, p->ff_kf, 1.0 / p->hp.p.alpha, phi, f, s));
+    p->mark(6, true, s);
+    PSWF_CUDA(cudaEventRecord(p->ev_join2, s));
+    s = caller;
+    PSWF_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
+    PSWF_CUDA(cudaStreamWaitEvent(s, p->ev_join2, 0));
+    p->mark(8, false, s);
+    pswf::k_combine_energy<<<p->epart_blocks, 256, 0, s>>>(phi, f, p->phi_sr, p->f_sr, rho, n, p->epart);
+    pswf::k_energy_final<<<1, 256, 0, s>>>(p->epart, p->epart_blocks, p->energy_d);
+    PSWF_CUDA(cudaGetLastError());
+    p->mark(8, true, s);
+    return EWALD_OK;
+}
+
 int eval_device(ewald_plan p, const double* x, const double* rho, double* phi, double* force, cudaStream_t s) {
     p->cur = nullptr;
     if (p->profiling) {
@@ -267,6 +382,7 @@ int eval_device(ewald_plan p, const double* x, const double* rho, double* phi, d
     }
     double* phi_d = phi ? phi : p->phi_int;
     double* f_d = force ? force : p->f_int;
+    if (p->ff) return run_pipeline_ff(p, x, rho, phi_d, f_d, s);
     if (p->fp64) return run_pipeline<double, cufftDoubleComplex>(p, x, rho, phi_d, f_d, s);
     return run_pipeline<float, cufftComplex>(p, x, rho, phi_d, f_d, s);
 }
@@ -339,7 +455,8 @@ int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, e
         return fail(EWALD_EINVAL, e.what());
     }
     const ewald_params& q = p->hp.p;
-    p->fp64 = q.precision == EWALD_FP64;
+    p->fp64 = q.precision != EWALD_MIXED;
+    p->ff = q.precision == EWALD_FLOATFLOAT;
     pswf::Geom& g = p->g;
     g.n = static_cast<int>(n);
     g.m = q.m;
@@ -399,7 +516,9 @@ int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, e
         }
     }
     if ((!p->fp64 && cudaMalloc(&p->sr_lo, 4 * sizeof(float) * n) != cudaSuccess) ||
-        (p->fp64 && cudaMalloc(reinterpret_cast<void**>(&p->sr_f32), sizeof(float4) * n) != cudaSuccess)) {
+        (p->fp64 && !p->ff && cudaMalloc(reinterpret_cast<void**>(&p->sr_f32), sizeof(float4) * n) != cudaSuccess) ||
+        (p->ff && cudaMalloc(reinterpret_cast<void**>(&p->sr_cz), sizeof(int) * n) != cudaSuccess) ||
+        (p->ff && cudaMalloc(&p->grid_ff, sizeof(float2) * m3) != cudaSuccess)) {
         cudaGetLastError();
         delete p;
         return fail(EWALD_ENOMEM, "device allocation failed (real-space residues)");
@@ -449,7 +568,16 @@ int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, e
         return fail(EWALD_ENOMEM, "pinned host allocation failed");
     }
     int rc = EWALD_OK;
-    if (p->fp64) {
+    if (p->ff) {
+        p->ff_kf = ff_split_index(p->hp);
+        if ((rc = upload_ff(reinterpret_cast<float**>(&p->wcoef), p->hp.wc)) ||
+            (rc = upload_ff(reinterpret_cast<float**>(&p->dwcoef), p->hp.dwc)) ||
+            (rc = upload<double>(reinterpret_cast<double**>(&p->iw), p->hp.iw)) ||
+            (rc = upload<double>(reinterpret_cast<double**>(&p->mtab), p->hp.mtab))) {
+            delete p;
+            return rc;
+        }
+    } else if (p->fp64) {
         if ((rc = upload<double>(reinterpret_cast<double**>(&p->wcoef), p->hp.wc)) ||
             (rc = upload<double>(reinterpret_cast<double**>(&p->dwcoef), p->hp.dwc)) ||
             (rc = upload<double>(reinterpret_cast<double**>(&p->p1c), p->hp.p1c)) ||

@@ -1,0 +1,512 @@
+// Float-float kernels for tight tolerances: spreading, halo sum, interpolation and the real-space sum
+// carried out in float-float arithmetic (ff.cuh) on the float32 pipes, about 48 significant bits; the
+// grid, the FFTs and the scaling stay float64 (the float64 path's cuFFT plans and k_scale), and the
+// outputs are float64.  Tiling, ownership and streaming are those of the kernels in device.cuh; only
+// the arithmetic and the record layouts differ.  On this GPU float64 issues at ~1/64 of float32, so a
+// float-float product (12-18 float32 operations) is several times cheaper than a float64 one.
+//
+// Inputs must lie in the float32 exponent range (|rho| and box sizes between ~1e-30 and ~1e30).
+#pragma once
+
+#include "device.cuh"
+#include "ff.cuh"
+
+namespace pswf {
+
+__device__ __forceinline__ void split_ff(double v, float& h, float& l) {
+    h = __double2float_rn(v);
+    l = __double2float_rn(v - static_cast<double>(h));
+}
+
+// Sorted records.  Spreading side (tile order): {z0, z1, z2, rho} as separate high and low float4
+// arrays, {packed offsets, original index}.  Real-space side (cell order): {local x, y, z, rho} high
+// and low parts, {cell id, original index} and the cell's z index.
+static __global__ void k_scatter_ff(const double* __restrict__ x, const double* __restrict__ rho, Geom g,
+                                    const int* __restrict__ key_rank, const int* __restrict__ tile_off,
+                                    const int* __restrict__ cell_off, float4* __restrict__ sp_h,
+                                    float4* __restrict__ sp_l, int2* __restrict__ sp_idx, float4* __restrict__ sr_h,
+                                    float4* __restrict__ sr_l, int2* __restrict__ sr_idx, int* __restrict__ sr_cz) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.n) return;
+    const Located r = locate(x + 3 * static_cast<size_t>(i), g);
+    double q = rho[i];
+    if (!isfinite(q)) q = 0.0;
+    const int4 kr = reinterpret_cast<const int4*>(key_rank)[i];
+    const int ps = tile_off[kr.x] + kr.y;
+    const int pc = cell_off[kr.z] + kr.w;
+    float4 h, l;
+    split_ff(r.z[0], h.x, l.x);
+    split_ff(r.z[1], h.y, l.y);
+    split_ff(r.z[2], h.z, l.z);
+    split_ff(q, h.w, l.w);
+    sp_h[ps] = h;
+    sp_l[ps] = l;
+    sp_idx[ps] = make_int2((r.lw[0] % g.T) | ((r.lw[1] % g.T) << 8) | ((r.lw[2] % g.T) << 16), i);
+    split_ff(r.loc[0], h.x, l.x);
+    split_ff(r.loc[1], h.y, l.y);
+    split_ff(r.loc[2], h.z, l.z);
+    sr_h[pc] = h;
+    sr_l[pc] = l;
+    sr_idx[pc] = make_int2(cell_of(r, g), i);
+    sr_cz[pc] = r.cell[2];
+}
+
+// Window weight a at z (float-float).  The high-order terms k >= kf are tiny (the per-interval
+// polynomials of the window decay fast) and are summed by a float32 Horner pass in z.h; the host picks
+// kf so that pass stays well below the fit tolerance.  The terms k < kf run in float-float.
+__device__ __forceinline__ ff window_weight_ff(const float* __restrict__ ch, const float* __restrict__ cl, int deg,
+                                               int kf, int a, ff z) {
+    const float* h = ch + a * (deg + 1);
+    const float* l = cl + a * (deg + 1);
+    float t = h[deg];
+    for (int k = deg - 1; k >= kf; --k) t = fmaf(t, z.h, h[k]);
+    ff w = ff_make(t);
+    for (int k = kf - 1; k >= 0; --k) w = ff_add(ff_mul(w, z), ff{h[k], l[k]});
+    return w;
+}
+
+// ---- Alg. 2 step 1: spreading with float-float register columns, float2 {h, l} slabs ----------------
+constexpr int kSpreadFFChunk = 32;
+
+template <int P>
+__global__ void __launch_bounds__(spread_threads<P>()) k_spread_ff(const float4* __restrict__ rec_h,
+                                                                   const float4* __restrict__ rec_l,
+                                                                   const int2* __restrict__ idx,
+                                                                   const int* __restrict__ tile_off,
+                                                                   const float* __restrict__ wc, int degw, int kf,
+                                                                   float2* __restrict__ scratch) {
+    constexpr int T = kTile, E = T + P - 1, CH = kSpreadFFChunk;
+    const int tile = blockIdx.x;
+    const int beg = tile_off[tile], end = tile_off[tile + 1];
+    if (beg == end) return;
+    const int nc = P * (degw + 1);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ff* sw = reinterpret_cast<ff*>(smem_raw);                        // CH * 3 * P
+    ff* srho = sw + CH * 3 * P;                                      // CH
+    float* sch = reinterpret_cast<float*>(srho + CH);                // P * (degw + 1), then the low parts
+    float* scl = sch + nc;
+    int* soff = reinterpret_cast<int*>(scl + nc);                    // CH
+    for (int i = threadIdx.x; i < 2 * nc; i += blockDim.x) sch[i] = wc[i];
+    const int col = threadIdx.x;
+    const bool own = col < E * E;
+    const int b = col / E, c = col % E;
+    ff acc[E];
+#pragma unroll
+    for (int a = 0; a < E; ++a) acc[a] = ff{0.f, 0.f};
+    for (int base = beg; base < end; base += CH) {
+        const int cnt = min(CH, end - base);
+        __syncthreads();
+        // one (particle, axis, weight) Horner evaluation per thread
+        for (int t = threadIdx.x; t < cnt * 3 * P; t += blockDim.x) {
+            const int j = t / (3 * P), d = (t / P) % 3, a = t % P;
+            const float4 rh = rec_h[base + j], rl = rec_l[base + j];
+            const ff z = d == 0 ? ff{rh.x, rl.x} : (d == 1 ? ff{rh.y, rl.y} : ff{rh.z, rl.z});
+            sw[t] = window_weight_ff(sch, scl, degw, kf, a, z);
+            if (d == 0 && a == 0) {
+                srho[j] = ff{rh.w, rl.w};
+                soff[j] = idx[base + j].x;
+            }
+        }
+        __syncthreads();
+        if (own) {
+            for (int j = 0; j < cnt; ++j) {
+                const int pk = soff[j];
+                const int ox = pk & 0xff, oy = (pk >> 8) & 0xff, oz = (pk >> 16) & 0xff;
+                const int bb = b - oy, cc = c - oz;
+                if (bb < 0 || bb >= P || cc < 0 || cc >= P) continue;
+                const ff wyz = ff_mul(ff_mul(srho[j], sw[(j * 3 + 1) * P + bb]), sw[(j * 3 + 2) * P + cc]);
+                const ff* wx = sw + (j * 3) * P;
+                switch (ox) {
+#define PSWF_SPREAD_FF_CASE(O)                                                                \
+    case O:                                                                                   \
+        _Pragma("unroll") for (int p = 0; p < P; ++p) ff_acc(acc[O + p], wyz, wx[p]);        \
+        break;
+                    PSWF_SPREAD_FF_CASE(0)
+                    PSWF_SPREAD_FF_CASE(1)
+                    PSWF_SPREAD_FF_CASE(2)
+                    PSWF_SPREAD_FF_CASE(3)
+#undef PSWF_SPREAD_FF_CASE
+                    default: break;
+                }
+            }
+        }
+    }
+    if (own) {
+        float2* out = scratch + static_cast<size_t>(tile) * E * E * E;
+#pragma unroll
+        for (int a = 0; a < E; ++a) {
+            const ff v = ff_norm(acc[a]);
+            out[a * E * E + col] = make_float2(v.h, v.l);
+        }
+    }
+}
+
+// Halo sum of the float-float slabs (same enumeration as k_halo) into the float64 grid.
+static __global__ void k_halo_ff(const float2* __restrict__ scratch, const int* __restrict__ tile_off, Geom g,
+                                 double* __restrict__ grid) {
+    const int m = g.m, T = g.T, nt = g.nt, E = g.T + g.P - 1;
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= m * m * m) return;
+    const int lz = id % m, ly = (id / m) % m, lx = id / (m * m);
+    const int tlx = lx / T, tly = ly / T, tlz = lz / T;
+    const int olx = lx - tlx * T, oly = ly - tly * T, olz = lz - tlz * T;
+    const size_t slab = static_cast<size_t>(E) * E * E;
+    ff s{0.f, 0.f};
+    int tx = tlx;
+    for (int ex = olx; ex < E; ex += T) {
+        int ty = tly;
+        for (int ey = oly; ey < E; ey += T) {
+            int tz = tlz;
+            for (int ez = olz; ez < E; ez += T) {
+                const int tile = (tx * nt + ty) * nt + tz;
+                if (tile_off[tile] != tile_off[tile + 1]) {
+                    const float2 v = scratch[static_cast<size_t>(tile) * slab + (ex * E + ey) * E + ez];
+                    s = ff_add(s, ff{v.x, v.y});
+                }
+                tz = tz == 0 ? nt - 1 : tz - 1;
+            }
+            ty = ty == 0 ? nt - 1 : ty - 1;
+        }
+        tx = tx == 0 ? nt - 1 : tx - 1;
+    }
+    grid[id] = ff_to_double(s);
+}
+
+// float64 grid -> float-float pairs (after the inverse FFT, so the interpolation does no float64 work)
+static __global__ void k_grid_to_ff(const double* __restrict__ grid, size_t count, float2* __restrict__ out) {
+    const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float h, l;
+    split_ff(grid[i], h, l);
+    out[i] = make_float2(h, l);
+}
+
+// ---- Alg. 2 step 5 with eq. force: interpolation in float-float ------------------------------------
+// Structure of k_interp (tile block in shared memory, a warp per batch of particles, lanes over the
+// (b, c) pairs of the stencil); the inner sums over a are compensated dot products (ff_acc).
+constexpr int kInterpFFNB = 4, kInterpFFWarps = 4;
+
+template <int P>
+__global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2* __restrict__ grid,
+                                                                   const float4* __restrict__ rec_h,
+                                                                   const float4* __restrict__ rec_l,
+                                                                   const int2* __restrict__ idx,
+                                                                   const int* __restrict__ tile_off,
+                                                                   const float* __restrict__ wc,
+                                                                   const float* __restrict__ dwc, int kf, Geom g,
+                                                                   float inv_alpha_h, float inv_alpha_l,
+                                                                   double* __restrict__ phi_out,
+                                                                   double* __restrict__ f_out) {
+    constexpr int T = kTile, E = T + P - 1, NB = kInterpFFNB, NWARP = kInterpFFWarps;
+    constexpr int NQ = (P * P + 31) / 32;
+    const int tile = blockIdx.x;
+    const int beg = tile_off[tile], end = tile_off[tile + 1];
+    if (beg == end) return;
+    const int m = g.m, nt = g.nt, degw = g.degw;
+    const int nc = P * (degw + 1);
+    const int tz = tile % nt, ty = (tile / nt) % nt, tx = tile / (nt * nt);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ff* G = reinterpret_cast<ff*>(smem_raw);                          // E^3
+    ff* sw = G + E * E * E;                                           // NWARP * NB * 6 * P
+    float* sch = reinterpret_cast<float*>(sw + NWARP * NB * 6 * P);   // window hi, lo, derivative hi, lo
+    float* scl = sch + nc;
+    float* sdh = scl + nc;
+    float* sdl = sdh + nc;
+    for (int i = threadIdx.x; i < 2 * nc; i += blockDim.x) {
+        sch[i] = wc[i];
+        sdh[i] = dwc[i];
+    }
+    for (int e = threadIdx.x; e < E * E * E; e += blockDim.x) {
+        const int ez = e % E, ey = (e / E) % E, ex = e / (E * E);
+        const int gx = (tx * T + ex) % m, gy = (ty * T + ey) % m, gz = (tz * T + ez) % m;
+        const float2 v = grid[(static_cast<size_t>(gx) * m + gy) * m + gz];
+        G[e] = ff{v.x, v.y};
+    }
+    __syncthreads();
+    const ff inv_alpha{inv_alpha_h, inv_alpha_l};
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    ff* ww = sw + warp * NB * 6 * P;
+    for (int b0 = beg + warp * NB; b0 < end; b0 += NWARP * NB) {
+        const int cnt = min(NB, end - b0);
+        __syncwarp();
+        // one (particle, kind, weight) Horner evaluation per lane; kinds 0-2 values, 3-5 derivatives
+        for (int task = lane; task < cnt * 6 * P; task += 32) {
+            const int j = task / (6 * P), kind = (task / P) % 6, a = task % P, d = kind % 3;
+            const float4 rh = rec_h[b0 + j], rl = rec_l[b0 + j];
+            const ff z = d == 0 ? ff{rh.x, rl.x} : (d == 1 ? ff{rh.y, rl.y} : ff{rh.z, rl.z});
+            ww[task] = kind < 3 ? window_weight_ff(sch, scl, degw, kf, a, z)
+                                : ff_mul(window_weight_ff(sdh, sdl, degw, kf, a, z), inv_alpha);
+        }
+        __syncwarp();
+        ff mph{0.f, 0.f}, mgx{0.f, 0.f}, mgy{0.f, 0.f}, mgz{0.f, 0.f};   // lane j keeps particle j
+        for (int j = 0; j < cnt; ++j) {
+            const int2 id = idx[b0 + j];
+            const int ox = id.x & 0xff, oy = (id.x >> 8) & 0xff, oz = (id.x >> 16) & 0xff;
+            const ff* wp = ww + j * 6 * P;
+            ff ph{0.f, 0.f}, gx{0.f, 0.f}, gy{0.f, 0.f}, gz{0.f, 0.f};
+#pragma unroll
+            for (int qi = 0; qi < NQ; ++qi) {
+                const int q = lane + 32 * qi;
+                if (q < P * P) {
+                    const int bb = q / P, cc = q - (q / P) * P;
+                    const ff* col = G + (ox * E + oy + bb) * E + oz + cc;
+                    ff s1{0.f, 0.f}, s2{0.f, 0.f};
+#pragma unroll
+                    for (int a = 0; a < P; ++a) {
+                        const ff v = col[a * E * E];
+                        ff_acc(s1, v, wp[a]);
+                        ff_acc(s2, v, wp[3 * P + a]);
+                    }
+                    s1 = ff_norm(s1);
+                    s2 = ff_norm(s2);
+                    const ff wy = wp[P + bb], wz = wp[2 * P + cc];
+                    const ff dwy = wp[4 * P + bb], dwz = wp[5 * P + cc];
+                    const ff yz = ff_mul(wy, wz);
+                    ff_acc(ph, s1, yz);
+                    ff_acc(gx, s2, yz);
+                    ff_acc(gy, s1, ff_mul(dwy, wz));
+                    ff_acc(gz, s1, ff_mul(wy, dwz));
+                }
+            }
+            ph = ff_norm(ph);
+            gx = ff_norm(gx);
+            gy = ff_norm(gy);
+            gz = ff_norm(gz);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                ph = ff_add(ph, ff_shfl_xor(ph, o));
+                gx = ff_add(gx, ff_shfl_xor(gx, o));
+                gy = ff_add(gy, ff_shfl_xor(gy, o));
+                gz = ff_add(gz, ff_shfl_xor(gz, o));
+            }
+            if (lane == j) {
+                mph = ph;
+                mgx = gx;
+                mgy = gy;
+                mgz = gz;
+            }
+        }
+        if (lane < cnt) {   // float64 outputs, lane-parallel
+            const int i = idx[b0 + lane].y;
+            const double q = static_cast<double>(rec_h[b0 + lane].w) + static_cast<double>(rec_l[b0 + lane].w);
+            phi_out[i] = ff_to_double(mph) - g.self * q;
+            f_out[3 * static_cast<size_t>(i) + 0] = -q * ff_to_double(mgx);
+            f_out[3 * static_cast<size_t>(i) + 1] = -q * ff_to_double(mgy);
+            f_out[3 * static_cast<size_t>(i) + 2] = -q * ff_to_double(mgz);
+        }
+    }
+}
+
+// ---- real-space sum of R in float-float (cell traversal of k_short) ---------------------------------
+// Candidates pass the float32 test of k_short (rounded positions, cutoff enlarged by 1e-4); survivors
+// get the displacement in float-float, d = (hi_i - (hi_j + s_hi)) + (lo_i - (lo_j + s_lo)) with the
+// first difference and the cell shift split exactly (TwoSum), then R and -R'/r from the radial
+// polynomials by float-float Horner, 1/r by a float32 estimate refined by one float-float Newton step,
+// and compensated accumulation.
+constexpr int kShortFFMaxT = 8;
+
+template <int D>
+struct ShortParamsFF {
+    float p1h[D + 1], p1l[D + 1], qh[D + 1], ql[D + 1];
+    float rc2h, rc2l, two_over_rc2_h, two_over_rc2_l;
+    float rc2f;
+};
+
+template <int D>
+__global__ void __launch_bounds__(32 * kShortWarps) k_short_ff(const float4* __restrict__ rec_h,
+                                                               const float4* __restrict__ rec_l,
+                                                               const int2* __restrict__ idx,
+                                                               const int* __restrict__ cz_of,
+                                                               const int* __restrict__ cell_off,
+                                                               const int4* __restrict__ cols, int ncols, Geom g,
+                                                               const __grid_constant__ ShortParamsFF<D> kp,
+                                                               double* __restrict__ phi_out,
+                                                               double* __restrict__ f_out) {
+    constexpr int NSH = 2 * kShortMaxR + 1, MT = kShortFFMaxT;
+    __shared__ float sh_hi[NSH], sh_lo[NSH];
+    __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
+    __shared__ int4 srng[kShortWarps][kShortMaxRanges];
+    __shared__ int spos[kShortWarps][kShortMaxRanges + 1];
+    __shared__ float4 sth[kShortWarps][MT], stl[kShortWarps][MT];
+    const int R = g.reach, nc = g.ncell;
+    for (int k = threadIdx.x; k < 2 * R + 1; k += blockDim.x) split_ff((k - R) * g.cellw, sh_hi[k], sh_lo[k]);
+    for (int k = threadIdx.x; k < ncols; k += blockDim.x) scol[k] = cols[k];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * kShortWarps + warp;
+    if (c >= nc * nc * nc) return;
+    const int tb = cell_off[c], te = cell_off[c + 1];
+    if (tb == te) return;
+    const int cz = c % nc, cy = (c / nc) % nc, cx = c / (nc * nc);
+    int4* rng = srng[warp];
+    int* pos = spos[warp];
+    auto wrap = [nc](int v) {   // v in (-2 nc, 2 nc) -> [0, nc)
+        v += v < 0 ? nc : 0;
+        v += v < 0 ? nc : 0;
+        v -= v >= nc ? nc : 0;
+        v -= v >= nc ? nc : 0;
+        return v;
+    };
+    // flatten the neighbour ranges (as in k_short)
+    int nr = 0;
+    for (int k0 = 0; k0 < ncols; k0 += 32) {
+        const int k = k0 + lane;
+        int npc = 0;
+        int4 col = make_int4(0, 0, -1, 0);
+        int base = 0;
+        if (k < ncols) {
+            col = scol[k];
+            base = (wrap(cx + col.x) * nc + wrap(cy + col.y)) * nc;
+            for (int d = -col.z; d <= col.z;) {
+                const int zw = wrap(cz + d);
+                d += min(col.z - d + 1, nc - zw);
+                ++npc;
+            }
+        }
+        int incl = npc;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int slot = nr + incl - npc;
+        if (k < ncols) {
+            for (int d = -col.z; d <= col.z;) {
+                const int zw = wrap(cz + d);
+                const int len = min(col.z - d + 1, nc - zw);
+                if (slot < kShortMaxRanges) {
+                    const int a = cell_off[base + zw], b = cell_off[base + zw + len];
+                    rng[slot] = make_int4(a, zw, d, k);
+                    pos[slot] = b - a;
+                }
+                ++slot;
+                d += len;
+            }
+        }
+        nr += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    nr = min(nr, kShortMaxRanges);
+    __syncwarp();
+    int total = 0;
+    for (int r0 = 0; r0 < nr; r0 += 32) {
+        const int r = r0 + lane;
+        const int len = r < nr ? pos[r] : 0;
+        int incl = len;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        __syncwarp();
+        if (r < nr) pos[r] = total + incl - len;
+        total += __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+    }
+    if (lane == 0) pos[nr] = total;
+    __syncwarp();
+
+    const ff rc2{kp.rc2h, kp.rc2l}, two_over_rc2{kp.two_over_rc2_h, kp.two_over_rc2_l};
+    for (int t0 = tb; t0 < te; t0 += MT) {
+        const int nt = min(MT, te - t0);
+        __syncwarp();
+        if (lane < nt) {
+            sth[warp][lane] = rec_h[t0 + lane];
+            stl[warp][lane] = rec_l[t0 + lane];
+        }
+        __syncwarp();
+        float tf[MT][3];
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+            const float4 a = sth[warp][t < nt ? t : 0];
+            tf[t][0] = a.x;
+            tf[t][1] = a.y;
+            tf[t][2] = a.z;
+        }
+        ff acc[MT][4];
+#pragma unroll
+        for (int t = 0; t < MT; ++t)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[t][v] = ff{0.f, 0.f};
+        int r = 0;
+        for (int s0 = 0; s0 < total; s0 += 32) {
+            const int p = s0 + lane;
+            if (p >= total) continue;
+            while (pos[r + 1] <= p) ++r;
+            const int4 rg = rng[r];
+            const int j = rg.x + (p - pos[r]);
+            const float4 sh = rec_h[j];
+            const int4 col = scol[rg.w];
+            const int ix = col.x + R, iy = col.y + R, iz = rg.z + (cz_of[j] - rg.y) + R;
+            const float px = sh.x + sh_hi[ix], py = sh.y + sh_hi[iy], pz = sh.z + sh_hi[iz];
+            bool loaded = false;
+            ff qj{0.f, 0.f}, ex{0.f, 0.f}, ey{0.f, 0.f}, ez{0.f, 0.f};
+            float lx = 0.f, ly = 0.f, lz = 0.f;
+#pragma unroll
+            for (int t = 0; t < MT; ++t) {
+                if (t >= nt) break;   // warp-uniform
+                const float dxf = tf[t][0] - px, dyf = tf[t][1] - py, dzf = tf[t][2] - pz;
+                const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
+                if (!(r2f < kp.rc2f && r2f > 0.f)) continue;
+                if (!loaded) {
+                    loaded = true;
+                    const float4 sl = rec_l[j];
+                    qj = ff{sh.w, sl.w};
+                    // source position seen from the target cell: (ex.h + ex.l) = hi_j + s_hi exactly,
+                    // plus the low parts lo_j + s_lo
+                    ex = two_sum(sh.x, sh_hi[ix]);
+                    ey = two_sum(sh.y, sh_hi[iy]);
+                    ez = two_sum(sh.z, sh_hi[iz]);
+                    lx = __fadd_rn(__fadd_rn(sl.x, sh_lo[ix]), ex.l);
+                    ly = __fadd_rn(__fadd_rn(sl.y, sh_lo[iy]), ey.l);
+                    lz = __fadd_rn(__fadd_rn(sl.z, sh_lo[iz]), ez.l);
+                }
+                const float4 tl = stl[warp][t];
+                ff dx = two_sum(tf[t][0], -ex.h), dy = two_sum(tf[t][1], -ey.h), dz = two_sum(tf[t][2], -ez.h);
+                dx = two_sum(dx.h, __fadd_rn(dx.l, __fadd_rn(tl.x, -lx)));
+                dy = two_sum(dy.h, __fadd_rn(dy.l, __fadd_rn(tl.y, -ly)));
+                dz = two_sum(dz.h, __fadd_rn(dz.l, __fadd_rn(tl.z, -lz)));
+                const ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
+                if (!(r2.h < rc2.h || (r2.h == rc2.h && r2.l < rc2.l)) || !(r2.h > 0.f)) continue;
+                const ff u = ff_add(ff_mul(r2, two_over_rc2), ff_make(-1.f));
+                ff p1{kp.p1h[D], kp.p1l[D]}, qq{kp.qh[D], kp.ql[D]};
+#pragma unroll
+                for (int kk = D - 1; kk >= 0; --kk) {
+                    p1 = ff_add(ff_mul(p1, u), ff{kp.p1h[kk], kp.p1l[kk]});
+                    qq = ff_add(ff_mul(qq, u), ff{kp.qh[kk], kp.ql[kk]});
+                }
+                const ff ri = ff_rsqrt(r2);
+                ff_acc(acc[t][0], qj, ff_sub(ri, p1));
+                const ff cf = ff_mul(qj, ff_add(ff_mul(ff_sqr(ri), ri), qq));
+                ff_acc(acc[t][1], cf, dx);
+                ff_acc(acc[t][2], cf, dy);
+                ff_acc(acc[t][3], cf, dz);
+            }
+        }
+        // reduce each target's sums over the lanes; lane t writes target t
+#pragma unroll
+        for (int t = 0; t < MT; ++t)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                ff x = ff_norm(acc[t][v]);
+                for (int o = 16; o > 0; o >>= 1) x = ff_add(x, ff_shfl_xor(x, o));
+                acc[t][v] = x;
+            }
+        ff mine[4] = {ff{0.f, 0.f}, ff{0.f, 0.f}, ff{0.f, 0.f}, ff{0.f, 0.f}};
+#pragma unroll
+        for (int t = 0; t < MT; ++t)
+            if (lane == t) {
+                mine[0] = acc[t][0];
+                mine[1] = acc[t][1];
+                mine[2] = acc[t][2];
+                mine[3] = acc[t][3];
+            }
+        if (lane < nt) {   // float64 conversions once per pass, lane-parallel
+            const int oi = idx[t0 + lane].y;
+            const double qi = static_cast<double>(sth[warp][lane].w) + static_cast<double>(stl[warp][lane].w);
+            phi_out[oi] = ff_to_double(mine[0]);
+            f_out[3 * static_cast<size_t>(oi) + 0] = qi * ff_to_double(mine[1]);
+            f_out[3 * static_cast<size_t>(oi) + 1] = qi * ff_to_double(mine[2]);
+            f_out[3 * static_cast<size_t>(oi) + 2] = qi * ff_to_double(mine[3]);
+        }
+    }
+}
+
+}  // namespace pswf

@@ -404,7 +404,8 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
     if (!(L > 0) || !std::isfinite(L)) throw std::invalid_argument("L must be positive and finite");
     if (n < 2) throw std::invalid_argument("n must be at least 2");
     if (!(tol >= 1e-13 && tol <= 1e-2)) throw std::invalid_argument("tol must lie in [1e-13, 1e-2]");
-    if (o.precision != EWALD_FP64 && o.precision != EWALD_MIXED) throw std::invalid_argument("unknown precision");
+    if (o.precision != EWALD_FP64 && o.precision != EWALD_MIXED && o.precision != EWALD_FLOATFLOAT)
+        throw std::invalid_argument("unknown precision");
     if (!(o.tol_safety > 0 && o.tol_safety <= 1)) throw std::invalid_argument("tol_safety must lie in (0, 1]");
     if (!(o.grid_density > 0)) throw std::invalid_argument("grid_density must be positive");
     if (o.window_extra < 0 || o.window_extra > 8) throw std::invalid_argument("window_extra must lie in [0, 8]");
@@ -463,8 +464,8 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
     p.cw_target = cw_t;
     p.cw = kPi * P / 2.0;                                 // eq. cwP
     p.alpha = P * p.h / 2.0;
-    // float32 products cannot reach tol < 1e-7; below it MIXED runs the float64 kernels
-    p.precision = (o.precision == EWALD_MIXED && tol < 1e-7) ? EWALD_FP64 : o.precision;
+    // float32 products cannot reach tol < 1e-7; below it MIXED runs the float-float kernels
+    p.precision = (o.precision == EWALD_MIXED && tol < 1e-7) ? EWALD_FLOATFLOAT : o.precision;
     p.tile = 4;
     // real-space cells of edge >= rc / reach; the automatic reach aims at ~3 particles per cell
     int reach = o.sr_reach;

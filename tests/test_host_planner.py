@@ -132,3 +132,19 @@ def test_scale_table_matches_oracle(L, n, tol):
     D = (ph1[:, None, None] * ph1[None, :, None] * ph1[None, None, :])[:, :, : p.m // 2 + 1] ** 2
     M = So * D
     assert np.max(np.abs(S * D - M)) <= 1e-12 * np.max(M)
+
+
+def test_precision_paths():
+    """MIXED below tol 1e-7 runs the float-float kernels; float-float plans size their fits like FP64."""
+    for tol in (1e-8, 1e-10, 1e-12):
+        pm = pe.plan_params(1.0, 50_000, tol, precision="mixed")
+        pf = pe.plan_params(1.0, 50_000, tol, precision="floatfloat")
+        p64 = pe.plan_params(1.0, 50_000, tol, precision="fp64")
+        assert pm.precision == pf.precision == pe.EWALD_FLOATFLOAT
+        assert p64.precision == pe.EWALD_FP64
+        for k in ("m", "P", "deg_w", "deg_r", "fit_tol", "rc"):
+            assert getattr(pf, k) == getattr(p64, k)
+    assert pe.plan_params(1.0, 50_000, 1e-6, precision="mixed").precision == pe.EWALD_MIXED
+    assert pe.plan_params(1.0, 50_000, 1e-6, precision="floatfloat").precision == pe.EWALD_FLOATFLOAT
+    with pytest.raises(pe.EwaldError):
+        pe.plan_params(1.0, 50_000, 1e-6, precision=7)
