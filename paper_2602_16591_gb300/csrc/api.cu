@@ -81,6 +81,27 @@ int ff_split_index(const pswf::HostPlan& hp) {
     return d;
 }
 
+// Smallest kr such that float32 Horner steps over the radial terms k >= kr err by at most
+// 2.5 fit_tol max|f| (= tol_plan / 20 of the polynomial's scale; the pair errors enter the potential with
+// random signs): 2^-23 (deg_r - kr + 1) sum_{k >= kr} |c_k| (|u| <= 1).  deg_r + 1: all float-float.
+int ff_radial_split(const pswf::HostPlan& hp) {
+    const int d = hp.p.deg_r;
+    auto smax = [&](const std::vector<double>& c) {
+        double m = 0;
+        for (int i = 0; i <= 200; ++i) m = std::max(m, std::fabs(pswf::horner(c.data(), d, -1.0 + i / 100.0)));
+        return m;
+    };
+    const double s1 = smax(hp.p1c), s2 = smax(hp.qc);
+    auto ok = [&](const std::vector<double>& c, int kr, double sc) {
+        double t = 0;
+        for (int k = kr; k <= d; ++k) t += std::fabs(c[k]);
+        return std::ldexp(t * (d - kr + 1), -23) <= 2.5 * hp.p.fit_tol * sc;
+    };
+    for (int kr = 1; kr <= d; ++kr)
+        if (ok(hp.p1c, kr, s1) && ok(hp.qc, kr, s2)) return kr;
+    return d + 1;
+}
+
 }  // namespace
 
 namespace pswf {
@@ -95,6 +116,7 @@ struct ewald_plan_s {
     bool fp64 = true;   // grid, FFT and scaling in float64 (EWALD_FP64 and EWALD_FLOATFLOAT plans)
     bool ff = false;    // float-float particle kernels (EWALD_FLOATFLOAT)
     int ff_kf = 1;      // window polynomial terms k >= ff_kf are summed in float32 (float-float plans)
+    int ff_kr = 1;      // radial polynomial terms k >= ff_kr likewise
     int ntiles = 0, ncells = 0, epart_blocks = 0;
     // workspace
     int* key_rank = nullptr;
@@ -323,7 +345,7 @@ int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* ph
     PSWF_CUDA(cudaStreamWaitEvent(p->s_short, p->ev_fork, 0));
     p->mark(7, false, p->s_short);
     PSWF_CUDA(LaunchFF::short_range(g, sr_h, sr_l, p->sr_idx, p->sr_cz, p->cell_off, p->sr_cols, p->n_cols,
-                                    p->hp.p1c.data(), p->hp.qc.data(), p->phi_sr, p->f_sr, p->s_short));
+                                    p->hp.p1c.data(), p->hp.qc.data(), p->ff_kr, p->phi_sr, p->f_sr, p->s_short));
     p->mark(7, true, p->s_short);
     PSWF_CUDA(cudaEventRecord(p->ev_join, p->s_short));
     const cudaStream_t caller = s;
@@ -570,6 +592,7 @@ int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, e
     int rc = EWALD_OK;
     if (p->ff) {
         p->ff_kf = ff_split_index(p->hp);
+        p->ff_kr = ff_radial_split(p->hp);
         if ((rc = upload_ff(reinterpret_cast<float**>(&p->wcoef), p->hp.wc)) ||
             (rc = upload_ff(reinterpret_cast<float**>(&p->dwcoef), p->hp.dwc)) ||
             (rc = upload<double>(reinterpret_cast<double**>(&p->iw), p->hp.iw)) ||

@@ -48,7 +48,7 @@ cudaError_t interp_p(int ntiles, const Geom& g, const float2* grid, const float4
 
 template <int D>
 cudaError_t short_d(const Geom& g, const float4* rh, const float4* rl, const int2* idx, const int* cz,
-                    const int* cell_off, const int4* cols, int ncols, const double* p1c, const double* qc,
+                    const int* cell_off, const int4* cols, int ncols, const double* p1c, const double* qc, int kr,
                     double* phi, double* f, cudaStream_t s) {
     ShortParamsFF<D> kp{};
     for (int k = 0; k <= D; ++k) {
@@ -58,6 +58,7 @@ cudaError_t short_d(const Geom& g, const float4* rh, const float4* rl, const int
     split(g.rc * g.rc, kp.rc2h, kp.rc2l);
     split(2.0 / (g.rc * g.rc), kp.two_over_rc2_h, kp.two_over_rc2_l);
     kp.rc2f = static_cast<float>(g.rc * g.rc * (1.0 + 1e-4));
+    kp.kr = kr;
     const int ncells = g.ncell * g.ncell * g.ncell;
     k_short_ff<D><<<(ncells + kShortWarps - 1) / kShortWarps, 32 * kShortWarps, 0, s>>>(
         rh, rl, idx, cz, cell_off, cols, ncols, g, kp, phi, f);
@@ -114,16 +115,16 @@ cudaError_t LaunchFF::interp(int ntiles, const Geom& g, const float2* grid, cons
 
 cudaError_t LaunchFF::short_range(const Geom& g, const float4* rec_h, const float4* rec_l, const int2* idx,
                                   const int* cz, const int* cell_off, const int4* cols, int ncols, const double* p1c,
-                                  const double* qc, double* phi, double* f, cudaStream_t s) {
+                                  const double* qc, int kr, double* phi, double* f, cudaStream_t s) {
     const int d = g.degr;
-    if (d <= 8) return short_d<8>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, phi, f, s);
-    if (d <= 12) return short_d<12>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, phi, f, s);
-    if (d <= 16) return short_d<16>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, phi, f, s);
-    if (d <= 20) return short_d<20>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, phi, f, s);
-    if (d <= 24) return short_d<24>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, phi, f, s);
-    if (d <= 32) return short_d<32>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, phi, f, s);
-    if (d <= 44) return short_d<44>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, phi, f, s);
-    return short_d<60>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, phi, f, s);
+    if (d <= 8) return short_d<8>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
+    if (d <= 12) return short_d<12>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
+    if (d <= 16) return short_d<16>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
+    if (d <= 20) return short_d<20>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
+    if (d <= 24) return short_d<24>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
+    if (d <= 32) return short_d<32>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
+    if (d <= 44) return short_d<44>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
+    return short_d<60>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
 }
 
 }  // namespace pswf

@@ -184,7 +184,7 @@ static __global__ void k_grid_to_ff(const double* __restrict__ grid, size_t coun
 // ---- Alg. 2 step 5 with eq. force: interpolation in float-float ------------------------------------
 // Structure of k_interp (tile block in shared memory, a warp per batch of particles, lanes over the
 // (b, c) pairs of the stencil); the inner sums over a are compensated dot products (ff_acc).
-constexpr int kInterpFFNB = 4, kInterpFFWarps = 4;
+constexpr int kInterpFFNB = 4, kInterpFFWarps = 8;
 
 template <int P>
 __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2* __restrict__ grid,
@@ -244,21 +244,27 @@ __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2*
             const int ox = id.x & 0xff, oy = (id.x >> 8) & 0xff, oz = (id.x >> 16) & 0xff;
             const ff* wp = ww + j * 6 * P;
             ff ph{0.f, 0.f}, gx{0.f, 0.f}, gy{0.f, 0.f}, gz{0.f, 0.f};
-#pragma unroll
-            for (int qi = 0; qi < NQ; ++qi) {
+#pragma unroll 1
+            for (int qi = 0; qi < NQ; ++qi) {   // not unrolled: the a-loop body is already P x 48 instructions
                 const int q = lane + 32 * qi;
                 if (q < P * P) {
                     const int bb = q / P, cc = q - (q / P) * P;
                     const ff* col = G + (ox * E + oy + bb) * E + oz + cc;
-                    ff s1{0.f, 0.f}, s2{0.f, 0.f};
+                    // four independent compensated chains (even / odd a) for instruction-level parallelism
+                    ff s1a{0.f, 0.f}, s1b{0.f, 0.f}, s2a{0.f, 0.f}, s2b{0.f, 0.f};
 #pragma unroll
-                    for (int a = 0; a < P; ++a) {
+                    for (int a = 0; a < P; a += 2) {
                         const ff v = col[a * E * E];
-                        ff_acc(s1, v, wp[a]);
-                        ff_acc(s2, v, wp[3 * P + a]);
+                        ff_acc(s1a, v, wp[a]);
+                        ff_acc(s2a, v, wp[3 * P + a]);
+                        if (a + 1 < P) {
+                            const ff v2 = col[(a + 1) * E * E];
+                            ff_acc(s1b, v2, wp[a + 1]);
+                            ff_acc(s2b, v2, wp[3 * P + a + 1]);
+                        }
                     }
-                    s1 = ff_norm(s1);
-                    s2 = ff_norm(s2);
+                    const ff s1 = ff_add(ff_norm(s1a), ff_norm(s1b));
+                    const ff s2 = ff_add(ff_norm(s2a), ff_norm(s2b));
                     const ff wy = wp[P + bb], wz = wp[2 * P + cc];
                     const ff dwy = wp[4 * P + bb], dwz = wp[5 * P + cc];
                     const ff yz = ff_mul(wy, wz);
@@ -297,23 +303,40 @@ __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2*
     }
 }
 
-// ---- real-space sum of R in float-float (cell traversal of k_short) ---------------------------------
-// Candidates pass the float32 test of k_short (rounded positions, cutoff enlarged by 1e-4); survivors
-// get the displacement in float-float, d = (hi_i - (hi_j + s_hi)) + (lo_i - (lo_j + s_lo)) with the
-// first difference and the cell shift split exactly (TwoSum), then R and -R'/r from the radial
-// polynomials by float-float Horner, 1/r by a float32 estimate refined by one float-float Newton step,
-// and compensated accumulation.
-constexpr int kShortFFMaxT = 8;
+// ---- real-space sum of R in float-float ---------------------------------------------------------
+// Cell traversal of k_short (a warp per target cell, flattened neighbour ranges), split in two phases
+// because one float-float pair costs ~40x a float32 cutoff test:
+//  scan     lanes take 32 consecutive candidate sources, test each against the pass's targets in
+//           float32 (rounded positions, cutoff enlarged by 1e-4) and append the passing (source,
+//           target) pairs to a per-warp queue in shared memory (warp prefix sum of the counts);
+//  compute  whenever 32 pairs are queued, every lane evaluates one pair in float-float: the
+//           displacement d = (hi_i - (hi_j + s_hi)) + (lo_i - (lo_j + s_lo)) with the leading
+//           difference and the cell shift split exactly (TwoSum), R and -R'/r from the radial
+//           polynomials by float-float Horner, 1/r from a float32 estimate with a float-float
+//           correction, and compensated accumulation into the lane's sums for that target.
+// The expensive part thus runs on full warps and exists once in the code.
+constexpr int kShortFFMaxT = 8;                                  // targets per pass (sums in registers)
+constexpr int kShortFFQueue = 32 + 32 * kShortFFMaxT;            // < 32 left after every drain
 
+// Radial polynomials padded with zeros to degree D; terms k >= kr (tiny, chosen on the host) are summed
+// by float32 Horner steps in u.h, the terms below kr in float-float.
 template <int D>
 struct ShortParamsFF {
     float p1h[D + 1], p1l[D + 1], qh[D + 1], ql[D + 1];
     float rc2h, rc2l, two_over_rc2_h, two_over_rc2_l;
     float rc2f;
+    int kr;
 };
 
+// acc += c for an unnormalised accumulator (error terms collected in acc.l)
+__device__ __forceinline__ void ff_acc_sum(ff& acc, ff c) {
+    const ff s = two_sum(acc.h, c.h);
+    acc.h = s.h;
+    acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, c.l));
+}
+
 template <int D>
-__global__ void __launch_bounds__(32 * kShortWarps) k_short_ff(const float4* __restrict__ rec_h,
+__global__ void __launch_bounds__(32 * kShortWarps, 4) k_short_ff(const float4* __restrict__ rec_h,
                                                                const float4* __restrict__ rec_l,
                                                                const int2* __restrict__ idx,
                                                                const int* __restrict__ cz_of,
@@ -323,11 +346,13 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_ff(const float4* __r
                                                                double* __restrict__ phi_out,
                                                                double* __restrict__ f_out) {
     constexpr int NSH = 2 * kShortMaxR + 1, MT = kShortFFMaxT;
+    static_assert(NSH <= 16 && MT <= 16, "queue entries pack 4-bit fields");
     __shared__ float sh_hi[NSH], sh_lo[NSH];
     __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
     __shared__ int4 srng[kShortWarps][kShortMaxRanges];
     __shared__ int spos[kShortWarps][kShortMaxRanges + 1];
     __shared__ float4 sth[kShortWarps][MT], stl[kShortWarps][MT];
+    __shared__ int2 sq[kShortWarps][kShortFFQueue];   // {source, target | ix << 4 | iy << 8 | iz << 12}
     const int R = g.reach, nc = g.ncell;
     for (int k = threadIdx.x; k < 2 * R + 1; k += blockDim.x) split_ff((k - R) * g.cellw, sh_hi[k], sh_lo[k]);
     for (int k = threadIdx.x; k < ncols; k += blockDim.x) scol[k] = cols[k];
@@ -340,6 +365,7 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_ff(const float4* __r
     const int cz = c % nc, cy = (c / nc) % nc, cx = c / (nc * nc);
     int4* rng = srng[warp];
     int* pos = spos[warp];
+    int2* queue = sq[warp];
     auto wrap = [nc](int v) {   // v in (-2 nc, 2 nc) -> [0, nc)
         v += v < 0 ? nc : 0;
         v += v < 0 ? nc : 0;
@@ -412,74 +438,106 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_ff(const float4* __r
             stl[warp][lane] = rec_l[t0 + lane];
         }
         __syncwarp();
-        float tf[MT][3];
-#pragma unroll
-        for (int t = 0; t < MT; ++t) {
-            const float4 a = sth[warp][t < nt ? t : 0];
-            tf[t][0] = a.x;
-            tf[t][1] = a.y;
-            tf[t][2] = a.z;
-        }
         ff acc[MT][4];
 #pragma unroll
         for (int t = 0; t < MT; ++t)
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[t][v] = ff{0.f, 0.f};
-        int r = 0;
-        for (int s0 = 0; s0 < total; s0 += 32) {
-            const int p = s0 + lane;
-            if (p >= total) continue;
-            while (pos[r + 1] <= p) ++r;
-            const int4 rg = rng[r];
-            const int j = rg.x + (p - pos[r]);
-            const float4 sh = rec_h[j];
-            const int4 col = scol[rg.w];
-            const int ix = col.x + R, iy = col.y + R, iz = rg.z + (cz_of[j] - rg.y) + R;
-            const float px = sh.x + sh_hi[ix], py = sh.y + sh_hi[iy], pz = sh.z + sh_hi[iz];
-            bool loaded = false;
-            ff qj{0.f, 0.f}, ex{0.f, 0.f}, ey{0.f, 0.f}, ez{0.f, 0.f};
-            float lx = 0.f, ly = 0.f, lz = 0.f;
+
+        // one queued pair -> the lane's sums of its target
+        auto pair = [&](int2 e) {
+            const int t = e.y & 15, ix = (e.y >> 4) & 15, iy = (e.y >> 8) & 15, iz = (e.y >> 12) & 15;
+            const float4 sh = rec_h[e.x], sl = rec_l[e.x];
+            const float4 th = sth[warp][t], tl = stl[warp][t];
+            const ff ex = two_sum(sh.x, sh_hi[ix]), ey = two_sum(sh.y, sh_hi[iy]), ez = two_sum(sh.z, sh_hi[iz]);
+            const float lx = __fadd_rn(__fadd_rn(sl.x, sh_lo[ix]), ex.l);
+            const float ly = __fadd_rn(__fadd_rn(sl.y, sh_lo[iy]), ey.l);
+            const float lz = __fadd_rn(__fadd_rn(sl.z, sh_lo[iz]), ez.l);
+            ff dx = two_sum(th.x, -ex.h), dy = two_sum(th.y, -ey.h), dz = two_sum(th.z, -ez.h);
+            dx = two_sum(dx.h, __fadd_rn(dx.l, __fadd_rn(tl.x, -lx)));
+            dy = two_sum(dy.h, __fadd_rn(dy.l, __fadd_rn(tl.y, -ly)));
+            dz = two_sum(dz.h, __fadd_rn(dz.l, __fadd_rn(tl.z, -lz)));
+            const ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
+            const bool in = (r2.h < rc2.h || (r2.h == rc2.h && r2.l < rc2.l)) && r2.h > 0.f;
+            const ff u = ff_add(ff_mul(r2, two_over_rc2), ff_make(-1.f));
+            float p1f = kp.p1h[D], qqf = kp.qh[D];
+            ff p1 = ff_make(p1f), qq = ff_make(qqf);
 #pragma unroll
-            for (int t = 0; t < MT; ++t) {
-                if (t >= nt) break;   // warp-uniform
-                const float dxf = tf[t][0] - px, dyf = tf[t][1] - py, dzf = tf[t][2] - pz;
-                const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
-                if (!(r2f < kp.rc2f && r2f > 0.f)) continue;
-                if (!loaded) {
-                    loaded = true;
-                    const float4 sl = rec_l[j];
-                    qj = ff{sh.w, sl.w};
-                    // source position seen from the target cell: (ex.h + ex.l) = hi_j + s_hi exactly,
-                    // plus the low parts lo_j + s_lo
-                    ex = two_sum(sh.x, sh_hi[ix]);
-                    ey = two_sum(sh.y, sh_hi[iy]);
-                    ez = two_sum(sh.z, sh_hi[iz]);
-                    lx = __fadd_rn(__fadd_rn(sl.x, sh_lo[ix]), ex.l);
-                    ly = __fadd_rn(__fadd_rn(sl.y, sh_lo[iy]), ey.l);
-                    lz = __fadd_rn(__fadd_rn(sl.z, sh_lo[iz]), ez.l);
-                }
-                const float4 tl = stl[warp][t];
-                ff dx = two_sum(tf[t][0], -ex.h), dy = two_sum(tf[t][1], -ey.h), dz = two_sum(tf[t][2], -ez.h);
-                dx = two_sum(dx.h, __fadd_rn(dx.l, __fadd_rn(tl.x, -lx)));
-                dy = two_sum(dy.h, __fadd_rn(dy.l, __fadd_rn(tl.y, -ly)));
-                dz = two_sum(dz.h, __fadd_rn(dz.l, __fadd_rn(tl.z, -lz)));
-                const ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
-                if (!(r2.h < rc2.h || (r2.h == rc2.h && r2.l < rc2.l)) || !(r2.h > 0.f)) continue;
-                const ff u = ff_add(ff_mul(r2, two_over_rc2), ff_make(-1.f));
-                ff p1{kp.p1h[D], kp.p1l[D]}, qq{kp.qh[D], kp.ql[D]};
-#pragma unroll
-                for (int kk = D - 1; kk >= 0; --kk) {
+            for (int kk = D - 1; kk >= 0; --kk) {
+                if (kk >= kp.kr) {   // warp-uniform
+                    p1f = fmaf(p1f, u.h, kp.p1h[kk]);
+                    qqf = fmaf(qqf, u.h, kp.qh[kk]);
+                    p1 = ff_make(p1f);
+                    qq = ff_make(qqf);
+                } else {
                     p1 = ff_add(ff_mul(p1, u), ff{kp.p1h[kk], kp.p1l[kk]});
                     qq = ff_add(ff_mul(qq, u), ff{kp.qh[kk], kp.ql[kk]});
                 }
-                const ff ri = ff_rsqrt(r2);
-                ff_acc(acc[t][0], qj, ff_sub(ri, p1));
-                const ff cf = ff_mul(qj, ff_add(ff_mul(ff_sqr(ri), ri), qq));
-                ff_acc(acc[t][1], cf, dx);
-                ff_acc(acc[t][2], cf, dy);
-                ff_acc(acc[t][3], cf, dz);
+            }
+            const ff ri = ff_rsqrt(in ? r2 : ff_make(1.f));
+            const ff qj = in ? ff{sh.w, sl.w} : ff{0.f, 0.f};
+            const ff c0 = ff_mul(qj, ff_sub(ri, p1));
+            const ff cf = ff_mul(qj, ff_add(ff_mul(ff_sqr(ri), ri), qq));
+            const ff c1 = ff_mul(cf, dx), c2 = ff_mul(cf, dy), c3 = ff_mul(cf, dz);
+#pragma unroll
+            for (int tt = 0; tt < MT; ++tt)
+                if (tt == t) {
+                    ff_acc_sum(acc[tt][0], c0);
+                    ff_acc_sum(acc[tt][1], c1);
+                    ff_acc_sum(acc[tt][2], c2);
+                    ff_acc_sum(acc[tt][3], c3);
+                }
+        };
+
+        int r = 0, qlen = 0;
+        for (int s0 = 0; s0 < total; s0 += 32) {
+            // scan: float32 test of candidate p against every target of the pass
+            const int p = s0 + lane;
+            unsigned mask = 0u;
+            int j = 0, meta = 0;
+            if (p < total) {
+                while (pos[r + 1] <= p) ++r;
+                const int4 rg = rng[r];
+                j = rg.x + (p - pos[r]);
+                const float4 sh = rec_h[j];
+                const int4 col = scol[rg.w];
+                const int ix = col.x + R, iy = col.y + R, iz = rg.z + (cz_of[j] - rg.y) + R;
+                const float px = sh.x + sh_hi[ix], py = sh.y + sh_hi[iy], pz = sh.z + sh_hi[iz];
+#pragma unroll
+                for (int t = 0; t < MT; ++t) {
+                    if (t >= nt) break;   // warp-uniform
+                    const float4 a = sth[warp][t];
+                    const float dxf = a.x - px, dyf = a.y - py, dzf = a.z - pz;
+                    const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
+                    if (r2f < kp.rc2f && r2f > 0.f) mask |= 1u << t;
+                }
+                meta = (ix << 4) | (iy << 8) | (iz << 12);
+            }
+            const int cnt = __popc(mask);
+            int incl = cnt;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            int slot = qlen + incl - cnt;
+            while (mask) {
+                const int t = __ffs(mask) - 1;
+                mask &= mask - 1u;
+                queue[slot++] = make_int2(j, meta | t);
+            }
+            qlen += __shfl_sync(0xffffffffu, incl, 31);
+            __syncwarp();
+            // compute: full warps of queued pairs
+            while (qlen >= 32) {
+                const int2 e = queue[qlen - 32 + lane];
+                __syncwarp();
+                qlen -= 32;
+                pair(e);
             }
         }
+        if (lane < qlen) pair(queue[lane]);
+        __syncwarp();
+
         // reduce each target's sums over the lanes; lane t writes target t
 #pragma unroll
         for (int t = 0; t < MT; ++t)

@@ -34,10 +34,11 @@ struct LaunchFF {
     static cudaError_t interp(int ntiles, const Geom& g, const float2* grid, const float4* rec_h, const float4* rec_l,
                               const int2* idx, const int* tile_off, const float* wc, const float* dwc, int kf,
                               double inv_alpha, double* phi, double* f, cudaStream_t s);
-    // radial polynomials p1c / qc of degree g.degr (float64 coefficients, split on the host)
+    // radial polynomials p1c / qc of degree g.degr (float64 coefficients, split on the host); terms
+    // k >= kr are summed in float32
     static cudaError_t short_range(const Geom& g, const float4* rec_h, const float4* rec_l, const int2* idx,
                                    const int* cz, const int* cell_off, const int4* cols, int ncols, const double* p1c,
-                                   const double* qc, double* phi, double* f, cudaStream_t s);
+                                   const double* qc, int kr, double* phi, double* f, cudaStream_t s);
 };
 
 }  // namespace pswf
