@@ -88,7 +88,8 @@ typedef struct ewald_params {
     int    P;          /* window support in grid points per axis */
     int    deg_w;      /* degree of the per-interval window polynomials (in z = 2f - 1) */
     int    deg_r;      /* degree of the radial polynomials (in u = 2 r^2 / r_c^2 - 1) */
-    int    tile;       /* spreading tile edge T (grid points), m % T == 0 */
+    int    tile;       /* spreading tile edge T (grid points), m % T == 0: 8 for EWALD_MIXED
+                          plans, 4 otherwise (m is rounded to a multiple of it) */
     int    ncell;      /* real-space cells per axis */
     int    sr_reach;   /* real-space neighbour reach in cells */
     int    precision;  /* path the plan runs: EWALD_FP64, EWALD_MIXED or EWALD_FLOATFLOAT */

@@ -73,8 +73,12 @@ def cw_of(cs, rc_over_L):
     return -0.5 * float(np.real(lambertw(z, -1)))
 
 
-def plan(L, n, tol, grid_density=1.0, rc=None, tol_safety=1.0):
-    """Alg. 3 with the readings above; returns a dict of plan parameters."""
+def plan(L, n, tol, grid_density=1.0, rc=None, tol_safety=1.0, mult=4):
+    """Alg. 3 with the readings above; returns a dict of plan parameters.
+
+    ``mult`` is the multiple m is rounded to (the library's spreading tile edge: 8 for its float32
+    plans, 4 otherwise); the paper only needs an even, FFT-friendly m.
+    """
     t = tol * tol_safety
 
     def cutoff(t):
@@ -92,7 +96,7 @@ def plan(L, n, tol, grid_density=1.0, rc=None, tol_safety=1.0):
         t *= 10.0 / m0
         rcl = cutoff(t)
     cs = cs_of(rcl, t)
-    m = good_size(math.ceil(cs / (math.pi * rcl)))
+    m = good_size(math.ceil(cs / (math.pi * rcl)), mult)
     rcl = cs / (math.pi * m)
     cw = cw_of(cs, rcl)
     alpha_over_L = rcl * cw / cs

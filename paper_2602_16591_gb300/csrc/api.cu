@@ -134,6 +134,7 @@ struct ewald_plan_s {
     void* grid_ff = nullptr;   // float-float plans: the interpolation grid as {hi, lo} float pairs
     int4* sr_cols = nullptr;   // real-space columns {dx, dy, dzmax, 0} with box distance < rc
     int n_cols = 0;
+    int sr_rcap = 0;           // bound on the contiguous source ranges of one neighbourhood
     void* scratch = nullptr;
     void* grid_a = nullptr;
     void* grid_b = nullptr;
@@ -211,8 +212,15 @@ cudaError_t launch_short_d(ewald_plan p, const pswf::Vec4<real>* sr_rec, const p
     kp.two_over_rc2 = static_cast<real>(2.0 / (g.rc * g.rc));
     kp.rc2f = static_cast<float>(g.rc * g.rc * (1.0 + 1e-4));
     const int ncells = g.ncell * g.ncell * g.ncell;
-    pswf::k_short<real, D><<<(ncells + pswf::kShortWarps - 1) / pswf::kShortWarps, 32 * pswf::kShortWarps, 0, s>>>(
-        sr_rec, p->sr_idx, sr_lo, p->sr_f32, p->cell_off, p->sr_cols, p->n_cols, g, kp, phi, f);
+    const size_t smem = pswf::short_dyn_smem(p->sr_rcap);
+    const int blocks = (ncells + pswf::kShortWarps - 1) / pswf::kShortWarps;
+    // float32 pairs are cheap: the direct kernel; float64 pairs: the two-phase (queued) kernel
+    if constexpr (sizeof(real) == 4)
+        pswf::k_short<real, D><<<blocks, 32 * pswf::kShortWarps, smem, s>>>(
+            sr_rec, p->sr_idx, sr_lo, p->sr_f32, p->cell_off, p->sr_cols, p->n_cols, p->sr_rcap, g, kp, phi, f);
+    else
+        pswf::k_short_q<real, D><<<blocks, 32 * pswf::kShortWarps, smem, s>>>(
+            sr_rec, p->sr_idx, sr_lo, p->sr_f32, p->cell_off, p->sr_cols, p->n_cols, p->sr_rcap, g, kp, phi, f);
     return cudaGetLastError();
 }
 
@@ -345,7 +353,8 @@ int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* ph
     PSWF_CUDA(cudaStreamWaitEvent(p->s_short, p->ev_fork, 0));
     p->mark(7, false, p->s_short);
     PSWF_CUDA(LaunchFF::short_range(g, sr_h, sr_l, p->sr_idx, p->sr_cz, p->cell_off, p->sr_cols, p->n_cols,
-                                    p->hp.p1c.data(), p->hp.qc.data(), p->ff_kr, p->phi_sr, p->f_sr, p->s_short));
+                                    p->sr_rcap, p->hp.p1c.data(), p->hp.qc.data(), p->ff_kr, p->phi_sr, p->f_sr,
+                                    p->s_short));
     p->mark(7, true, p->s_short);
     PSWF_CUDA(cudaEventRecord(p->ev_join, p->s_short));
     const cudaStream_t caller = s;
@@ -563,7 +572,8 @@ int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, e
         p->n_cols = static_cast<int>(cols.size());
         // every column's z-run splits into at most ceil((2R+1)/nc) + 1 contiguous pieces
         const int pieces = (2 * R + 1 + g.ncell - 1) / g.ncell + 1;
-        if (p->n_cols * pieces > pswf::kShortMaxRanges) {
+        p->sr_rcap = p->n_cols * pieces;
+        if (p->sr_rcap > pswf::kShortMaxRanges) {
             delete p;
             return fail(EWALD_EINVAL, "real-space neighbourhood has too many cell ranges for the kernel");
         }

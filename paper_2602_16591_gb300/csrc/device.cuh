@@ -28,7 +28,13 @@ struct Geom {
     double L, invL, h, invh, cellw, invcellw, rc, self;
 };
 
-constexpr int kTile = 4;   // spreading tile edge (grid points); m is a multiple of it
+// Spreading / interpolation tile edge (grid points); m is a multiple of it.  float32 plans use 8 (the
+// extended blocks of neighbouring tiles overlap (1 + (P-1)/8)^3 times instead of (1 + (P-1)/4)^3, and
+// an interpolation block serves ~8x more particles per staged grid block); float64 and float-float
+// plans, whose extended blocks are twice as large per value, use 4.
+constexpr int kTile32 = 8, kTile64 = 4;
+template <typename real>
+constexpr int spread_tile() { return sizeof(real) == 4 ? kTile32 : kTile64; }
 
 // Everything a particle needs, computed once from its position (float64).
 struct Located {
@@ -229,14 +235,14 @@ __device__ __forceinline__ void window_weights(const real* __restrict__ c, int d
 // block is written to a per-tile scratch slab; k_halo sums overlapping slabs (no atomics anywhere).
 constexpr int kSpreadChunk = 64;
 
-template <int P>
-constexpr int spread_threads() { return (((kTile + P - 1) * (kTile + P - 1) + 31) / 32) * 32; }
+template <int P, int T>
+constexpr int spread_threads() { return (((T + P - 1) * (T + P - 1) + 31) / 32) * 32; }
 
 template <typename real, int P>
-__global__ void __launch_bounds__(spread_threads<P>()) k_spread(const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
+__global__ void __launch_bounds__(spread_threads<P, spread_tile<real>()>()) k_spread(const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
                                                  const int* __restrict__ tile_off, const real* __restrict__ wcoef,
                                                  int degw, real* __restrict__ scratch) {
-    constexpr int T = kTile, E = T + P - 1, CH = kSpreadChunk;
+    constexpr int T = spread_tile<real>(), E = T + P - 1, CH = kSpreadChunk;
     const int tile = blockIdx.x;
     const int beg = tile_off[tile], end = tile_off[tile + 1];
     if (beg == end) return;
@@ -280,14 +286,20 @@ __global__ void __launch_bounds__(spread_threads<P>()) k_spread(const Vec4<real>
                 const real wyz = srho[j] * sw[(j * 3 + 1) * P + bb] * sw[(j * 3 + 2) * P + cc];
                 const real* wx = sw + (j * 3) * P;
                 switch (ox) {
-#define PSWF_SPREAD_CASE(O)                                               \
-    case O:                                                               \
-        _Pragma("unroll") for (int p = 0; p < P; ++p) acc[O + p] = fma(wyz, wx[p], acc[O + p]); \
+#define PSWF_SPREAD_CASE(O)                                                                    \
+    case O:                                                                                    \
+        if constexpr (O < T) {                                                                 \
+            _Pragma("unroll") for (int p = 0; p < P; ++p) acc[O + p] = fma(wyz, wx[p], acc[O + p]); \
+        }                                                                                      \
         break;
                     PSWF_SPREAD_CASE(0)
                     PSWF_SPREAD_CASE(1)
                     PSWF_SPREAD_CASE(2)
                     PSWF_SPREAD_CASE(3)
+                    PSWF_SPREAD_CASE(4)
+                    PSWF_SPREAD_CASE(5)
+                    PSWF_SPREAD_CASE(6)
+                    PSWF_SPREAD_CASE(7)
 #undef PSWF_SPREAD_CASE
                     default: break;
                 }
@@ -367,7 +379,7 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
                                                 const real* __restrict__ wcoef, const real* __restrict__ dwcoef,
                                                 Geom g, real inv_alpha, double* __restrict__ phi_out,
                                                 double* __restrict__ f_out) {
-    constexpr int T = kTile, E = T + P - 1;
+    constexpr int T = spread_tile<real>(), E = T + P - 1;
     constexpr int NB = InterpCfg<real>::NB, NWARP = InterpCfg<real>::NWARP;
     constexpr int NQ = (P * P + 31) / 32;
     const int tile = blockIdx.x;
@@ -519,50 +531,20 @@ constexpr int kShortMaxT = 8;       // targets per pass
 constexpr int kShortMaxR = 4;       // largest reach
 constexpr int kShortMaxRanges = 256;   // >= 81 columns x 3 pieces (nc >= 2R since rc <= L/2)
 
-// Per-plan constants of the real-space kernel, passed by value (kernel parameter space): the radial
-// polynomials padded with leading zeros to the compile-time degree D, so the fully unrolled Horner
-// loops read every coefficient as a constant operand.
-template <typename real, int D>
-struct ShortParams {
-    real p1[D + 1], q[D + 1];
-    real rc2, two_over_rc2;
-    float rc2f;
-};
+// Per-warp range arrays of the real-space kernels live in dynamic shared memory, sized by the host's
+// bound on the pieces of one neighbourhood (columns x pieces per column <= kShortMaxRanges).
+__host__ __device__ constexpr size_t short_dyn_smem(int rcap) {
+    return static_cast<size_t>(kShortWarps) * (16u * rcap + 4u * (rcap + 1));
+}
 
-template <typename real, int D>
-__global__ void __launch_bounds__(32 * kShortWarps) k_short(const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
-                                                            const Vec4<real>* __restrict__ lo, const float4* __restrict__ pf,
-                                                            const int* __restrict__ cell_off, const int4* __restrict__ cols,
-                                                            int ncols, Geom g, const __grid_constant__ ShortParams<real, D> kp,
-                                                            double* __restrict__ phi_out, double* __restrict__ f_out) {
-    constexpr bool kF32 = sizeof(real) == 4;
-    constexpr int NSH = 2 * kShortMaxR + 1;
-    __shared__ float sh_hi[NSH], sh_lo[NSH];
-    __shared__ double sh_d[NSH];
-    __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
-    __shared__ int4 srng[kShortWarps][kShortMaxRanges];        // {first particle, z cell, dz, column}
-    __shared__ int spos[kShortWarps][kShortMaxRanges + 1];     // stream offset of each range
-    __shared__ real stx[kShortWarps][kShortMaxT][4];           // exact target position and charge
-    __shared__ float stl[kShortWarps][kShortMaxT][4];          // float path: lo parts
-    const int R = g.reach, nc = g.ncell;
-    for (int k = threadIdx.x; k < 2 * R + 1; k += blockDim.x) {
-        const double o = (k - R) * g.cellw;
-        sh_d[k] = o;
-        sh_hi[k] = static_cast<float>(o);
-        sh_lo[k] = static_cast<float>(o - static_cast<double>(sh_hi[k]));
-    }
-    for (int k = threadIdx.x; k < ncols; k += blockDim.x) scol[k] = cols[k];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c = blockIdx.x * kShortWarps + warp;
-    if (c >= nc * nc * nc) return;
-    const int tb = cell_off[c], te = cell_off[c + 1];
-    if (tb == te) return;
-    const int cz = c % nc, cy = (c / nc) % nc, cx = c / (nc * nc);
-    int4* rng = srng[warp];
-    int* pos = spos[warp];
-
-    // ---- flatten the neighbour ranges of this cell (pieces of each column's z-run)
+// Flattens the source ranges of target cell (cx, cy, cz) for one warp: every column (dx, dy, dzmax) of
+// scol contributes its z-run dz in [-dzmax, dzmax], split into contiguous pieces of the z-fastest cell
+// order (one piece per wrap of the periodic box).  rng[r] = {first particle, first z cell, dz of that
+// cell, column}, pos[r] = offset of piece r in the flattened candidate stream, pos[nr] = total.
+// Returns the total number of candidates (warp-uniform).  Pieces beyond cap are dropped; the host sizes
+// cap from the columns and the largest number of pieces per column, so none are.
+__device__ __forceinline__ int short_ranges(const int4* __restrict__ scol, int ncols, const int* __restrict__ cell_off,
+                                            int nc, int cx, int cy, int cz, int lane, int cap, int4* rng, int* pos) {
     auto wrap = [nc](int v) {   // v in (-2 nc, 2 nc) -> [0, nc)
         v += v < 0 ? nc : 0;
         v += v < 0 ? nc : 0;
@@ -595,7 +577,7 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short(const Vec4<real>* __
             for (int d = -col.z; d <= col.z;) {
                 const int zw = wrap(cz + d);
                 const int len = min(col.z - d + 1, nc - zw);
-                if (slot < kShortMaxRanges) {
+                if (slot < cap) {
                     const int a = cell_off[base + zw], b = cell_off[base + zw + len];
                     rng[slot] = make_int4(a, zw, d, k);
                     pos[slot] = b - a;            // length, turned into offsets below
@@ -606,7 +588,7 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short(const Vec4<real>* __
         }
         nr += __shfl_sync(0xffffffffu, incl, 31);
     }
-    nr = min(nr, kShortMaxRanges);
+    nr = min(nr, cap);
     __syncwarp();
     int total = 0;
     for (int r0 = 0; r0 < nr; r0 += 32) {
@@ -624,11 +606,76 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short(const Vec4<real>* __
     }
     if (lane == 0) pos[nr] = total;
     __syncwarp();
+    return total;
+}
+
+// Per-target pair queues of the two-phase real-space kernels (k_short_q, k_short_ff).  The float32
+// cutoff scan of a chunk of 32 candidates appends each passing (source, target t) pair to queue t
+// (warp ballot + prefix popcount); every queue holding 32 or more pairs is drained by one full-warp
+// evaluation with t warp-uniform, so the accumulation needs no per-lane target selection.
+constexpr int kShortQCap = 64;   // < 32 left after a drain, at most 32 added per chunk
+
+__device__ __forceinline__ void short_enqueue(unsigned mask, int nt, int2 entry, int lane, int2 (*queue)[kShortQCap],
+                                              int* qlen) {
+    const unsigned lt = (1u << lane) - 1u;
+    for (int t = 0; t < nt; ++t) {
+        const bool mine = (mask >> t) & 1u;
+        const unsigned b = __ballot_sync(0xffffffffu, mine);
+        if (mine) queue[t][qlen[t] + __popc(b & lt)] = entry;
+        __syncwarp();
+        if (lane == 0) qlen[t] += __popc(b);
+        __syncwarp();
+    }
+}
+
+// Per-plan constants of the real-space kernel, passed by value (kernel parameter space): the radial
+// polynomials padded with leading zeros to the compile-time degree D, so the fully unrolled Horner
+// loops read every coefficient as a constant operand.
+template <typename real, int D>
+struct ShortParams {
+    real p1[D + 1], q[D + 1];
+    real rc2, two_over_rc2;
+    float rc2f;
+};
+
+// 7 resident blocks per SM (<= 73 registers; measured best for the float32 instantiations)
+template <typename real, int D>
+__global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
+                                                            const Vec4<real>* __restrict__ lo, const float4* __restrict__ pf,
+                                                            const int* __restrict__ cell_off, const int4* __restrict__ cols,
+                                                            int ncols, int rcap, Geom g, const __grid_constant__ ShortParams<real, D> kp,
+                                                            double* __restrict__ phi_out, double* __restrict__ f_out) {
+    constexpr bool kF32 = sizeof(real) == 4;
+    constexpr int NSH = 2 * kShortMaxR + 1;
+    __shared__ float sh_hi[NSH], sh_lo[NSH];
+    __shared__ double sh_d[NSH];
+    __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
+    __shared__ real stx[kShortWarps][kShortMaxT][4];           // exact target position and charge
+    __shared__ float stl[kShortWarps][kShortMaxT][4];          // float path: lo parts
+    const int R = g.reach, nc = g.ncell;
+    for (int k = threadIdx.x; k < 2 * R + 1; k += blockDim.x) {
+        const double o = (k - R) * g.cellw;
+        sh_d[k] = o;
+        sh_hi[k] = static_cast<float>(o);
+        sh_lo[k] = static_cast<float>(o - static_cast<double>(sh_hi[k]));
+    }
+    for (int k = threadIdx.x; k < ncols; k += blockDim.x) scol[k] = cols[k];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * kShortWarps + warp;
+    if (c >= nc * nc * nc) return;
+    const int tb = cell_off[c], te = cell_off[c + 1];
+    if (tb == te) return;
+    const int cz = c % nc, cy = (c / nc) % nc, cx = c / (nc * nc);
+    extern __shared__ __align__(16) unsigned char short_dyn[];
+    int4* rng = reinterpret_cast<int4*>(short_dyn) + warp * rcap;
+    int* pos = reinterpret_cast<int*>(reinterpret_cast<int4*>(short_dyn) + kShortWarps * rcap) + warp * (rcap + 1);
+
+    const int total = short_ranges(scol, ncols, cell_off, nc, cx, cy, cz, lane, rcap, rng, pos);
 
     for (int t0 = tb; t0 < te; t0 += kShortMaxT) {
         const int nt = min(kShortMaxT, te - t0);
-        // targets: float32 test copies in registers of every lane, exact parts in shared memory
-        float tf[kShortMaxT][3];
+        // targets: exact parts and float32 test copies in shared memory (broadcast reads)
         __syncwarp();
         if (lane < nt) {
             const Vec4<real> a = rec[t0 + lane];
@@ -649,19 +696,6 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short(const Vec4<real>* __
             }
         }
         __syncwarp();
-#pragma unroll
-        for (int t = 0; t < kShortMaxT; ++t) {
-            const int tt = t < nt ? t : 0;
-            if constexpr (kF32) {
-                tf[t][0] = static_cast<float>(stx[warp][tt][0]);
-                tf[t][1] = static_cast<float>(stx[warp][tt][1]);
-                tf[t][2] = static_cast<float>(stx[warp][tt][2]);
-            } else {
-                tf[t][0] = stl[warp][tt][0];
-                tf[t][1] = stl[warp][tt][1];
-                tf[t][2] = stl[warp][tt][2];
-            }
-        }
         real acc[kShortMaxT][4];
 #pragma unroll
         for (int t = 0; t < kShortMaxT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = real(0);
@@ -690,7 +724,13 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short(const Vec4<real>* __
 #pragma unroll
             for (int t = 0; t < kShortMaxT; ++t) {
                 if (t >= nt) break;   // nt is warp-uniform
-                const float dxf = tf[t][0] - px, dyf = tf[t][1] - py, dzf = tf[t][2] - pz;
+                float tx, ty, tz;
+                if constexpr (kF32) {
+                    tx = stx[warp][t][0]; ty = stx[warp][t][1]; tz = stx[warp][t][2];
+                } else {
+                    tx = stl[warp][t][0]; ty = stl[warp][t][1]; tz = stl[warp][t][2];
+                }
+                const float dxf = tx - px, dyf = ty - py, dzf = tz - pz;
                 const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
                 if (r2f < kp.rc2f && r2f > 0.f) {
                     if (!loaded) {
@@ -766,6 +806,200 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short(const Vec4<real>* __
             f_out[3 * static_cast<size_t>(oi) + 1] = qi * static_cast<double>(mine[2]);
             f_out[3 * static_cast<size_t>(oi) + 2] = qi * static_cast<double>(mine[3]);
         }
+    }
+}
+
+// Two-phase form of k_short (float64 plans): the float32 cutoff scan fills per-target pair queues, full
+// warps of queued pairs are evaluated with the arithmetic of k_short, so the costly float64 pair
+// evaluation runs without divergence.
+template <typename real, int D>
+__global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
+                                                              const Vec4<real>* __restrict__ lo, const float4* __restrict__ pf,
+                                                              const int* __restrict__ cell_off, const int4* __restrict__ cols,
+                                                              int ncols, int rcap, Geom g, const __grid_constant__ ShortParams<real, D> kp,
+                                                              double* __restrict__ phi_out, double* __restrict__ f_out) {
+    constexpr bool kF32 = sizeof(real) == 4;
+    constexpr int NSH = 2 * kShortMaxR + 1, MT = kShortMaxT;
+    static_assert(NSH <= 16, "queue entries pack 4-bit shift indices");
+    __shared__ float sh_hi[NSH], sh_lo[NSH];
+    __shared__ double sh_d[NSH];
+    __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
+    __shared__ real stx[kShortWarps][MT][4];          // exact target position and charge
+    __shared__ float stl[kShortWarps][MT][4];         // float path: lo parts; float64 path: float32 copy
+    __shared__ int2 sq[kShortWarps][MT][kShortQCap];  // {source, ix | iy << 4 | iz << 8}
+    __shared__ int sqlen[kShortWarps][MT];
+    const int R = g.reach, nc = g.ncell;
+    for (int k = threadIdx.x; k < 2 * R + 1; k += blockDim.x) {
+        const double o = (k - R) * g.cellw;
+        sh_d[k] = o;
+        sh_hi[k] = static_cast<float>(o);
+        sh_lo[k] = static_cast<float>(o - static_cast<double>(sh_hi[k]));
+    }
+    for (int k = threadIdx.x; k < ncols; k += blockDim.x) scol[k] = cols[k];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = blockIdx.x * kShortWarps + warp;
+    if (c >= nc * nc * nc) return;
+    const int tb = cell_off[c], te = cell_off[c + 1];
+    if (tb == te) return;
+    const int cz = c % nc, cy = (c / nc) % nc, cx = c / (nc * nc);
+    extern __shared__ __align__(16) unsigned char short_dyn[];
+    int4* rng = reinterpret_cast<int4*>(short_dyn) + warp * rcap;
+    int* pos = reinterpret_cast<int*>(reinterpret_cast<int4*>(short_dyn) + kShortWarps * rcap) + warp * (rcap + 1);
+    int* qlen = sqlen[warp];
+    const int total = short_ranges(scol, ncols, cell_off, nc, cx, cy, cz, lane, rcap, rng, pos);
+
+    for (int t0 = tb; t0 < te; t0 += MT) {
+        const int nt = min(MT, te - t0);
+        __syncwarp();
+        if (lane < nt) {
+            const Vec4<real> a = rec[t0 + lane];
+            stx[warp][lane][0] = a.x;
+            stx[warp][lane][1] = a.y;
+            stx[warp][lane][2] = a.z;
+            stx[warp][lane][3] = a.w;
+            if constexpr (kF32) {
+                const Vec4<real> l = lo[t0 + lane];
+                stl[warp][lane][0] = l.x;
+                stl[warp][lane][1] = l.y;
+                stl[warp][lane][2] = l.z;
+            } else {
+                const float4 f = pf[t0 + lane];
+                stl[warp][lane][0] = f.x;
+                stl[warp][lane][1] = f.y;
+                stl[warp][lane][2] = f.z;
+            }
+        }
+        if (lane < MT) qlen[lane] = 0;
+        __syncwarp();
+        real acc[MT][4];
+#pragma unroll
+        for (int t = 0; t < MT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = real(0);
+
+        // evaluates one queued pair for target t (warp-uniform) and accumulates it
+        auto pair = [&](int2 e, int t, bool active) {
+            const int ix = e.y & 15, iy = (e.y >> 4) & 15, iz = (e.y >> 8) & 15;
+            const Vec4<real> a = rec[active ? e.x : t0];
+            real ddx, ddy, ddz;
+            if constexpr (kF32) {
+                const Vec4<real> l = lo[active ? e.x : t0];
+                const float px = a.x + sh_hi[ix], py = a.y + sh_hi[iy], pz = a.z + sh_hi[iz];
+                ddx = (stx[warp][t][0] - px) + (stl[warp][t][0] - (l.x + sh_lo[ix]));
+                ddy = (stx[warp][t][1] - py) + (stl[warp][t][1] - (l.y + sh_lo[iy]));
+                ddz = (stx[warp][t][2] - pz) + (stl[warp][t][2] - (l.z + sh_lo[iz]));
+            } else {
+                ddx = stx[warp][t][0] - (a.x + sh_d[ix]);
+                ddy = stx[warp][t][1] - (a.y + sh_d[iy]);
+                ddz = stx[warp][t][2] - (a.z + sh_d[iz]);
+            }
+            const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+            const bool in = active && r2 < kp.rc2 && r2 > real(0);
+            const real u = fma(r2, kp.two_over_rc2, real(-1));
+            real p1 = kp.p1[D], qq = kp.q[D];
+#pragma unroll
+            for (int kk = D - 1; kk >= 0; --kk) {
+                p1 = fma(p1, u, kp.p1[kk]);
+                qq = fma(qq, u, kp.q[kk]);
+            }
+            const real ri = rsqrt_r<real>(in ? r2 : real(1));
+            const real qj = in ? a.w : real(0);
+            const real c0 = qj * (ri - p1);
+            const real cf = qj * fma(ri * ri, ri, qq);
+#pragma unroll
+            for (int tt = 0; tt < MT; ++tt)
+                if (tt == t) {   // warp-uniform
+                    acc[tt][0] += c0;
+                    acc[tt][1] = fma(cf, ddx, acc[tt][1]);
+                    acc[tt][2] = fma(cf, ddy, acc[tt][2]);
+                    acc[tt][3] = fma(cf, ddz, acc[tt][3]);
+                }
+        };
+
+        int r = 0;
+        for (int s0 = 0;; s0 += 32) {   // one extra round after the last chunk flushes the queues
+            const bool fin = s0 >= total;
+            if (!fin) {
+                // scan: float32 test of candidate p against every target of the pass
+                const int p = s0 + lane;
+                unsigned mask = 0u;
+                int2 entry = make_int2(0, 0);
+                if (p < total) {
+                    while (pos[r + 1] <= p) ++r;
+                    const int4 rg = rng[r];
+                    const int j = rg.x + (p - pos[r]);
+                    float sfx, sfy, sfz, szc;
+                    if constexpr (kF32) {
+                        const Vec4<real> a = rec[j];
+                        sfx = a.x; sfy = a.y; sfz = a.z;
+                        szc = lo[j].w;
+                    } else {
+                        const float4 f = pf[j];
+                        sfx = f.x; sfy = f.y; sfz = f.z;
+                        szc = f.w;
+                    }
+                    const int4 col = scol[rg.w];
+                    const int ix = col.x + R, iy = col.y + R, iz = rg.z + (static_cast<int>(szc) - rg.y) + R;
+                    const float px = sfx + sh_hi[ix], py = sfy + sh_hi[iy], pz = sfz + sh_hi[iz];
+#pragma unroll
+                    for (int t = 0; t < MT; ++t) {
+                        if (t >= nt) break;   // warp-uniform
+                        float tx, ty, tz;
+                        if constexpr (kF32) {
+                            tx = stx[warp][t][0]; ty = stx[warp][t][1]; tz = stx[warp][t][2];
+                        } else {
+                            tx = stl[warp][t][0]; ty = stl[warp][t][1]; tz = stl[warp][t][2];
+                        }
+                        const float dxf = tx - px, dyf = ty - py, dzf = tz - pz;
+                        const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
+                        if (r2f < kp.rc2f && r2f > 0.f) mask |= 1u << t;
+                    }
+                    entry = make_int2(j, ix | (iy << 4) | (iz << 8));
+                }
+                short_enqueue(mask, nt, entry, lane, sq[warp], qlen);
+            }
+            // compute: drain every full queue (every non-empty one in the final round)
+            for (int t = 0; t < nt; ++t) {
+                while (qlen[t] >= 32 || (fin && qlen[t] > 0)) {
+                    const int q = max(qlen[t] - 32, 0);
+                    const bool act = lane < qlen[t] - q;
+                    const int2 e = sq[warp][t][q + (act ? lane : 0)];
+                    __syncwarp();
+                    if (lane == 0) qlen[t] = q;
+                    __syncwarp();
+                    pair(e, t, act);
+                }
+            }
+            if (fin) break;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                real x = acc[t][v];
+                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+                acc[t][v] = x;
+            }
+        }
+        real mine[4] = {real(0), real(0), real(0), real(0)};
+#pragma unroll
+        for (int t = 0; t < MT; ++t) {
+            if (lane == t) {
+                mine[0] = acc[t][0];
+                mine[1] = acc[t][1];
+                mine[2] = acc[t][2];
+                mine[3] = acc[t][3];
+            }
+        }
+        if (lane < nt) {
+            const int oi = idx[t0 + lane].y;
+            const double qi = static_cast<double>(stx[warp][lane][3]);
+            phi_out[oi] = static_cast<double>(mine[0]);
+            f_out[3 * static_cast<size_t>(oi) + 0] = qi * static_cast<double>(mine[1]);
+            f_out[3 * static_cast<size_t>(oi) + 1] = qi * static_cast<double>(mine[2]);
+            f_out[3 * static_cast<size_t>(oi) + 2] = qi * static_cast<double>(mine[3]);
+        }
+        __syncwarp();
     }
 }
 

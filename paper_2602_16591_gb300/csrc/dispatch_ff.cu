@@ -18,7 +18,7 @@ size_t spread_smem_ff(int P, int degw) {
 }
 
 size_t interp_smem_ff(int P, int degw) {
-    const int E = kTile + P - 1;
+    const int E = kTile64 + P - 1;
     return sizeof(ff) * (static_cast<size_t>(E) * E * E + kInterpFFWarps * kInterpFFNB * 6 * P) +
            sizeof(float) * 4 * P * (degw + 1);
 }
@@ -30,7 +30,7 @@ cudaError_t spread_p(int ntiles, const Geom& g, const float4* rh, const float4* 
     auto kern = k_spread_ff<P>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    kern<<<ntiles, spread_threads<P>(), smem, s>>>(rh, rl, idx, tile_off, wc, g.degw, kf, scratch);
+    kern<<<ntiles, spread_threads<P, kTile64>(), smem, s>>>(rh, rl, idx, tile_off, wc, g.degw, kf, scratch);
     return cudaGetLastError();
 }
 
@@ -48,8 +48,8 @@ cudaError_t interp_p(int ntiles, const Geom& g, const float2* grid, const float4
 
 template <int D>
 cudaError_t short_d(const Geom& g, const float4* rh, const float4* rl, const int2* idx, const int* cz,
-                    const int* cell_off, const int4* cols, int ncols, const double* p1c, const double* qc, int kr,
-                    double* phi, double* f, cudaStream_t s) {
+                    const int* cell_off, const int4* cols, int ncols, int rcap, const double* p1c, const double* qc,
+                    int kr, double* phi, double* f, cudaStream_t s) {
     ShortParamsFF<D> kp{};
     for (int k = 0; k <= D; ++k) {
         split(k <= g.degr ? p1c[k] : 0.0, kp.p1h[k], kp.p1l[k]);
@@ -60,8 +60,9 @@ cudaError_t short_d(const Geom& g, const float4* rh, const float4* rl, const int
     kp.rc2f = static_cast<float>(g.rc * g.rc * (1.0 + 1e-4));
     kp.kr = kr;
     const int ncells = g.ncell * g.ncell * g.ncell;
-    k_short_ff<D><<<(ncells + kShortWarps - 1) / kShortWarps, 32 * kShortWarps, 0, s>>>(
-        rh, rl, idx, cz, cell_off, cols, ncols, g, kp, phi, f);
+    const size_t smem = short_dyn_smem(rcap);
+    k_short_ff<D><<<(ncells + kShortWarps - 1) / kShortWarps, 32 * kShortWarps, smem, s>>>(
+        rh, rl, idx, cz, cell_off, cols, ncols, rcap, g, kp, phi, f);
     return cudaGetLastError();
 }
 
@@ -114,17 +115,17 @@ cudaError_t LaunchFF::interp(int ntiles, const Geom& g, const float2* grid, cons
 }
 
 cudaError_t LaunchFF::short_range(const Geom& g, const float4* rec_h, const float4* rec_l, const int2* idx,
-                                  const int* cz, const int* cell_off, const int4* cols, int ncols, const double* p1c,
-                                  const double* qc, int kr, double* phi, double* f, cudaStream_t s) {
+                                  const int* cz, const int* cell_off, const int4* cols, int ncols, int rcap,
+                                  const double* p1c, const double* qc, int kr, double* phi, double* f, cudaStream_t s) {
     const int d = g.degr;
-    if (d <= 8) return short_d<8>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
-    if (d <= 12) return short_d<12>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
-    if (d <= 16) return short_d<16>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
-    if (d <= 20) return short_d<20>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
-    if (d <= 24) return short_d<24>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
-    if (d <= 32) return short_d<32>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
-    if (d <= 44) return short_d<44>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
-    return short_d<60>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, p1c, qc, kr, phi, f, s);
+    if (d <= 8) return short_d<8>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, rcap, p1c, qc, kr, phi, f, s);
+    if (d <= 12) return short_d<12>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, rcap, p1c, qc, kr, phi, f, s);
+    if (d <= 16) return short_d<16>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, rcap, p1c, qc, kr, phi, f, s);
+    if (d <= 20) return short_d<20>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, rcap, p1c, qc, kr, phi, f, s);
+    if (d <= 24) return short_d<24>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, rcap, p1c, qc, kr, phi, f, s);
+    if (d <= 32) return short_d<32>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, rcap, p1c, qc, kr, phi, f, s);
+    if (d <= 44) return short_d<44>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, rcap, p1c, qc, kr, phi, f, s);
+    return short_d<60>(g, rec_h, rec_l, idx, cz, cell_off, cols, ncols, rcap, p1c, qc, kr, phi, f, s);
 }
 
 }  // namespace pswf

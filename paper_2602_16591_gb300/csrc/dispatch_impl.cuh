@@ -9,7 +9,7 @@ namespace {
 template <int P>
 cudaError_t spread_p(int ntiles, const Vec4<real_t>* rec, const int2* idx, const int* tile_off, const real_t* wcoef,
                      int degw, real_t* scratch, cudaStream_t s) {
-    const int threads = spread_threads<P>();
+    const int threads = spread_threads<P, spread_tile<real_t>()>();
     const size_t smem = Launch<real_t>::spread_smem(P, degw);
     auto kern = k_spread<real_t, P>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
@@ -40,7 +40,7 @@ size_t Launch<real_t>::spread_smem(int P, int degw) {
 
 template <>
 size_t Launch<real_t>::interp_smem(int P, int degw) {
-    const int E = kTile + P - 1;
+    const int E = spread_tile<real_t>() + P - 1;
     return sizeof(real_t) * (static_cast<size_t>(E) * E * E + 2 * P * (degw + 1) +
                            InterpCfg<real_t>::NWARP * InterpCfg<real_t>::NB * 6 * P);
 }

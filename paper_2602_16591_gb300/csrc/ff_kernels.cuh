@@ -69,13 +69,13 @@ __device__ __forceinline__ ff window_weight_ff(const float* __restrict__ ch, con
 constexpr int kSpreadFFChunk = 32;
 
 template <int P>
-__global__ void __launch_bounds__(spread_threads<P>()) k_spread_ff(const float4* __restrict__ rec_h,
+__global__ void __launch_bounds__(spread_threads<P, kTile64>()) k_spread_ff(const float4* __restrict__ rec_h,
                                                                    const float4* __restrict__ rec_l,
                                                                    const int2* __restrict__ idx,
                                                                    const int* __restrict__ tile_off,
                                                                    const float* __restrict__ wc, int degw, int kf,
                                                                    float2* __restrict__ scratch) {
-    constexpr int T = kTile, E = T + P - 1, CH = kSpreadFFChunk;
+    constexpr int T = kTile64, E = T + P - 1, CH = kSpreadFFChunk;
     const int tile = blockIdx.x;
     const int beg = tile_off[tile], end = tile_off[tile + 1];
     if (beg == end) return;
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2*
                                                                    float inv_alpha_h, float inv_alpha_l,
                                                                    double* __restrict__ phi_out,
                                                                    double* __restrict__ f_out) {
-    constexpr int T = kTile, E = T + P - 1, NB = kInterpFFNB, NWARP = kInterpFFWarps;
+    constexpr int T = kTile64, E = T + P - 1, NB = kInterpFFNB, NWARP = kInterpFFWarps;
     constexpr int NQ = (P * P + 31) / 32;
     const int tile = blockIdx.x;
     const int beg = tile_off[tile], end = tile_off[tile + 1];
@@ -304,19 +304,14 @@ __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2*
 }
 
 // ---- real-space sum of R in float-float ---------------------------------------------------------
-// Cell traversal of k_short (a warp per target cell, flattened neighbour ranges), split in two phases
-// because one float-float pair costs ~40x a float32 cutoff test:
-//  scan     lanes take 32 consecutive candidate sources, test each against the pass's targets in
-//           float32 (rounded positions, cutoff enlarged by 1e-4) and append the passing (source,
-//           target) pairs to a per-warp queue in shared memory (warp prefix sum of the counts);
-//  compute  whenever 32 pairs are queued, every lane evaluates one pair in float-float: the
-//           displacement d = (hi_i - (hi_j + s_hi)) + (lo_i - (lo_j + s_lo)) with the leading
-//           difference and the cell shift split exactly (TwoSum), R and -R'/r from the radial
-//           polynomials by float-float Horner, 1/r from a float32 estimate with a float-float
-//           correction, and compensated accumulation into the lane's sums for that target.
-// The expensive part thus runs on full warps and exists once in the code.
-constexpr int kShortFFMaxT = 8;                                  // targets per pass (sums in registers)
-constexpr int kShortFFQueue = 32 + 32 * kShortFFMaxT;            // < 32 left after every drain
+// Cell traversal of k_short (a warp per target cell, flattened neighbour ranges) in the two-phase form
+// of k_short_q, since one float-float pair costs ~40x a float32 cutoff test: the float32 scan fills
+// per-target pair queues, and full warps of queued pairs are evaluated in float-float: the
+// displacement d = (hi_i - (hi_j + s_hi)) + (lo_i - (lo_j + s_lo)) with the leading difference and the
+// cell shift split exactly (TwoSum), R and -R'/r from the radial polynomials by Horner (float32 for
+// the tiny leading terms k >= kr, float-float below), 1/r from a float32 estimate with a float-float
+// correction, and compensated accumulation.  The pair evaluation exists once in the code.
+constexpr int kShortFFMaxT = kShortMaxT;   // targets per pass (sums in registers)
 
 // Radial polynomials padded with zeros to degree D; terms k >= kr (tiny, chosen on the host) are summed
 // by float32 Horner steps in u.h, the terms below kr in float-float.
@@ -337,22 +332,21 @@ __device__ __forceinline__ void ff_acc_sum(ff& acc, ff c) {
 
 template <int D>
 __global__ void __launch_bounds__(32 * kShortWarps, 4) k_short_ff(const float4* __restrict__ rec_h,
-                                                               const float4* __restrict__ rec_l,
-                                                               const int2* __restrict__ idx,
-                                                               const int* __restrict__ cz_of,
-                                                               const int* __restrict__ cell_off,
-                                                               const int4* __restrict__ cols, int ncols, Geom g,
-                                                               const __grid_constant__ ShortParamsFF<D> kp,
-                                                               double* __restrict__ phi_out,
-                                                               double* __restrict__ f_out) {
+                                                                  const float4* __restrict__ rec_l,
+                                                                  const int2* __restrict__ idx,
+                                                                  const int* __restrict__ cz_of,
+                                                                  const int* __restrict__ cell_off,
+                                                                  const int4* __restrict__ cols, int ncols, int rcap,
+                                                                  Geom g, const __grid_constant__ ShortParamsFF<D> kp,
+                                                                  double* __restrict__ phi_out,
+                                                                  double* __restrict__ f_out) {
     constexpr int NSH = 2 * kShortMaxR + 1, MT = kShortFFMaxT;
-    static_assert(NSH <= 16 && MT <= 16, "queue entries pack 4-bit fields");
+    static_assert(NSH <= 16, "queue entries pack 4-bit shift indices");
     __shared__ float sh_hi[NSH], sh_lo[NSH];
     __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
-    __shared__ int4 srng[kShortWarps][kShortMaxRanges];
-    __shared__ int spos[kShortWarps][kShortMaxRanges + 1];
     __shared__ float4 sth[kShortWarps][MT], stl[kShortWarps][MT];
-    __shared__ int2 sq[kShortWarps][kShortFFQueue];   // {source, target | ix << 4 | iy << 8 | iz << 12}
+    __shared__ int2 sq[kShortWarps][MT][kShortQCap];   // {source, ix | iy << 4 | iz << 8}
+    __shared__ int sqlen[kShortWarps][MT];
     const int R = g.reach, nc = g.ncell;
     for (int k = threadIdx.x; k < 2 * R + 1; k += blockDim.x) split_ff((k - R) * g.cellw, sh_hi[k], sh_lo[k]);
     for (int k = threadIdx.x; k < ncols; k += blockDim.x) scol[k] = cols[k];
@@ -363,71 +357,11 @@ __global__ void __launch_bounds__(32 * kShortWarps, 4) k_short_ff(const float4* 
     const int tb = cell_off[c], te = cell_off[c + 1];
     if (tb == te) return;
     const int cz = c % nc, cy = (c / nc) % nc, cx = c / (nc * nc);
-    int4* rng = srng[warp];
-    int* pos = spos[warp];
-    int2* queue = sq[warp];
-    auto wrap = [nc](int v) {   // v in (-2 nc, 2 nc) -> [0, nc)
-        v += v < 0 ? nc : 0;
-        v += v < 0 ? nc : 0;
-        v -= v >= nc ? nc : 0;
-        v -= v >= nc ? nc : 0;
-        return v;
-    };
-    // flatten the neighbour ranges (as in k_short)
-    int nr = 0;
-    for (int k0 = 0; k0 < ncols; k0 += 32) {
-        const int k = k0 + lane;
-        int npc = 0;
-        int4 col = make_int4(0, 0, -1, 0);
-        int base = 0;
-        if (k < ncols) {
-            col = scol[k];
-            base = (wrap(cx + col.x) * nc + wrap(cy + col.y)) * nc;
-            for (int d = -col.z; d <= col.z;) {
-                const int zw = wrap(cz + d);
-                d += min(col.z - d + 1, nc - zw);
-                ++npc;
-            }
-        }
-        int incl = npc;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        int slot = nr + incl - npc;
-        if (k < ncols) {
-            for (int d = -col.z; d <= col.z;) {
-                const int zw = wrap(cz + d);
-                const int len = min(col.z - d + 1, nc - zw);
-                if (slot < kShortMaxRanges) {
-                    const int a = cell_off[base + zw], b = cell_off[base + zw + len];
-                    rng[slot] = make_int4(a, zw, d, k);
-                    pos[slot] = b - a;
-                }
-                ++slot;
-                d += len;
-            }
-        }
-        nr += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    nr = min(nr, kShortMaxRanges);
-    __syncwarp();
-    int total = 0;
-    for (int r0 = 0; r0 < nr; r0 += 32) {
-        const int r = r0 + lane;
-        const int len = r < nr ? pos[r] : 0;
-        int incl = len;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        __syncwarp();
-        if (r < nr) pos[r] = total + incl - len;
-        total += __shfl_sync(0xffffffffu, incl, 31);
-        __syncwarp();
-    }
-    if (lane == 0) pos[nr] = total;
-    __syncwarp();
+    extern __shared__ __align__(16) unsigned char short_dyn[];
+    int4* rng = reinterpret_cast<int4*>(short_dyn) + warp * rcap;
+    int* pos = reinterpret_cast<int*>(reinterpret_cast<int4*>(short_dyn) + kShortWarps * rcap) + warp * (rcap + 1);
+    int* qlen = sqlen[warp];
+    const int total = short_ranges(scol, ncols, cell_off, nc, cx, cy, cz, lane, rcap, rng, pos);
 
     const ff rc2{kp.rc2h, kp.rc2l}, two_over_rc2{kp.two_over_rc2_h, kp.two_over_rc2_l};
     for (int t0 = tb; t0 < te; t0 += MT) {
@@ -437,6 +371,7 @@ __global__ void __launch_bounds__(32 * kShortWarps, 4) k_short_ff(const float4* 
             sth[warp][lane] = rec_h[t0 + lane];
             stl[warp][lane] = rec_l[t0 + lane];
         }
+        if (lane < MT) qlen[lane] = 0;
         __syncwarp();
         ff acc[MT][4];
 #pragma unroll
@@ -444,10 +379,11 @@ __global__ void __launch_bounds__(32 * kShortWarps, 4) k_short_ff(const float4* 
 #pragma unroll
             for (int v = 0; v < 4; ++v) acc[t][v] = ff{0.f, 0.f};
 
-        // one queued pair -> the lane's sums of its target
-        auto pair = [&](int2 e) {
-            const int t = e.y & 15, ix = (e.y >> 4) & 15, iy = (e.y >> 8) & 15, iz = (e.y >> 12) & 15;
-            const float4 sh = rec_h[e.x], sl = rec_l[e.x];
+        // one queued pair for target t (warp-uniform) -> the lane's sums of that target
+        auto pair = [&](int2 e, int t, bool active) {
+            const int ix = e.y & 15, iy = (e.y >> 4) & 15, iz = (e.y >> 8) & 15;
+            const int j = active ? e.x : t0;
+            const float4 sh = rec_h[j], sl = rec_l[j];
             const float4 th = sth[warp][t], tl = stl[warp][t];
             const ff ex = two_sum(sh.x, sh_hi[ix]), ey = two_sum(sh.y, sh_hi[iy]), ez = two_sum(sh.z, sh_hi[iz]);
             const float lx = __fadd_rn(__fadd_rn(sl.x, sh_lo[ix]), ex.l);
@@ -458,7 +394,7 @@ __global__ void __launch_bounds__(32 * kShortWarps, 4) k_short_ff(const float4* 
             dy = two_sum(dy.h, __fadd_rn(dy.l, __fadd_rn(tl.y, -ly)));
             dz = two_sum(dz.h, __fadd_rn(dz.l, __fadd_rn(tl.z, -lz)));
             const ff r2 = ff_add(ff_add(ff_sqr(dx), ff_sqr(dy)), ff_sqr(dz));
-            const bool in = (r2.h < rc2.h || (r2.h == rc2.h && r2.l < rc2.l)) && r2.h > 0.f;
+            const bool in = active && (r2.h < rc2.h || (r2.h == rc2.h && r2.l < rc2.l)) && r2.h > 0.f;
             const ff u = ff_add(ff_mul(r2, two_over_rc2), ff_make(-1.f));
             float p1f = kp.p1h[D], qqf = kp.qh[D];
             ff p1 = ff_make(p1f), qq = ff_make(qqf);
@@ -481,7 +417,7 @@ __global__ void __launch_bounds__(32 * kShortWarps, 4) k_short_ff(const float4* 
             const ff c1 = ff_mul(cf, dx), c2 = ff_mul(cf, dy), c3 = ff_mul(cf, dz);
 #pragma unroll
             for (int tt = 0; tt < MT; ++tt)
-                if (tt == t) {
+                if (tt == t) {   // warp-uniform
                     ff_acc_sum(acc[tt][0], c0);
                     ff_acc_sum(acc[tt][1], c1);
                     ff_acc_sum(acc[tt][2], c2);
@@ -489,54 +425,48 @@ __global__ void __launch_bounds__(32 * kShortWarps, 4) k_short_ff(const float4* 
                 }
         };
 
-        int r = 0, qlen = 0;
-        for (int s0 = 0; s0 < total; s0 += 32) {
-            // scan: float32 test of candidate p against every target of the pass
-            const int p = s0 + lane;
-            unsigned mask = 0u;
-            int j = 0, meta = 0;
-            if (p < total) {
-                while (pos[r + 1] <= p) ++r;
-                const int4 rg = rng[r];
-                j = rg.x + (p - pos[r]);
-                const float4 sh = rec_h[j];
-                const int4 col = scol[rg.w];
-                const int ix = col.x + R, iy = col.y + R, iz = rg.z + (cz_of[j] - rg.y) + R;
-                const float px = sh.x + sh_hi[ix], py = sh.y + sh_hi[iy], pz = sh.z + sh_hi[iz];
+        int r = 0;
+        for (int s0 = 0;; s0 += 32) {   // one extra round after the last chunk flushes the queues
+            const bool fin = s0 >= total;
+            if (!fin) {
+                // scan: float32 test of candidate p against every target of the pass
+                const int p = s0 + lane;
+                unsigned mask = 0u;
+                int2 entry = make_int2(0, 0);
+                if (p < total) {
+                    while (pos[r + 1] <= p) ++r;
+                    const int4 rg = rng[r];
+                    const int j = rg.x + (p - pos[r]);
+                    const float4 sh = rec_h[j];
+                    const int4 col = scol[rg.w];
+                    const int ix = col.x + R, iy = col.y + R, iz = rg.z + (cz_of[j] - rg.y) + R;
+                    const float px = sh.x + sh_hi[ix], py = sh.y + sh_hi[iy], pz = sh.z + sh_hi[iz];
 #pragma unroll
-                for (int t = 0; t < MT; ++t) {
-                    if (t >= nt) break;   // warp-uniform
-                    const float4 a = sth[warp][t];
-                    const float dxf = a.x - px, dyf = a.y - py, dzf = a.z - pz;
-                    const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
-                    if (r2f < kp.rc2f && r2f > 0.f) mask |= 1u << t;
+                    for (int t = 0; t < MT; ++t) {
+                        if (t >= nt) break;   // warp-uniform
+                        const float4 a = sth[warp][t];
+                        const float dxf = a.x - px, dyf = a.y - py, dzf = a.z - pz;
+                        const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
+                        if (r2f < kp.rc2f && r2f > 0.f) mask |= 1u << t;
+                    }
+                    entry = make_int2(j, ix | (iy << 4) | (iz << 8));
                 }
-                meta = (ix << 4) | (iy << 8) | (iz << 12);
+                short_enqueue(mask, nt, entry, lane, sq[warp], qlen);
             }
-            const int cnt = __popc(mask);
-            int incl = cnt;
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += y;
+            // compute: drain every full queue (every non-empty one in the final round)
+            for (int t = 0; t < nt; ++t) {
+                while (qlen[t] >= 32 || (fin && qlen[t] > 0)) {
+                    const int q = max(qlen[t] - 32, 0);
+                    const bool act = lane < qlen[t] - q;
+                    const int2 e = sq[warp][t][q + (act ? lane : 0)];
+                    __syncwarp();
+                    if (lane == 0) qlen[t] = q;
+                    __syncwarp();
+                    pair(e, t, act);
+                }
             }
-            int slot = qlen + incl - cnt;
-            while (mask) {
-                const int t = __ffs(mask) - 1;
-                mask &= mask - 1u;
-                queue[slot++] = make_int2(j, meta | t);
-            }
-            qlen += __shfl_sync(0xffffffffu, incl, 31);
-            __syncwarp();
-            // compute: full warps of queued pairs
-            while (qlen >= 32) {
-                const int2 e = queue[qlen - 32 + lane];
-                __syncwarp();
-                qlen -= 32;
-                pair(e);
-            }
+            if (fin) break;
         }
-        if (lane < qlen) pair(queue[lane]);
-        __syncwarp();
 
         // reduce each target's sums over the lanes; lane t writes target t
 #pragma unroll
@@ -564,6 +494,7 @@ __global__ void __launch_bounds__(32 * kShortWarps, 4) k_short_ff(const float4* 
             f_out[3 * static_cast<size_t>(oi) + 1] = qi * ff_to_double(mine[2]);
             f_out[3 * static_cast<size_t>(oi) + 2] = qi * ff_to_double(mine[3]);
         }
+        __syncwarp();
     }
 }
 

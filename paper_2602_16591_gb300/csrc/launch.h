@@ -37,8 +37,8 @@ struct LaunchFF {
     // radial polynomials p1c / qc of degree g.degr (float64 coefficients, split on the host); terms
     // k >= kr are summed in float32
     static cudaError_t short_range(const Geom& g, const float4* rec_h, const float4* rec_l, const int2* idx,
-                                   const int* cz, const int* cell_off, const int4* cols, int ncols, const double* p1c,
-                                   const double* qc, int kr, double* phi, double* f, cudaStream_t s);
+                                   const int* cz, const int* cell_off, const int4* cols, int ncols, int rcap,
+                                   const double* p1c, const double* qc, int kr, double* phi, double* f, cudaStream_t s);
 };
 
 }  // namespace pswf

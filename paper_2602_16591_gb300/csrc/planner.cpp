@@ -441,7 +441,10 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
     const double cs = cs_of(rcl);
     const double mraw = std::ceil(cs / (kPi * rcl));      // eq. m_cs_dimless
     if (mraw > 1024) throw std::length_error("grid beyond 1024^3");
-    const int m = good_size(static_cast<int>(mraw), 4);
+    // float32 plans tile the grid by 8, the others by 4 (spreading tile edge; m is a multiple of it)
+    const int precision = (o.precision == EWALD_MIXED && tol < 1e-7) ? EWALD_FLOATFLOAT : o.precision;
+    const int tile = precision == EWALD_MIXED ? 8 : 4;
+    const int m = good_size(static_cast<int>(mraw), tile);
     if (m > 1024) throw std::length_error("grid beyond 1024^3");
     rcl = cs / (kPi * m);                                 // eq. csrc holds exactly
     const double bw = (As / Aw) * std::sqrt(rcl);
@@ -465,8 +468,8 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
     p.cw = kPi * P / 2.0;                                 // eq. cwP
     p.alpha = P * p.h / 2.0;
     // float32 products cannot reach tol < 1e-7; below it MIXED runs the float-float kernels
-    p.precision = (o.precision == EWALD_MIXED && tol < 1e-7) ? EWALD_FLOATFLOAT : o.precision;
-    p.tile = 4;
+    p.precision = precision;
+    p.tile = tile;
     // real-space cells of edge >= rc / reach; the automatic reach aims at ~3 particles per cell
     int reach = o.sr_reach;
     if (reach <= 0) {

@@ -47,7 +47,7 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
                                    void* stream) {
     if (!p || !x || !rho || !grid) return fail_static(EWALD_EINVAL, "NULL argument");
     if (p->n < 1 || p->n > (int64_t(1) << 30)) return fail_static(EWALD_EINVAL, "particle count out of range");
-    if (p->P < pswf::kPMin || p->P > pswf::kPMax || p->tile != pswf::kTile || p->m % p->tile != 0 ||
+    if (p->P < pswf::kPMin || p->P > pswf::kPMax || p->tile != pswf::kTile64 || p->m % p->tile != 0 ||
         p->deg_w < 1 || p->deg_w > pswf::kDegWMax || !(p->L > 0) || !(p->alpha > 0))
         return fail_static(EWALD_EINVAL, "parameters do not come from ewald_plan_params");
 

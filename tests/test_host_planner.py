@@ -74,6 +74,17 @@ def test_plan_params_match_oracle_alg3(L, n, tol):
     assert p.ncell >= 1 and p.L / p.ncell >= p.rc / p.sr_reach - 1e-15
 
 
+@pytest.mark.parametrize("L,n,tol", [c for c in CFGS if c[2] >= 1e-7])
+def test_mixed_plan_params_match_oracle_alg3(L, n, tol):
+    """float32 plans round m to a multiple of their tile edge 8."""
+    p = pe.plan_params(L, n, tol, precision="mixed")
+    q = oparams.plan(L, n, tol, tol_safety=0.25, grid_density=3.0, mult=8)
+    assert p.precision == pe.EWALD_MIXED and p.tile == 8 and p.m % 8 == 0
+    assert (p.m, p.P) == (q["m"], q["P"])
+    for k in ("rc", "cs", "cw", "alpha", "h"):
+        assert abs(getattr(p, k) / q[k] - 1) <= 1e-11, k
+
+
 def test_plan_rejects_bad_arguments():
     for args in [(0.0, 100, 1e-6), (1.0, 1, 1e-6), (1.0, 100, 1e-1), (1.0, 100, 1e-15), (-1.0, 100, 1e-6)]:
         with pytest.raises(pe.EwaldError) as ei:
