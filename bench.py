@@ -258,7 +258,9 @@ def run_ours(args, rank, world, local_rank):
         except (ValueError, IndexError):
             pass
 
-    popts = {} if args.grid_density is None else {"grid_density": args.grid_density}
+    # the plan's grid density (the real-space / Alg. 2 balance) is tuned at plan creation unless given
+    popts = {"autotune": 0, "grid_density": args.grid_density} if args.grid_density is not None else \
+        {"autotune": 0 if args.no_autotune else 1}
     plan = pe.Plan(L, n, args.tol, precision=args.precision, **popts)
     with ClockSampler(gpu_index) as clk:
         ms_local, stages = timed(plan, args.steps, args.warmup, profile=True)
@@ -310,6 +312,38 @@ def run_ours(args, rank, world, local_rank):
                              "value": world * n / (vms / 1000.0), "stages_ms": vst})
             del vp
 
+    batch = None
+    if not args.no_variants:
+        # batched workload: 256 independent systems, n log-uniform in [500, 20000], L = (n/100)^(1/3)
+        from paper_2602_16591_gb300.workloads import batched_systems
+        systems = batched_systems(nsys=256, seed=rank)
+        bx = torch.tensor(np.concatenate([sy[0] for sy in systems]), device="cuda")
+        brho = torch.tensor(np.concatenate([sy[1] for sy in systems]), device="cuda")
+        bLs = np.array([sy[2] for sy in systems])
+        bns = np.array([len(sy[1]) for sy in systems], dtype=np.int64)
+        bp = pe.BatchPlan(bLs, bns, 1e-6, precision="mixed")
+        bphi = torch.empty(len(brho), dtype=torch.float64, device="cuda")
+        bF = torch.empty(len(brho), 3, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            bp.eval(bx, brho, bphi, bF)
+        reps = max(5, args.steps // 3)
+        torch.cuda.synchronize()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            flush.zero_()
+            bp.eval(bx, brho, bphi, bF)
+        b.record(stream)
+        torch.cuda.synchronize()
+        bms = reduce_max(a.elapsed_time(b) / reps)
+        N = int(bns.sum())
+        batch = {"workload": "256 independent systems, n log-uniform in [500, 20000] (total %d), L = (n/100)^(1/3), "
+                             "rel tol 1e-6, mixed; one captured graph per call, energies copied back" % N,
+                 "ms_per_step": bms, "value": world * N / (bms / 1000.0), "unit": UNIT,
+                 "systems_per_s": world * 256 / (bms / 1000.0)}
+        del bp
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = oracle_sample(n, 48)
@@ -323,11 +357,12 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": prec_tag, "data": "synthetic",
             "config": dict(workload_config(n, args.tol, args.precision), m=p.m, P=p.P, rc=p.rc, cs=p.cs, cw=p.cw,
-                           deg_w=p.deg_w, deg_r=p.deg_r),
+                           deg_w=p.deg_w, deg_r=p.deg_r, tile=p.tile, plan=dict(popts)),
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
                     "d2h_bytes_per_step": 32 * n + 8},
             "gpu_launches": 10 * args.steps, "clocks": clocks, "stages_ms": stages, "variants": variants,
+            "batched": batch,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -346,6 +381,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=("mixed", "fp64", "floatfloat"))
     ap.add_argument("--grid-density", type=float, default=None, help="m^3/n target of the cutoff rule")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="plan with the default grid density")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

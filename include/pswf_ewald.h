@@ -67,6 +67,12 @@ typedef struct ewald_opts {
     int    sr_reach;      /* cells per cutoff radius in the real-space cell list, 1..4;
                              0 (default) picks it for ~3 particles per cell */
     int    window_extra;  /* window support added to the Alg. 3 value of P (default 0) */
+    int    autotune;      /* 1: ewald_plan_create times the candidate grid densities
+                             {1.5, 2, 3, 4, 6, 8, 12} (distinct m only) on a synthetic uniform
+                             system of n alternating unit charges in the plan's box and keeps
+                             the fastest plan; grid_density is then ignored.  The cutoff, and
+                             with it the balance between the real-space sum and Alg. 2, is what
+                             the paper leaves to measurement (Sec. 6.2.2).  0 (default): off. */
 } ewald_opts;
 
 /* ---- derived parameters (Alg. 3 and the library's readings of it) ------ */
@@ -140,7 +146,37 @@ int ewald_check(ewald_plan plan, void* stream);
  * host_out must hold m^3 doubles.  Synchronises the device. */
 int ewald_debug_grid(ewald_plan plan, int which, double* host_out);
 
+/* Release a plan (single-system or batch).  NULL is ignored. */
 void ewald_plan_destroy(ewald_plan plan);
+
+/* ---- batches of independent systems ------------------------------------
+ * Many small periodic systems evaluated by one call, e.g. an ensemble of
+ * MD replicas or a screening set (the paper's method applied per system;
+ * Sec. 7 evaluates single systems).  Each system b has its own cubic box
+ * L[b], particle count n[b] and plan (Alg. 3 per system, every opts field
+ * applied, autotune ignored); all share tol.
+ *
+ * ewald_plan_batch_create: nsys in [1, 4096]; L and n are HOST arrays of
+ * nsys entries.  Returns a batch plan for ewald_eval_batch / ewald_plan_query
+ * (which reports system 0) / ewald_plan_destroy; ewald_eval on a batch plan
+ * returns EWALD_EINVAL.
+ *
+ * ewald_eval_batch: offsets is a HOST array of nsys + 1 entries with
+ * offsets[0] = 0 and offsets[b+1] - offsets[b] = n[b]; system b occupies
+ * rows offsets[b] .. offsets[b+1]-1 of the DEVICE arrays x (rows of 3),
+ * rho, phi and force (phi, force may be NULL).  energy: HOST array of nsys
+ * entries or NULL.  The call enqueues every system's pipeline as one CUDA
+ * graph on `stream` (captured on the first call and again whenever a buffer
+ * pointer changes; the systems' pipelines are independent branches that run
+ * concurrently), then synchronises `stream` and reports the first system
+ * found non-neutral (EWALD_ENONNEUTRAL) or with non-finite input
+ * (EWALD_ENONFINITE); ewald_last_error() names the system.  The batch plan
+ * is not reentrant: one call at a time per plan. */
+int ewald_plan_batch_create(int nsys, const double* L, const int64_t* n, double tol,
+                            const ewald_opts* opts, ewald_plan* out);
+int ewald_eval_batch(ewald_plan plan, const int64_t* offsets, const double* x,
+                     const double* rho, double* phi, double* force, double* energy,
+                     void* stream);
 
 /* ---- per-stage timing ----------------------------------------------------
  * Stages, in pipeline order: 0 bin+sort, 1 spread (Alg. 2 step 1), 2 halo sum,

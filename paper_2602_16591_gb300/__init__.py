@@ -25,7 +25,8 @@ PATH_NAMES = {EWALD_FP64: "f64", EWALD_MIXED: "f32", EWALD_FLOATFLOAT: "ff"}
 
 class ewald_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rc", ctypes.c_double), ("grid_density", ctypes.c_double),
-                ("tol_safety", ctypes.c_double), ("sr_reach", ctypes.c_int), ("window_extra", ctypes.c_int)]
+                ("tol_safety", ctypes.c_double), ("sr_reach", ctypes.c_int), ("window_extra", ctypes.c_int),
+                ("autotune", ctypes.c_int)]
 
 
 class ewald_params(ctypes.Structure):
@@ -69,6 +70,8 @@ def _load():
         "ewald_profile": (I, [P, I]),
         "ewald_profile_read": (I, [P, P, ctypes.POINTER(ctypes.c_int)]),
         "ewald_spread_static": (I, [ctypes.POINTER(ewald_params), P, P, P, P]),
+        "ewald_plan_batch_create": (I, [I, P, P, D, ctypes.POINTER(ewald_opts), ctypes.POINTER(P)]),
+        "ewald_eval_batch": (I, [P, P, P, P, P, P, P, P]),
         "ewald_error_string": (ctypes.c_char_p, [I]),
         "ewald_last_error": (ctypes.c_char_p, []),
     }
@@ -88,7 +91,8 @@ def _check(code):
         raise EwaldError(code, _lib.ewald_last_error().decode())
 
 
-def make_opts(precision="fp64", rc=None, grid_density=None, tol_safety=None, sr_reach=None, window_extra=None):
+def make_opts(precision="fp64", rc=None, grid_density=None, tol_safety=None, sr_reach=None, window_extra=None,
+              autotune=None):
     o = ewald_opts()
     _check(_lib.ewald_opts_default(ctypes.byref(o)))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -102,6 +106,8 @@ def make_opts(precision="fp64", rc=None, grid_density=None, tol_safety=None, sr_
         o.sr_reach = int(sr_reach)
     if window_extra is not None:
         o.window_extra = int(window_extra)
+    if autotune is not None:
+        o.autotune = int(bool(autotune))
     return o
 
 
@@ -275,3 +281,60 @@ def energy(x, rho, plan):
     except NameError:
         fn = _ENERGY_FN = _EwaldEnergy.build()
     return fn.apply(x, rho, plan)
+
+
+class BatchPlan:
+    """Independent systems evaluated by one call (C ABI: ewald_plan_batch_create / ewald_eval_batch).
+
+    ``Ls`` and ``ns`` give each system's box edge and particle count; all share ``tol`` and the
+    ewald_opts keywords.  ``eval`` takes the systems' rows concatenated in order.
+    """
+
+    def __init__(self, Ls, ns, tol, precision="fp64", **opts):
+        import torch  # device memory and streams only
+        self._torch = torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("PSWF Ewald plans need a CUDA device (no CPU fallback)")
+        torch.cuda.init()
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        Ls = np.ascontiguousarray(Ls, dtype=np.float64)
+        ns = np.ascontiguousarray(ns, dtype=np.int64)
+        if Ls.shape != ns.shape or Ls.ndim != 1:
+            raise ValueError("Ls and ns must be 1-D arrays of equal length")
+        self.nsys = len(ns)
+        self.offsets = np.concatenate([[0], np.cumsum(ns)]).astype(np.int64)
+        o = make_opts(precision=precision, **opts)
+        h = ctypes.c_void_p()
+        _check(_lib.ewald_plan_batch_create(self.nsys, Ls.ctypes.data_as(ctypes.c_void_p),
+                                            ns.ctypes.data_as(ctypes.c_void_p), float(tol), ctypes.byref(o),
+                                            ctypes.byref(h)))
+        self._h = h
+        p = ewald_params()
+        _check(_lib.ewald_plan_query(self._h, ctypes.byref(p)))
+        self.params0 = p
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.ewald_plan_destroy(h)
+            self._h = None
+
+    def eval(self, x, rho, phi=None, force=None):
+        """phi (N,), F (N,3) device tensors and per-system energies (NumPy) for the concatenated rows."""
+        torch = self._torch
+        N = int(self.offsets[-1])
+        x = x.to(device=self.device, dtype=torch.float64).contiguous()
+        rho = rho.to(device=self.device, dtype=torch.float64).contiguous()
+        if x.shape != (N, 3) or rho.shape != (N,):
+            raise ValueError("x must be (N,3) and rho (N,) with N = %d" % N)
+        if phi is None:
+            phi = torch.empty(N, dtype=torch.float64, device=self.device)
+        if force is None:
+            force = torch.empty(N, 3, dtype=torch.float64, device=self.device)
+        E = np.empty(self.nsys)
+        stream = ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+        _check(_lib.ewald_eval_batch(self._h, self.offsets.ctypes.data_as(ctypes.c_void_p),
+                                     ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(rho.data_ptr()),
+                                     ctypes.c_void_p(phi.data_ptr()), ctypes.c_void_p(force.data_ptr()),
+                                     E.ctypes.data_as(ctypes.c_void_p), stream))
+        return phi, force, E

@@ -161,6 +161,19 @@ struct ewald_plan_s {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     double* phi_sr = nullptr;   // real-space potential and forces, merged by k_combine_energy
     double* f_sr = nullptr;
+    // batch plans (ewald_plan_batch_create): one plan per system, evaluated as one captured graph
+    bool is_batch = false;
+    std::vector<ewald_plan_s*> members;
+    std::vector<int64_t> offsets;              // prefix sums of the systems' particle counts
+    std::vector<cudaStream_t> bstreams;         // per-system streams of the capture (fork / join)
+    std::vector<cudaEvent_t> bevents;
+    cudaEvent_t bstart = nullptr;
+    cudaStream_t bcap = nullptr;                // capture origin
+    cudaGraphExec_t bexec = nullptr;
+    const void* bkey[4] = {nullptr, nullptr, nullptr, nullptr};   // buffers the graph was captured with
+    double* bout_d = nullptr;                   // per system {sum rho, sum |rho|, non-finite, energy}
+    double* bout_h = nullptr;                   // pinned
+    const double** bsrc_d = nullptr;            // per system {status, energy} device pointers
     bool profiling = false;
     std::vector<std::vector<cudaEvent_t>> prof;   // begin/end event of every stage per recorded evaluation
     std::vector<cudaEvent_t>* cur = nullptr;
@@ -192,6 +205,15 @@ struct ewald_plan_s {
         if (s_alg2) cudaStreamDestroy(s_alg2);
         if (have_fwd) cufftDestroy(fwd);
         if (have_inv) cufftDestroy(inv);
+        for (ewald_plan_s* m : members) delete m;
+        for (cudaStream_t st : bstreams) cudaStreamDestroy(st);
+        for (cudaEvent_t e : bevents) cudaEventDestroy(e);
+        if (bstart) cudaEventDestroy(bstart);
+        if (bcap) cudaStreamDestroy(bcap);
+        if (bexec) cudaGraphExecDestroy(bexec);
+        if (bout_d) cudaFree(bout_d);
+        if (bout_h) cudaFreeHost(bout_h);
+        if (bsrc_d) cudaFree(bsrc_d);
     }
 };
 
@@ -443,20 +465,31 @@ int check_ptr_device(const void* ptr, const char* name) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-int ewald_opts_default(ewald_opts* opts) {
-    if (!opts) return fail(EWALD_EINVAL, "opts is NULL");
-    *opts = pswf::default_opts();
-    return EWALD_OK;
+int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out);
+
+// Synthetic tuning system: n uniform points in [0, L)^3 (xorshift64*), charges +1, -1, ... (the last
+// one 0 for odd n), neutral.
+void tuning_system(double L, int64_t n, std::vector<double>& x, std::vector<double>& rho) {
+    x.resize(3 * static_cast<size_t>(n));
+    rho.resize(static_cast<size_t>(n));
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    for (auto& v : x) {
+        st ^= st >> 12;
+        st ^= st << 25;
+        st ^= st >> 27;
+        v = L * static_cast<double>((st * 0x2545F4914F6CDD1Dull) >> 11) * 0x1.0p-53;
+    }
+    for (int64_t i = 0; i < n; ++i) rho[i] = (i % 2 == 0) ? 1.0 : -1.0;
+    if (n % 2) rho[n - 1] = 0.0;
 }
 
-int ewald_plan_params(double L, int64_t n, double tol, const ewald_opts* opts, ewald_params* out) {
-    if (!out) return fail(EWALD_EINVAL, "out is NULL");
+int plan_autotune(double L, int64_t n, double tol, const ewald_opts& o, ewald_plan* out) {
+    ewald_opts base = o;
+    base.autotune = 0;
     try {
-        const ewald_opts o = opts ? *opts : pswf::default_opts();
-        *out = pswf::make_plan(L, n, tol, o).p;
-        return EWALD_OK;
+        pswf::make_plan(L, n, tol, base);   // argument validation before any allocation
     } catch (const std::invalid_argument& e) {
         return fail(EWALD_EINVAL, e.what());
     } catch (const std::length_error& e) {
@@ -464,9 +497,73 @@ int ewald_plan_params(double L, int64_t n, double tol, const ewald_opts* opts, e
     } catch (const std::exception& e) {
         return fail(EWALD_EINVAL, e.what());
     }
+    std::vector<double> xh, rh;
+    tuning_system(L, n, xh, rh);
+    double *xd = nullptr, *rd = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&]() {
+        if (xd) cudaFree(xd);
+        if (rd) cudaFree(rd);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (st) cudaStreamDestroy(st);
+    };
+    if (cudaMalloc(&xd, sizeof(double) * xh.size()) != cudaSuccess ||
+        cudaMalloc(&rd, sizeof(double) * rh.size()) != cudaSuccess ||
+        cudaMemcpy(xd, xh.data(), sizeof(double) * xh.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(rd, rh.data(), sizeof(double) * rh.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return fail(EWALD_ENOMEM, "autotune: device allocation failed");
+    }
+    ewald_plan best = nullptr;
+    float best_ms = 0.f;
+    std::vector<int> seen_m;
+    for (const double gd : {1.5, 2.0, 3.0, 4.0, 6.0, 8.0, 12.0}) {
+        ewald_opts c = base;
+        c.grid_density = gd;
+        int m = 0;
+        try {
+            m = pswf::make_plan(L, n, tol, c).p.m;
+        } catch (const std::exception&) {
+            continue;   // e.g. a grid beyond the size limit
+        }
+        if (std::find(seen_m.begin(), seen_m.end(), m) != seen_m.end()) continue;
+        seen_m.push_back(m);
+        ewald_plan cand = nullptr;
+        if (plan_create_impl(L, n, tol, &c, &cand) != EWALD_OK) continue;
+        int rc = eval_device(cand, xd, rd, nullptr, nullptr, st);   // warm-up
+        float ms = 0.f;
+        if (rc == EWALD_OK) {
+            cudaEventRecord(e0, st);
+            for (int k = 0; k < 3 && rc == EWALD_OK; ++k) rc = eval_device(cand, xd, rd, nullptr, nullptr, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                rc = EWALD_ECUDA;
+        }
+        if (rc != EWALD_OK) {
+            delete cand;
+            cleanup();
+            return rc;
+        }
+        if (!best || ms < best_ms) {
+            delete best;
+            best = cand;
+            best_ms = ms;
+        } else {
+            delete cand;
+        }
+    }
+    cleanup();
+    if (!best) return fail(EWALD_EINVAL, "autotune: no candidate plan could be created");
+    *out = best;
+    return EWALD_OK;
 }
 
-int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out) {
+int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out) {
     if (!out) return fail(EWALD_EINVAL, "out is NULL");
     *out = nullptr;
     if (n > (int64_t(1) << 30)) return fail(EWALD_ETOOBIG, "n beyond 2^30 particles");
@@ -646,6 +743,99 @@ int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, e
     return EWALD_OK;
 }
 
+// Per-system status triple and energy of a batch, gathered for one device-to-host copy.
+__global__ void k_batch_gather(const double* const* __restrict__ src, int nsys, double* __restrict__ out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nsys) return;
+    const double* st = src[2 * b];
+    const double* en = src[2 * b + 1];
+    out[4 * b + 0] = st[0];
+    out[4 * b + 1] = st[1];
+    out[4 * b + 2] = st[2];
+    out[4 * b + 3] = en[0];
+}
+
+// Captures every member's pipeline into one graph: the origin stream forks to one stream per system,
+// each runs eval_device (which forks further to the member's own real-space / Alg. 2 streams), and the
+// origin joins them all before the gather.
+int capture_batch(ewald_plan p, const double* x, const double* rho, double* phi, double* f) {
+    if (p->bexec) {
+        cudaGraphExecDestroy(p->bexec);
+        p->bexec = nullptr;
+    }
+    PSWF_CUDA(cudaStreamBeginCapture(p->bcap, cudaStreamCaptureModeThreadLocal));
+    int rc = EWALD_OK;
+    auto step = [&](cudaError_t e) {
+        if (rc == EWALD_OK && e != cudaSuccess) rc = fail(EWALD_ECUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    };
+    step(cudaEventRecord(p->bstart, p->bcap));
+    const int ns = static_cast<int>(p->members.size());
+    for (int b = 0; b < ns && rc == EWALD_OK; ++b) {
+        const size_t o = static_cast<size_t>(p->offsets[b]);
+        step(cudaStreamWaitEvent(p->bstreams[b], p->bstart, 0));
+        if (rc == EWALD_OK)
+            rc = eval_device(p->members[b], x + 3 * o, rho + o, phi ? phi + o : nullptr, f ? f + 3 * o : nullptr,
+                             p->bstreams[b]);
+        step(cudaEventRecord(p->bevents[b], p->bstreams[b]));
+        step(cudaStreamWaitEvent(p->bcap, p->bevents[b], 0));
+    }
+    if (rc == EWALD_OK) {
+        k_batch_gather<<<(ns + 127) / 128, 128, 0, p->bcap>>>(p->bsrc_d, ns, p->bout_d);
+        step(cudaGetLastError());
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(p->bcap, &graph);
+    if (rc == EWALD_OK && ee != cudaSuccess) rc = fail(EWALD_ECUDA, std::string("batch capture: ") + cudaGetErrorString(ee));
+    if (rc == EWALD_OK) {
+        const cudaError_t ei = cudaGraphInstantiate(&p->bexec, graph, 0);
+        if (ei != cudaSuccess) {
+            p->bexec = nullptr;
+            rc = fail(EWALD_ECUDA, std::string("batch graph instantiation: ") + cudaGetErrorString(ei));
+        }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    if (rc == EWALD_OK) {
+        p->bkey[0] = x;
+        p->bkey[1] = rho;
+        p->bkey[2] = phi;
+        p->bkey[3] = f;
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ewald_opts_default(ewald_opts* opts) {
+    if (!opts) return fail(EWALD_EINVAL, "opts is NULL");
+    *opts = pswf::default_opts();
+    return EWALD_OK;
+}
+
+int ewald_plan_params(double L, int64_t n, double tol, const ewald_opts* opts, ewald_params* out) {
+    if (!out) return fail(EWALD_EINVAL, "out is NULL");
+    try {
+        const ewald_opts o = opts ? *opts : pswf::default_opts();
+        *out = pswf::make_plan(L, n, tol, o).p;
+        return EWALD_OK;
+    } catch (const std::invalid_argument& e) {
+        return fail(EWALD_EINVAL, e.what());
+    } catch (const std::length_error& e) {
+        return fail(EWALD_ETOOBIG, e.what());
+    } catch (const std::exception& e) {
+        return fail(EWALD_EINVAL, e.what());
+    }
+}
+
+int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out) {
+    if (!out) return fail(EWALD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (opts && opts->autotune == 1) return plan_autotune(L, n, tol, *opts, out);
+    return plan_create_impl(L, n, tol, opts, out);
+}
+
 int ewald_plan_query(ewald_plan plan, ewald_params* out) {
     if (!plan || !out) return fail(EWALD_EINVAL, "NULL argument");
     *out = plan->hp.p;
@@ -655,6 +845,7 @@ int ewald_plan_query(ewald_plan plan, ewald_params* out) {
 int ewald_eval(ewald_plan plan, const double* x, const double* rho, double* phi, double* force, double* energy,
                void* stream) {
     if (!plan || !x || !rho) return fail(EWALD_EINVAL, "NULL plan, x or rho");
+    if (plan->is_batch) return fail(EWALD_EINVAL, "batch plan: use ewald_eval_batch");
     int rc;
     if ((rc = check_ptr_device(x, "x")) || (rc = check_ptr_device(rho, "rho")) ||
         (rc = check_ptr_device(phi, "phi")) || (rc = check_ptr_device(force, "force")))
@@ -668,6 +859,7 @@ int ewald_eval(ewald_plan plan, const double* x, const double* rho, double* phi,
 int ewald_eval_host(ewald_plan plan, const double* x, const double* rho, double* phi, double* force, double* energy,
                     void* stream) {
     if (!plan || !x || !rho) return fail(EWALD_EINVAL, "NULL plan, x or rho");
+    if (plan->is_batch) return fail(EWALD_EINVAL, "batch plan: use ewald_eval_batch");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t n = static_cast<size_t>(plan->g.n);
     PSWF_CUDA(cudaMemcpyAsync(plan->x_stage, x, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s));
@@ -683,12 +875,12 @@ int ewald_eval_host(ewald_plan plan, const double* x, const double* rho, double*
 }
 
 int ewald_check(ewald_plan plan, void* stream) {
-    if (!plan) return fail(EWALD_EINVAL, "NULL plan");
+    if (!plan || plan->is_batch) return fail(EWALD_EINVAL, "NULL or batch plan");
     return read_status(plan, static_cast<cudaStream_t>(stream), nullptr);
 }
 
 int ewald_debug_grid(ewald_plan plan, int which, double* host_out) {
-    if (!plan || !host_out || (which != 0 && which != 1)) return fail(EWALD_EINVAL, "bad argument");
+    if (!plan || plan->is_batch || !host_out || (which != 0 && which != 1)) return fail(EWALD_EINVAL, "bad argument");
     PSWF_CUDA(cudaDeviceSynchronize());
     const size_t m3 = static_cast<size_t>(plan->g.m) * plan->g.m * plan->g.m;
     const void* src = which == 0 ? plan->grid_a : plan->grid_b;
@@ -704,8 +896,88 @@ int ewald_debug_grid(ewald_plan plan, int which, double* host_out) {
 
 void ewald_plan_destroy(ewald_plan plan) { delete plan; }
 
+int ewald_plan_batch_create(int nsys, const double* L, const int64_t* n, double tol, const ewald_opts* opts,
+                            ewald_plan* out) {
+    if (!out) return fail(EWALD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nsys < 1 || nsys > 4096) return fail(EWALD_EINVAL, "nsys must lie in [1, 4096]");
+    if (!L || !n) return fail(EWALD_EINVAL, "NULL L or n");
+    ewald_opts o = opts ? *opts : pswf::default_opts();
+    o.autotune = 0;
+    ewald_plan p = new (std::nothrow) ewald_plan_s();
+    if (!p) return fail(EWALD_ENOMEM, "host allocation failed");
+    p->is_batch = true;
+    p->offsets.push_back(0);
+    for (int b = 0; b < nsys; ++b) {
+        ewald_plan m = nullptr;
+        const int rc = plan_create_impl(L[b], n[b], tol, &o, &m);
+        if (rc != EWALD_OK) {
+            const std::string why = g_last_error;
+            delete p;
+            return fail(rc, "system " + std::to_string(b) + ": " + why);
+        }
+        p->members.push_back(m);
+        p->offsets.push_back(p->offsets.back() + n[b]);
+    }
+    p->hp = p->members[0]->hp;
+    p->g = p->members[0]->g;
+    cudaGetDevice(&p->device);
+    p->bstreams.assign(nsys, nullptr);
+    p->bevents.assign(nsys, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&p->bcap, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&p->bstart, cudaEventDisableTiming) == cudaSuccess;
+    for (int b = 0; b < nsys && ok; ++b)
+        ok = cudaStreamCreateWithFlags(&p->bstreams[b], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&p->bevents[b], cudaEventDisableTiming) == cudaSuccess;
+    std::vector<const double*> src(2 * static_cast<size_t>(nsys));
+    for (int b = 0; b < nsys; ++b) {
+        src[2 * b] = p->members[b]->status;
+        src[2 * b + 1] = p->members[b]->energy_d;
+    }
+    ok = ok && cudaMalloc(reinterpret_cast<void**>(&p->bout_d), sizeof(double) * 4 * nsys) == cudaSuccess &&
+         cudaMallocHost(reinterpret_cast<void**>(&p->bout_h), sizeof(double) * 4 * nsys) == cudaSuccess &&
+         cudaMalloc(reinterpret_cast<void**>(&p->bsrc_d), sizeof(double*) * src.size()) == cudaSuccess &&
+         cudaMemcpy(p->bsrc_d, src.data(), sizeof(double*) * src.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        delete p;
+        return fail(EWALD_ENOMEM, "batch plan: stream, event or buffer allocation failed");
+    }
+    *out = p;
+    return EWALD_OK;
+}
+
+int ewald_eval_batch(ewald_plan plan, const int64_t* offsets, const double* x, const double* rho, double* phi,
+                     double* force, double* energy, void* stream) {
+    if (!plan || !plan->is_batch) return fail(EWALD_EINVAL, "not a batch plan");
+    if (!offsets || !x || !rho) return fail(EWALD_EINVAL, "NULL offsets, x or rho");
+    const int ns = static_cast<int>(plan->members.size());
+    for (int b = 0; b <= ns; ++b)
+        if (offsets[b] != plan->offsets[b])
+            return fail(EWALD_EINVAL, "offsets do not match the batch plan's particle counts (entry " +
+                                          std::to_string(b) + ")");
+    int rc;
+    if ((rc = check_ptr_device(x, "x")) || (rc = check_ptr_device(rho, "rho")) ||
+        (rc = check_ptr_device(phi, "phi")) || (rc = check_ptr_device(force, "force")))
+        return rc;
+    if (!plan->bexec || plan->bkey[0] != x || plan->bkey[1] != rho || plan->bkey[2] != phi || plan->bkey[3] != force)
+        if ((rc = capture_batch(plan, x, rho, phi, force))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PSWF_CUDA(cudaGraphLaunch(plan->bexec, s));
+    PSWF_CUDA(cudaMemcpyAsync(plan->bout_h, plan->bout_d, sizeof(double) * 4 * ns, cudaMemcpyDeviceToHost, s));
+    PSWF_CUDA(cudaStreamSynchronize(s));
+    for (int b = 0; b < ns; ++b) {
+        const double* o = plan->bout_h + 4 * b;
+        if (energy) energy[b] = o[3];
+        if (o[2] > 0) return fail(EWALD_ENONFINITE, "system " + std::to_string(b) + ": non-finite position or charge");
+        if (std::fabs(o[0]) > 1e-10 * o[1])
+            return fail(EWALD_ENONNEUTRAL, "system " + std::to_string(b) + ": charges are not neutral");
+    }
+    return EWALD_OK;
+}
+
 int ewald_profile(ewald_plan plan, int enable) {
-    if (!plan) return fail(EWALD_EINVAL, "NULL plan");
+    if (!plan || plan->is_batch) return fail(EWALD_EINVAL, "NULL or batch plan");
     if (enable) {
         PSWF_CUDA(cudaDeviceSynchronize());
         plan->clear_prof();

@@ -289,6 +289,7 @@ ewald_opts default_opts() {
     o.tol_safety = 0.25;
     o.sr_reach = 0;
     o.window_extra = 0;
+    o.autotune = 0;
     return o;
 }
 
@@ -409,6 +410,7 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
     if (!(o.tol_safety > 0 && o.tol_safety <= 1)) throw std::invalid_argument("tol_safety must lie in (0, 1]");
     if (!(o.grid_density > 0)) throw std::invalid_argument("grid_density must be positive");
     if (o.window_extra < 0 || o.window_extra > 8) throw std::invalid_argument("window_extra must lie in [0, 8]");
+    if (o.autotune != 0 && o.autotune != 1) throw std::invalid_argument("autotune must be 0 or 1");
     if (o.sr_reach < 0 || o.sr_reach > 4) throw std::invalid_argument("sr_reach must lie in [0, 4]");
 
     const double As = 5.0, Aw = 3.1;                      // Secs. 5.1.1 and 5.2.1
