@@ -4,6 +4,11 @@
 
 #include <algorithm>
 #include <cmath>
+#include <future>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <tuple>
 #include <cstring>
 #include <stdexcept>
 #include <string>
@@ -109,6 +114,43 @@ namespace pswf {
 void record_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace pswf
 
+namespace {
+
+// cuFFT plans are shared process-wide by (device, m, type): creating them dominates the setup of small
+// plans, and batches hold many systems of the same grid size.  A shared handle is used only under
+// g_fft_mu: each exec first sets the calling plan's stream and its own work area (the work area
+// pointer is fixed into the launched kernels at exec time, also during graph capture).
+struct FftCache {
+    std::mutex mu;
+    std::map<std::tuple<int, int, int>, std::pair<cufftHandle, size_t>> plans;   // -> (handle, work bytes)
+};
+FftCache& fft_cache() {
+    static FftCache* c = new FftCache();   // never destroyed: handles outlive static teardown order
+    return *c;
+}
+
+int shared_fft(int device, int m, cufftType type, cufftHandle* h, size_t* work) {
+    FftCache& c = fft_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    const auto key = std::make_tuple(device, m, static_cast<int>(type));
+    auto it = c.plans.find(key);
+    if (it == c.plans.end()) {
+        cufftHandle nh = 0;
+        size_t ws = 0;
+        if (cufftCreate(&nh) != CUFFT_SUCCESS) return fail(EWALD_ECUFFT, "cufftCreate failed");
+        if (cufftSetAutoAllocation(nh, 0) != CUFFT_SUCCESS || cufftMakePlan3d(nh, m, m, m, type, &ws) != CUFFT_SUCCESS) {
+            cufftDestroy(nh);
+            return fail(EWALD_ECUFFT, "cufftMakePlan3d failed for m = " + std::to_string(m));
+        }
+        it = c.plans.emplace(key, std::make_pair(nh, ws)).first;
+    }
+    *h = it->second.first;
+    *work = it->second.second;
+    return EWALD_OK;
+}
+
+}  // namespace
+
 struct ewald_plan_s {
     pswf::HostPlan hp;
     pswf::Geom g{};
@@ -153,8 +195,8 @@ struct ewald_plan_s {
     double* x_stage = nullptr;
     double* rho_stage = nullptr;
     double* status_h = nullptr;   // pinned
-    cufftHandle fwd = 0, inv = 0;
-    bool have_fwd = false, have_inv = false;
+    cufftHandle fwd = 0, inv = 0;   // shared (fft_cache), not owned
+    void* fft_work = nullptr;        // this plan's cuFFT work area (forward and inverse run in sequence)
     // the real-space sum runs on its own stream, concurrently with spread -> FFT -> interpolation
     // (Alg. 2 on a high-priority stream so its short kernels are not starved by the real-space blocks)
     cudaStream_t s_short = nullptr, s_alg2 = nullptr;
@@ -203,8 +245,7 @@ struct ewald_plan_s {
         if (ev_join2) cudaEventDestroy(ev_join2);
         if (s_short) cudaStreamDestroy(s_short);
         if (s_alg2) cudaStreamDestroy(s_alg2);
-        if (have_fwd) cufftDestroy(fwd);
-        if (have_inv) cufftDestroy(inv);
+        if (fft_work) cudaFree(fft_work);
         for (ewald_plan_s* m : members) delete m;
         for (cudaStream_t st : bstreams) cudaStreamDestroy(st);
         for (cudaEvent_t e : bevents) cudaEventDestroy(e);
@@ -218,6 +259,16 @@ struct ewald_plan_s {
 };
 
 namespace {
+
+// Runs a shared cuFFT plan on stream s with plan p's work area.
+template <class F>
+int fft_exec(ewald_plan p, cufftHandle h, cudaStream_t s, F exec) {
+    std::lock_guard<std::mutex> lk(fft_cache().mu);
+    PSWF_CUFFT(cufftSetStream(h, s));
+    PSWF_CUFFT(cufftSetWorkArea(h, p->fft_work));
+    PSWF_CUFFT(exec());
+    return EWALD_OK;
+}
 
 template <typename real, int D>
 cudaError_t launch_short_d(ewald_plan p, const pswf::Vec4<real>* sr_rec, const pswf::Vec4<real>* sr_lo, double* phi,
@@ -306,13 +357,17 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     // Alg. 2 steps 2-4
     p->mark(2, true, s);
     p->mark(3, false, s);
-    PSWF_CUFFT(cufftSetStream(p->fwd, s));
-    PSWF_CUFFT(cufftSetStream(p->inv, s));
+    int frc;
     if constexpr (sizeof(real) == 8) {
-        PSWF_CUFFT(cufftExecD2Z(p->fwd, static_cast<cufftDoubleReal*>(p->grid_a), static_cast<cufftDoubleComplex*>(p->spec)));
+        frc = fft_exec(p, p->fwd, s, [&] {
+            return cufftExecD2Z(p->fwd, static_cast<cufftDoubleReal*>(p->grid_a), static_cast<cufftDoubleComplex*>(p->spec));
+        });
     } else {
-        PSWF_CUFFT(cufftExecR2C(p->fwd, static_cast<cufftReal*>(p->grid_a), static_cast<cufftComplex*>(p->spec)));
+        frc = fft_exec(p, p->fwd, s, [&] {
+            return cufftExecR2C(p->fwd, static_cast<cufftReal*>(p->grid_a), static_cast<cufftComplex*>(p->spec));
+        });
     }
+    if (frc) return frc;
     p->mark(3, true, s);
     p->mark(4, false, s);
     const int ns = m * m * (m / 2 + 1);
@@ -323,10 +378,15 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     p->mark(4, true, s);
     p->mark(5, false, s);
     if constexpr (sizeof(real) == 8) {
-        PSWF_CUFFT(cufftExecZ2D(p->inv, static_cast<cufftDoubleComplex*>(p->spec), static_cast<cufftDoubleReal*>(p->grid_b)));
+        frc = fft_exec(p, p->inv, s, [&] {
+            return cufftExecZ2D(p->inv, static_cast<cufftDoubleComplex*>(p->spec), static_cast<cufftDoubleReal*>(p->grid_b));
+        });
     } else {
-        PSWF_CUFFT(cufftExecC2R(p->inv, static_cast<cufftComplex*>(p->spec), static_cast<cufftReal*>(p->grid_b)));
+        frc = fft_exec(p, p->inv, s, [&] {
+            return cufftExecC2R(p->inv, static_cast<cufftComplex*>(p->spec), static_cast<cufftReal*>(p->grid_b));
+        });
     }
+    if (frc) return frc;
     p->mark(5, true, s);
     p->mark(6, false, s);
     // Alg. 2 step 5 + self term + forces
@@ -392,9 +452,10 @@ int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* ph
     PSWF_CUDA(LaunchFF::halo(static_cast<const float2*>(p->scratch), p->tile_off, g, static_cast<double*>(p->grid_a), s));
     p->mark(2, true, s);
     p->mark(3, false, s);
-    PSWF_CUFFT(cufftSetStream(p->fwd, s));
-    PSWF_CUFFT(cufftSetStream(p->inv, s));
-    PSWF_CUFFT(cufftExecD2Z(p->fwd, static_cast<cufftDoubleReal*>(p->grid_a), static_cast<cufftDoubleComplex*>(p->spec)));
+    int frc = fft_exec(p, p->fwd, s, [&] {
+        return cufftExecD2Z(p->fwd, static_cast<cufftDoubleReal*>(p->grid_a), static_cast<cufftDoubleComplex*>(p->spec));
+    });
+    if (frc) return frc;
     p->mark(3, true, s);
     p->mark(4, false, s);
     const int ns = m * m * (m / 2 + 1);
@@ -404,7 +465,10 @@ int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* ph
     PSWF_CUDA(cudaGetLastError());
     p->mark(4, true, s);
     p->mark(5, false, s);
-    PSWF_CUFFT(cufftExecZ2D(p->inv, static_cast<cufftDoubleComplex*>(p->spec), static_cast<cufftDoubleReal*>(p->grid_b)));
+    frc = fft_exec(p, p->inv, s, [&] {
+        return cufftExecZ2D(p->inv, static_cast<cufftDoubleComplex*>(p->spec), static_cast<cufftDoubleReal*>(p->grid_b));
+    });
+    if (frc) return frc;
     const size_t m3 = static_cast<size_t>(m) * m * m;
     PSWF_CUDA(LaunchFF::to_ff(static_cast<const double*>(p->grid_b), m3, static_cast<float2*>(p->grid_ff), s));
     p->mark(5, true, s);
@@ -467,7 +531,8 @@ int check_ptr_device(const void* ptr, const char* name) {
 
 namespace {
 
-int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out);
+int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out,
+                     const pswf::HostPlan* pre = nullptr);
 
 // Synthetic tuning system: n uniform points in [0, L)^3 (xorshift64*), charges +1, -1, ... (the last
 // one 0 for odd n), neutral.
@@ -563,7 +628,9 @@ int plan_autotune(double L, int64_t n, double tol, const ewald_opts& o, ewald_pl
     return EWALD_OK;
 }
 
-int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out) {
+// pre: the host plan computed already (batches plan their systems on several threads first)
+int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out,
+                     const pswf::HostPlan* pre) {
     if (!out) return fail(EWALD_EINVAL, "out is NULL");
     *out = nullptr;
     if (n > (int64_t(1) << 30)) return fail(EWALD_ETOOBIG, "n beyond 2^30 particles");
@@ -571,7 +638,7 @@ int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ew
     if (!p) return fail(EWALD_ENOMEM, "host allocation failed");
     try {
         const ewald_opts o = opts ? *opts : pswf::default_opts();
-        p->hp = pswf::make_plan(L, n, tol, o);
+        p->hp = pre ? *pre : pswf::make_plan(L, n, tol, o);
     } catch (const std::invalid_argument& e) {
         delete p;
         return fail(EWALD_EINVAL, e.what());
@@ -729,16 +796,16 @@ int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ew
         }
     }
     const cufftType tf = p->fp64 ? CUFFT_D2Z : CUFFT_R2C, ti = p->fp64 ? CUFFT_Z2D : CUFFT_C2R;
-    if (cufftPlan3d(&p->fwd, g.m, g.m, g.m, tf) != CUFFT_SUCCESS) {
+    size_t wf = 0, wi = 0;
+    if ((rc = shared_fft(p->device, g.m, tf, &p->fwd, &wf)) || (rc = shared_fft(p->device, g.m, ti, &p->inv, &wi))) {
         delete p;
-        return fail(EWALD_ECUFFT, "cufftPlan3d (forward) failed");
+        return rc;
     }
-    p->have_fwd = true;
-    if (cufftPlan3d(&p->inv, g.m, g.m, g.m, ti) != CUFFT_SUCCESS) {
+    if (cudaMalloc(&p->fft_work, std::max<size_t>(std::max(wf, wi), 256)) != cudaSuccess) {
+        cudaGetLastError();
         delete p;
-        return fail(EWALD_ECUFFT, "cufftPlan3d (inverse) failed");
+        return fail(EWALD_ENOMEM, "device allocation of the cuFFT work area failed");
     }
-    p->have_inv = true;
     *out = p;
     return EWALD_OK;
 }
@@ -908,9 +975,40 @@ int ewald_plan_batch_create(int nsys, const double* L, const int64_t* n, double 
     if (!p) return fail(EWALD_ENOMEM, "host allocation failed");
     p->is_batch = true;
     p->offsets.push_back(0);
+    // host planning (Alg. 3, fits, tables) of the systems on parallel threads
+    std::vector<pswf::HostPlan> hps(nsys);
+    std::vector<std::string> errs(nsys);
+    std::vector<int> codes(nsys, EWALD_OK);
+    {
+        const int nth = std::max(1, std::min<int>(nsys, static_cast<int>(std::thread::hardware_concurrency())));
+        std::vector<std::thread> th;
+        for (int t = 0; t < nth; ++t)
+            th.emplace_back([&, t] {
+                for (int b = t; b < nsys; b += nth) {
+                    try {
+                        hps[b] = pswf::make_plan(L[b], n[b], tol, o);
+                    } catch (const std::invalid_argument& e) {
+                        codes[b] = EWALD_EINVAL;
+                        errs[b] = e.what();
+                    } catch (const std::length_error& e) {
+                        codes[b] = EWALD_ETOOBIG;
+                        errs[b] = e.what();
+                    } catch (const std::exception& e) {
+                        codes[b] = EWALD_EINVAL;
+                        errs[b] = e.what();
+                    }
+                }
+            });
+        for (auto& t : th) t.join();
+    }
+    for (int b = 0; b < nsys; ++b)
+        if (codes[b] != EWALD_OK) {
+            delete p;
+            return fail(codes[b], "system " + std::to_string(b) + ": " + errs[b]);
+        }
     for (int b = 0; b < nsys; ++b) {
         ewald_plan m = nullptr;
-        const int rc = plan_create_impl(L[b], n[b], tol, &o, &m);
+        const int rc = plan_create_impl(L[b], n[b], tol, &o, &m, &hps[b]);
         if (rc != EWALD_OK) {
             const std::string why = g_last_error;
             delete p;

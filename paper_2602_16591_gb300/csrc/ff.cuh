@@ -97,6 +97,19 @@ __device__ __forceinline__ void ff_acc_f(ff& acc, ff a, float b) {
     acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, e));
 }
 
+// Horner step p * u + c keeping p unnormalised: the product's rounding error (FMA) and the cross terms
+// go to the low word, the sum with c.h is exact (TwoSum) and its error joins the low word too; no
+// renormalisation between steps (|p.l| stays within a few ulp(p.h)).  12 operations instead of 18 for
+// ff_add(ff_mul(p, u), c).  Renormalise the result with ff_norm.
+__device__ __forceinline__ ff ff_horner_step(ff p, ff u, ff c) {
+    const float ph = __fmul_rn(p.h, u.h);
+    float pl = __fmaf_rn(p.h, u.h, -ph);
+    pl = __fmaf_rn(p.h, u.l, pl);
+    pl = __fmaf_rn(p.l, u.h, pl);
+    const ff s = two_sum(ph, c.h);
+    return ff{s.h, __fadd_rn(s.l, __fadd_rn(pl, c.l))};
+}
+
 // renormalise an accumulator (|l| <= ulp(h)/2 afterwards)
 __device__ __forceinline__ ff ff_norm(ff a) { return two_sum(a.h, a.l); }
 

@@ -61,8 +61,8 @@ __device__ __forceinline__ ff window_weight_ff(const float* __restrict__ ch, con
     float t = h[deg];
     for (int k = deg - 1; k >= kf; --k) t = fmaf(t, z.h, h[k]);
     ff w = ff_make(t);
-    for (int k = kf - 1; k >= 0; --k) w = ff_add(ff_mul(w, z), ff{h[k], l[k]});
-    return w;
+    for (int k = kf - 1; k >= 0; --k) w = ff_horner_step(w, z, ff{h[k], l[k]});
+    return ff_norm(w);
 }
 
 // ---- Alg. 2 step 1: spreading with float-float register columns, float2 {h, l} slabs ----------------
@@ -406,10 +406,12 @@ __global__ void __launch_bounds__(32 * kShortWarps, 4) k_short_ff(const float4* 
                     p1 = ff_make(p1f);
                     qq = ff_make(qqf);
                 } else {
-                    p1 = ff_add(ff_mul(p1, u), ff{kp.p1h[kk], kp.p1l[kk]});
-                    qq = ff_add(ff_mul(qq, u), ff{kp.qh[kk], kp.ql[kk]});
+                    p1 = ff_horner_step(p1, u, ff{kp.p1h[kk], kp.p1l[kk]});
+                    qq = ff_horner_step(qq, u, ff{kp.qh[kk], kp.ql[kk]});
                 }
             }
+            p1 = ff_norm(p1);
+            qq = ff_norm(qq);
             const ff ri = ff_rsqrt(in ? r2 : ff_make(1.f));
             const ff qj = in ? ff{sh.w, sl.w} : ff{0.f, 0.f};
             const ff c0 = ff_mul(qj, ff_sub(ri, p1));

@@ -159,3 +159,31 @@ def test_precision_paths():
     assert pe.plan_params(1.0, 50_000, 1e-6, precision="floatfloat").precision == pe.EWALD_FLOATFLOAT
     with pytest.raises(pe.EwaldError):
         pe.plan_params(1.0, 50_000, 1e-6, precision=7)
+
+
+def test_opts_defaults_and_autotune_validation():
+    import ctypes
+    o = pe.make_opts()
+    assert o.autotune == 0 and o.grid_density == 3.0 and o.tol_safety == 0.25 and o.window_extra == 0
+    o.autotune = 2
+    p = pe.ewald_params()
+    assert pe.lib.ewald_plan_params(1.0, 1000, 1e-6, ctypes.byref(o), ctypes.byref(p)) == pe.EWALD_EINVAL
+
+
+def test_batch_arguments_rejected_before_any_device_work():
+    import ctypes
+    h = ctypes.c_void_p()
+    L = np.array([1.0, 2.0])
+    n = np.array([100, 200], dtype=np.int64)
+    o = pe.make_opts()
+    args = lambda k, Lp, np_: (k, Lp, np_, 1e-6, ctypes.byref(o), ctypes.byref(h))  # noqa: E731
+    Lp, Np = L.ctypes.data_as(ctypes.c_void_p), n.ctypes.data_as(ctypes.c_void_p)
+    assert pe.lib.ewald_plan_batch_create(*args(0, Lp, Np)) == pe.EWALD_EINVAL
+    assert pe.lib.ewald_plan_batch_create(*args(5000, Lp, Np)) == pe.EWALD_EINVAL
+    assert pe.lib.ewald_plan_batch_create(*args(2, None, Np)) == pe.EWALD_EINVAL
+    bad = np.array([-1.0, 2.0])
+    assert pe.lib.ewald_plan_batch_create(*args(2, bad.ctypes.data_as(ctypes.c_void_p), Np)) == pe.EWALD_EINVAL
+    assert b"system 0" in pe.lib.ewald_last_error()
+    off = np.array([0, 100, 300], dtype=np.int64)
+    assert pe.lib.ewald_eval_batch(None, off.ctypes.data_as(ctypes.c_void_p), None, None, None, None, None,
+                                   None) == pe.EWALD_EINVAL
