@@ -17,9 +17,9 @@ size_t spread_smem_ff(int P, int degw) {
            sizeof(int) * kSpreadFFChunk;
 }
 
-size_t interp_smem_ff(int P, int degw) {
+size_t interp_smem_ff(int P, int degw, bool staged) {
     const int E = kTile64 + P - 1;
-    return sizeof(ff) * (static_cast<size_t>(E) * E * E + kInterpFFWarps * kInterpFFNB * 6 * P) +
+    return sizeof(ff) * ((staged ? static_cast<size_t>(E) * E * E : 0) + kInterpFFWarps * kInterpFFNB * 6 * P) +
            sizeof(float) * 4 * P * (degw + 1);
 }
 
@@ -38,8 +38,11 @@ template <int P>
 cudaError_t interp_p(int ntiles, const Geom& g, const float2* grid, const float4* rh, const float4* rl,
                      const int2* idx, const int* tile_off, const float* wc, const float* dwc, int kf, float iah,
                      float ial, double* phi, double* f, cudaStream_t s) {
-    const size_t smem = interp_smem_ff(P, g.degw);
-    auto kern = k_interp_ff<P>;
+    // stage the tile's block while two blocks still fit an SM (measured: staged wins at P = 16, direct
+    // L1/L2 reads win at P = 19, where a staged block allows one block per SM)
+    const bool staged = interp_smem_ff(P, g.degw, true) <= 113 * 1024;
+    const size_t smem = interp_smem_ff(P, g.degw, staged);
+    auto kern = staged ? k_interp_ff<P, true> : k_interp_ff<P, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     kern<<<ntiles, 32 * kInterpFFWarps, smem, s>>>(grid, rh, rl, idx, tile_off, wc, dwc, kf, g, iah, ial, phi, f);

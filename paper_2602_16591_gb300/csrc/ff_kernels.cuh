@@ -186,7 +186,10 @@ static __global__ void k_grid_to_ff(const double* __restrict__ grid, size_t coun
 // (b, c) pairs of the stencil); the inner sums over a are compensated dot products (ff_acc).
 constexpr int kInterpFFNB = 4, kInterpFFWarps = 8;
 
-template <int P>
+// STAGED: the tile's extended block is staged in shared memory (E^3 float2); otherwise the grid is read
+// through L1/L2 (it is L2-resident at these sizes) with per-particle wrapped index tables, so the block
+// needs little shared memory and occupancy is set by registers.
+template <int P, bool STAGED>
 __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2* __restrict__ grid,
                                                                    const float4* __restrict__ rec_h,
                                                                    const float4* __restrict__ rec_l,
@@ -206,8 +209,8 @@ __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2*
     const int nc = P * (degw + 1);
     const int tz = tile % nt, ty = (tile / nt) % nt, tx = tile / (nt * nt);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ff* G = reinterpret_cast<ff*>(smem_raw);                          // E^3
-    ff* sw = G + E * E * E;                                           // NWARP * NB * 6 * P
+    ff* G = reinterpret_cast<ff*>(smem_raw);                          // E^3 (STAGED only)
+    ff* sw = G + (STAGED ? E * E * E : 0);                            // NWARP * NB * 6 * P
     float* sch = reinterpret_cast<float*>(sw + NWARP * NB * 6 * P);   // window hi, lo, derivative hi, lo
     float* scl = sch + nc;
     float* sdh = scl + nc;
@@ -216,11 +219,14 @@ __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2*
         sch[i] = wc[i];
         sdh[i] = dwc[i];
     }
-    for (int e = threadIdx.x; e < E * E * E; e += blockDim.x) {
-        const int ez = e % E, ey = (e / E) % E, ex = e / (E * E);
-        const int gx = (tx * T + ex) % m, gy = (ty * T + ey) % m, gz = (tz * T + ez) % m;
-        const float2 v = grid[(static_cast<size_t>(gx) * m + gy) * m + gz];
-        G[e] = ff{v.x, v.y};
+    __shared__ int sxo[NWARP][P], syo[NWARP][P], szo[NWARP][P];   // unstaged: wrapped grid offsets
+    if constexpr (STAGED) {
+        for (int e = threadIdx.x; e < E * E * E; e += blockDim.x) {
+            const int ez = e % E, ey = (e / E) % E, ex = e / (E * E);
+            const int gx = (tx * T + ex) % m, gy = (ty * T + ey) % m, gz = (tz * T + ez) % m;
+            const float2 v = grid[(static_cast<size_t>(gx) * m + gy) * m + gz];
+            G[e] = ff{v.x, v.y};
+        }
     }
     __syncthreads();
     const ff inv_alpha{inv_alpha_h, inv_alpha_l};
@@ -243,22 +249,41 @@ __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2*
             const int2 id = idx[b0 + j];
             const int ox = id.x & 0xff, oy = (id.x >> 8) & 0xff, oz = (id.x >> 16) & 0xff;
             const ff* wp = ww + j * 6 * P;
+            int xo[P];
+            if constexpr (!STAGED) {   // wrapped row offsets of the particle's stencil
+                __syncwarp();
+                if (lane < P) {
+                    sxo[warp][lane] = ((tx * T + ox + lane) % m) * m * m;
+                    syo[warp][lane] = ((ty * T + oy + lane) % m) * m;
+                    szo[warp][lane] = (tz * T + oz + lane) % m;
+                }
+                __syncwarp();
+#pragma unroll
+                for (int a = 0; a < P; ++a) xo[a] = sxo[warp][a];
+            }
             ff ph{0.f, 0.f}, gx{0.f, 0.f}, gy{0.f, 0.f}, gz{0.f, 0.f};
 #pragma unroll 1
             for (int qi = 0; qi < NQ; ++qi) {   // not unrolled: the a-loop body is already P x 48 instructions
                 const int q = lane + 32 * qi;
                 if (q < P * P) {
                     const int bb = q / P, cc = q - (q / P) * P;
-                    const ff* col = G + (ox * E + oy + bb) * E + oz + cc;
+                    auto at = [&](int a) -> ff {
+                        if constexpr (STAGED) {
+                            return G[((ox + a) * E + oy + bb) * E + oz + cc];
+                        } else {
+                            const float2 v = __ldg(grid + xo[a] + syo[warp][bb] + szo[warp][cc]);
+                            return ff{v.x, v.y};
+                        }
+                    };
                     // four independent compensated chains (even / odd a) for instruction-level parallelism
                     ff s1a{0.f, 0.f}, s1b{0.f, 0.f}, s2a{0.f, 0.f}, s2b{0.f, 0.f};
 #pragma unroll
                     for (int a = 0; a < P; a += 2) {
-                        const ff v = col[a * E * E];
+                        const ff v = at(a);
                         ff_acc(s1a, v, wp[a]);
                         ff_acc(s2a, v, wp[3 * P + a]);
                         if (a + 1 < P) {
-                            const ff v2 = col[(a + 1) * E * E];
+                            const ff v2 = at(a + 1);
                             ff_acc(s1b, v2, wp[a + 1]);
                             ff_acc(s2b, v2, wp[3 * P + a + 1]);
                         }
