@@ -289,11 +289,11 @@ cudaError_t launch_short_d(ewald_plan p, const pswf::Vec4<real>* sr_rec, const p
     const int blocks = (ncells + pswf::kShortWarps - 1) / pswf::kShortWarps;
     // float32 pairs are cheap: the direct kernel; float64 pairs: the two-phase (queued) kernel
     if constexpr (sizeof(real) == 4)
-        pswf::k_short<real, D><<<blocks, 32 * pswf::kShortWarps, smem, s>>>(
-            sr_rec, p->sr_idx, sr_lo, p->sr_f32, p->cell_off, p->sr_cols, p->n_cols, p->sr_rcap, g, kp, phi, f);
+        pswf::k_short<D><<<blocks, 32 * pswf::kShortWarps, smem, s>>>(
+            sr_rec, p->sr_idx, sr_lo, p->cell_off, p->sr_cols, p->n_cols, p->sr_rcap, g, kp, phi, f);
     else
-        pswf::k_short_q<real, D><<<blocks, 32 * pswf::kShortWarps, smem, s>>>(
-            sr_rec, p->sr_idx, sr_lo, p->sr_f32, p->cell_off, p->sr_cols, p->n_cols, p->sr_rcap, g, kp, phi, f);
+        pswf::k_short_q<D><<<blocks, 32 * pswf::kShortWarps, smem, s>>>(
+            sr_rec, p->sr_idx, p->sr_f32, p->cell_off, p->sr_cols, p->n_cols, p->sr_rcap, g, kp, phi, f);
     return cudaGetLastError();
 }
 

@@ -638,24 +638,21 @@ struct ShortParams {
     float rc2f;
 };
 
-// 7 resident blocks per SM (<= 73 registers; measured best for the float32 instantiations)
-template <typename real, int D>
-__global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
-                                                            const Vec4<real>* __restrict__ lo, const float4* __restrict__ pf,
+// float32 plans.  7 resident blocks per SM (<= 73 registers; measured best).
+template <int D>
+__global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<float>* __restrict__ rec, const int2* __restrict__ idx,
+                                                            const Vec4<float>* __restrict__ lo,
                                                             const int* __restrict__ cell_off, const int4* __restrict__ cols,
-                                                            int ncols, int rcap, Geom g, const __grid_constant__ ShortParams<real, D> kp,
+                                                            int ncols, int rcap, Geom g, const __grid_constant__ ShortParams<float, D> kp,
                                                             double* __restrict__ phi_out, double* __restrict__ f_out) {
-    constexpr bool kF32 = sizeof(real) == 4;
     constexpr int NSH = 2 * kShortMaxR + 1;
     __shared__ float sh_hi[NSH], sh_lo[NSH];
-    __shared__ double sh_d[NSH];
     __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
-    __shared__ real stx[kShortWarps][kShortMaxT][4];           // exact target position and charge
-    __shared__ float stl[kShortWarps][kShortMaxT][4];          // float path: lo parts
+    __shared__ float stx[kShortWarps][kShortMaxT][4];          // target position (hi parts) and charge
+    __shared__ float stl[kShortWarps][kShortMaxT][4];          // lo parts of the position
     const int R = g.reach, nc = g.ncell;
     for (int k = threadIdx.x; k < 2 * R + 1; k += blockDim.x) {
         const double o = (k - R) * g.cellw;
-        sh_d[k] = o;
         sh_hi[k] = static_cast<float>(o);
         sh_lo[k] = static_cast<float>(o - static_cast<double>(sh_hi[k]));
     }
@@ -678,27 +675,20 @@ __global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<real>*
         // targets: exact parts and float32 test copies in shared memory (broadcast reads)
         __syncwarp();
         if (lane < nt) {
-            const Vec4<real> a = rec[t0 + lane];
+            const Vec4<float> a = rec[t0 + lane];
             stx[warp][lane][0] = a.x;
             stx[warp][lane][1] = a.y;
             stx[warp][lane][2] = a.z;
             stx[warp][lane][3] = a.w;
-            if constexpr (kF32) {
-                const Vec4<real> l = lo[t0 + lane];
-                stl[warp][lane][0] = l.x;
-                stl[warp][lane][1] = l.y;
-                stl[warp][lane][2] = l.z;
-            } else {
-                const float4 f = pf[t0 + lane];
-                stl[warp][lane][0] = f.x;
-                stl[warp][lane][1] = f.y;
-                stl[warp][lane][2] = f.z;
-            }
+            const Vec4<float> l = lo[t0 + lane];
+            stl[warp][lane][0] = l.x;
+            stl[warp][lane][1] = l.y;
+            stl[warp][lane][2] = l.z;
         }
         __syncwarp();
-        real acc[kShortMaxT][4];
+        float acc[kShortMaxT][4];
 #pragma unroll
-        for (int t = 0; t < kShortMaxT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = real(0);
+        for (int t = 0; t < kShortMaxT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
         int r = 0;
         for (int s0 = 0; s0 < total; s0 += 32) {
             const int p = s0 + lane;
@@ -707,70 +697,46 @@ __global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<real>*
             const int4 rg = rng[r];
             const int j = rg.x + (p - pos[r]);
             float sfx, sfy, sfz, szc;
-            if constexpr (kF32) {
-                const Vec4<real> a = rec[j];
-                sfx = a.x; sfy = a.y; sfz = a.z;
-                szc = lo[j].w;
-            } else {
-                const float4 f = pf[j];
-                sfx = f.x; sfy = f.y; sfz = f.z;
-                szc = f.w;
-            }
+            const Vec4<float> a = rec[j];
+            sfx = a.x; sfy = a.y; sfz = a.z;
+            szc = lo[j].w;
             const int4 col = scol[rg.w];
             const int ix = col.x + R, iy = col.y + R, iz = rg.z + (static_cast<int>(szc) - rg.y) + R;
             const float px = sfx + sh_hi[ix], py = sfy + sh_hi[iy], pz = sfz + sh_hi[iz];
             bool loaded = false;
-            real qj = real(0), ex = real(0), ey = real(0), ez = real(0);
+            float qj = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
 #pragma unroll
             for (int t = 0; t < kShortMaxT; ++t) {
                 if (t >= nt) break;   // nt is warp-uniform
                 float tx, ty, tz;
-                if constexpr (kF32) {
-                    tx = stx[warp][t][0]; ty = stx[warp][t][1]; tz = stx[warp][t][2];
-                } else {
-                    tx = stl[warp][t][0]; ty = stl[warp][t][1]; tz = stl[warp][t][2];
-                }
+                tx = stx[warp][t][0]; ty = stx[warp][t][1]; tz = stx[warp][t][2];
                 const float dxf = tx - px, dyf = ty - py, dzf = tz - pz;
                 const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
                 if (r2f < kp.rc2f && r2f > 0.f) {
                     if (!loaded) {
                         loaded = true;
-                        if constexpr (kF32) {
-                            const Vec4<real> l = lo[j];
-                            qj = rec[j].w;
-                            ex = l.x + sh_lo[ix];
-                            ey = l.y + sh_lo[iy];
-                            ez = l.z + sh_lo[iz];
-                        } else {
-                            const Vec4<real> a = rec[j];
-                            qj = a.w;
-                            ex = a.x + sh_d[ix];
-                            ey = a.y + sh_d[iy];
-                            ez = a.z + sh_d[iz];
-                        }
+                        const Vec4<float> l = lo[j];
+                        qj = rec[j].w;
+                        ex = l.x + sh_lo[ix];
+                        ey = l.y + sh_lo[iy];
+                        ez = l.z + sh_lo[iz];
                     }
-                    real ddx, ddy, ddz;
-                    if constexpr (kF32) {
-                        ddx = dxf + (stl[warp][t][0] - ex);
-                        ddy = dyf + (stl[warp][t][1] - ey);
-                        ddz = dzf + (stl[warp][t][2] - ez);
-                    } else {
-                        ddx = stx[warp][t][0] - ex;
-                        ddy = stx[warp][t][1] - ey;
-                        ddz = stx[warp][t][2] - ez;
-                    }
-                    const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    if (r2 < kp.rc2 && r2 > real(0)) {
-                        const real u = fma(r2, kp.two_over_rc2, real(-1));
-                        real p1 = kp.p1[D], qq = kp.q[D];
+                    float ddx, ddy, ddz;
+                    ddx = dxf + (stl[warp][t][0] - ex);
+                    ddy = dyf + (stl[warp][t][1] - ey);
+                    ddz = dzf + (stl[warp][t][2] - ez);
+                    const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+                    if (r2 < kp.rc2 && r2 > 0.f) {
+                        const float u = fma(r2, kp.two_over_rc2, float(-1));
+                        float p1 = kp.p1[D], qq = kp.q[D];
 #pragma unroll
                         for (int kk = D - 1; kk >= 0; --kk) {
                             p1 = fma(p1, u, kp.p1[kk]);
                             qq = fma(qq, u, kp.q[kk]);
                         }
-                        const real ri = rsqrt_r<real>(r2);
+                        const float ri = rsqrtf(r2);
                         acc[t][0] = fma(qj, ri - p1, acc[t][0]);
-                        const real cf = qj * fma(ri * ri, ri, qq);
+                        const float cf = qj * fma(ri * ri, ri, qq);
                         acc[t][1] = fma(cf, ddx, acc[t][1]);
                         acc[t][2] = fma(cf, ddy, acc[t][2]);
                         acc[t][3] = fma(cf, ddz, acc[t][3]);
@@ -783,12 +749,12 @@ __global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<real>*
         for (int t = 0; t < kShortMaxT; ++t) {
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                real x = acc[t][v];
+                float x = acc[t][v];
                 for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
                 acc[t][v] = x;
             }
         }
-        real mine[4] = {real(0), real(0), real(0), real(0)};
+        float mine[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
         for (int t = 0; t < kShortMaxT; ++t) {
             if (lane == t) {
@@ -812,20 +778,19 @@ __global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<real>*
 // Two-phase form of k_short (float64 plans): the float32 cutoff scan fills per-target pair queues, full
 // warps of queued pairs are evaluated with the arithmetic of k_short, so the costly float64 pair
 // evaluation runs without divergence.
-template <typename real, int D>
-__global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
-                                                              const Vec4<real>* __restrict__ lo, const float4* __restrict__ pf,
+template <int D>
+__global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<double>* __restrict__ rec, const int2* __restrict__ idx,
+                                                              const float4* __restrict__ pf,
                                                               const int* __restrict__ cell_off, const int4* __restrict__ cols,
-                                                              int ncols, int rcap, Geom g, const __grid_constant__ ShortParams<real, D> kp,
+                                                              int ncols, int rcap, Geom g, const __grid_constant__ ShortParams<double, D> kp,
                                                               double* __restrict__ phi_out, double* __restrict__ f_out) {
-    constexpr bool kF32 = sizeof(real) == 4;
     constexpr int NSH = 2 * kShortMaxR + 1, MT = kShortMaxT;
     static_assert(NSH <= 16, "queue entries pack 4-bit shift indices");
-    __shared__ float sh_hi[NSH], sh_lo[NSH];
+    __shared__ float sh_hi[NSH];
     __shared__ double sh_d[NSH];
     __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
-    __shared__ real stx[kShortWarps][MT][4];          // exact target position and charge
-    __shared__ float stl[kShortWarps][MT][4];         // float path: lo parts; float64 path: float32 copy
+    __shared__ double stx[kShortWarps][MT][4];          // exact target position and charge
+    __shared__ float stl[kShortWarps][MT][4];         // float32 copy of the target (cutoff pre-test)
     __shared__ int2 sq[kShortWarps][MT][kShortQCap];  // {source, ix | iy << 4 | iz << 8}
     __shared__ int sqlen[kShortWarps][MT];
     const int R = g.reach, nc = g.ncell;
@@ -833,7 +798,6 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<real>* 
         const double o = (k - R) * g.cellw;
         sh_d[k] = o;
         sh_hi[k] = static_cast<float>(o);
-        sh_lo[k] = static_cast<float>(o - static_cast<double>(sh_hi[k]));
     }
     for (int k = threadIdx.x; k < ncols; k += blockDim.x) scol[k] = cols[k];
     __syncthreads();
@@ -853,58 +817,43 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<real>* 
         const int nt = min(MT, te - t0);
         __syncwarp();
         if (lane < nt) {
-            const Vec4<real> a = rec[t0 + lane];
+            const Vec4<double> a = rec[t0 + lane];
             stx[warp][lane][0] = a.x;
             stx[warp][lane][1] = a.y;
             stx[warp][lane][2] = a.z;
             stx[warp][lane][3] = a.w;
-            if constexpr (kF32) {
-                const Vec4<real> l = lo[t0 + lane];
-                stl[warp][lane][0] = l.x;
-                stl[warp][lane][1] = l.y;
-                stl[warp][lane][2] = l.z;
-            } else {
-                const float4 f = pf[t0 + lane];
-                stl[warp][lane][0] = f.x;
-                stl[warp][lane][1] = f.y;
-                stl[warp][lane][2] = f.z;
-            }
+            const float4 f = pf[t0 + lane];
+            stl[warp][lane][0] = f.x;
+            stl[warp][lane][1] = f.y;
+            stl[warp][lane][2] = f.z;
         }
         if (lane < MT) qlen[lane] = 0;
         __syncwarp();
-        real acc[MT][4];
+        double acc[MT][4];
 #pragma unroll
-        for (int t = 0; t < MT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = real(0);
+        for (int t = 0; t < MT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.0;
 
         // evaluates one queued pair for target t (warp-uniform) and accumulates it
         auto pair = [&](int2 e, int t, bool active) {
             const int ix = e.y & 15, iy = (e.y >> 4) & 15, iz = (e.y >> 8) & 15;
-            const Vec4<real> a = rec[active ? e.x : t0];
-            real ddx, ddy, ddz;
-            if constexpr (kF32) {
-                const Vec4<real> l = lo[active ? e.x : t0];
-                const float px = a.x + sh_hi[ix], py = a.y + sh_hi[iy], pz = a.z + sh_hi[iz];
-                ddx = (stx[warp][t][0] - px) + (stl[warp][t][0] - (l.x + sh_lo[ix]));
-                ddy = (stx[warp][t][1] - py) + (stl[warp][t][1] - (l.y + sh_lo[iy]));
-                ddz = (stx[warp][t][2] - pz) + (stl[warp][t][2] - (l.z + sh_lo[iz]));
-            } else {
-                ddx = stx[warp][t][0] - (a.x + sh_d[ix]);
-                ddy = stx[warp][t][1] - (a.y + sh_d[iy]);
-                ddz = stx[warp][t][2] - (a.z + sh_d[iz]);
-            }
-            const real r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-            const bool in = active && r2 < kp.rc2 && r2 > real(0);
-            const real u = fma(r2, kp.two_over_rc2, real(-1));
-            real p1 = kp.p1[D], qq = kp.q[D];
+            const Vec4<double> a = rec[active ? e.x : t0];
+            double ddx, ddy, ddz;
+            ddx = stx[warp][t][0] - (a.x + sh_d[ix]);
+            ddy = stx[warp][t][1] - (a.y + sh_d[iy]);
+            ddz = stx[warp][t][2] - (a.z + sh_d[iz]);
+            const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+            const bool in = active && r2 < kp.rc2 && r2 > 0.0;
+            const double u = fma(r2, kp.two_over_rc2, double(-1));
+            double p1 = kp.p1[D], qq = kp.q[D];
 #pragma unroll
             for (int kk = D - 1; kk >= 0; --kk) {
                 p1 = fma(p1, u, kp.p1[kk]);
                 qq = fma(qq, u, kp.q[kk]);
             }
-            const real ri = rsqrt_r<real>(in ? r2 : real(1));
-            const real qj = in ? a.w : real(0);
-            const real c0 = qj * (ri - p1);
-            const real cf = qj * fma(ri * ri, ri, qq);
+            const double ri = rsqrt_r<double>(in ? r2 : double(1));
+            const double qj = in ? a.w : 0.0;
+            const double c0 = qj * (ri - p1);
+            const double cf = qj * fma(ri * ri, ri, qq);
 #pragma unroll
             for (int tt = 0; tt < MT; ++tt)
                 if (tt == t) {   // warp-uniform
@@ -928,15 +877,9 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<real>* 
                     const int4 rg = rng[r];
                     const int j = rg.x + (p - pos[r]);
                     float sfx, sfy, sfz, szc;
-                    if constexpr (kF32) {
-                        const Vec4<real> a = rec[j];
-                        sfx = a.x; sfy = a.y; sfz = a.z;
-                        szc = lo[j].w;
-                    } else {
-                        const float4 f = pf[j];
-                        sfx = f.x; sfy = f.y; sfz = f.z;
-                        szc = f.w;
-                    }
+                    const float4 f = pf[j];
+                    sfx = f.x; sfy = f.y; sfz = f.z;
+                    szc = f.w;
                     const int4 col = scol[rg.w];
                     const int ix = col.x + R, iy = col.y + R, iz = rg.z + (static_cast<int>(szc) - rg.y) + R;
                     const float px = sfx + sh_hi[ix], py = sfy + sh_hi[iy], pz = sfz + sh_hi[iz];
@@ -944,11 +887,7 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<real>* 
                     for (int t = 0; t < MT; ++t) {
                         if (t >= nt) break;   // warp-uniform
                         float tx, ty, tz;
-                        if constexpr (kF32) {
-                            tx = stx[warp][t][0]; ty = stx[warp][t][1]; tz = stx[warp][t][2];
-                        } else {
-                            tx = stl[warp][t][0]; ty = stl[warp][t][1]; tz = stl[warp][t][2];
-                        }
+                        tx = stl[warp][t][0]; ty = stl[warp][t][1]; tz = stl[warp][t][2];
                         const float dxf = tx - px, dyf = ty - py, dzf = tz - pz;
                         const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
                         if (r2f < kp.rc2f && r2f > 0.f) mask |= 1u << t;
@@ -976,12 +915,12 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<real>* 
         for (int t = 0; t < MT; ++t) {
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-                real x = acc[t][v];
+                double x = acc[t][v];
                 for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
                 acc[t][v] = x;
             }
         }
-        real mine[4] = {real(0), real(0), real(0), real(0)};
+        double mine[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
         for (int t = 0; t < MT; ++t) {
             if (lane == t) {

@@ -336,7 +336,7 @@ __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2*
 // cell shift split exactly (TwoSum), R and -R'/r from the radial polynomials by Horner (float32 for
 // the tiny leading terms k >= kr, float-float below), 1/r from a float32 estimate with a float-float
 // correction, and compensated accumulation.  The pair evaluation exists once in the code.
-constexpr int kShortFFMaxT = kShortMaxT;   // targets per pass (sums in registers)
+constexpr int kShortFFMaxT = 4;   // targets per pass (float-float sums in registers: 32 of them)
 
 // Radial polynomials padded with zeros to degree D; terms k >= kr (tiny, chosen on the host) are summed
 // by float32 Horner steps in u.h, the terms below kr in float-float.
@@ -356,7 +356,7 @@ __device__ __forceinline__ void ff_acc_sum(ff& acc, ff c) {
 }
 
 template <int D>
-__global__ void __launch_bounds__(32 * kShortWarps, 4) k_short_ff(const float4* __restrict__ rec_h,
+__global__ void __launch_bounds__(32 * kShortWarps, 6) k_short_ff(const float4* __restrict__ rec_h,
                                                                   const float4* __restrict__ rec_l,
                                                                   const int2* __restrict__ idx,
                                                                   const int* __restrict__ cz_of,

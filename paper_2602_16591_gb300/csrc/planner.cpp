@@ -472,10 +472,13 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
     // float32 products cannot reach tol < 1e-7; below it MIXED runs the float-float kernels
     p.precision = precision;
     p.tile = tile;
-    // real-space cells of edge >= rc / reach; the automatic reach aims at ~3 particles per cell
+    // real-space cells of edge >= rc / reach; the automatic reach aims at ~3 particles per cell, or
+    // ~1.5 for float-float plans, whose pairs cost ~15x a float32 pair: finer cells approximate the
+    // cutoff sphere better (fewer candidates per pair) and fit the kernel's 4 targets per pass
     int reach = o.sr_reach;
     if (reach <= 0) {
-        reach = static_cast<int>(std::lround(rcl * std::cbrt(static_cast<double>(n) / 3.0)));
+        const double per_cell = precision == EWALD_FLOATFLOAT ? 1.5 : 3.0;
+        reach = static_cast<int>(std::lround(rcl * std::cbrt(static_cast<double>(n) / per_cell)));
         reach = std::max(1, std::min(reach, 4));
     }
     p.sr_reach = reach;

