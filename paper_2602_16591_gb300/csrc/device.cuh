@@ -18,6 +18,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace pswf {
 
 template <typename real> struct alignas(4 * sizeof(real)) Vec4 { real x, y, z, w; };
@@ -247,9 +249,13 @@ __global__ void __launch_bounds__(spread_threads<P, spread_tile<real>()>()) k_sp
     const int beg = tile_off[tile], end = tile_off[tile + 1];
     if (beg == end) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    real* sc = reinterpret_cast<real*>(smem_raw);                 // P * (degw + 1)
-    real* sw = sc + P * (degw + 1);                                // CH * 3 * P
-    real* srho = sw + CH * 3 * P;                                  // CH
+    // weight rows padded to whole 16-byte vectors so a thread reads a particle's P x-weights with
+    // PP / VW broadcast vector loads instead of P scalar ones
+    constexpr int VW = 16 / static_cast<int>(sizeof(real)), PP = (P + VW - 1) / VW * VW;
+    using V = typename std::conditional<sizeof(real) == 4, float4, double2>::type;
+    real* sw = reinterpret_cast<real*>(smem_raw);                  // CH * 3 * PP
+    real* sc = sw + CH * 3 * PP;                                   // P * (degw + 1)
+    real* srho = sc + P * (degw + 1);                              // CH
     int* soff = reinterpret_cast<int*>(srho + CH);                 // CH
     for (int i = threadIdx.x; i < P * (degw + 1); i += blockDim.x) sc[i] = wcoef[i];
 
@@ -270,7 +276,7 @@ __global__ void __launch_bounds__(spread_threads<P, spread_tile<real>()>()) k_sp
             real w[P];
             window_weights<real, P>(sc, degw, z, w);
 #pragma unroll
-            for (int a = 0; a < P; ++a) sw[(j * 3 + d) * P + a] = w[a];
+            for (int a = 0; a < P; ++a) sw[(j * 3 + d) * PP + a] = w[a];
             if (d == 0) {
                 srho[j] = r.w;
                 soff[j] = idx[base + j].x;
@@ -283,8 +289,22 @@ __global__ void __launch_bounds__(spread_threads<P, spread_tile<real>()>()) k_sp
                 const int ox = pk & 0xff, oy = (pk >> 8) & 0xff, oz = (pk >> 16) & 0xff;
                 const int bb = b - oy, cc = c - oz;
                 if (bb < 0 || bb >= P || cc < 0 || cc >= P) continue;
-                const real wyz = srho[j] * sw[(j * 3 + 1) * P + bb] * sw[(j * 3 + 2) * P + cc];
-                const real* wx = sw + (j * 3) * P;
+                const real wyz = srho[j] * sw[(j * 3 + 1) * PP + bb] * sw[(j * 3 + 2) * PP + cc];
+                real wx[PP];
+                const V* wv = reinterpret_cast<const V*>(sw + (j * 3) * PP);
+#pragma unroll
+                for (int v = 0; v < PP / VW; ++v) {
+                    const V t = wv[v];
+                    if constexpr (sizeof(real) == 4) {
+                        wx[4 * v] = t.x;
+                        wx[4 * v + 1] = t.y;
+                        wx[4 * v + 2] = t.z;
+                        wx[4 * v + 3] = t.w;
+                    } else {
+                        wx[2 * v] = t.x;
+                        wx[2 * v + 1] = t.y;
+                    }
+                }
                 switch (ox) {
 #define PSWF_SPREAD_CASE(O)                                                                    \
     case O:                                                                                    \
@@ -387,11 +407,14 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
     if (beg == end) return;
     const int m = g.m, nt = g.nt, degw = g.degw;
     const int tz = tile % nt, ty = (tile / nt) % nt, tx = tile / (nt * nt);
+    // weight rows padded to whole 16-byte vectors (vector loads of a particle's x-weights)
+    constexpr int VW = 16 / static_cast<int>(sizeof(real)), PP = (P + VW - 1) / VW * VW;
+    using V = typename std::conditional<sizeof(real) == 4, float4, double2>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    real* G = reinterpret_cast<real*>(smem_raw);                 // E^3
+    real* sw = reinterpret_cast<real*>(smem_raw);                 // NWARP * NB * 6 * PP
+    real* G = sw + NWARP * NB * 6 * PP;                           // E^3
     real* sc = G + E * E * E;                                     // P * (degw + 1)
     real* sd = sc + P * (degw + 1);                               // P * (degw + 1)
-    real* sw = sd + P * (degw + 1);                               // NWARP * NB * 6 * P
     for (int i = threadIdx.x; i < P * (degw + 1); i += blockDim.x) {
         sc[i] = wcoef[i];
         sd[i] = dwcoef[i];
@@ -411,7 +434,7 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    real* ww = sw + warp * NB * 6 * P;
+    real* ww = sw + warp * NB * 6 * PP;
     for (int b0 = beg + warp * NB; b0 < end; b0 += NWARP * NB) {
         const int cnt = min(NB, end - b0);
         __syncwarp();
@@ -423,11 +446,11 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
             if (kind < 3) {
                 window_weights<real, P>(sc, degw, z, w);
 #pragma unroll
-                for (int a = 0; a < P; ++a) ww[(j * 6 + kind) * P + a] = w[a];
+                for (int a = 0; a < P; ++a) ww[(j * 6 + kind) * PP + a] = w[a];
             } else {
                 window_weights<real, P>(sd, degw, z, w);
 #pragma unroll
-                for (int a = 0; a < P; ++a) ww[(j * 6 + kind) * P + a] = w[a] * inv_alpha;
+                for (int a = 0; a < P; ++a) ww[(j * 6 + kind) * PP + a] = w[a] * inv_alpha;
             }
         }
         __syncwarp();
@@ -435,12 +458,22 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
         for (int j = 0; j < cnt; ++j) {
             const int2 id = idx[b0 + j];
             const int ox = id.x & 0xff, oy = (id.x >> 8) & 0xff, oz = (id.x >> 16) & 0xff;
-            const real* wp = ww + j * 6 * P;
-            real wx[P], dwx[P];
+            const real* wp = ww + j * 6 * PP;
+            real wx[PP], dwx[PP];
+            {
+                const V* v0 = reinterpret_cast<const V*>(wp);
+                const V* v3 = reinterpret_cast<const V*>(wp + 3 * PP);
 #pragma unroll
-            for (int a = 0; a < P; ++a) {
-                wx[a] = wp[a];
-                dwx[a] = wp[3 * P + a];
+                for (int v = 0; v < PP / VW; ++v) {
+                    const V a0 = v0[v], a3 = v3[v];
+                    if constexpr (sizeof(real) == 4) {
+                        wx[4 * v] = a0.x; wx[4 * v + 1] = a0.y; wx[4 * v + 2] = a0.z; wx[4 * v + 3] = a0.w;
+                        dwx[4 * v] = a3.x; dwx[4 * v + 1] = a3.y; dwx[4 * v + 2] = a3.z; dwx[4 * v + 3] = a3.w;
+                    } else {
+                        wx[2 * v] = a0.x; wx[2 * v + 1] = a0.y;
+                        dwx[2 * v] = a3.x; dwx[2 * v + 1] = a3.y;
+                    }
+                }
             }
             real ph = 0, gx = 0, gy = 0, gz = 0;
 #pragma unroll
@@ -462,8 +495,8 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
                         }
                     }
                     const real s1 = s1a + s1b, s2 = s2a + s2b;
-                    const real wy = wp[P + bb], wz = wp[2 * P + cc];
-                    const real dwy = wp[4 * P + bb], dwz = wp[5 * P + cc];
+                    const real wy = wp[PP + bb], wz = wp[2 * PP + cc];
+                    const real dwy = wp[4 * PP + bb], dwz = wp[5 * PP + cc];
                     const real yz = wy * wz;
                     ph = fma(s1, yz, ph);
                     gx = fma(s2, yz, gx);

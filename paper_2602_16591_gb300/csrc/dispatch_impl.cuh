@@ -35,14 +35,18 @@ cudaError_t interp_p(int ntiles, const real_t* grid, const Vec4<real_t>* rec, co
 
 template <>
 size_t Launch<real_t>::spread_smem(int P, int degw) {
-    return sizeof(real_t) * (P * (degw + 1) + kSpreadChunk * 3 * P + kSpreadChunk) + sizeof(int) * kSpreadChunk;
+    constexpr int VW = 16 / static_cast<int>(sizeof(real_t));
+    const int PP = (P + VW - 1) / VW * VW;   // padded weight rows (k_spread)
+    return sizeof(real_t) * (kSpreadChunk * 3 * PP + P * (degw + 1) + kSpreadChunk) + sizeof(int) * kSpreadChunk;
 }
 
 template <>
 size_t Launch<real_t>::interp_smem(int P, int degw) {
     const int E = spread_tile<real_t>() + P - 1;
+    constexpr int VW = 16 / static_cast<int>(sizeof(real_t));
+    const int PP = (P + VW - 1) / VW * VW;   // padded weight rows (k_interp)
     return sizeof(real_t) * (static_cast<size_t>(E) * E * E + 2 * P * (degw + 1) +
-                           InterpCfg<real_t>::NWARP * InterpCfg<real_t>::NB * 6 * P);
+                             InterpCfg<real_t>::NWARP * InterpCfg<real_t>::NB * 6 * PP);
 }
 
 #define PSWF_P_CASES(X) \

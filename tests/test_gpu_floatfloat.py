@@ -88,6 +88,7 @@ CASES = [
     ("uni4000", 1e-8, "mixed"),
     ("uni4000", 1e-10, "mixed"),
     ("uni4000", 1e-12, "floatfloat"),
+    ("uni4000", 1e-13, "mixed"),       # the tightest tolerance the API accepts
 ]
 
 
