@@ -28,6 +28,10 @@ window half-width alpha = P h / 2 (Sec. 6.3, eq. alpha and the relation alpha = 
 psi is evaluated exactly from its Legendre series (no polynomial fits), the
 FFTs are NumPy's complex FFTs, and k runs over I_m = {-m/2, ..., m/2-1}.
 
+Cuboid boxes (Remark on cuboid domains, Sec. 6.1): L and m may be given per axis; then h_d = L_d/m_d,
+alpha_d = P h_d/2 (the window support is P points on every axis), w_d = 2 pi k_d/L_d, V = prod L_d,
+and the retained modes are the ellipsoid 0 < |w| < pi min_d m_d/L_d.
+
 Parity status: pinned (tests/test_oracle_alg2.py) against the converged Ewald sum
 of ``exact`` (its difference is the method's own error, compared with the error
 models of Sec. 5) and by a single-charge DFT identity.
@@ -42,66 +46,89 @@ from .exact import wrap, realspace
 class Alg2:
     def __init__(self, L, m, P, cs, cw, rc, ball=True):
         self.ball = bool(ball)
-        self.L, self.m, self.P = float(L), int(m), int(P)
+        self.Lv = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,)).copy()
+        self.mv = np.broadcast_to(np.asarray(m, dtype=np.int64), (3,)).copy()
+        self.P = int(P)
         self.cs, self.cw, self.rc = float(cs), float(cw), float(rc)
-        self.h = self.L / self.m
-        self.alpha = self.P * self.h / 2.0
+        self.hv = self.Lv / self.mv
+        self.alphav = self.P * self.hv / 2.0
+        # scalar views (cubes)
+        self.L, self.m, self.h, self.alpha = float(self.Lv[0]), int(self.mv[0]), float(self.hv[0]), float(self.alphav[0])
         self.win = PSWF(self.cw)
         self.split = PSWFSplit(self.cs, self.rc)
 
     # -- window ------------------------------------------------------------------
     def _stencil(self, x):
         """Per-axis grid indices (n,3,P) and window arguments s = (x - h l)/alpha."""
-        t = x / self.h
+        h, al, mv = self.hv[None, :, None], self.alphav[None, :, None], self.mv[None, :, None]
+        t = x / self.hv[None, :]
         l0 = np.ceil(t - self.P / 2.0)
         a = np.arange(self.P, dtype=np.float64)
         l = l0[:, :, None] + a[None, None, :]
-        s = (x[:, :, None] - self.h * l) / self.alpha
-        idx = np.mod(l.astype(np.int64), self.m)
+        s = (x[:, :, None] - h * l) / al
+        idx = np.mod(l.astype(np.int64), mv)
         return idx, s
 
     def window_1d(self, s):
         return self.win.psi(s) / self.win.psi0
 
     def dwindow_1d(self, s):
-        return self.win.dpsi(s) / (self.win.psi0 * self.alpha)
+        """d/dy of the window on every axis (s has the axis as its second index)."""
+        return self.win.dpsi(s) / (self.win.psi0 * self.alphav[None, :, None])
 
     # -- Alg. 2 steps -----------------------------------------------------------
     def spread(self, x, rho, chunk=4096):
-        x = wrap(x, self.L)
-        m, P = self.m, self.P
-        a = np.zeros(m ** 3)
+        x = wrap(x, self.Lv)
+        (mx, my, mz), P = self.mv, self.P
+        a = np.zeros(mx * my * mz)
         for s0 in range(0, len(x), chunk):
             idx, s = self._stencil(x[s0:s0 + chunk])
             w = self.window_1d(s)
             r = np.asarray(rho[s0:s0 + chunk], dtype=np.float64)
             vals = (r[:, None, None, None] * w[:, 0, :, None, None]
                     * w[:, 1, None, :, None] * w[:, 2, None, None, :])
-            flat = (idx[:, 0, :, None, None] * m + idx[:, 1, None, :, None]) * m + idx[:, 2, None, None, :]
-            a += np.bincount(flat.ravel(), weights=vals.ravel(), minlength=m ** 3)
-        return a.reshape(m, m, m)
+            flat = (idx[:, 0, :, None, None] * my + idx[:, 1, None, :, None]) * mz + idx[:, 2, None, None, :]
+            a += np.bincount(flat.ravel(), weights=vals.ravel(), minlength=mx * my * mz)
+        return a.reshape(mx, my, mz)
 
-    def kgrid(self):
-        """Integer k in I_m for each FFT index (index m/2 is k = -m/2)."""
-        return np.rint(np.fft.fftfreq(self.m) * self.m).astype(np.int64)
+    def kgrid(self, axis=0):
+        """Integer k in I_m for each FFT index of an axis (index m/2 is k = -m/2)."""
+        m = int(self.mv[axis])
+        return np.rint(np.fft.fftfreq(m) * m).astype(np.int64)
+
+    def window_ft(self, axis):
+        """(1/h) int_{-alpha}^{alpha} psi(y/alpha)/psi(0) cos(w y) dy for the FFT indices of an axis."""
+        w = 2.0 * np.pi * self.kgrid(axis) / self.Lv[axis]
+        al = self.alphav[axis]
+        return al * self.win.cos_transform(w * al) / (self.win.psi0 * self.hv[axis])
 
     def scaling(self):
-        """S(k) on the full m^3 index grid (S(0) = 0)."""
-        m, L = self.m, self.L
-        k = self.kgrid()
-        # window transform per axis, divided by h: (1/h) int_{-alpha}^{alpha} psi(y/alpha)/psi(0) cos(w y) dy
-        w = 2.0 * np.pi * k / L
-        ph1 = self.alpha * self.win.cos_transform(w * self.alpha) / (self.win.psi0 * self.h)
-        KX, KY, KZ = np.meshgrid(k, k, k, indexing='ij')
-        k2 = (KX ** 2 + KY ** 2 + KZ ** 2)
-        S = np.zeros(k2.shape)
-        nz = k2 > 0
-        uk, inv = np.unique(k2[nz], return_inverse=True)
-        Mh = self.split.Mhat_k2(uk, L)[inv]
-        den = (ph1[:, None, None] * ph1[None, :, None] * ph1[None, None, :]) ** 2
-        S[nz] = Mh / (L ** 3) / den[nz]
+        """S(k) on the full index grid (S(0) = 0)."""
+        ph = [self.window_ft(d) for d in range(3)]
+        den = (ph[0][:, None, None] * ph[1][None, :, None] * ph[2][None, None, :]) ** 2
+        cube = np.all(self.Lv == self.Lv[0]) and np.all(self.mv == self.mv[0])
+        if cube:
+            m, L = self.m, self.L
+            k = self.kgrid()
+            KX, KY, KZ = np.meshgrid(k, k, k, indexing='ij')
+            k2 = (KX ** 2 + KY ** 2 + KZ ** 2)
+            S = np.zeros(k2.shape)
+            nz = k2 > 0
+            uk, inv = np.unique(k2[nz], return_inverse=True)
+            Mh = self.split.Mhat_k2(uk, L)[inv]
+            S[nz] = Mh / (L ** 3) / den[nz]
+            if self.ball:
+                S[4 * k2 >= m * m] = 0.0
+            return S
+        KX, KY, KZ = np.meshgrid(*(self.kgrid(d) for d in range(3)), indexing='ij')
+        w2 = (2.0 * np.pi) ** 2 * ((KX / self.Lv[0]) ** 2 + (KY / self.Lv[1]) ** 2 + (KZ / self.Lv[2]) ** 2)
+        S = np.zeros(w2.shape)
+        nz = w2 > 0
+        uw, inv = np.unique(w2[nz], return_inverse=True)
+        S[nz] = self.split.Mhat_w2(uw)[inv] / float(np.prod(self.Lv)) / den[nz]
         if self.ball:
-            S[4 * k2 >= m * m] = 0.0
+            wmax = np.pi * np.min(self.mv / self.Lv)
+            S[w2 >= wmax * wmax] = 0.0
         return S
 
     def fft(self, a):
@@ -111,8 +138,8 @@ class Alg2:
         return np.fft.fftn(bh)                           # e^{-2 pi i k.l/m}, unnormalised
 
     def interp(self, x, b, chunk=4096):
-        x = wrap(x, self.L)
-        m = self.m
+        x = wrap(x, self.Lv)
+        mx, my, mz = self.mv
         bf = b.ravel()
         phi = np.zeros(len(x))
         grad = np.zeros((len(x), 3))
@@ -120,7 +147,7 @@ class Alg2:
             idx, s = self._stencil(x[s0:s0 + chunk])
             w = self.window_1d(s)
             dw = self.dwindow_1d(s)
-            flat = (idx[:, 0, :, None, None] * m + idx[:, 1, None, :, None]) * m + idx[:, 2, None, None, :]
+            flat = (idx[:, 0, :, None, None] * my + idx[:, 1, None, :, None]) * mz + idx[:, 2, None, None, :]
             G = bf[flat]                                  # (c, P, P, P)
             # contract the z axis, then y, then x (plain tensor contractions)
             Gz = np.einsum('nabc,nc->nab', G, w[:, 2])
@@ -151,7 +178,7 @@ class Alg2:
         rho = np.asarray(rho, dtype=np.float64)
         out = self.far(x, rho, stages=stages, targets=targets)
         pf, gf = out[0], out[1]
-        pl, gl = realspace(x, rho, self.L, self.split, self.rc, targets=targets)
+        pl, gl = realspace(x, rho, self.Lv, self.split, self.rc, targets=targets)
         if targets is not None:
             r = rho[targets]
         else:

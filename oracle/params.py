@@ -104,3 +104,47 @@ def plan(L, n, tol, grid_density=1.0, rc=None, tol_safety=1.0, mult=4):
     h = L / m
     return dict(L=L, rc=rcl * L, cs=cs, cw_target=cw, cw=math.pi * P / 2.0, m=m, P=P,
                 h=h, alpha=P * h / 2.0)
+
+
+def plan_box(Ls, n, tol, grid_density=1.0, rc=None, tol_safety=1.0, mult=4):
+    """Alg. 3 for a cuboid box (Remark on cuboid domains, Sec. 6.1).
+
+    The parameters are derived in units of L_min = min_d L_d (the nondimensionalisation of the
+    Remark): r_c/L_min and the Lambert-W equations as for a cube of edge L_min; the cutoff rule uses
+    the common target spacing h = (V/(g n))^{1/3}.  Each axis gets m_d = ceil(c_s L_d/(pi r_c)),
+    rounded as in ``plan``; then r_c := c_s h_max/pi with h_max = max_d L_d/m_d (eq. csrc on the
+    coarsest axis; the other axes resolve more modes than the retained ellipsoid uses), and
+    P = ceil(2 alpha/h_max) with alpha = r_c c_w/c_s, i.e. P = ceil(2 c_w/pi), instantiated with
+    c_w := pi P/2 and alpha_d := P h_d/2 per axis.  A cube gives exactly ``plan``.
+    """
+    Lv = np.broadcast_to(np.asarray(Ls, dtype=np.float64), (3,))
+    if np.all(Lv == Lv[0]):
+        q = plan(float(Lv[0]), n, tol, grid_density=grid_density, rc=rc, tol_safety=tol_safety, mult=mult)
+        q.update(m=[q["m"]] * 3, h=[q["h"]] * 3, alpha=[q["alpha"]] * 3, L=[q["L"]] * 3)
+        return q
+    Lmin, V = float(np.min(Lv)), float(np.prod(Lv))
+    t = tol * tol_safety
+
+    def cutoff(t):
+        if rc is None:
+            h = (V / (grid_density * n)) ** (1.0 / 3.0)
+            r = 0.1
+            for _ in range(12):
+                r = min(cs_of(r, t) * h / (math.pi * Lmin), 0.5)
+            return r
+        return min(rc / Lmin, 0.5)
+
+    rcl = cutoff(t)
+    m0 = cs_of(rcl, t) / (math.pi * rcl)
+    if m0 > 10.0:
+        t *= 10.0 / m0
+        rcl = cutoff(t)
+    cs = cs_of(rcl, t)
+    ms = [good_size(math.ceil(cs * L / (math.pi * rcl * Lmin)), mult) for L in Lv]
+    hs = [float(L) / m for L, m in zip(Lv, ms)]
+    hmax = max(hs)
+    rcl = cs * hmax / (math.pi * Lmin)
+    cw = cw_of(cs, rcl)
+    P = int(math.ceil(2.0 * (rcl * cw / cs) * Lmin / hmax))
+    return dict(L=[float(L) for L in Lv], rc=rcl * Lmin, cs=cs, cw_target=cw, cw=math.pi * P / 2.0, m=ms, P=P,
+                h=hs, alpha=[P * h / 2.0 for h in hs])

@@ -81,6 +81,11 @@ class PSWFSplit:
         omega = 2.0 * np.pi * np.sqrt(k2) / L
         return L * L / (np.pi * k2) * self.gammahat(omega)
 
+    def Mhat_w2(self, w2):
+        """Mhat at |omega|^2 = w2 > 0 (any box shape): 4 pi / w2 * gammahat(sqrt(w2))."""
+        w2 = np.asarray(w2, dtype=np.float64)
+        return 4.0 * np.pi / w2 * self.gammahat(np.sqrt(w2))
+
     def self_coeff(self):
         return 2.0 / (self.f.lam * self.rc)
 
@@ -107,6 +112,10 @@ class GaussianSplit:
         k2 = np.asarray(k2, dtype=np.float64)
         omega2 = (2.0 * np.pi / L) ** 2 * k2
         return 4.0 * np.pi / omega2 * np.exp(-self.sigma ** 2 * omega2 / 4.0)
+
+    def Mhat_w2(self, w2):
+        w2 = np.asarray(w2, dtype=np.float64)
+        return 4.0 * np.pi / w2 * np.exp(-self.sigma ** 2 * w2 / 4.0)
 
     def self_coeff(self):
         return 2.0 / (np.sqrt(np.pi) * self.sigma)

@@ -129,3 +129,51 @@ def test_lambertw_branches():
     z = -2 * params.KAPPA * 1e-12 / params.A_W ** 2
     w = float(np.real(lambertw(z, -1)))
     assert w < -1 and abs(w * math.exp(w) / z - 1) < 1e-12
+
+
+# ------------------------------------------------------------------ cuboid boxes (Remark, Sec. 6.1) --
+def test_cuboid_alg2_supercell_equals_cube():
+    """Alg. 2 on a 1x1x2 supercell grid (m, m, 2m) is the cube's Alg. 2 for every copy (same discrete
+    operators: the spread grid and the scaled modes of the supercell are those of the cube interleaved)."""
+    from oracle import params as op
+    rng = np.random.default_rng(7)
+    x = rng.random((60, 3))
+    q = rng.uniform(-1, 1, 60)
+    q -= q.mean()
+    p = op.plan(1.0, 60, 1e-6, grid_density=8.0)
+    A = Alg2(1.0, p["m"], p["P"], p["cs"], p["cw"], p["rc"])
+    phi, grad, E, F = A.total(x, q)
+    B = Alg2((1.0, 1.0, 2.0), (p["m"], p["m"], 2 * p["m"]), p["P"], p["cs"], p["cw"], p["rc"])
+    xs = np.concatenate([x, x + np.array([0.0, 0.0, 1.0])])
+    phis, grads, Es, Fs = B.total(xs, np.tile(q, 2))
+    for c in range(2):
+        assert np.max(np.abs(phis[c * 60:(c + 1) * 60] - phi)) <= 1e-12 * np.max(np.abs(phi))
+        assert np.max(np.abs(Fs[c * 60:(c + 1) * 60] - F)) <= 1e-11 * np.max(np.abs(F))
+    assert abs(Es - 2 * E) <= 1e-12 * abs(2 * E)
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-6, 1e-8])
+def test_cuboid_alg2_meets_tolerance(tol):
+    """The cuboid plan rule (oracle params.plan_box) meets tol against the converged cuboid sum."""
+    from oracle import params as op
+    Lv = (1.0, 1.25, 0.75)
+    rng = np.random.default_rng(8)
+    x = rng.random((400, 3)) * np.array(Lv)
+    q = rng.uniform(-1, 1, 400)
+    q -= q.mean()
+    p = op.plan_box(Lv, 400, tol, grid_density=3.0, tol_safety=0.25)
+    assert len(set(p["m"])) >= 2          # a genuinely anisotropic grid
+    A = Alg2(Lv, p["m"], p["P"], p["cs"], p["cw"], p["rc"])
+    phi, grad, E, F = A.total(x, q)
+    ref = exact.pswf_exact(x, q, Lv)
+    rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)  # noqa: E731
+    assert rel(phi, ref[0]) <= tol
+    assert rel(F, ref[3]) <= 2 * tol
+
+
+def test_cuboid_plan_reduces_to_cube():
+    from oracle import params as op
+    for tol in (1e-4, 1e-8):
+        a = op.plan(1.3, 5000, tol, grid_density=3.0, tol_safety=0.25)
+        b = op.plan_box((1.3, 1.3, 1.3), 5000, tol, grid_density=3.0, tol_safety=0.25)
+        assert b["m"] == [a["m"]] * 3 and b["P"] == a["P"] and b["rc"] == a["rc"]

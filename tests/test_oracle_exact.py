@@ -109,3 +109,50 @@ def test_rms_potential_matches_kappa():
         phi = exact.pswf_exact(x, rho, L)[0]
         r.append(np.sqrt(np.mean(phi ** 2)) / np.linalg.norm(rho))
     assert abs(np.mean(r) / np.sqrt(KAPPA) - 1.0) < 0.15
+
+
+# ------------------------------------------------------------------ cuboid boxes (Remark, Sec. 6.1) --
+def _neutral(n, seed, Lv):
+    rng = np.random.default_rng(seed)
+    x = rng.random((n, 3)) * np.asarray(Lv)
+    q = rng.uniform(-1, 1, n)
+    return x, q - q.mean()
+
+
+@pytest.mark.parametrize("reps", [(1, 1, 2), (3, 1, 1)])
+def test_cuboid_supercell_reproduces_cube(reps):
+    """A cubic system replicated into a cuboid supercell has the same periodic potential: every copy
+    of particle i sees phi_i of the cube (and the same force); the energy scales with the copies."""
+    x, q = _neutral(30, 4, (1.0, 1.0, 1.0))
+    phi, grad, E, F = exact.pswf_exact(x, q, 1.0)
+    shifts = np.array([(a, b, c) for a in range(reps[0]) for b in range(reps[1]) for c in range(reps[2])], float)
+    xs = np.concatenate([x + s for s in shifts])
+    qs = np.tile(q, len(shifts))
+    phis, grads, Es, Fs = exact.pswf_exact(xs, qs, np.array(reps, float))
+    n = len(q)
+    for c in range(len(shifts)):
+        assert np.max(np.abs(phis[c * n:(c + 1) * n] - phi)) <= 1e-11 * np.max(np.abs(phi))
+        assert np.max(np.abs(Fs[c * n:(c + 1) * n] - F)) <= 1e-10 * np.max(np.abs(F))
+    assert abs(Es - len(shifts) * E) <= 1e-11 * abs(len(shifts) * E)
+
+
+def test_cuboid_split_independence():
+    """Two PSWF cutoffs and the Gaussian split give the same Ewald sum in a cuboid (1, 1.3, 0.8)."""
+    Lv = (1.0, 1.3, 0.8)
+    x, q = _neutral(40, 5, Lv)
+    a = exact.pswf_exact(x, q, Lv, rc_frac=0.5)
+    b = exact.pswf_exact(x, q, Lv, rc_frac=0.35)
+    c = exact.gaussian_exact(x, q, Lv)
+    for r in (b, c):
+        assert np.max(np.abs(r[0] - a[0])) <= 1e-12 * np.max(np.abs(a[0]))
+        assert np.max(np.abs(r[3] - a[3])) <= 1e-11 * np.max(np.abs(a[3]))
+        assert abs(r[2] - a[2]) <= 1e-12 * abs(a[2])
+
+
+def test_cuboid_translation_invariance_and_wrap():
+    Lv = np.array([0.9, 1.2, 1.5])
+    x, q = _neutral(25, 6, Lv)
+    a = exact.pswf_exact(x, q, Lv)
+    b = exact.pswf_exact(x + np.array([0.31, -2.7, 4.1]), q, Lv)
+    assert np.max(np.abs(b[0] - a[0])) <= 1e-12 * np.max(np.abs(a[0]))
+    assert np.max(np.abs(np.sum(a[3], axis=0))) <= 1e-11 * np.max(np.abs(a[3]))
