@@ -223,11 +223,13 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    def timed(plan, steps, warmup, profile=False):
-        phi = torch.empty(n, dtype=torch.float64, device="cuda")
-        F = torch.empty(n, 3, dtype=torch.float64, device="cuda")
+    def timed(plan, steps, warmup, profile=False, xr=None):
+        xx, rr = (x, rho) if xr is None else xr
+        nn = len(rr)
+        phi = torch.empty(nn, dtype=torch.float64, device="cuda")
+        F = torch.empty(nn, 3, dtype=torch.float64, device="cuda")
         for _ in range(warmup):
-            plan.eval(x, rho, phi, F, energy=False)
+            plan.eval(xx, rr, phi, F, energy=False)
         torch.cuda.synchronize()
         if profile:
             plan.profile(True)
@@ -237,7 +239,7 @@ def run_ours(args, rank, world, local_rank):
         for k in range(steps):
             flush.zero_()
             ev[k][0].record(stream)
-            plan.eval(x, rho, phi, F, energy=False)
+            plan.eval(xx, rr, phi, F, energy=False)
             ev[k][1].record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -311,6 +313,20 @@ def run_ours(args, rank, world, local_rank):
                              "m": vp.params.m, "P": vp.params.P, "ms_per_step": vms,
                              "value": world * n / (vms / 1000.0), "stages_ms": vst})
             del vp
+
+    if not args.no_variants:
+        # cuboid box (Remark on cuboid domains): the headline density in a 1 x 1 x 2 box, twice the particles
+        from paper_2602_16591_gb300.workloads import uniform_neutral_box
+        cb = (1.0, 1.0, 2.0)
+        cxn, crn, _ = uniform_neutral_box(2 * n, cb, seed=rank)
+        cxr = (torch.tensor(cxn, device="cuda"), torch.tensor(crn, device="cuda"))
+        cp = pe.Plan(cb, 2 * n, args.tol, precision=args.precision, **popts)
+        cms, cst = timed(cp, max(5, args.steps // 3), 3, profile=True, xr=cxr)
+        cms = reduce_max(cms)
+        variants.append({"tol": args.tol, "precision": args.precision, "box": list(cb), "n": 2 * n,
+                         "path": pe.PATH_NAMES[cp.params.precision], "grid": list(cp.params.grid), "P": cp.params.P,
+                         "ms_per_step": cms, "value": world * 2 * n / (cms / 1000.0), "stages_ms": cst})
+        del cp, cxr
 
     batch = None
     if not args.no_variants:

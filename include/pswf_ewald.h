@@ -99,6 +99,13 @@ typedef struct ewald_params {
     int    ncell;      /* real-space cells per axis */
     int    sr_reach;   /* real-space neighbour reach in cells */
     int    precision;  /* path the plan runs: EWALD_FP64, EWALD_MIXED or EWALD_FLOATFLOAT */
+    /* box shape (cuboid boxes: Remark on cuboid domains in Sec. 6.1).  A cube has box = (L, L, L),
+     * grid = (m, m, m), cells = (ncell, ncell, ncell) and deg_g = 0.  For a cuboid the scalar L, m,
+     * h, alpha and ncell above are those of the x axis; rc, cs, cw, P are common to all axes. */
+    double box[3];     /* edges L_x, L_y, L_z */
+    int    grid[3];    /* FFT grid points per axis (each a multiple of tile, prime factors <= 7) */
+    int    cells[3];   /* real-space cells per axis */
+    int    deg_g;      /* cuboids: degree of the in-band mollifier transform polynomial (scaling) */
 } ewald_params;
 
 typedef struct ewald_plan_s* ewald_plan;   /* opaque, owned by the library */
@@ -116,6 +123,17 @@ int ewald_plan_params(double L, int64_t n, double tol, const ewald_opts* opts,
  * On success *out holds the plan; release it with ewald_plan_destroy. */
 int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts,
                       ewald_plan* out);
+
+/* Cuboid boxes (Remark on cuboid domains, Sec. 6.1): as ewald_plan_params / ewald_plan_create for the
+ * box [0, L[0]) x [0, L[1]) x [0, L[2]) (L: HOST array of 3 edges).  The parameters are derived in
+ * units of the shortest edge; every axis gets its own grid size (common spacing up to rounding) and
+ * real-space cell count; ewald_params.box / grid / cells report them.  Equal edges give exactly the
+ * cube's plan.  Positions wrap per axis; everything else (layouts, errors, evaluation entry points)
+ * is as for cubes.  Batches (ewald_plan_batch_create) and ewald_spread_static take cubes only. */
+int ewald_plan_params_box(const double* L, int64_t n, double tol, const ewald_opts* opts,
+                          ewald_params* out);
+int ewald_plan_create_box(const double* L, int64_t n, double tol, const ewald_opts* opts,
+                          ewald_plan* out);
 
 /* Copy the plan's parameters into *out. */
 int ewald_plan_query(ewald_plan plan, ewald_params* out);

@@ -33,10 +33,15 @@ class ewald_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in
                 ("L", "rc", "cs", "cw", "cw_target", "alpha", "h", "lambda_s", "lambda_w", "self_coeff",
                  "tol", "fit_tol")] + [("n", ctypes.c_int64)] + [(k, ctypes.c_int) for k in
-                ("m", "P", "deg_w", "deg_r", "tile", "ncell", "sr_reach", "precision")]
+                ("m", "P", "deg_w", "deg_r", "tile", "ncell", "sr_reach", "precision")] + \
+        [("box", ctypes.c_double * 3), ("grid", ctypes.c_int * 3), ("cells", ctypes.c_int * 3), ("deg_g", ctypes.c_int)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if k in ("box", "grid", "cells") else v
+        return out
 
 
 class EwaldError(RuntimeError):
@@ -56,6 +61,8 @@ def _load():
         "ewald_opts_default": (I, [ctypes.POINTER(ewald_opts)]),
         "ewald_plan_params": (I, [D, I64, D, ctypes.POINTER(ewald_opts), ctypes.POINTER(ewald_params)]),
         "ewald_plan_create": (I, [D, I64, D, ctypes.POINTER(ewald_opts), ctypes.POINTER(P)]),
+        "ewald_plan_params_box": (I, [P, I64, D, ctypes.POINTER(ewald_opts), ctypes.POINTER(ewald_params)]),
+        "ewald_plan_create_box": (I, [P, I64, D, ctypes.POINTER(ewald_opts), ctypes.POINTER(P)]),
         "ewald_plan_query": (I, [P, ctypes.POINTER(ewald_params)]),
         "ewald_eval": (I, [P, P, P, P, P, dp, P]),
         "ewald_eval_host": (I, [P, P, P, P, P, dp, P]),
@@ -111,11 +118,21 @@ def make_opts(precision="fp64", rc=None, grid_density=None, tol_safety=None, sr_
     return o
 
 
+def _box(L):
+    """(L, is_cube): a scalar edge or three edges (cuboid box) as a C double[3]."""
+    Lv = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,))
+    return (ctypes.c_double * 3)(*[float(v) for v in Lv]), bool(np.ndim(L) == 0)
+
+
 def plan_params(L, n, tol, **opts):
-    """Alg. 3 parameters on the host (no GPU needed)."""
+    """Alg. 3 parameters on the host (no GPU needed).  L: edge of a cube, or three edges of a cuboid."""
     o = make_opts(**opts)
     p = ewald_params()
-    _check(_lib.ewald_plan_params(float(L), int(n), float(tol), ctypes.byref(o), ctypes.byref(p)))
+    box, cube = _box(L)
+    if cube:
+        _check(_lib.ewald_plan_params(float(L), int(n), float(tol), ctypes.byref(o), ctypes.byref(p)))
+    else:
+        _check(_lib.ewald_plan_params_box(box, int(n), float(tol), ctypes.byref(o), ctypes.byref(p)))
     return p
 
 
@@ -171,7 +188,7 @@ def scale_table(params):
 class Plan:
     """A PSWF Ewald plan on the current CUDA device (C ABI: ewald_plan_create).
 
-    ``precision`` is "fp64", "mixed" or "floatfloat" ("mixed" below tol 1e-7 runs the float-float
+    ``L`` is the edge of a cube or the three edges of a cuboid box.  ``precision`` is "fp64", "mixed" or "floatfloat" ("mixed" below tol 1e-7 runs the float-float
     kernels; ``params.precision`` reports the path); other keywords are the ewald_opts fields.
     """
 
@@ -184,13 +201,17 @@ class Plan:
         self.device = torch.device("cuda", torch.cuda.current_device())
         o = make_opts(precision=precision, **opts)
         h = ctypes.c_void_p()
-        _check(_lib.ewald_plan_create(float(L), int(n), float(tol), ctypes.byref(o), ctypes.byref(h)))
+        box, cube = _box(L)
+        if cube:
+            _check(_lib.ewald_plan_create(float(L), int(n), float(tol), ctypes.byref(o), ctypes.byref(h)))
+        else:
+            _check(_lib.ewald_plan_create_box(box, int(n), float(tol), ctypes.byref(o), ctypes.byref(h)))
         self._h = h
         p = ewald_params()
         _check(_lib.ewald_plan_query(self._h, ctypes.byref(p)))
         self.params = p
         self.n = int(n)
-        self.L = float(L)
+        self.L = float(L) if cube else tuple(float(v) for v in box)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -245,8 +266,7 @@ class Plan:
         return dict(zip(self.STAGES, ms.tolist())), cnt.value
 
     def debug_grid(self, which):
-        m = self.params.m
-        out = np.empty((m, m, m))
+        out = np.empty(tuple(self.params.grid))
         _check(_lib.ewald_debug_grid(self._h, int(which), _ptr(out)))
         return out
 

@@ -122,25 +122,27 @@ namespace {
 // pointer is fixed into the launched kernels at exec time, also during graph capture).
 struct FftCache {
     std::mutex mu;
-    std::map<std::tuple<int, int, int>, std::pair<cufftHandle, size_t>> plans;   // -> (handle, work bytes)
+    std::map<std::tuple<int, int, int, int, int>, std::pair<cufftHandle, size_t>> plans;   // -> (handle, work)
 };
 FftCache& fft_cache() {
     static FftCache* c = new FftCache();   // never destroyed: handles outlive static teardown order
     return *c;
 }
 
-int shared_fft(int device, int m, cufftType type, cufftHandle* h, size_t* work) {
+int shared_fft(int device, const int* m, cufftType type, cufftHandle* h, size_t* work) {
     FftCache& c = fft_cache();
     std::lock_guard<std::mutex> lk(c.mu);
-    const auto key = std::make_tuple(device, m, static_cast<int>(type));
+    const auto key = std::make_tuple(device, m[0], m[1], m[2], static_cast<int>(type));
     auto it = c.plans.find(key);
     if (it == c.plans.end()) {
         cufftHandle nh = 0;
         size_t ws = 0;
         if (cufftCreate(&nh) != CUFFT_SUCCESS) return fail(EWALD_ECUFFT, "cufftCreate failed");
-        if (cufftSetAutoAllocation(nh, 0) != CUFFT_SUCCESS || cufftMakePlan3d(nh, m, m, m, type, &ws) != CUFFT_SUCCESS) {
+        if (cufftSetAutoAllocation(nh, 0) != CUFFT_SUCCESS ||
+            cufftMakePlan3d(nh, m[0], m[1], m[2], type, &ws) != CUFFT_SUCCESS) {
             cufftDestroy(nh);
-            return fail(EWALD_ECUFFT, "cufftMakePlan3d failed for m = " + std::to_string(m));
+            return fail(EWALD_ECUFFT, "cufftMakePlan3d failed for a " + std::to_string(m[0]) + " x " +
+                                          std::to_string(m[1]) + " x " + std::to_string(m[2]) + " grid");
         }
         it = c.plans.emplace(key, std::make_pair(nh, ws)).first;
     }
@@ -160,6 +162,7 @@ struct ewald_plan_s {
     int ff_kf = 1;      // window polynomial terms k >= ff_kf are summed in float32 (float-float plans)
     int ff_kr = 1;      // radial polynomial terms k >= ff_kr likewise
     int ntiles = 0, ncells = 0, epart_blocks = 0;
+    size_t m3 = 0, nspec = 0;   // grid points, half-spectrum modes
     // workspace
     int* key_rank = nullptr;
     int* tile_cnt = nullptr;
@@ -187,6 +190,7 @@ struct ewald_plan_s {
     void* qc = nullptr;
     void* iw = nullptr;
     void* mtab = nullptr;
+    void* gcoef = nullptr;   // cuboid boxes: mollifier transform polynomial (scaling step)
     double* phi_int = nullptr;
     double* f_int = nullptr;
     double* status = nullptr;
@@ -232,7 +236,7 @@ struct ewald_plan_s {
 
     ~ewald_plan_s() {
         void* bufs[] = {key_rank, tile_cnt, tile_off, cell_cnt, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, sr_lo, sr_f32, sr_cz, grid_ff, sr_cols, scratch,
-                        grid_a, grid_b, spec, wcoef, dwcoef, p1c, qc, iw, mtab, phi_int, f_int, status, epart,
+                        grid_a, grid_b, spec, wcoef, dwcoef, p1c, qc, iw, mtab, gcoef, phi_int, f_int, status, epart,
                         energy_d, x_stage, rho_stage};
         for (void* b : bufs)
             if (b) cudaFree(b);
@@ -260,6 +264,24 @@ struct ewald_plan_s {
 
 namespace {
 
+template <typename real>
+pswf::ScaleParams<real> scale_params(ewald_plan p) {
+    pswf::ScaleParams<real> sp{};
+    const ewald_params& q = p->hp.p;
+    for (int d = 0; d < 3; ++d) {
+        sp.m[d] = q.grid[d];
+        sp.w2[d] = static_cast<real>((2.0 * 3.14159265358979323846 / q.box[d]) * (2.0 * 3.14159265358979323846 / q.box[d]));
+    }
+    sp.cube = q.deg_g == 0;
+    sp.degg = q.deg_g;
+    sp.tscale = static_cast<real>((q.rc / q.cs) * (q.rc / q.cs));
+    sp.four_pi_over_V = static_cast<real>(4.0 * 3.14159265358979323846 / (q.box[0] * q.box[1] * q.box[2]));
+    sp.iw = static_cast<const real*>(p->iw);
+    sp.mtab = static_cast<const real*>(p->mtab);
+    sp.gc = static_cast<const real*>(p->gcoef);
+    return sp;
+}
+
 // Runs a shared cuFFT plan on stream s with plan p's work area.
 template <class F>
 int fft_exec(ewald_plan p, cufftHandle h, cudaStream_t s, F exec) {
@@ -284,7 +306,7 @@ cudaError_t launch_short_d(ewald_plan p, const pswf::Vec4<real>* sr_rec, const p
     kp.rc2 = static_cast<real>(g.rc * g.rc);
     kp.two_over_rc2 = static_cast<real>(2.0 / (g.rc * g.rc));
     kp.rc2f = static_cast<float>(g.rc * g.rc * (1.0 + 1e-4));
-    const int ncells = g.ncell * g.ncell * g.ncell;
+    const int ncells = g.ncell[0] * g.ncell[1] * g.ncell[2];
     const size_t smem = pswf::short_dyn_smem(p->sr_rcap);
     const int blocks = (ncells + pswf::kShortWarps - 1) / pswf::kShortWarps;
     // float32 pairs are cheap: the direct kernel; float64 pairs: the two-phase (queued) kernel
@@ -316,7 +338,7 @@ template <typename real, typename cplx>
 int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, double* f, cudaStream_t s) {
     using pswf::Vec4;
     const pswf::Geom& g = p->g;
-    const int n = g.n, m = g.m;
+    const int n = g.n;
     p->mark(0, false, s);
     PSWF_CUDA(cudaMemsetAsync(p->tile_cnt, 0, sizeof(int) * p->ntiles, s));
     PSWF_CUDA(cudaMemsetAsync(p->cell_cnt, 0, sizeof(int) * p->ncells, s));
@@ -350,7 +372,7 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
                                          static_cast<const real*>(p->wcoef), g.degw, static_cast<real*>(p->scratch), s));
     p->mark(1, true, s);
     p->mark(2, false, s);
-    const int mm = m * m * m;
+    const int mm = static_cast<int>(p->m3);
     pswf::k_halo<real><<<(mm + 255) / 256, 256, 0, s>>>(static_cast<const real*>(p->scratch), p->tile_off, g,
                                                         static_cast<real*>(p->grid_a));
     PSWF_CUDA(cudaGetLastError());
@@ -370,10 +392,8 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     if (frc) return frc;
     p->mark(3, true, s);
     p->mark(4, false, s);
-    const int ns = m * m * (m / 2 + 1);
-    pswf::k_scale<real, cplx><<<(ns + 255) / 256, 256, 0, s>>>(static_cast<cplx*>(p->spec), m,
-                                                               static_cast<const real*>(p->iw),
-                                                               static_cast<const real*>(p->mtab));
+    const int ns = static_cast<int>(p->nspec);
+    pswf::k_scale<real, cplx><<<(ns + 255) / 256, 256, 0, s>>>(static_cast<cplx*>(p->spec), scale_params<real>(p));
     PSWF_CUDA(cudaGetLastError());
     p->mark(4, true, s);
     p->mark(5, false, s);
@@ -390,7 +410,10 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     p->mark(5, true, s);
     p->mark(6, false, s);
     // Alg. 2 step 5 + self term + forces
-    const real inv_alpha = static_cast<real>(1.0 / p->hp.p.alpha);
+    // 1/alpha_d = 2 m_d / (P L_d) per axis (alpha_d = P h_d / 2; equal for cubes)
+    const pswf::Vec4<real> inv_alpha{static_cast<real>(2.0 * g.m[0] / (g.P * g.L[0])),
+                                     static_cast<real>(2.0 * g.m[1] / (g.P * g.L[1])),
+                                     static_cast<real>(2.0 * g.m[2] / (g.P * g.L[2])), real(0)};
     PSWF_CUDA(pswf::Launch<real>::interp(g.P, p->ntiles, static_cast<const real*>(p->grid_b), sp_rec, p->sp_idx,
                                          p->tile_off, static_cast<const real*>(p->wcoef),
                                          static_cast<const real*>(p->dwcoef), g, inv_alpha, phi, f, s));
@@ -413,7 +436,7 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
 int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* phi, double* f, cudaStream_t s) {
     using pswf::LaunchFF;
     const pswf::Geom& g = p->g;
-    const int n = g.n, m = g.m;
+    const int n = g.n;
     const size_t nn = static_cast<size_t>(n);
     p->mark(0, false, s);
     PSWF_CUDA(cudaMemsetAsync(p->tile_cnt, 0, sizeof(int) * p->ntiles, s));
@@ -458,10 +481,9 @@ int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* ph
     if (frc) return frc;
     p->mark(3, true, s);
     p->mark(4, false, s);
-    const int ns = m * m * (m / 2 + 1);
+    const int ns = static_cast<int>(p->nspec);
     pswf::k_scale<double, cufftDoubleComplex><<<(ns + 255) / 256, 256, 0, s>>>(
-        static_cast<cufftDoubleComplex*>(p->spec), m, static_cast<const double*>(p->iw),
-        static_cast<const double*>(p->mtab));
+        static_cast<cufftDoubleComplex*>(p->spec), scale_params<double>(p));
     PSWF_CUDA(cudaGetLastError());
     p->mark(4, true, s);
     p->mark(5, false, s);
@@ -469,12 +491,14 @@ int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* ph
         return cufftExecZ2D(p->inv, static_cast<cufftDoubleComplex*>(p->spec), static_cast<cufftDoubleReal*>(p->grid_b));
     });
     if (frc) return frc;
-    const size_t m3 = static_cast<size_t>(m) * m * m;
+    const size_t m3 = p->m3;
     PSWF_CUDA(LaunchFF::to_ff(static_cast<const double*>(p->grid_b), m3, static_cast<float2*>(p->grid_ff), s));
     p->mark(5, true, s);
     p->mark(6, false, s);
+    const double inv_alpha[3] = {2.0 * g.m[0] / (g.P * g.L[0]), 2.0 * g.m[1] / (g.P * g.L[1]),
+                                 2.0 * g.m[2] / (g.P * g.L[2])};   // 1/alpha_d per axis
     PSWF_CUDA(LaunchFF::interp(p->ntiles, g, static_cast<const float2*>(p->grid_ff), sp_h, sp_l, p->sp_idx,
-                               p->tile_off, wc, dwc, p->ff_kf, 1.0 / p->hp.p.alpha, phi, f, s));
+                               p->tile_off, wc, dwc, p->ff_kf, inv_alpha, phi, f, s));
     p->mark(6, true, s);
     PSWF_CUDA(cudaEventRecord(p->ev_join2, s));
     s = caller;
@@ -531,30 +555,30 @@ int check_ptr_device(const void* ptr, const char* name) {
 
 namespace {
 
-int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out,
+int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out,
                      const pswf::HostPlan* pre = nullptr);
 
-// Synthetic tuning system: n uniform points in [0, L)^3 (xorshift64*), charges +1, -1, ... (the last
+// Synthetic tuning system: n uniform points in the box (xorshift64*), charges +1, -1, ... (the last
 // one 0 for odd n), neutral.
-void tuning_system(double L, int64_t n, std::vector<double>& x, std::vector<double>& rho) {
+void tuning_system(const double* box, int64_t n, std::vector<double>& x, std::vector<double>& rho) {
     x.resize(3 * static_cast<size_t>(n));
     rho.resize(static_cast<size_t>(n));
     uint64_t st = 0x9E3779B97F4A7C15ull;
-    for (auto& v : x) {
+    for (size_t i = 0; i < x.size(); ++i) {
         st ^= st >> 12;
         st ^= st << 25;
         st ^= st >> 27;
-        v = L * static_cast<double>((st * 0x2545F4914F6CDD1Dull) >> 11) * 0x1.0p-53;
+        x[i] = box[i % 3] * static_cast<double>((st * 0x2545F4914F6CDD1Dull) >> 11) * 0x1.0p-53;
     }
     for (int64_t i = 0; i < n; ++i) rho[i] = (i % 2 == 0) ? 1.0 : -1.0;
     if (n % 2) rho[n - 1] = 0.0;
 }
 
-int plan_autotune(double L, int64_t n, double tol, const ewald_opts& o, ewald_plan* out) {
+int plan_autotune(const double* box, int64_t n, double tol, const ewald_opts& o, ewald_plan* out) {
     ewald_opts base = o;
     base.autotune = 0;
     try {
-        pswf::make_plan(L, n, tol, base);   // argument validation before any allocation
+        pswf::make_plan_box(box, n, tol, base);   // argument validation before any allocation
     } catch (const std::invalid_argument& e) {
         return fail(EWALD_EINVAL, e.what());
     } catch (const std::length_error& e) {
@@ -563,7 +587,7 @@ int plan_autotune(double L, int64_t n, double tol, const ewald_opts& o, ewald_pl
         return fail(EWALD_EINVAL, e.what());
     }
     std::vector<double> xh, rh;
-    tuning_system(L, n, xh, rh);
+    tuning_system(box, n, xh, rh);
     double *xd = nullptr, *rd = nullptr;
     cudaStream_t st = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -586,20 +610,21 @@ int plan_autotune(double L, int64_t n, double tol, const ewald_opts& o, ewald_pl
     }
     ewald_plan best = nullptr;
     float best_ms = 0.f;
-    std::vector<int> seen_m;
+    std::vector<int64_t> seen_m;   // grid sizes tried (m_x m_y m_z)
     for (const double gd : {1.5, 2.0, 3.0, 4.0, 6.0, 8.0, 12.0}) {
         ewald_opts c = base;
         c.grid_density = gd;
-        int m = 0;
+        int64_t m = 0;
         try {
-            m = pswf::make_plan(L, n, tol, c).p.m;
+            const ewald_params q = pswf::make_plan_box(box, n, tol, c).p;
+            m = static_cast<int64_t>(q.grid[0]) * q.grid[1] * q.grid[2];
         } catch (const std::exception&) {
             continue;   // e.g. a grid beyond the size limit
         }
         if (std::find(seen_m.begin(), seen_m.end(), m) != seen_m.end()) continue;
         seen_m.push_back(m);
         ewald_plan cand = nullptr;
-        if (plan_create_impl(L, n, tol, &c, &cand) != EWALD_OK) continue;
+        if (plan_create_impl(box, n, tol, &c, &cand) != EWALD_OK) continue;
         int rc = eval_device(cand, xd, rd, nullptr, nullptr, st);   // warm-up
         float ms = 0.f;
         if (rc == EWALD_OK) {
@@ -629,7 +654,7 @@ int plan_autotune(double L, int64_t n, double tol, const ewald_opts& o, ewald_pl
 }
 
 // pre: the host plan computed already (batches plan their systems on several threads first)
-int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out,
+int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out,
                      const pswf::HostPlan* pre) {
     if (!out) return fail(EWALD_EINVAL, "out is NULL");
     *out = nullptr;
@@ -638,7 +663,7 @@ int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ew
     if (!p) return fail(EWALD_ENOMEM, "host allocation failed");
     try {
         const ewald_opts o = opts ? *opts : pswf::default_opts();
-        p->hp = pre ? *pre : pswf::make_plan(L, n, tol, o);
+        p->hp = pre ? *pre : pswf::make_plan_box(box, n, tol, o);
     } catch (const std::invalid_argument& e) {
         delete p;
         return fail(EWALD_EINVAL, e.what());
@@ -654,31 +679,33 @@ int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ew
     p->ff = q.precision == EWALD_FLOATFLOAT;
     pswf::Geom& g = p->g;
     g.n = static_cast<int>(n);
-    g.m = q.m;
     g.P = q.P;
     g.T = q.tile;
-    g.nt = q.m / q.tile;
-    g.ncell = q.ncell;
     g.reach = q.sr_reach;
     g.degw = q.deg_w;
     g.degr = q.deg_r;
-    g.L = q.L;
-    g.invL = 1.0 / q.L;
-    g.h = q.h;
-    g.invh = q.m / q.L;
-    g.cellw = q.L / q.ncell;
-    g.invcellw = q.ncell / q.L;
+    for (int d = 0; d < 3; ++d) {
+        g.m[d] = q.grid[d];
+        g.nt[d] = q.grid[d] / q.tile;
+        g.ncell[d] = q.cells[d];
+        g.L[d] = q.box[d];
+        g.invL[d] = 1.0 / q.box[d];
+        g.invh[d] = q.grid[d] / q.box[d];
+        g.cellw[d] = q.box[d] / q.cells[d];
+        g.invcellw[d] = q.cells[d] / q.box[d];
+    }
     g.rc = q.rc;
     g.self = q.self_coeff;
-    p->ntiles = g.nt * g.nt * g.nt;
-    p->ncells = g.ncell * g.ncell * g.ncell;
+    p->ntiles = g.nt[0] * g.nt[1] * g.nt[2];
+    p->ncells = g.ncell[0] * g.ncell[1] * g.ncell[2];
+    p->m3 = static_cast<size_t>(g.m[0]) * g.m[1] * g.m[2];
+    p->nspec = static_cast<size_t>(g.m[0]) * g.m[1] * (g.m[2] / 2 + 1);
     p->epart_blocks = 256;
     cudaGetDevice(&p->device);
 
     const size_t rs = p->fp64 ? sizeof(double) : sizeof(float);
     const int E = g.T + g.P - 1;
-    const size_t m3 = static_cast<size_t>(g.m) * g.m * g.m;
-    const size_t nspec = static_cast<size_t>(g.m) * g.m * (g.m / 2 + 1);
+    const size_t m3 = p->m3, nspec = p->nspec;
     struct A { void** ptr; size_t bytes; } allocs[] = {
         {reinterpret_cast<void**>(&p->key_rank), sizeof(int4) * n},
         {reinterpret_cast<void**>(&p->tile_cnt), sizeof(int) * (p->ntiles + 1)},
@@ -723,19 +750,20 @@ int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ew
         // distance between target and source cell below rc
         std::vector<int4> cols;
         const int R = g.reach;
-        auto gap = [](int d) { return d == 0 ? 0 : std::abs(d) - 1; };
-        const double lim = (g.rc / g.cellw) * (g.rc / g.cellw);
+        // box distance between cells offset by (dx, dy, dz): sum_d (max(|d| - 1, 0) w_d)^2
+        auto gap = [&](int k, int d) { return (k == 0 ? 0 : std::abs(k) - 1) * g.cellw[d]; };
+        const double lim = g.rc * g.rc;
         for (int dx = -R; dx <= R; ++dx)
             for (int dy = -R; dy <= R; ++dy) {
-                const double gxy = double(gap(dx)) * gap(dx) + double(gap(dy)) * gap(dy);
+                const double gxy = gap(dx, 0) * gap(dx, 0) + gap(dy, 1) * gap(dy, 1);
                 if (gxy >= lim) continue;
                 int dzmax = 0;
-                while (dzmax < R && gxy + double(gap(dzmax + 1)) * gap(dzmax + 1) < lim) ++dzmax;
+                while (dzmax < R && gxy + gap(dzmax + 1, 2) * gap(dzmax + 1, 2) < lim) ++dzmax;
                 cols.push_back(make_int4(dx, dy, dzmax, 0));
             }
         p->n_cols = static_cast<int>(cols.size());
         // every column's z-run splits into at most ceil((2R+1)/nc) + 1 contiguous pieces
-        const int pieces = (2 * R + 1 + g.ncell - 1) / g.ncell + 1;
+        const int pieces = (2 * R + 1 + g.ncell[2] - 1) / g.ncell[2] + 1;
         p->sr_rcap = p->n_cols * pieces;
         if (p->sr_rcap > pswf::kShortMaxRanges) {
             delete p;
@@ -770,7 +798,8 @@ int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ew
         if ((rc = upload_ff(reinterpret_cast<float**>(&p->wcoef), p->hp.wc)) ||
             (rc = upload_ff(reinterpret_cast<float**>(&p->dwcoef), p->hp.dwc)) ||
             (rc = upload<double>(reinterpret_cast<double**>(&p->iw), p->hp.iw)) ||
-            (rc = upload<double>(reinterpret_cast<double**>(&p->mtab), p->hp.mtab))) {
+            (rc = upload<double>(reinterpret_cast<double**>(&p->mtab), p->hp.mtab)) ||
+            (rc = upload<double>(reinterpret_cast<double**>(&p->gcoef), p->hp.gc))) {
             delete p;
             return rc;
         }
@@ -780,7 +809,8 @@ int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ew
             (rc = upload<double>(reinterpret_cast<double**>(&p->p1c), p->hp.p1c)) ||
             (rc = upload<double>(reinterpret_cast<double**>(&p->qc), p->hp.qc)) ||
             (rc = upload<double>(reinterpret_cast<double**>(&p->iw), p->hp.iw)) ||
-            (rc = upload<double>(reinterpret_cast<double**>(&p->mtab), p->hp.mtab))) {
+            (rc = upload<double>(reinterpret_cast<double**>(&p->mtab), p->hp.mtab)) ||
+            (rc = upload<double>(reinterpret_cast<double**>(&p->gcoef), p->hp.gc))) {
             delete p;
             return rc;
         }
@@ -790,7 +820,8 @@ int plan_create_impl(double L, int64_t n, double tol, const ewald_opts* opts, ew
             (rc = upload<float>(reinterpret_cast<float**>(&p->p1c), p->hp.p1c)) ||
             (rc = upload<float>(reinterpret_cast<float**>(&p->qc), p->hp.qc)) ||
             (rc = upload<float>(reinterpret_cast<float**>(&p->iw), p->hp.iw)) ||
-            (rc = upload<float>(reinterpret_cast<float**>(&p->mtab), p->hp.mtab))) {
+            (rc = upload<float>(reinterpret_cast<float**>(&p->mtab), p->hp.mtab)) ||
+            (rc = upload<float>(reinterpret_cast<float**>(&p->gcoef), p->hp.gc))) {
             delete p;
             return rc;
         }
@@ -881,11 +912,11 @@ int ewald_opts_default(ewald_opts* opts) {
     return EWALD_OK;
 }
 
-int ewald_plan_params(double L, int64_t n, double tol, const ewald_opts* opts, ewald_params* out) {
-    if (!out) return fail(EWALD_EINVAL, "out is NULL");
+int ewald_plan_params_box(const double* L, int64_t n, double tol, const ewald_opts* opts, ewald_params* out) {
+    if (!out || !L) return fail(EWALD_EINVAL, "NULL L or out");
     try {
         const ewald_opts o = opts ? *opts : pswf::default_opts();
-        *out = pswf::make_plan(L, n, tol, o).p;
+        *out = pswf::make_plan_box(L, n, tol, o).p;
         return EWALD_OK;
     } catch (const std::invalid_argument& e) {
         return fail(EWALD_EINVAL, e.what());
@@ -896,11 +927,22 @@ int ewald_plan_params(double L, int64_t n, double tol, const ewald_opts* opts, e
     }
 }
 
-int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out) {
+int ewald_plan_params(double L, int64_t n, double tol, const ewald_opts* opts, ewald_params* out) {
+    const double box[3] = {L, L, L};
+    return ewald_plan_params_box(box, n, tol, opts, out);
+}
+
+int ewald_plan_create_box(const double* L, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out) {
     if (!out) return fail(EWALD_EINVAL, "out is NULL");
     *out = nullptr;
+    if (!L) return fail(EWALD_EINVAL, "L is NULL");
     if (opts && opts->autotune == 1) return plan_autotune(L, n, tol, *opts, out);
     return plan_create_impl(L, n, tol, opts, out);
+}
+
+int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out) {
+    const double box[3] = {L, L, L};
+    return ewald_plan_create_box(box, n, tol, opts, out);
 }
 
 int ewald_plan_query(ewald_plan plan, ewald_params* out) {
@@ -949,7 +991,7 @@ int ewald_check(ewald_plan plan, void* stream) {
 int ewald_debug_grid(ewald_plan plan, int which, double* host_out) {
     if (!plan || plan->is_batch || !host_out || (which != 0 && which != 1)) return fail(EWALD_EINVAL, "bad argument");
     PSWF_CUDA(cudaDeviceSynchronize());
-    const size_t m3 = static_cast<size_t>(plan->g.m) * plan->g.m * plan->g.m;
+    const size_t m3 = plan->m3;
     const void* src = which == 0 ? plan->grid_a : plan->grid_b;
     if (plan->fp64) {
         PSWF_CUDA(cudaMemcpy(host_out, src, sizeof(double) * m3, cudaMemcpyDeviceToHost));
@@ -1008,7 +1050,8 @@ int ewald_plan_batch_create(int nsys, const double* L, const int64_t* n, double 
         }
     for (int b = 0; b < nsys; ++b) {
         ewald_plan m = nullptr;
-        const int rc = plan_create_impl(L[b], n[b], tol, &o, &m, &hps[b]);
+        const double box[3] = {L[b], L[b], L[b]};
+        const int rc = plan_create_impl(box, n[b], tol, &o, &m, &hps[b]);
         if (rc != EWALD_OK) {
             const std::string why = g_last_error;
             delete p;

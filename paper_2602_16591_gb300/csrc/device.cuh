@@ -24,10 +24,13 @@ namespace pswf {
 
 template <typename real> struct alignas(4 * sizeof(real)) Vec4 { real x, y, z, w; };
 
-// Geometry and sizes shared by the kernels of one plan (passed by value).
+// Geometry and sizes shared by the kernels of one plan (passed by value).  Per-axis arrays (x, y, z)
+// describe cuboid boxes (Remark on cuboid domains, Sec. 6.1); a cube has three equal entries.
 struct Geom {
-    int n, m, P, T, nt, ncell, reach, degw, degr;
-    double L, invL, h, invh, cellw, invcellw, rc, self;
+    int n, P, T, reach, degw, degr;
+    int m[3], nt[3], ncell[3];
+    double L[3], invL[3], invh[3], cellw[3], invcellw[3];
+    double rc, self;
 };
 
 // Spreading / interpolation tile edge (grid points); m is a multiple of it.  float32 plans use 8 (the
@@ -54,29 +57,29 @@ __device__ inline Located locate(const double* xp, const Geom& g) {
     for (int d = 0; d < 3; ++d) {
         double x = xp[d];
         if (!isfinite(x)) { r.finite = false; x = 0.0; }
-        double w = x - g.L * floor(x * g.invL);
-        if (w >= g.L) w -= g.L;
+        double w = x - g.L[d] * floor(x * g.invL[d]);
+        if (w >= g.L[d]) w -= g.L[d];
         if (w < 0.0) w = 0.0;
         r.w[d] = w;
-        const double t = w * g.invh;
+        const double t = w * g.invh[d];
         const int l0 = static_cast<int>(ceil(t - 0.5 * g.P));
         r.z[d] = 2.0 * (t - l0) - (g.P - 1);
-        int lw = l0 % g.m;
-        if (lw < 0) lw += g.m;
+        int lw = l0 % g.m[d];
+        if (lw < 0) lw += g.m[d];
         r.lw[d] = lw;
-        int c = static_cast<int>(w * g.invcellw);   // no float64 division: multiply, then clamp
-        c = c < 0 ? 0 : (c >= g.ncell ? g.ncell - 1 : c);
+        int c = static_cast<int>(w * g.invcellw[d]);   // no float64 division: multiply, then clamp
+        c = c < 0 ? 0 : (c >= g.ncell[d] ? g.ncell[d] - 1 : c);
         r.cell[d] = c;
-        r.loc[d] = w - c * g.cellw;
+        r.loc[d] = w - c * g.cellw[d];
     }
     return r;
 }
 
 __device__ inline int tile_of(const Located& r, const Geom& g) {
-    return ((r.lw[0] / g.T) * g.nt + r.lw[1] / g.T) * g.nt + r.lw[2] / g.T;
+    return ((r.lw[0] / g.T) * g.nt[1] + r.lw[1] / g.T) * g.nt[2] + r.lw[2] / g.T;
 }
 __device__ inline int cell_of(const Located& r, const Geom& g) {
-    return (r.cell[0] * g.ncell + r.cell[1]) * g.ncell + r.cell[2];
+    return (r.cell[0] * g.ncell[1] + r.cell[1]) * g.ncell[2] + r.cell[2];
 }
 
 // status[0] = sum rho, status[1] = sum |rho|, status[2] = number of non-finite inputs
@@ -339,10 +342,11 @@ __global__ void __launch_bounds__(spread_threads<P, spread_tile<real>()>()) k_sp
 template <typename real>
 __global__ void k_halo(const real* __restrict__ scratch, const int* __restrict__ tile_off, Geom g,
                        real* __restrict__ grid) {
-    const int m = g.m, T = g.T, nt = g.nt, E = g.T + g.P - 1;
+    const int my = g.m[1], mz = g.m[2], T = g.T, E = g.T + g.P - 1;
+    const int ntx = g.nt[0], nty = g.nt[1], ntz = g.nt[2];
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= m * m * m) return;
-    const int lz = id % m, ly = (id / m) % m, lx = id / (m * m);
+    if (id >= g.m[0] * my * mz) return;
+    const int lz = id % mz, ly = (id / mz) % my, lx = id / (mz * my);
     const int tlx = lx / T, tly = ly / T, tlz = lz / T;
     const int olx = lx - tlx * T, oly = ly - tly * T, olz = lz - tlz * T;
     const size_t slab = static_cast<size_t>(E) * E * E;
@@ -353,30 +357,58 @@ __global__ void k_halo(const real* __restrict__ scratch, const int* __restrict__
         for (int ey = oly; ey < E; ey += T) {
             int tz = tlz;
             for (int ez = olz; ez < E; ez += T) {
-                const int tile = (tx * nt + ty) * nt + tz;
+                const int tile = (tx * nty + ty) * ntz + tz;
                 if (tile_off[tile] != tile_off[tile + 1])
                     s += scratch[static_cast<size_t>(tile) * slab + (ex * E + ey) * E + ez];
-                tz = tz == 0 ? nt - 1 : tz - 1;
+                tz = tz == 0 ? ntz - 1 : tz - 1;
             }
-            ty = ty == 0 ? nt - 1 : ty - 1;
+            ty = ty == 0 ? nty - 1 : ty - 1;
         }
-        tx = tx == 0 ? nt - 1 : tx - 1;
+        tx = tx == 0 ? ntx - 1 : tx - 1;
     }
     grid[id] = s;
 }
 
 // ---- Alg. 2 step 3: diagonal scaling on the R2C half spectrum ------------------------------------
+// Cube: S = mtab[|k|^2] iw[kx] iw[ky] iw[kz] on the open ball |k| < m/2 (host table over integer |k|^2).
+// Cuboid: |omega|^2 = sum_d (2 pi k_d / L_d)^2 is not an integer function, so
+// S = (4 pi / (V |omega|^2)) g(2 t - 1) iw_x[kx] iw_y[ky] iw_z[kz] with t = (|omega| r_c / c_s)^2 < 1 (the
+// retained ellipsoid) and g the host fit of the in-band mollifier transform psi(sqrt t)/psi(0).
+template <typename real>
+struct ScaleParams {
+    int m[3];
+    int cube, degg;
+    real w2[3];          // (2 pi / L_d)^2
+    real tscale;         // (r_c / c_s)^2
+    real four_pi_over_V;
+    const real* iw;      // cube: m entries; cuboid: m_x + m_y + m_z entries
+    const real* mtab;    // cube only
+    const real* gc;      // cuboid only: degg + 1 monomial coefficients
+};
+
 template <typename real, typename cplx>
-__global__ void k_scale(cplx* __restrict__ spec, int m, const real* __restrict__ iw, const real* __restrict__ mtab) {
-    const int mh = m / 2 + 1;
+__global__ void k_scale(cplx* __restrict__ spec, ScaleParams<real> sp) {
+    const int mx = sp.m[0], my = sp.m[1], mz = sp.m[2], mh = mz / 2 + 1;
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= m * m * mh) return;
-    const int iz = id % mh, iy = (id / mh) % m, ix = id / (mh * m);
-    const int kx = ix < m / 2 ? ix : ix - m, ky = iy < m / 2 ? iy : iy - m, kz = iz;
-    const int q = kx * kx + ky * ky + kz * kz;
-    const int qmax = (m / 2) * (m / 2);
+    if (id >= mx * my * mh) return;
+    const int iz = id % mh, iy = (id / mh) % my, ix = id / (mh * my);
+    const int kx = ix < mx / 2 ? ix : ix - mx, ky = iy < my / 2 ? iy : iy - my, kz = iz;
     real s = real(0);
-    if (q > 0 && q < qmax) s = mtab[q] * iw[ix] * iw[iy] * iw[iz];   // open ball |k| < m/2
+    if (sp.cube) {
+        const int m = mx;
+        const int q = kx * kx + ky * ky + kz * kz;
+        const int qmax = (m / 2) * (m / 2);
+        if (q > 0 && q < qmax) s = sp.mtab[q] * sp.iw[ix] * sp.iw[iy] * sp.iw[iz];   // open ball |k| < m/2
+    } else {
+        const real w2 = sp.w2[0] * real(kx * kx) + sp.w2[1] * real(ky * ky) + sp.w2[2] * real(kz * kz);
+        const real t = w2 * sp.tscale;
+        if (w2 > real(0) && t < real(1)) {
+            const real u = real(2) * t - real(1);
+            real gh = sp.gc[sp.degg];
+            for (int k = sp.degg - 1; k >= 0; --k) gh = fma(gh, u, sp.gc[k]);
+            s = sp.four_pi_over_V / w2 * gh * sp.iw[ix] * sp.iw[mx + iy] * sp.iw[mx + my + iz];
+        }
+    }
     cplx v = spec[id];
     v.x *= s;
     v.y *= s;
@@ -397,7 +429,7 @@ template <typename real, int P>
 __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, const Vec4<real>* __restrict__ rec,
                                                 const int2* __restrict__ idx, const int* __restrict__ tile_off,
                                                 const real* __restrict__ wcoef, const real* __restrict__ dwcoef,
-                                                Geom g, real inv_alpha, double* __restrict__ phi_out,
+                                                Geom g, Vec4<real> inv_alpha, double* __restrict__ phi_out,
                                                 double* __restrict__ f_out) {
     constexpr int T = spread_tile<real>(), E = T + P - 1;
     constexpr int NB = InterpCfg<real>::NB, NWARP = InterpCfg<real>::NWARP;
@@ -405,8 +437,8 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
     const int tile = blockIdx.x;
     const int beg = tile_off[tile], end = tile_off[tile + 1];
     if (beg == end) return;
-    const int m = g.m, nt = g.nt, degw = g.degw;
-    const int tz = tile % nt, ty = (tile / nt) % nt, tx = tile / (nt * nt);
+    const int mx = g.m[0], my = g.m[1], mz = g.m[2], degw = g.degw;
+    const int tz = tile % g.nt[2], ty = (tile / g.nt[2]) % g.nt[1], tx = tile / (g.nt[2] * g.nt[1]);
     // weight rows padded to whole 16-byte vectors (vector loads of a particle's x-weights)
     constexpr int VW = 16 / static_cast<int>(sizeof(real)), PP = (P + VW - 1) / VW * VW;
     using V = typename std::conditional<sizeof(real) == 4, float4, double2>::type;
@@ -422,15 +454,15 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
     for (int e = threadIdx.x; e < E * E * E; e += blockDim.x) {
         const int ez = e % E, ey = (e / E) % E, ex = e / (E * E);
         int gx = tx * T + ex, gy = ty * T + ey, gz = tz * T + ez;
-        gx -= gx >= m ? m : 0;
-        gy -= gy >= m ? m : 0;
-        gz -= gz >= m ? m : 0;
-        if (gx >= m || gy >= m || gz >= m) {   // extended block wider than the grid (small m)
-            gx %= m;
-            gy %= m;
-            gz %= m;
+        gx -= gx >= mx ? mx : 0;
+        gy -= gy >= my ? my : 0;
+        gz -= gz >= mz ? mz : 0;
+        if (gx >= mx || gy >= my || gz >= mz) {   // extended block wider than the grid (small m)
+            gx %= mx;
+            gy %= my;
+            gz %= mz;
         }
-        G[e] = grid[(static_cast<size_t>(gx) * m + gy) * m + gz];
+        G[e] = grid[(static_cast<size_t>(gx) * my + gy) * mz + gz];
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -449,8 +481,9 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
                 for (int a = 0; a < P; ++a) ww[(j * 6 + kind) * PP + a] = w[a];
             } else {
                 window_weights<real, P>(sd, degw, z, w);
+                const real ia = d == 0 ? inv_alpha.x : (d == 1 ? inv_alpha.y : inv_alpha.z);   // 1/alpha_d
 #pragma unroll
-                for (int a = 0; a < P; ++a) ww[(j * 6 + kind) * PP + a] = w[a] * inv_alpha;
+                for (int a = 0; a < P; ++a) ww[(j * 6 + kind) * PP + a] = w[a] * ia;
             }
         }
         __syncwarp();
@@ -577,14 +610,17 @@ __host__ __device__ constexpr size_t short_dyn_smem(int rcap) {
 // Returns the total number of candidates (warp-uniform).  Pieces beyond cap are dropped; the host sizes
 // cap from the columns and the largest number of pieces per column, so none are.
 __device__ __forceinline__ int short_ranges(const int4* __restrict__ scol, int ncols, const int* __restrict__ cell_off,
-                                            int nc, int cx, int cy, int cz, int lane, int cap, int4* rng, int* pos) {
-    auto wrap = [nc](int v) {   // v in (-2 nc, 2 nc) -> [0, nc)
-        v += v < 0 ? nc : 0;
-        v += v < 0 ? nc : 0;
-        v -= v >= nc ? nc : 0;
-        v -= v >= nc ? nc : 0;
+                                            const int* nc3, int cx, int cy, int cz, int lane, int cap, int4* rng,
+                                            int* pos) {
+    const int ncx = nc3[0], ncy = nc3[1], nc = nc3[2];   // nc: cells along z (the contiguous axis)
+    auto wrapn = [](int v, int n) {   // v in (-2 n, 2 n) -> [0, n)
+        v += v < 0 ? n : 0;
+        v += v < 0 ? n : 0;
+        v -= v >= n ? n : 0;
+        v -= v >= n ? n : 0;
         return v;
     };
+    auto wrap = [&](int v) { return wrapn(v, nc); };
     int nr = 0;
     for (int k0 = 0; k0 < ncols; k0 += 32) {
         const int k = k0 + lane;
@@ -593,7 +629,7 @@ __device__ __forceinline__ int short_ranges(const int4* __restrict__ scol, int n
         int base = 0;
         if (k < ncols) {
             col = scol[k];
-            base = (wrap(cx + col.x) * nc + wrap(cy + col.y)) * nc;
+            base = (wrapn(cx + col.x, ncx) * ncy + wrapn(cy + col.y, ncy)) * nc;
             for (int d = -col.z; d <= col.z;) {
                 const int zw = wrap(cz + d);
                 d += min(col.z - d + 1, nc - zw);
@@ -679,29 +715,30 @@ __global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<float>
                                                             int ncols, int rcap, Geom g, const __grid_constant__ ShortParams<float, D> kp,
                                                             double* __restrict__ phi_out, double* __restrict__ f_out) {
     constexpr int NSH = 2 * kShortMaxR + 1;
-    __shared__ float sh_hi[NSH], sh_lo[NSH];
+    __shared__ float sh_hi[3][NSH], sh_lo[3][NSH];   // cell shifts (k - R) w_d, hi and lo parts
     __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
     __shared__ float stx[kShortWarps][kShortMaxT][4];          // target position (hi parts) and charge
     __shared__ float stl[kShortWarps][kShortMaxT][4];          // lo parts of the position
-    const int R = g.reach, nc = g.ncell;
-    for (int k = threadIdx.x; k < 2 * R + 1; k += blockDim.x) {
-        const double o = (k - R) * g.cellw;
-        sh_hi[k] = static_cast<float>(o);
-        sh_lo[k] = static_cast<float>(o - static_cast<double>(sh_hi[k]));
+    const int R = g.reach;
+    for (int k = threadIdx.x; k < 3 * (2 * R + 1); k += blockDim.x) {
+        const int d = k / (2 * R + 1), i = k % (2 * R + 1);
+        const double o = (i - R) * g.cellw[d];
+        sh_hi[d][i] = static_cast<float>(o);
+        sh_lo[d][i] = static_cast<float>(o - static_cast<double>(sh_hi[d][i]));
     }
     for (int k = threadIdx.x; k < ncols; k += blockDim.x) scol[k] = cols[k];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c = blockIdx.x * kShortWarps + warp;
-    if (c >= nc * nc * nc) return;
+    if (c >= g.ncell[0] * g.ncell[1] * g.ncell[2]) return;
     const int tb = cell_off[c], te = cell_off[c + 1];
     if (tb == te) return;
-    const int cz = c % nc, cy = (c / nc) % nc, cx = c / (nc * nc);
+    const int cz = c % g.ncell[2], cy = (c / g.ncell[2]) % g.ncell[1], cx = c / (g.ncell[2] * g.ncell[1]);
     extern __shared__ __align__(16) unsigned char short_dyn[];
     int4* rng = reinterpret_cast<int4*>(short_dyn) + warp * rcap;
     int* pos = reinterpret_cast<int*>(reinterpret_cast<int4*>(short_dyn) + kShortWarps * rcap) + warp * (rcap + 1);
 
-    const int total = short_ranges(scol, ncols, cell_off, nc, cx, cy, cz, lane, rcap, rng, pos);
+    const int total = short_ranges(scol, ncols, cell_off, g.ncell, cx, cy, cz, lane, rcap, rng, pos);
 
     for (int t0 = tb; t0 < te; t0 += kShortMaxT) {
         const int nt = min(kShortMaxT, te - t0);
@@ -735,7 +772,7 @@ __global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<float>
             szc = lo[j].w;
             const int4 col = scol[rg.w];
             const int ix = col.x + R, iy = col.y + R, iz = rg.z + (static_cast<int>(szc) - rg.y) + R;
-            const float px = sfx + sh_hi[ix], py = sfy + sh_hi[iy], pz = sfz + sh_hi[iz];
+            const float px = sfx + sh_hi[0][ix], py = sfy + sh_hi[1][iy], pz = sfz + sh_hi[2][iz];
             bool loaded = false;
             float qj = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
 #pragma unroll
@@ -750,9 +787,9 @@ __global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<float>
                         loaded = true;
                         const Vec4<float> l = lo[j];
                         qj = rec[j].w;
-                        ex = l.x + sh_lo[ix];
-                        ey = l.y + sh_lo[iy];
-                        ez = l.z + sh_lo[iz];
+                        ex = l.x + sh_lo[0][ix];
+                        ey = l.y + sh_lo[1][iy];
+                        ez = l.z + sh_lo[2][iz];
                     }
                     float ddx, ddy, ddz;
                     ddx = dxf + (stl[warp][t][0] - ex);
@@ -819,32 +856,33 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<double>
                                                               double* __restrict__ phi_out, double* __restrict__ f_out) {
     constexpr int NSH = 2 * kShortMaxR + 1, MT = kShortMaxT;
     static_assert(NSH <= 16, "queue entries pack 4-bit shift indices");
-    __shared__ float sh_hi[NSH];
-    __shared__ double sh_d[NSH];
+    __shared__ float sh_hi[3][NSH];
+    __shared__ double sh_d[3][NSH];
     __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
     __shared__ double stx[kShortWarps][MT][4];          // exact target position and charge
     __shared__ float stl[kShortWarps][MT][4];         // float32 copy of the target (cutoff pre-test)
     __shared__ int2 sq[kShortWarps][MT][kShortQCap];  // {source, ix | iy << 4 | iz << 8}
     __shared__ int sqlen[kShortWarps][MT];
-    const int R = g.reach, nc = g.ncell;
-    for (int k = threadIdx.x; k < 2 * R + 1; k += blockDim.x) {
-        const double o = (k - R) * g.cellw;
-        sh_d[k] = o;
-        sh_hi[k] = static_cast<float>(o);
+    const int R = g.reach;
+    for (int k = threadIdx.x; k < 3 * (2 * R + 1); k += blockDim.x) {
+        const int d = k / (2 * R + 1), i = k % (2 * R + 1);
+        const double o = (i - R) * g.cellw[d];
+        sh_d[d][i] = o;
+        sh_hi[d][i] = static_cast<float>(o);
     }
     for (int k = threadIdx.x; k < ncols; k += blockDim.x) scol[k] = cols[k];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c = blockIdx.x * kShortWarps + warp;
-    if (c >= nc * nc * nc) return;
+    if (c >= g.ncell[0] * g.ncell[1] * g.ncell[2]) return;
     const int tb = cell_off[c], te = cell_off[c + 1];
     if (tb == te) return;
-    const int cz = c % nc, cy = (c / nc) % nc, cx = c / (nc * nc);
+    const int cz = c % g.ncell[2], cy = (c / g.ncell[2]) % g.ncell[1], cx = c / (g.ncell[2] * g.ncell[1]);
     extern __shared__ __align__(16) unsigned char short_dyn[];
     int4* rng = reinterpret_cast<int4*>(short_dyn) + warp * rcap;
     int* pos = reinterpret_cast<int*>(reinterpret_cast<int4*>(short_dyn) + kShortWarps * rcap) + warp * (rcap + 1);
     int* qlen = sqlen[warp];
-    const int total = short_ranges(scol, ncols, cell_off, nc, cx, cy, cz, lane, rcap, rng, pos);
+    const int total = short_ranges(scol, ncols, cell_off, g.ncell, cx, cy, cz, lane, rcap, rng, pos);
 
     for (int t0 = tb; t0 < te; t0 += MT) {
         const int nt = min(MT, te - t0);
@@ -871,9 +909,9 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<double>
             const int ix = e.y & 15, iy = (e.y >> 4) & 15, iz = (e.y >> 8) & 15;
             const Vec4<double> a = rec[active ? e.x : t0];
             double ddx, ddy, ddz;
-            ddx = stx[warp][t][0] - (a.x + sh_d[ix]);
-            ddy = stx[warp][t][1] - (a.y + sh_d[iy]);
-            ddz = stx[warp][t][2] - (a.z + sh_d[iz]);
+            ddx = stx[warp][t][0] - (a.x + sh_d[0][ix]);
+            ddy = stx[warp][t][1] - (a.y + sh_d[1][iy]);
+            ddz = stx[warp][t][2] - (a.z + sh_d[2][iz]);
             const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
             const bool in = active && r2 < kp.rc2 && r2 > 0.0;
             const double u = fma(r2, kp.two_over_rc2, double(-1));
@@ -915,7 +953,7 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<double>
                     szc = f.w;
                     const int4 col = scol[rg.w];
                     const int ix = col.x + R, iy = col.y + R, iz = rg.z + (static_cast<int>(szc) - rg.y) + R;
-                    const float px = sfx + sh_hi[ix], py = sfy + sh_hi[iy], pz = sfz + sh_hi[iz];
+                    const float px = sfx + sh_hi[0][ix], py = sfy + sh_hi[1][iy], pz = sfz + sh_hi[2][iz];
 #pragma unroll
                     for (int t = 0; t < MT; ++t) {
                         if (t >= nt) break;   // warp-uniform

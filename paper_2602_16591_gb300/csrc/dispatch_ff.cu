@@ -36,8 +36,8 @@ cudaError_t spread_p(int ntiles, const Geom& g, const float4* rh, const float4* 
 
 template <int P>
 cudaError_t interp_p(int ntiles, const Geom& g, const float2* grid, const float4* rh, const float4* rl,
-                     const int2* idx, const int* tile_off, const float* wc, const float* dwc, int kf, float iah,
-                     float ial, double* phi, double* f, cudaStream_t s) {
+                     const int2* idx, const int* tile_off, const float* wc, const float* dwc, int kf, float4 iah,
+                     float4 ial, double* phi, double* f, cudaStream_t s) {
     // stage the tile's block while two blocks still fit an SM (measured: staged wins at P = 16, direct
     // L1/L2 reads win at P = 19, where a staged block allows one block per SM)
     const bool staged = interp_smem_ff(P, g.degw, true) <= 113 * 1024;
@@ -62,7 +62,7 @@ cudaError_t short_d(const Geom& g, const float4* rh, const float4* rl, const int
     split(2.0 / (g.rc * g.rc), kp.two_over_rc2_h, kp.two_over_rc2_l);
     kp.rc2f = static_cast<float>(g.rc * g.rc * (1.0 + 1e-4));
     kp.kr = kr;
-    const int ncells = g.ncell * g.ncell * g.ncell;
+    const int ncells = g.ncell[0] * g.ncell[1] * g.ncell[2];
     const size_t smem = short_dyn_smem(rcap);
     k_short_ff<D><<<(ncells + kShortWarps - 1) / kShortWarps, 32 * kShortWarps, smem, s>>>(
         rh, rl, idx, cz, cell_off, cols, ncols, rcap, g, kp, phi, f);
@@ -94,7 +94,7 @@ cudaError_t LaunchFF::spread(int ntiles, const Geom& g, const float4* rec_h, con
 }
 
 cudaError_t LaunchFF::halo(const float2* scratch, const int* tile_off, const Geom& g, double* grid, cudaStream_t s) {
-    const int mm = g.m * g.m * g.m;
+    const int mm = g.m[0] * g.m[1] * g.m[2];
     k_halo_ff<<<(mm + 255) / 256, 256, 0, s>>>(scratch, tile_off, g, grid);
     return cudaGetLastError();
 }
@@ -106,9 +106,11 @@ cudaError_t LaunchFF::to_ff(const double* grid, size_t count, float2* out, cudaS
 
 cudaError_t LaunchFF::interp(int ntiles, const Geom& g, const float2* grid, const float4* rec_h, const float4* rec_l,
                              const int2* idx, const int* tile_off, const float* wc, const float* dwc, int kf,
-                             double inv_alpha, double* phi, double* f, cudaStream_t s) {
-    float iah, ial;
-    split(inv_alpha, iah, ial);
+                             const double* inv_alpha, double* phi, double* f, cudaStream_t s) {
+    float4 iah{}, ial{};
+    split(inv_alpha[0], iah.x, ial.x);
+    split(inv_alpha[1], iah.y, ial.y);
+    split(inv_alpha[2], iah.z, ial.z);
     switch (g.P) {
 #define X(p) case p: return interp_p<p>(ntiles, g, grid, rec_h, rec_l, idx, tile_off, wc, dwc, kf, iah, ial, phi, f, s);
         PSWF_FF_P_CASES(X)

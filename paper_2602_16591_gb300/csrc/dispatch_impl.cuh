@@ -20,7 +20,7 @@ cudaError_t spread_p(int ntiles, const Vec4<real_t>* rec, const int2* idx, const
 
 template <int P>
 cudaError_t interp_p(int ntiles, const real_t* grid, const Vec4<real_t>* rec, const int2* idx, const int* tile_off,
-                     const real_t* wcoef, const real_t* dwcoef, const Geom& g, real_t inv_alpha, double* phi, double* f,
+                     const real_t* wcoef, const real_t* dwcoef, const Geom& g, Vec4<real_t> inv_alpha, double* phi, double* f,
                      cudaStream_t s) {
     const size_t smem = Launch<real_t>::interp_smem(P, g.degw);
     auto kern = k_interp<real_t, P>;
@@ -66,7 +66,7 @@ cudaError_t Launch<real_t>::spread(int P, int ntiles, const Vec4<real_t>* rec, c
 template <>
 cudaError_t Launch<real_t>::interp(int P, int ntiles, const real_t* grid, const Vec4<real_t>* rec, const int2* idx,
                                  const int* tile_off, const real_t* wcoef, const real_t* dwcoef, const Geom& g,
-                                 real_t inv_alpha, double* phi, double* f, cudaStream_t s) {
+                                 Vec4<real_t> inv_alpha, double* phi, double* f, cudaStream_t s) {
     switch (P) {
 #define X(p) case p: return interp_p<p>(ntiles, grid, rec, idx, tile_off, wcoef, dwcoef, g, inv_alpha, phi, f, s);
         PSWF_P_CASES(X)

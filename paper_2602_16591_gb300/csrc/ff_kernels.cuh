@@ -144,10 +144,11 @@ __global__ void __launch_bounds__(spread_threads<P, kTile64>()) k_spread_ff(cons
 // Halo sum of the float-float slabs (same enumeration as k_halo) into the float64 grid.
 static __global__ void k_halo_ff(const float2* __restrict__ scratch, const int* __restrict__ tile_off, Geom g,
                                  double* __restrict__ grid) {
-    const int m = g.m, T = g.T, nt = g.nt, E = g.T + g.P - 1;
+    const int my = g.m[1], mz = g.m[2], T = g.T, E = g.T + g.P - 1;
+    const int ntx = g.nt[0], nty = g.nt[1], ntz = g.nt[2];
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= m * m * m) return;
-    const int lz = id % m, ly = (id / m) % m, lx = id / (m * m);
+    if (id >= g.m[0] * my * mz) return;
+    const int lz = id % mz, ly = (id / mz) % my, lx = id / (mz * my);
     const int tlx = lx / T, tly = ly / T, tlz = lz / T;
     const int olx = lx - tlx * T, oly = ly - tly * T, olz = lz - tlz * T;
     const size_t slab = static_cast<size_t>(E) * E * E;
@@ -158,16 +159,16 @@ static __global__ void k_halo_ff(const float2* __restrict__ scratch, const int* 
         for (int ey = oly; ey < E; ey += T) {
             int tz = tlz;
             for (int ez = olz; ez < E; ez += T) {
-                const int tile = (tx * nt + ty) * nt + tz;
+                const int tile = (tx * nty + ty) * ntz + tz;
                 if (tile_off[tile] != tile_off[tile + 1]) {
                     const float2 v = scratch[static_cast<size_t>(tile) * slab + (ex * E + ey) * E + ez];
                     s = ff_add(s, ff{v.x, v.y});
                 }
-                tz = tz == 0 ? nt - 1 : tz - 1;
+                tz = tz == 0 ? ntz - 1 : tz - 1;
             }
-            ty = ty == 0 ? nt - 1 : ty - 1;
+            ty = ty == 0 ? nty - 1 : ty - 1;
         }
-        tx = tx == 0 ? nt - 1 : tx - 1;
+        tx = tx == 0 ? ntx - 1 : tx - 1;
     }
     grid[id] = ff_to_double(s);
 }
@@ -197,7 +198,7 @@ __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2*
                                                                    const int* __restrict__ tile_off,
                                                                    const float* __restrict__ wc,
                                                                    const float* __restrict__ dwc, int kf, Geom g,
-                                                                   float inv_alpha_h, float inv_alpha_l,
+                                                                   float4 inv_alpha_h, float4 inv_alpha_l,
                                                                    double* __restrict__ phi_out,
                                                                    double* __restrict__ f_out) {
     constexpr int T = kTile64, E = T + P - 1, NB = kInterpFFNB, NWARP = kInterpFFWarps;
@@ -205,9 +206,9 @@ __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2*
     const int tile = blockIdx.x;
     const int beg = tile_off[tile], end = tile_off[tile + 1];
     if (beg == end) return;
-    const int m = g.m, nt = g.nt, degw = g.degw;
+    const int mx = g.m[0], my = g.m[1], mz = g.m[2], degw = g.degw;
     const int nc = P * (degw + 1);
-    const int tz = tile % nt, ty = (tile / nt) % nt, tx = tile / (nt * nt);
+    const int tz = tile % g.nt[2], ty = (tile / g.nt[2]) % g.nt[1], tx = tile / (g.nt[2] * g.nt[1]);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ff* G = reinterpret_cast<ff*>(smem_raw);                          // E^3 (STAGED only)
     ff* sw = G + (STAGED ? E * E * E : 0);                            // NWARP * NB * 6 * P
@@ -223,13 +224,13 @@ __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2*
     if constexpr (STAGED) {
         for (int e = threadIdx.x; e < E * E * E; e += blockDim.x) {
             const int ez = e % E, ey = (e / E) % E, ex = e / (E * E);
-            const int gx = (tx * T + ex) % m, gy = (ty * T + ey) % m, gz = (tz * T + ez) % m;
-            const float2 v = grid[(static_cast<size_t>(gx) * m + gy) * m + gz];
+            const int gx = (tx * T + ex) % mx, gy = (ty * T + ey) % my, gz = (tz * T + ez) % mz;
+            const float2 v = grid[(static_cast<size_t>(gx) * my + gy) * mz + gz];
             G[e] = ff{v.x, v.y};
         }
     }
     __syncthreads();
-    const ff inv_alpha{inv_alpha_h, inv_alpha_l};
+
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ff* ww = sw + warp * NB * 6 * P;
     for (int b0 = beg + warp * NB; b0 < end; b0 += NWARP * NB) {
@@ -241,7 +242,9 @@ __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2*
             const float4 rh = rec_h[b0 + j], rl = rec_l[b0 + j];
             const ff z = d == 0 ? ff{rh.x, rl.x} : (d == 1 ? ff{rh.y, rl.y} : ff{rh.z, rl.z});
             ww[task] = kind < 3 ? window_weight_ff(sch, scl, degw, kf, a, z)
-                                : ff_mul(window_weight_ff(sdh, sdl, degw, kf, a, z), inv_alpha);
+                                : ff_mul(window_weight_ff(sdh, sdl, degw, kf, a, z),
+                                         d == 0 ? ff{inv_alpha_h.x, inv_alpha_l.x}
+                                                : (d == 1 ? ff{inv_alpha_h.y, inv_alpha_l.y} : ff{inv_alpha_h.z, inv_alpha_l.z}));
         }
         __syncwarp();
         ff mph{0.f, 0.f}, mgx{0.f, 0.f}, mgy{0.f, 0.f}, mgz{0.f, 0.f};   // lane j keeps particle j
@@ -253,9 +256,9 @@ __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2*
             if constexpr (!STAGED) {   // wrapped row offsets of the particle's stencil
                 __syncwarp();
                 if (lane < P) {
-                    sxo[warp][lane] = ((tx * T + ox + lane) % m) * m * m;
-                    syo[warp][lane] = ((ty * T + oy + lane) % m) * m;
-                    szo[warp][lane] = (tz * T + oz + lane) % m;
+                    sxo[warp][lane] = ((tx * T + ox + lane) % mx) * my * mz;
+                    syo[warp][lane] = ((ty * T + oy + lane) % my) * mz;
+                    szo[warp][lane] = (tz * T + oz + lane) % mz;
                 }
                 __syncwarp();
 #pragma unroll
@@ -367,26 +370,29 @@ __global__ void __launch_bounds__(32 * kShortWarps, 6) k_short_ff(const float4* 
                                                                   double* __restrict__ f_out) {
     constexpr int NSH = 2 * kShortMaxR + 1, MT = kShortFFMaxT;
     static_assert(NSH <= 16, "queue entries pack 4-bit shift indices");
-    __shared__ float sh_hi[NSH], sh_lo[NSH];
+    __shared__ float sh_hi[3][NSH], sh_lo[3][NSH];   // cell shifts (k - R) w_d, hi and lo parts
     __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
     __shared__ float4 sth[kShortWarps][MT], stl[kShortWarps][MT];
     __shared__ int2 sq[kShortWarps][MT][kShortQCap];   // {source, ix | iy << 4 | iz << 8}
     __shared__ int sqlen[kShortWarps][MT];
-    const int R = g.reach, nc = g.ncell;
-    for (int k = threadIdx.x; k < 2 * R + 1; k += blockDim.x) split_ff((k - R) * g.cellw, sh_hi[k], sh_lo[k]);
+    const int R = g.reach;
+    for (int k = threadIdx.x; k < 3 * (2 * R + 1); k += blockDim.x) {
+        const int d = k / (2 * R + 1), i = k % (2 * R + 1);
+        split_ff((i - R) * g.cellw[d], sh_hi[d][i], sh_lo[d][i]);
+    }
     for (int k = threadIdx.x; k < ncols; k += blockDim.x) scol[k] = cols[k];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c = blockIdx.x * kShortWarps + warp;
-    if (c >= nc * nc * nc) return;
+    if (c >= g.ncell[0] * g.ncell[1] * g.ncell[2]) return;
     const int tb = cell_off[c], te = cell_off[c + 1];
     if (tb == te) return;
-    const int cz = c % nc, cy = (c / nc) % nc, cx = c / (nc * nc);
+    const int cz = c % g.ncell[2], cy = (c / g.ncell[2]) % g.ncell[1], cx = c / (g.ncell[2] * g.ncell[1]);
     extern __shared__ __align__(16) unsigned char short_dyn[];
     int4* rng = reinterpret_cast<int4*>(short_dyn) + warp * rcap;
     int* pos = reinterpret_cast<int*>(reinterpret_cast<int4*>(short_dyn) + kShortWarps * rcap) + warp * (rcap + 1);
     int* qlen = sqlen[warp];
-    const int total = short_ranges(scol, ncols, cell_off, nc, cx, cy, cz, lane, rcap, rng, pos);
+    const int total = short_ranges(scol, ncols, cell_off, g.ncell, cx, cy, cz, lane, rcap, rng, pos);
 
     const ff rc2{kp.rc2h, kp.rc2l}, two_over_rc2{kp.two_over_rc2_h, kp.two_over_rc2_l};
     for (int t0 = tb; t0 < te; t0 += MT) {
@@ -410,10 +416,10 @@ __global__ void __launch_bounds__(32 * kShortWarps, 6) k_short_ff(const float4* 
             const int j = active ? e.x : t0;
             const float4 sh = rec_h[j], sl = rec_l[j];
             const float4 th = sth[warp][t], tl = stl[warp][t];
-            const ff ex = two_sum(sh.x, sh_hi[ix]), ey = two_sum(sh.y, sh_hi[iy]), ez = two_sum(sh.z, sh_hi[iz]);
-            const float lx = __fadd_rn(__fadd_rn(sl.x, sh_lo[ix]), ex.l);
-            const float ly = __fadd_rn(__fadd_rn(sl.y, sh_lo[iy]), ey.l);
-            const float lz = __fadd_rn(__fadd_rn(sl.z, sh_lo[iz]), ez.l);
+            const ff ex = two_sum(sh.x, sh_hi[0][ix]), ey = two_sum(sh.y, sh_hi[1][iy]), ez = two_sum(sh.z, sh_hi[2][iz]);
+            const float lx = __fadd_rn(__fadd_rn(sl.x, sh_lo[0][ix]), ex.l);
+            const float ly = __fadd_rn(__fadd_rn(sl.y, sh_lo[1][iy]), ey.l);
+            const float lz = __fadd_rn(__fadd_rn(sl.z, sh_lo[2][iz]), ez.l);
             ff dx = two_sum(th.x, -ex.h), dy = two_sum(th.y, -ey.h), dz = two_sum(th.z, -ez.h);
             dx = two_sum(dx.h, __fadd_rn(dx.l, __fadd_rn(tl.x, -lx)));
             dy = two_sum(dy.h, __fadd_rn(dy.l, __fadd_rn(tl.y, -ly)));
@@ -467,7 +473,7 @@ __global__ void __launch_bounds__(32 * kShortWarps, 6) k_short_ff(const float4* 
                     const float4 sh = rec_h[j];
                     const int4 col = scol[rg.w];
                     const int ix = col.x + R, iy = col.y + R, iz = rg.z + (cz_of[j] - rg.y) + R;
-                    const float px = sh.x + sh_hi[ix], py = sh.y + sh_hi[iy], pz = sh.z + sh_hi[iz];
+                    const float px = sh.x + sh_hi[0][ix], py = sh.y + sh_hi[1][iy], pz = sh.z + sh_hi[2][iz];
 #pragma unroll
                     for (int t = 0; t < MT; ++t) {
                         if (t >= nt) break;   // warp-uniform

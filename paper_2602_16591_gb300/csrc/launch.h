@@ -17,7 +17,7 @@ struct Launch {
                               const real* wcoef, int degw, real* scratch, cudaStream_t s);
     static cudaError_t interp(int P, int ntiles, const real* grid, const Vec4<real>* rec, const int2* idx,
                               const int* tile_off, const real* wcoef, const real* dwcoef, const Geom& g,
-                              real inv_alpha, double* phi, double* f, cudaStream_t s);
+                              Vec4<real> inv_alpha, double* phi, double* f, cudaStream_t s);
 };
 
 // Float-float path (dispatch_ff.cu): float-float records, spreading, interpolation and real-space sum;
@@ -33,7 +33,7 @@ struct LaunchFF {
     static cudaError_t to_ff(const double* grid, size_t count, float2* out, cudaStream_t s);
     static cudaError_t interp(int ntiles, const Geom& g, const float2* grid, const float4* rec_h, const float4* rec_l,
                               const int2* idx, const int* tile_off, const float* wc, const float* dwc, int kf,
-                              double inv_alpha, double* phi, double* f, cudaStream_t s);
+                              const double* inv_alpha, double* phi, double* f, cudaStream_t s);
     // radial polynomials p1c / qc of degree g.degr (float64 coefficients, split on the host); terms
     // k >= kr are summed in float32
     static cudaError_t short_range(const Geom& g, const float4* rec_h, const float4* rec_l, const int2* idx,

@@ -380,6 +380,22 @@ std::vector<double> fit_radial(const Prolate& ps, double rc_d, int deg, int whic
 
 void scale_tables(const ewald_params& p, const Prolate& ps, const Prolate& pw, std::vector<double>& iw,
                   std::vector<double>& mtab) {
+    if (!(p.box[0] == p.box[1] && p.box[1] == p.box[2] && p.grid[0] == p.grid[1] && p.grid[1] == p.grid[2])) {
+        // cuboid: 1/(phihat_d/h_d)^2 per axis (x, then y, then z entries); M-hat from the gamma polynomial
+        iw.clear();
+        for (int d = 0; d < 3; ++d) {
+            const int m = p.grid[d];
+            const double L = p.box[d], h = L / m, alpha = p.P * h / 2.0;
+            const CosQuadrature qw(pw, kPi * (m / 2) * alpha * 2.0 / L + 1.0);
+            for (int i = 0; i < m; ++i) {
+                const int k = i < m / 2 ? i : i - m;
+                const double ph = alpha * qw(2.0 * kPi * k / L * alpha) / (pw.psi0 * h);
+                iw.push_back(1.0 / (ph * ph));
+            }
+        }
+        mtab.clear();
+        return;
+    }
     const int m = p.m;
     const double L = p.L;
     iw.resize(m);
@@ -401,8 +417,30 @@ void scale_tables(const ewald_params& p, const Prolate& ps, const Prolate& pw, s
     }
 }
 
+// In-band mollifier transform for cuboid boxes: gammahat(omega) = psi(s)/psi(0), s = omega r_c/c_s
+// (Lemma 2 applied to eq. gammahatintegral; every retained mode has s < 1).  Fitted as a polynomial in
+// u = 2 s^2 - 1 (Chebyshev nodes, monomial coefficients); max_err is absolute (the function is <= 1).
+std::vector<double> fit_gamma(const Prolate& ps, int deg, double* max_err) {
+    auto f = [&](double u) {
+        const double sv = std::sqrt(std::max(0.0, (u + 1.0) / 2.0));
+        return ps.psi(sv) / ps.psi0;
+    };
+    auto c = cheb_monomial_fit(f, deg);
+    if (max_err) *max_err = max_fit_error(f, c, deg, 8 * (deg + 1));
+    return c;
+}
+
 HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
-    if (!(L > 0) || !std::isfinite(L)) throw std::invalid_argument("L must be positive and finite");
+    const double box[3] = {L, L, L};
+    return make_plan_box(box, n, tol, o);
+}
+
+HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opts& o) {
+    for (int d = 0; d < 3; ++d)
+        if (!(box[d] > 0) || !std::isfinite(box[d])) throw std::invalid_argument("box edges must be positive and finite");
+    const bool cube = box[0] == box[1] && box[1] == box[2];
+    const double L = std::min(box[0], std::min(box[1], box[2]));   // the cube's edge, or the shortest edge
+    const double V = box[0] * box[1] * box[2];
     if (n < 2) throw std::invalid_argument("n must be at least 2");
     if (!(tol >= 1e-13 && tol <= 1e-2)) throw std::invalid_argument("tol must lie in [1e-13, 1e-2]");
     if (o.precision != EWALD_FP64 && o.precision != EWALD_MIXED && o.precision != EWALD_FLOATFLOAT)
@@ -425,7 +463,10 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
         if (o.rc > 0) {
             rcl = std::min(o.rc / L, 0.5);
         } else {
-            const double mstar = std::cbrt(o.grid_density * static_cast<double>(n));
+            // cube: m* = (g n)^{1/3} points per edge; cuboid (in units of the shortest edge L):
+            // m* = L / h with the common spacing h = (V / (g n))^{1/3}
+            const double mstar = cube ? std::cbrt(o.grid_density * static_cast<double>(n))
+                                      : L / std::cbrt(V / (o.grid_density * static_cast<double>(n)));
             rcl = 0.1;
             for (int it = 0; it < 12; ++it) rcl = std::min(cs_of(rcl) / (kPi * mstar), 0.5);
         }
@@ -446,24 +487,43 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
     // float32 plans tile the grid by 8, the others by 4 (spreading tile edge; m is a multiple of it)
     const int precision = (o.precision == EWALD_MIXED && tol < 1e-7) ? EWALD_FLOATFLOAT : o.precision;
     const int tile = precision == EWALD_MIXED ? 8 : 4;
-    const int m = good_size(static_cast<int>(mraw), tile);
-    if (m > 1024) throw std::length_error("grid beyond 1024^3");
-    rcl = cs / (kPi * m);                                 // eq. csrc holds exactly
+    int mv[3];
+    double hmax = 0;
+    if (cube) {
+        mv[0] = mv[1] = mv[2] = good_size(static_cast<int>(mraw), tile);
+    } else {
+        // cuboid: m_d = ceil(c_s L_d / (pi r_c)) per axis, rounded like the cube's m
+        for (int d = 0; d < 3; ++d) {
+            const double md = std::ceil(cs * (box[d] / L) / (kPi * rcl));
+            if (md > 1024) throw std::length_error("grid beyond 1024 points on an axis");
+            mv[d] = good_size(static_cast<int>(md), tile);
+            hmax = std::max(hmax, box[d] / mv[d]);
+        }
+    }
+    const int m = mv[0];
+    if (mv[0] > 1024 || mv[1] > 1024 || mv[2] > 1024) throw std::length_error("grid beyond 1024^3");
+    // eq. csrc holds exactly (on the coarsest axis of a cuboid: r_c = c_s h_max / pi)
+    rcl = cube ? cs / (kPi * m) : cs * hmax / (kPi * L);
     const double bw = (As / Aw) * std::sqrt(rcl);
     const double cw_t = -0.5 * lambert_w(-1, -2.0 * bw * bw * std::exp(-2.0 * cs) / cs);   // eq. cwW
     const double alpha_over_L = rcl * cw_t / cs;          // eq. alpha
-    int P = static_cast<int>(std::ceil(2.0 * alpha_over_L * m));   // eq. P_dimless
+    // eq. P_dimless (cuboid: P = ceil(2 alpha / h_max), the support in points of the coarsest axis)
+    int P = static_cast<int>(std::ceil(2.0 * alpha_over_L * (cube ? m : L / hmax)));
     P = std::max(P + o.window_extra, 3);
     if (P > 24) throw std::length_error("window support P > 24 (tolerance too tight)");
 
     HostPlan hp;
     ewald_params& p = hp.p;
-    p.L = L;
+    for (int d = 0; d < 3; ++d) {
+        p.box[d] = box[d];
+        p.grid[d] = mv[d];
+    }
+    p.L = box[0];
     p.n = n;
     p.tol = tol;
     p.m = m;
     p.P = P;
-    p.h = L / m;
+    p.h = box[0] / m;
     p.rc = rcl * L;
     p.cs = cs;
     p.cw_target = cw_t;
@@ -482,9 +542,11 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
         reach = std::max(1, std::min(reach, 4));
     }
     p.sr_reach = reach;
-    int nc = static_cast<int>(std::floor(reach / rcl));
-    nc = std::max(1, std::min(nc, 1024));
-    p.ncell = nc;
+    for (int d = 0; d < 3; ++d) {   // cells of edge L_d / ncell_d >= rc / reach on every axis
+        int nc = static_cast<int>(std::floor(reach * (box[d] / L) / rcl));
+        p.cells[d] = std::max(1, std::min(nc, 1024));
+    }
+    p.ncell = p.cells[0];
     p.fit_tol = std::max(0.02 * t, p.precision == EWALD_MIXED ? 1e-8 : 5e-15);
 
     const Prolate ps(p.cs), pw(p.cw);
@@ -525,6 +587,21 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
             }
         }
         if (!ok) throw std::runtime_error("radial polynomial fit did not converge");
+    }
+    // ---- cuboid boxes: mollifier transform polynomial for the scaling step
+    p.deg_g = 0;
+    if (!cube) {
+        bool ok = false;
+        for (int deg = 4; deg <= kDegRMax && !ok; ++deg) {
+            double e = 0;
+            auto gc = fit_gamma(ps, deg, &e);
+            if (e <= p.fit_tol) {
+                ok = true;
+                p.deg_g = deg;
+                hp.gc = gc;
+            }
+        }
+        if (!ok) throw std::runtime_error("mollifier transform fit did not converge");
     }
     scale_tables(p, ps, pw, hp.iw, hp.mtab);
     return hp;

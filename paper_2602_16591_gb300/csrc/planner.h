@@ -42,8 +42,10 @@ struct HostPlan {
     // radial polynomials in u = 2 r^2/rc^2 - 1: R(r) = 1/r - P1(u), -R'(r)/r = 1/r^3 + Q(u)
     std::vector<double> p1c, qc;
     // scaling: S(k) = mtab[|k|^2] * iw[kx] * iw[ky] * iw[kz] for 0 < |k|^2 < (m/2)^2, else 0
-    std::vector<double> iw;         // indexed by grid index 0..m-1
-    std::vector<double> mtab;       // indexed by |k|^2 = 0..(m/2)^2, mtab[0] = 0
+    std::vector<double> iw;         // indexed by grid index 0..m-1 (cuboids: m_x + m_y + m_z entries, by axis)
+    std::vector<double> mtab;       // indexed by |k|^2 = 0..(m/2)^2, mtab[0] = 0 (cubes only)
+    // cuboids: gammahat(omega) = g(2 s^2 - 1), s = |omega| r_c / c_s, monomial coefficients of g
+    std::vector<double> gc;
 };
 
 constexpr int kDegWMax = 40, kDegRMax = 60;
@@ -55,6 +57,8 @@ void scale_tables(const ewald_params& p, const Prolate& ps, const Prolate& pw, s
 
 // Throws std::invalid_argument / std::runtime_error with a message on failure.
 HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& opts);
+HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opts& opts);   // box[3]
+std::vector<double> fit_gamma(const Prolate& ps, int deg, double* max_err);
 ewald_opts default_opts();
 
 // Sets the thread-local message returned by ewald_last_error() (defined in api.cu).

@@ -50,6 +50,9 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
     if (p->P < pswf::kPMin || p->P > pswf::kPMax || p->tile != pswf::kTile64 || p->m % p->tile != 0 ||
         p->deg_w < 1 || p->deg_w > pswf::kDegWMax || !(p->L > 0) || !(p->alpha > 0))
         return fail_static(EWALD_EINVAL, "parameters do not come from ewald_plan_params");
+    if (!(p->box[0] == p->L && p->box[1] == p->L && p->box[2] == p->L && p->grid[0] == p->m && p->grid[1] == p->m &&
+          p->grid[2] == p->m))
+        return fail_static(EWALD_EINVAL, "ewald_spread_static takes cubic boxes only");
 
     // ---- carve the static array: counts, offsets, sort records, tile slabs, window table
     const int64_t n = p->n;
@@ -126,20 +129,21 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
 
     pswf::Geom g{};
     g.n = static_cast<int>(n);
-    g.m = m;
     g.P = P;
     g.T = T;
-    g.nt = nt;
-    g.ncell = 1;
     g.reach = 1;
     g.degw = p->deg_w;
     g.degr = 0;
-    g.L = p->L;
-    g.invL = 1.0 / p->L;
-    g.h = p->L / m;
-    g.invh = m / p->L;
-    g.cellw = p->L;
-    g.invcellw = 1.0 / p->L;
+    for (int d = 0; d < 3; ++d) {
+        g.m[d] = m;
+        g.nt[d] = nt;
+        g.ncell[d] = 1;
+        g.L[d] = p->L;
+        g.invL[d] = 1.0 / p->L;
+        g.invh[d] = m / p->L;
+        g.cellw[d] = p->L;
+        g.invcellw[d] = 1.0 / p->L;
+    }
     g.rc = p->rc;
     g.self = 0.0;
 

@@ -25,6 +25,13 @@ def uniform_alternating(n=1000, L=1.0, seed=0):
     return x, rho, float(L)
 
 
+def uniform_neutral_box(n, box=(1.0, 1.0, 2.0), seed=0):
+    """n uniform points in the cuboid prod_d [0, box_d); rho ~ U[-1, 1] minus its mean."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.random((n, 3)) * np.asarray(box, dtype=np.float64)
+    return x, _neutralise(rng.uniform(-1.0, 1.0, n)), tuple(float(b) for b in box)
+
+
 def uniform_neutral(n=100_000, L=1.0, seed=0, dist="uniform"):
     """n uniform points; rho ~ U[-1, 1] (or N(0,1)) minus its mean."""
     rng = np.random.Generator(np.random.PCG64(seed))

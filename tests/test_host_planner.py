@@ -187,3 +187,26 @@ def test_batch_arguments_rejected_before_any_device_work():
     off = np.array([0, 100, 300], dtype=np.int64)
     assert pe.lib.ewald_eval_batch(None, off.ctypes.data_as(ctypes.c_void_p), None, None, None, None, None,
                                    None) == pe.EWALD_EINVAL
+
+
+# ------------------------------------------------------------------ cuboid boxes (Remark, Sec. 6.1) --
+@pytest.mark.parametrize("box,n,tol,prec,mult", [((1.0, 1.25, 0.75), 5000, 1e-6, "fp64", 4),
+                                                 ((1.0, 1.25, 0.75), 5000, 1e-6, "mixed", 8),
+                                                 ((2.0, 1.0, 1.0), 100_000, 1e-10, "fp64", 4),
+                                                 ((0.9, 1.7, 1.2), 40_000, 1e-8, "floatfloat", 4)])
+def test_cuboid_plan_params_match_oracle(box, n, tol, prec, mult):
+    p = pe.plan_params(box, n, tol, precision=prec)
+    q = oparams.plan_box(box, n, tol, tol_safety=0.25, grid_density=3.0, mult=mult)
+    assert list(p.grid) == q["m"] and p.P == q["P"] and p.deg_g > 0
+    assert list(p.box) == list(box)
+    for k in ("rc", "cs", "cw"):
+        assert abs(getattr(p, k) / q[k] - 1) <= 1e-11, k
+    for d in range(3):   # cells of edge >= rc / reach on every axis
+        assert box[d] / p.cells[d] >= p.rc / p.sr_reach - 1e-15
+
+
+def test_box_api_with_equal_edges_is_the_cube():
+    for prec in ("fp64", "mixed"):
+        a = pe.plan_params(1.3, 20_000, 1e-7, precision=prec).as_dict()
+        b = pe.plan_params((1.3, 1.3, 1.3), 20_000, 1e-7, precision=prec).as_dict()
+        assert a == b and a["deg_g"] == 0
