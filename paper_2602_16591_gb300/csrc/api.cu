@@ -194,6 +194,8 @@ struct ewald_plan_s {
     double* phi_int = nullptr;
     double* f_int = nullptr;
     double* status = nullptr;
+    void* zeroed = nullptr;      // status words, tile and cell counters: one block, cleared by one memset
+    size_t zeroed_bytes = 0;
     double* epart = nullptr;
     double* energy_d = nullptr;
     double* x_stage = nullptr;
@@ -235,8 +237,8 @@ struct ewald_plan_s {
     }
 
     ~ewald_plan_s() {
-        void* bufs[] = {key_rank, tile_cnt, tile_off, cell_cnt, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, sr_lo, sr_f32, sr_cz, grid_ff, sr_cols, scratch,
-                        grid_a, grid_b, spec, wcoef, dwcoef, p1c, qc, iw, mtab, gcoef, phi_int, f_int, status, epart,
+        void* bufs[] = {key_rank, zeroed, tile_off, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, sr_lo, sr_f32, sr_cz, grid_ff, sr_cols, scratch,
+                        grid_a, grid_b, spec, wcoef, dwcoef, p1c, qc, iw, mtab, gcoef, phi_int, f_int, epart,
                         energy_d, x_stage, rho_stage};
         for (void* b : bufs)
             if (b) cudaFree(b);
@@ -340,9 +342,7 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     const pswf::Geom& g = p->g;
     const int n = g.n;
     p->mark(0, false, s);
-    PSWF_CUDA(cudaMemsetAsync(p->tile_cnt, 0, sizeof(int) * p->ntiles, s));
-    PSWF_CUDA(cudaMemsetAsync(p->cell_cnt, 0, sizeof(int) * p->ncells, s));
-    PSWF_CUDA(cudaMemsetAsync(p->status, 0, sizeof(double) * 3, s));
+    PSWF_CUDA(cudaMemsetAsync(p->zeroed, 0, p->zeroed_bytes, s));
     const int tb = 256, nb = (n + tb - 1) / tb;
     pswf::k_prep<<<nb, tb, 0, s>>>(x, rho, g, p->key_rank, p->tile_cnt, p->cell_cnt, p->status);
     PSWF_CUDA(cudaGetLastError());
@@ -439,9 +439,7 @@ int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* ph
     const int n = g.n;
     const size_t nn = static_cast<size_t>(n);
     p->mark(0, false, s);
-    PSWF_CUDA(cudaMemsetAsync(p->tile_cnt, 0, sizeof(int) * p->ntiles, s));
-    PSWF_CUDA(cudaMemsetAsync(p->cell_cnt, 0, sizeof(int) * p->ncells, s));
-    PSWF_CUDA(cudaMemsetAsync(p->status, 0, sizeof(double) * 3, s));
+    PSWF_CUDA(cudaMemsetAsync(p->zeroed, 0, p->zeroed_bytes, s));
     const int tb = 256, nb = (n + tb - 1) / tb;
     pswf::k_prep<<<nb, tb, 0, s>>>(x, rho, g, p->key_rank, p->tile_cnt, p->cell_cnt, p->status);
     PSWF_CUDA(cudaGetLastError());
@@ -708,9 +706,8 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
     const size_t m3 = p->m3, nspec = p->nspec;
     struct A { void** ptr; size_t bytes; } allocs[] = {
         {reinterpret_cast<void**>(&p->key_rank), sizeof(int4) * n},
-        {reinterpret_cast<void**>(&p->tile_cnt), sizeof(int) * (p->ntiles + 1)},
+        {&p->zeroed, sizeof(double) * 4 + sizeof(int) * (((p->ntiles + 1 + 3) / 4) * 4 + p->ncells + 1)},
         {reinterpret_cast<void**>(&p->tile_off), sizeof(int) * (p->ntiles + 1)},
-        {reinterpret_cast<void**>(&p->cell_cnt), sizeof(int) * (p->ncells + 1)},
         {reinterpret_cast<void**>(&p->cell_off), sizeof(int) * (p->ncells + 1)},
         {&p->sp_rec, 4 * rs * n},
         {reinterpret_cast<void**>(&p->sp_idx), sizeof(int2) * n},
@@ -722,7 +719,6 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
         {&p->spec, 2 * rs * nspec},
         {reinterpret_cast<void**>(&p->phi_int), sizeof(double) * n},
         {reinterpret_cast<void**>(&p->f_int), sizeof(double) * 3 * n},
-        {reinterpret_cast<void**>(&p->status), sizeof(double) * 4},
         {reinterpret_cast<void**>(&p->epart), sizeof(double) * p->epart_blocks},
         {reinterpret_cast<void**>(&p->energy_d), sizeof(double)},
         {reinterpret_cast<void**>(&p->x_stage), sizeof(double) * 3 * n},
@@ -737,6 +733,11 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
             return fail(EWALD_ENOMEM, "device allocation failed (" + std::to_string(a.bytes) + " bytes)");
         }
     }
+    // carve the zero-initialised block: status (4 doubles), tile counters, cell counters (16-byte aligned)
+    p->status = static_cast<double*>(p->zeroed);
+    p->tile_cnt = reinterpret_cast<int*>(p->status + 4);
+    p->cell_cnt = p->tile_cnt + ((p->ntiles + 1 + 3) / 4) * 4;
+    p->zeroed_bytes = sizeof(double) * 4 + sizeof(int) * (((p->ntiles + 1 + 3) / 4) * 4 + p->ncells + 1);
     if ((!p->fp64 && cudaMalloc(&p->sr_lo, 4 * sizeof(float) * n) != cudaSuccess) ||
         (p->fp64 && !p->ff && cudaMalloc(reinterpret_cast<void**>(&p->sr_f32), sizeof(float4) * n) != cudaSuccess) ||
         (p->ff && cudaMalloc(reinterpret_cast<void**>(&p->sr_cz), sizeof(int) * n) != cudaSuccess) ||

@@ -138,15 +138,26 @@ static __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cn
     __shared__ int wsum[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int carry = 0;
-    constexpr int ITEMS = 4;
+    constexpr int ITEMS = 16;   // 16K counters per round: the ~3e4 cell counters of a 1e5-particle plan in 2 rounds
     for (int base = 0; base < N; base += blockDim.x * ITEMS) {
         int v[ITEMS], s = 0;
         const int i0 = base + threadIdx.x * ITEMS;
+        if (i0 + ITEMS <= N) {   // whole 64-byte runs: vector loads (the arrays are cudaMalloc-aligned)
+            const int4* c4 = reinterpret_cast<const int4*>(cnt + i0);
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) {
-            v[k] = (i0 + k < N) ? cnt[i0 + k] : 0;
-            s += v[k];
+            for (int q = 0; q < ITEMS / 4; ++q) {
+                const int4 t = c4[q];
+                v[4 * q] = t.x;
+                v[4 * q + 1] = t.y;
+                v[4 * q + 2] = t.z;
+                v[4 * q + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < ITEMS; ++k) v[k] = (i0 + k < N) ? cnt[i0 + k] : 0;
         }
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) s += v[k];
         int x = s;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -166,10 +177,27 @@ static __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cn
         }
         __syncthreads();
         int e = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - s;
+        if (i0 + ITEMS <= N) {
+            int4* o4 = reinterpret_cast<int4*>(off + i0);
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) {
-            if (i0 + k < N) off[i0 + k] = e;
-            e += v[k];
+            for (int q = 0; q < ITEMS / 4; ++q) {
+                int4 t;
+                t.x = e;
+                e += v[4 * q];
+                t.y = e;
+                e += v[4 * q + 1];
+                t.z = e;
+                e += v[4 * q + 2];
+                t.w = e;
+                e += v[4 * q + 3];
+                o4[q] = t;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < ITEMS; ++k) {
+                if (i0 + k < N) off[i0 + k] = e;
+                e += v[k];
+            }
         }
         const int total = wsum[nw - 1];
         __syncthreads();
