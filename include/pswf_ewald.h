@@ -201,8 +201,12 @@ int ewald_eval_batch(ewald_plan plan, const int64_t* offsets, const double* x,
  * 3 forward FFT (step 2), 4 scaling (step 3), 5 inverse FFT (step 4),
  * 6 interpolation (step 5), 7 real-space sum, 8 energy reduction.
  * While enabled, every ewald_eval / ewald_eval_host records CUDA events on its
- * stream at the stage boundaries (no synchronisation).  enable != 0 also
- * clears the accumulated records. */
+ * stream at the stage boundaries (no synchronisation).  enable = 1: the
+ * real-space sum stays concurrent with Alg. 2 (stage times include the
+ * overlap); enable = 2: the two are serialised on the caller's stream, so each
+ * stage time is its kernels' duration alone (same kernels, no overlap).
+ * enable != 0 also clears the accumulated records; enable = 0 stops recording
+ * and restores concurrent execution. */
 #define EWALD_NSTAGES 9
 int ewald_profile(ewald_plan plan, int enable);
 

@@ -255,8 +255,9 @@ class Plan:
 
     STAGES = ("sort", "spread", "halo", "fft_fwd", "scale", "fft_inv", "interp", "short", "energy")
 
-    def profile(self, enable=True):
-        _check(_lib.ewald_profile(self._h, 1 if enable else 0))
+    def profile(self, enable=True, serial=False):
+        """Per-stage CUDA events on (serial: with the real-space sum and Alg. 2 serialised) or off."""
+        _check(_lib.ewald_profile(self._h, (2 if serial else 1) if enable else 0))
 
     def profile_read(self):
         """Summed milliseconds per stage over the evaluations recorded since profile(True)."""

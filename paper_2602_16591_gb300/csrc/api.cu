@@ -223,6 +223,7 @@ struct ewald_plan_s {
     double* bout_h = nullptr;                   // pinned
     const double** bsrc_d = nullptr;            // per system {status, energy} device pointers
     bool profiling = false;
+    bool serial = false;   // profiling mode 2: real-space sum and Alg. 2 serialised on the caller's stream
     std::vector<std::vector<cudaEvent_t>> prof;   // begin/end event of every stage per recorded evaluation
     std::vector<cudaEvent_t>* cur = nullptr;
 
@@ -356,16 +357,19 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     PSWF_CUDA(cudaGetLastError());
     p->mark(0, true, s);
     // real-space sum on the second stream, concurrent with Alg. 2
+    // the real-space sum and Alg. 2 run concurrently on two streams, or one after the other on the
+    // caller's stream when profiling in serial mode (stage times without overlap)
+    const cudaStream_t s_short = p->serial ? s : p->s_short, s_alg2 = p->serial ? s : p->s_alg2;
     PSWF_CUDA(cudaEventRecord(p->ev_fork, s));
-    PSWF_CUDA(cudaStreamWaitEvent(p->s_short, p->ev_fork, 0));
-    p->mark(7, false, p->s_short);
-    PSWF_CUDA(launch_short<real>(p, sr_rec, sr_lo, p->phi_sr, p->f_sr, p->s_short));
-    p->mark(7, true, p->s_short);
-    PSWF_CUDA(cudaEventRecord(p->ev_join, p->s_short));
+    PSWF_CUDA(cudaStreamWaitEvent(s_short, p->ev_fork, 0));
+    p->mark(7, false, s_short);
+    PSWF_CUDA(launch_short<real>(p, sr_rec, sr_lo, p->phi_sr, p->f_sr, s_short));
+    p->mark(7, true, s_short);
+    PSWF_CUDA(cudaEventRecord(p->ev_join, s_short));
     // Alg. 2 on the high-priority stream
     const cudaStream_t caller = s;
-    PSWF_CUDA(cudaStreamWaitEvent(p->s_alg2, p->ev_fork, 0));
-    s = p->s_alg2;
+    PSWF_CUDA(cudaStreamWaitEvent(s_alg2, p->ev_fork, 0));
+    s = s_alg2;
     // Alg. 2 step 1
     p->mark(1, false, s);
     PSWF_CUDA(pswf::Launch<real>::spread(g.P, p->ntiles, sp_rec, p->sp_idx, p->tile_off,
@@ -452,17 +456,20 @@ int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* ph
     PSWF_CUDA(LaunchFF::scatter(x, rho, g, p->key_rank, p->tile_off, p->cell_off, sp_h, sp_l, p->sp_idx, sr_h, sr_l,
                                 p->sr_idx, p->sr_cz, s));
     p->mark(0, true, s);
+    // the real-space sum and Alg. 2 run concurrently on two streams, or one after the other on the
+    // caller's stream when profiling in serial mode (stage times without overlap)
+    const cudaStream_t s_short = p->serial ? s : p->s_short, s_alg2 = p->serial ? s : p->s_alg2;
     PSWF_CUDA(cudaEventRecord(p->ev_fork, s));
-    PSWF_CUDA(cudaStreamWaitEvent(p->s_short, p->ev_fork, 0));
-    p->mark(7, false, p->s_short);
+    PSWF_CUDA(cudaStreamWaitEvent(s_short, p->ev_fork, 0));
+    p->mark(7, false, s_short);
     PSWF_CUDA(LaunchFF::short_range(g, sr_h, sr_l, p->sr_idx, p->sr_cz, p->cell_off, p->sr_cols, p->n_cols,
                                     p->sr_rcap, p->hp.p1c.data(), p->hp.qc.data(), p->ff_kr, p->phi_sr, p->f_sr,
-                                    p->s_short));
-    p->mark(7, true, p->s_short);
-    PSWF_CUDA(cudaEventRecord(p->ev_join, p->s_short));
+                                    s_short));
+    p->mark(7, true, s_short);
+    PSWF_CUDA(cudaEventRecord(p->ev_join, s_short));
     const cudaStream_t caller = s;
-    PSWF_CUDA(cudaStreamWaitEvent(p->s_alg2, p->ev_fork, 0));
-    s = p->s_alg2;
+    PSWF_CUDA(cudaStreamWaitEvent(s_alg2, p->ev_fork, 0));
+    s = s_alg2;
     const auto* wc = static_cast<const float*>(p->wcoef);
     const auto* dwc = static_cast<const float*>(p->dwcoef);
     p->mark(1, false, s);
@@ -1124,7 +1131,9 @@ int ewald_profile(ewald_plan plan, int enable) {
         PSWF_CUDA(cudaDeviceSynchronize());
         plan->clear_prof();
     }
+    if (enable < 0 || enable > 2) return fail(EWALD_EINVAL, "enable must be 0, 1 or 2");
     plan->profiling = enable != 0;
+    plan->serial = enable == 2;
     return EWALD_OK;
 }
 

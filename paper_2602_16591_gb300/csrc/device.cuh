@@ -449,6 +449,11 @@ __global__ void k_scale(cplx* __restrict__ spec, ScaleParams<real> sp) {
 // (value and x-derivative per axis) of the batch, one (particle, axis, kind) Horner vector per lane,
 // then contract each particle's P^3 stencil cooperatively: lanes take (b, c) pairs, reduce over a in
 // registers (two independent chains), and the warp sums the four results with shuffles.
+// The block is stored y-major ([y][x][z]) with the y-plane stride padded to SP = P (mod 32): lane
+// q = b P + c of a particle then reads word q (mod 32) of its x-row, so the 32 lanes hit 32 different
+// banks (a z-row-major block of width E = T + P - 1 put two y-rows on the same banks).
+template <int P, int E>
+constexpr int interp_plane() { return E * E + (((P - E * E) % 32) + 32) % 32; }
 template <typename real> struct InterpCfg;
 template <> struct InterpCfg<float> { static constexpr int NB = 8, NWARP = 4; };
 template <> struct InterpCfg<double> { static constexpr int NB = 8, NWARP = 4; };
@@ -472,8 +477,9 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
     using V = typename std::conditional<sizeof(real) == 4, float4, double2>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real* sw = reinterpret_cast<real*>(smem_raw);                 // NWARP * NB * 6 * PP
-    real* G = sw + NWARP * NB * 6 * PP;                           // E^3
-    real* sc = G + E * E * E;                                     // P * (degw + 1)
+    constexpr int SP = interp_plane<P, E>();
+    real* G = sw + NWARP * NB * 6 * PP;                           // E planes of SP (y-major)
+    real* sc = G + E * SP;                                        // P * (degw + 1)
     real* sd = sc + P * (degw + 1);                               // P * (degw + 1)
     for (int i = threadIdx.x; i < P * (degw + 1); i += blockDim.x) {
         sc[i] = wcoef[i];
@@ -490,7 +496,7 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
             gy %= my;
             gz %= mz;
         }
-        G[e] = grid[(static_cast<size_t>(gx) * my + gy) * mz + gz];
+        G[ey * SP + ex * E + ez] = grid[(static_cast<size_t>(gx) * my + gy) * mz + gz];
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -542,15 +548,15 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
                 const int q = lane + 32 * qi;
                 if (q < P * P) {
                     const int bb = q / P, cc = q - (q / P) * P;
-                    const real* col = G + (ox * E + oy + bb) * E + oz + cc;
+                    const real* col = G + (oy + bb) * SP + ox * E + oz + cc;
                     real s1a = 0, s1b = 0, s2a = 0, s2b = 0;
 #pragma unroll
                     for (int a = 0; a < P; a += 2) {
-                        const real v = col[a * E * E];
+                        const real v = col[a * E];
                         s1a = fma(v, wx[a], s1a);
                         s2a = fma(v, dwx[a], s2a);
                         if (a + 1 < P) {
-                            const real v2 = col[(a + 1) * E * E];
+                            const real v2 = col[(a + 1) * E];
                             s1b = fma(v2, wx[a + 1], s1b);
                             s2b = fma(v2, dwx[a + 1], s2b);
                         }
