@@ -191,7 +191,7 @@ constexpr int kInterpFFNB = 4, kInterpFFWarps = 8;
 // through L1/L2 (it is L2-resident at these sizes) with per-particle wrapped index tables, so the block
 // needs little shared memory and occupancy is set by registers.
 template <int P, bool STAGED>
-__global__ void __launch_bounds__(32 * kInterpFFWarps, STAGED ? 1 : 3) k_interp_ff(const float2* __restrict__ grid,
+__global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2* __restrict__ grid,
                                                                    const float4* __restrict__ rec_h,
                                                                    const float4* __restrict__ rec_l,
                                                                    const int2* __restrict__ idx,
