@@ -18,8 +18,9 @@ Steps of Alg. 3 with the readings the library uses (all recorded in the design doc):
   above this equals ceil(2 c_w/pi).  The window is instantiated with
   c_w := pi P/2 and alpha := P h/2 (eq. cwP), so c_s/rc = c_w/alpha (eq. bandwidth).
 * Forces (no model in the paper): measured relative force errors are ~m/10 times the
-  potential errors, so the potential target tol*tol_safety is multiplied by
-  min(1, 10/m0), m0 = c_s/(pi rc/L) before rounding, and rc re-derived.
+  potential errors and follow the split truncation (c_s), not the window, so the split
+  target tol*tol_safety is multiplied by min(1, 10/m0), m0 = c_s/(pi rc/L) before rounding,
+  and rc re-derived; c_w (the window) is balanced against the untightened target.
 
 Parity status: pinned in tests/test_oracle_params.py (Lambert-W identities,
 balance equation eq. cwcs_model_dimless, kappa against a direct lattice sum).
@@ -90,6 +91,7 @@ def plan(L, n, tol, grid_density=1.0, rc=None, tol_safety=1.0, mult=4):
             return r
         return min(rc / L, 0.5)
 
+    t_pot = t
     rcl = cutoff(t)
     m0 = cs_of(rcl, t) / (math.pi * rcl)
     if m0 > 10.0:
@@ -98,7 +100,7 @@ def plan(L, n, tol, grid_density=1.0, rc=None, tol_safety=1.0, mult=4):
     cs = cs_of(rcl, t)
     m = good_size(math.ceil(cs / (math.pi * rcl)), mult)
     rcl = cs / (math.pi * m)
-    cw = cw_of(cs, rcl)
+    cw = cw_of(cs_of(rcl, t_pot), rcl)      # window balanced against the potential target
     alpha_over_L = rcl * cw / cs
     P = int(math.ceil(2.0 * alpha_over_L * m))
     h = L / m
@@ -134,6 +136,7 @@ def plan_box(Ls, n, tol, grid_density=1.0, rc=None, tol_safety=1.0, mult=4):
             return r
         return min(rc / Lmin, 0.5)
 
+    t_pot = t
     rcl = cutoff(t)
     m0 = cs_of(rcl, t) / (math.pi * rcl)
     if m0 > 10.0:
@@ -144,7 +147,7 @@ def plan_box(Ls, n, tol, grid_density=1.0, rc=None, tol_safety=1.0, mult=4):
     hs = [float(L) / m for L, m in zip(Lv, ms)]
     hmax = max(hs)
     rcl = cs * hmax / (math.pi * Lmin)
-    cw = cw_of(cs, rcl)
+    cw = cw_of(cs_of(rcl, t_pot), rcl)      # window balanced against the potential target
     P = int(math.ceil(2.0 * (rcl * cw / cs) * Lmin / hmax))
     return dict(L=[float(L) for L in Lv], rc=rcl * Lmin, cs=cs, cw_target=cw, cw=math.pi * P / 2.0, m=ms, P=P,
                 h=hs, alpha=[P * h / 2.0 for h in hs])

@@ -453,11 +453,13 @@ HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opt
 
     const double As = 5.0, Aw = 3.1;                      // Secs. 5.1.1 and 5.2.1
     static const double kappa = kappa_constant();
-    double t = tol * o.tol_safety;
-    auto cs_of = [&](double rcl) {
-        const double bs_eps = As * std::sqrt(rcl) / (std::sqrt(kappa) * t);
+    const double t_pot = tol * o.tol_safety;   // potential target (window / aliasing side)
+    double t = t_pot;                            // split target (tightened for forces below)
+    auto cs_at = [&](double rcl, double tt) {
+        const double bs_eps = As * std::sqrt(rcl) / (std::sqrt(kappa) * tt);
         return 0.5 * lambert_w(0, 2.0 * bs_eps * bs_eps);   // eq. cs_dimless
     };
+    auto cs_of = [&](double rcl) { return cs_at(rcl, t); };
     auto cutoff = [&]() {
         double rcl;
         if (o.rc > 0) {
@@ -505,7 +507,10 @@ HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opt
     // eq. csrc holds exactly (on the coarsest axis of a cuboid: r_c = c_s h_max / pi)
     rcl = cube ? cs / (kPi * m) : cs * hmax / (kPi * L);
     const double bw = (As / Aw) * std::sqrt(rcl);
-    const double cw_t = -0.5 * lambert_w(-1, -2.0 * bw * bw * std::exp(-2.0 * cs) / cs);   // eq. cwW
+    // eq. cwW balances the aliasing error against the potential target: the force factor above
+    // tightens the split only (forces follow the split truncation, not the window; see the sizing notes)
+    const double cs_w = cs_at(rcl, t_pot);
+    const double cw_t = -0.5 * lambert_w(-1, -2.0 * bw * bw * std::exp(-2.0 * cs_w) / cs_w);
     const double alpha_over_L = rcl * cw_t / cs;          // eq. alpha
     // eq. P_dimless (cuboid: P = ceil(2 alpha / h_max), the support in points of the coarsest axis)
     int P = static_cast<int>(std::ceil(2.0 * alpha_over_L * (cube ? m : L / hmax)));
