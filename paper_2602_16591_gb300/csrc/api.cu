@@ -328,6 +328,8 @@ cudaError_t launch_short(ewald_plan p, const pswf::Vec4<real>* sr_rec, const psw
                          double* f, cudaStream_t s) {
     const int d = p->g.degr;
     if (d <= 8) return launch_short_d<real, 8>(p, sr_rec, sr_lo, phi, f, s);
+    if (d <= 10) return launch_short_d<real, 10>(p, sr_rec, sr_lo, phi, f, s);
+    if (d == 11) return launch_short_d<real, 11>(p, sr_rec, sr_lo, phi, f, s);   // tol ~1e-6
     if (d <= 12) return launch_short_d<real, 12>(p, sr_rec, sr_lo, phi, f, s);
     if (d <= 16) return launch_short_d<real, 16>(p, sr_rec, sr_lo, phi, f, s);
     if (d <= 20) return launch_short_d<real, 20>(p, sr_rec, sr_lo, phi, f, s);
@@ -345,7 +347,7 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     p->mark(0, false, s);
     PSWF_CUDA(cudaMemsetAsync(p->zeroed, 0, p->zeroed_bytes, s));
     const int tb = 256, nb = (n + tb - 1) / tb;
-    pswf::k_prep<<<nb, tb, 0, s>>>(x, rho, g, p->key_rank, p->tile_cnt, p->cell_cnt, p->status);
+    pswf::k_prep<std::is_same<real, float>::value><<<nb, tb, 0, s>>>(x, rho, g, p->key_rank, p->tile_cnt, p->cell_cnt, p->status);
     PSWF_CUDA(cudaGetLastError());
     pswf::k_scan<<<2, 1024, 0, s>>>(p->tile_cnt, p->tile_off, p->ntiles, p->cell_cnt, p->cell_off, p->ncells);
     PSWF_CUDA(cudaGetLastError());
@@ -377,8 +379,16 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     p->mark(1, true, s);
     p->mark(2, false, s);
     const int mm = static_cast<int>(p->m3);
-    pswf::k_halo<real><<<(mm + 255) / 256, 256, 0, s>>>(static_cast<const real*>(p->scratch), p->tile_off, g,
-                                                        static_cast<real*>(p->grid_a));
+    {
+        const int ni = (g.T + g.P - 1 + g.T - 1) / g.T;   // overlapping slabs per axis
+        const auto* sc = static_cast<const real*>(p->scratch);
+        auto* ga = static_cast<real*>(p->grid_a);
+        const int hb = (mm + 255) / 256;
+        if (ni <= 2) pswf::k_halo<real, 2><<<hb, 256, 0, s>>>(sc, p->tile_off, g, ga);
+        else if (ni == 3) pswf::k_halo<real, 3><<<hb, 256, 0, s>>>(sc, p->tile_off, g, ga);
+        else if (ni == 4) pswf::k_halo<real, 4><<<hb, 256, 0, s>>>(sc, p->tile_off, g, ga);
+        else pswf::k_halo<real, 0><<<hb, 256, 0, s>>>(sc, p->tile_off, g, ga);
+    }
     PSWF_CUDA(cudaGetLastError());
     // Alg. 2 steps 2-4
     p->mark(2, true, s);
@@ -428,8 +438,8 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     PSWF_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
     PSWF_CUDA(cudaStreamWaitEvent(s, p->ev_join2, 0));
     p->mark(8, false, s);
-    pswf::k_combine_energy<<<p->epart_blocks, 256, 0, s>>>(phi, f, p->phi_sr, p->f_sr, rho, n, p->epart);
-    pswf::k_energy_final<<<1, 256, 0, s>>>(p->epart, p->epart_blocks, p->energy_d);
+    pswf::k_combine_energy<<<p->epart_blocks, 256, 0, s>>>(phi, f, p->phi_sr, p->f_sr, rho, n, p->epart,
+                                                           reinterpret_cast<unsigned*>(p->status + 3), p->energy_d);
     PSWF_CUDA(cudaGetLastError());
     p->mark(8, true, s);
     return EWALD_OK;
@@ -445,7 +455,7 @@ int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* ph
     p->mark(0, false, s);
     PSWF_CUDA(cudaMemsetAsync(p->zeroed, 0, p->zeroed_bytes, s));
     const int tb = 256, nb = (n + tb - 1) / tb;
-    pswf::k_prep<<<nb, tb, 0, s>>>(x, rho, g, p->key_rank, p->tile_cnt, p->cell_cnt, p->status);
+    pswf::k_prep<false><<<nb, tb, 0, s>>>(x, rho, g, p->key_rank, p->tile_cnt, p->cell_cnt, p->status);
     PSWF_CUDA(cudaGetLastError());
     pswf::k_scan<<<2, 1024, 0, s>>>(p->tile_cnt, p->tile_off, p->ntiles, p->cell_cnt, p->cell_off, p->ncells);
     PSWF_CUDA(cudaGetLastError());
@@ -510,8 +520,8 @@ int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* ph
     PSWF_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
     PSWF_CUDA(cudaStreamWaitEvent(s, p->ev_join2, 0));
     p->mark(8, false, s);
-    pswf::k_combine_energy<<<p->epart_blocks, 256, 0, s>>>(phi, f, p->phi_sr, p->f_sr, rho, n, p->epart);
-    pswf::k_energy_final<<<1, 256, 0, s>>>(p->epart, p->epart_blocks, p->energy_d);
+    pswf::k_combine_energy<<<p->epart_blocks, 256, 0, s>>>(phi, f, p->phi_sr, p->f_sr, rho, n, p->epart,
+                                                           reinterpret_cast<unsigned*>(p->status + 3), p->energy_d);
     PSWF_CUDA(cudaGetLastError());
     p->mark(8, true, s);
     return EWALD_OK;
@@ -698,6 +708,15 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
         g.invh[d] = q.grid[d] / q.box[d];
         g.cellw[d] = q.box[d] / q.cells[d];
         g.invcellw[d] = q.cells[d] / q.box[d];
+        auto split = [](double v, float (&o)[2]) {
+            o[0] = static_cast<float>(v);
+            o[1] = static_cast<float>(v - static_cast<double>(o[0]));
+        };
+        split(g.L[d], g.Lf[d]);
+        split(g.invL[d], g.invLf[d]);
+        split(g.invh[d], g.invhf[d]);
+        split(g.cellw[d], g.cellwf[d]);
+        split(g.invcellw[d], g.invcellwf[d]);
     }
     g.rc = q.rc;
     g.self = q.self_coeff;
@@ -740,7 +759,8 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
             return fail(EWALD_ENOMEM, "device allocation failed (" + std::to_string(a.bytes) + " bytes)");
         }
     }
-    // carve the zero-initialised block: status (4 doubles), tile counters, cell counters (16-byte aligned)
+    // carve the zero-initialised block: status (4 doubles: sum rho, sum |rho|, non-finite count, ticket
+    // counter of k_combine_energy), tile counters, cell counters (16-byte aligned)
     p->status = static_cast<double*>(p->zeroed);
     p->tile_cnt = reinterpret_cast<int*>(p->status + 4);
     p->cell_cnt = p->tile_cnt + ((p->ntiles + 1 + 3) / 4) * 4;

@@ -20,6 +20,8 @@
 
 #include <type_traits>
 
+#include "ff.cuh"
+
 namespace pswf {
 
 template <typename real> struct alignas(4 * sizeof(real)) Vec4 { real x, y, z, w; };
@@ -31,6 +33,8 @@ struct Geom {
     int m[3], nt[3], ncell[3];
     double L[3], invL[3], invh[3], cellw[3], invcellw[3];
     double rc, self;
+    // float-float (hi, lo) copies of L, 1/L, 1/h, cell width and its inverse for locate_ff
+    float Lf[3][2], invLf[3][2], invhf[3][2], cellwf[3][2], invcellwf[3][2];
 };
 
 // Spreading / interpolation tile edge (grid points); m is a multiple of it.  float32 plans use 8 (the
@@ -75,61 +79,140 @@ __device__ inline Located locate(const double* xp, const Geom& g) {
     return r;
 }
 
-__device__ inline int tile_of(const Located& r, const Geom& g) {
+// locate() in float-float arithmetic for the float32 plans, whose records are float32 (z) and
+// float-float (local coordinates): each coordinate is split once into hi + lo floats (~48 bits), then
+// wrapping, stencil start, window coordinate and cell use float32 operations only.  GB300 issues
+// float64 at ~1/64 of the float32 rate, and the float64 locate() made the sort kernels FP64-bound.
+// Positions more than 2^22 box lengths from the origin take the float64 route.
+struct LocatedF {
+    float z[3];      // window coordinate
+    int lw[3];       // stencil start l0 mod m
+    int cell[3];     // real-space cell
+    ff loc[3];       // position relative to the cell origin (normalised hi + lo)
+    bool finite;
+};
+
+__device__ __forceinline__ ff ff_c(const float (&v)[2]) { return ff{v[0], v[1]}; }
+
+// floor / ceil of a normalised float-float value (|l| <= ulp(h)/2: only an integral h can be moved)
+__device__ __forceinline__ float ff_floor(ff a) {
+    const float f = floorf(a.h);
+    return f == a.h ? f - (a.l < 0.f ? 1.f : 0.f) : f;
+}
+__device__ __forceinline__ float ff_ceil(ff a) {
+    const float c = ceilf(a.h);
+    return c == a.h ? c + (a.l > 0.f ? 1.f : 0.f) : c;
+}
+
+__device__ inline LocatedF locate_ff(const double* xp, const Geom& g) {
+    LocatedF r;
+    r.finite = true;
+    for (int d = 0; d < 3; ++d) {
+        double x = xp[d];
+        if ((__double2hiint(x) & 0x7ff00000) == 0x7ff00000) { r.finite = false; x = 0.0; }
+        const ff L = ff_c(g.Lf[d]);
+        ff w = ff_from_double(x);
+        const bool inside = (w.h > 0.f || (w.h == 0.f && w.l >= 0.f)) && (w.h < L.h || (w.h == L.h && w.l < L.l));
+        if (!inside) {
+            const ff u = ff_mul(w, ff_c(g.invLf[d]));
+            if (fabsf(u.h) < 4194304.f) {
+                w = ff_sub(w, ff_mul_f(L, ff_floor(u)));
+            } else {   // far outside the box: float64 reduction
+                const double wd = x - g.L[d] * floor(x * g.invL[d]);
+                w = ff_from_double(wd);
+            }
+            if (w.h < 0.f || (w.h == 0.f && w.l < 0.f)) w = ff_add(w, L);
+            if (w.h > L.h || (w.h == L.h && w.l >= L.l)) w = ff_sub(w, L);
+            if (w.h < 0.f || (w.h == 0.f && w.l < 0.f)) w = ff{0.f, 0.f};
+        }
+        const ff t = ff_mul(w, ff_c(g.invhf[d]));
+        const float l0 = ff_ceil(ff_add(t, ff_make(-0.5f * g.P)));
+        const ff dt = ff_sub(t, ff_make(l0));                    // in (P/2 - 1, P/2]
+        r.z[d] = __fadd_rn(__fmaf_rn(2.f, dt.h, static_cast<float>(1 - g.P)), __fmul_rn(2.f, dt.l));
+        int lw = static_cast<int>(l0) % g.m[d];
+        if (lw < 0) lw += g.m[d];
+        r.lw[d] = lw;
+        int c = static_cast<int>(ff_floor(ff_mul(w, ff_c(g.invcellwf[d]))));
+        c = c < 0 ? 0 : (c >= g.ncell[d] ? g.ncell[d] - 1 : c);
+        r.cell[d] = c;
+        r.loc[d] = ff_sub(w, ff_mul_f(ff_c(g.cellwf[d]), static_cast<float>(c)));
+    }
+    return r;
+}
+
+template <typename Loc>
+__device__ inline int tile_of(const Loc& r, const Geom& g) {
     return ((r.lw[0] / g.T) * g.nt[1] + r.lw[1] / g.T) * g.nt[2] + r.lw[2] / g.T;
 }
-__device__ inline int cell_of(const Located& r, const Geom& g) {
+template <typename Loc>
+__device__ inline int cell_of(const Loc& r, const Geom& g) {
     return (r.cell[0] * g.ncell[1] + r.cell[1]) * g.ncell[2] + r.cell[2];
 }
 
-// status[0] = sum rho, status[1] = sum |rho|, status[2] = number of non-finite inputs
-static __global__ void k_prep(const double* __restrict__ x, const double* __restrict__ rho, Geom g,
-                       int* __restrict__ key_rank, int* __restrict__ tile_cnt, int* __restrict__ cell_cnt,
-                       double* __restrict__ status) {
+// status[0] = sum rho, status[1] = sum |rho|, status[2] = number of non-finite inputs.
+// FFLOC: locate in float-float (float32 plans) instead of float64; k_scatter of the same plan must use
+// the same routine (the keys and ranks written here place its records).
+template <bool FFLOC>
+__global__ void __launch_bounds__(256) k_prep(const double* __restrict__ x, const double* __restrict__ rho, Geom g,
+                                              int* __restrict__ key_rank, int* __restrict__ tile_cnt,
+                                              int* __restrict__ cell_cnt, double* __restrict__ status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double q = 0.0, aq = 0.0, bad = 0.0;
+    double q = 0.0;
+    int bad = 0;
     if (i < g.n) {
-        const Located r = locate(x + 3 * static_cast<size_t>(i), g);
-        double rq = rho[i];
-        if (!isfinite(rq) || !r.finite) bad = 1.0;
-        if (!isfinite(rq)) rq = 0.0;
-        q = rq;
-        aq = fabs(rq);
-        const int t = tile_of(r, g), c = cell_of(r, g);
+        q = rho[i];
+        if ((__double2hiint(q) & 0x7ff00000) == 0x7ff00000) { bad = 1; q = 0.0; }
+        int t, c;
+        if constexpr (FFLOC) {
+            const LocatedF r = locate_ff(x + 3 * static_cast<size_t>(i), g);
+            if (!r.finite) bad = 1;
+            t = tile_of(r, g);
+            c = cell_of(r, g);
+        } else {
+            const Located r = locate(x + 3 * static_cast<size_t>(i), g);
+            if (!r.finite) bad = 1;
+            t = tile_of(r, g);
+            c = cell_of(r, g);
+        }
         const int rt = atomicAdd(tile_cnt + t, 1);
         const int rc = atomicAdd(cell_cnt + c, 1);
-        int4 kr = make_int4(t, rt, c, rc);
-        reinterpret_cast<int4*>(key_rank)[i] = kr;
+        reinterpret_cast<int4*>(key_rank)[i] = make_int4(t, rt, c, rc);
     }
-    // block reduction of the neutrality / finiteness diagnostics
-    for (int o = 16; o > 0; o >>= 1) {
-        q += __shfl_xor_sync(0xffffffffu, q, o);
-        aq += __shfl_xor_sync(0xffffffffu, aq, o);
-        bad += __shfl_xor_sync(0xffffffffu, bad, o);
-    }
-    __shared__ double red[3][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) { red[0][warp] = q; red[1][warp] = aq; red[2][warp] = bad; }
+    // block sums of the neutrality diagnostics: staged in shared memory and added by one warp, so the
+    // float64 additions run once per 8 values instead of in every lane's shuffle tree
+    __shared__ double red[256];
+    __shared__ int nbad;
+    if (threadIdx.x == 0) nbad = 0;
+    red[threadIdx.x] = q;
     __syncthreads();
-    if (warp == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        q = lane < nw ? red[0][lane] : 0.0;
-        aq = lane < nw ? red[1][lane] : 0.0;
-        bad = lane < nw ? red[2][lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) {
-            q += __shfl_xor_sync(0xffffffffu, q, o);
-            aq += __shfl_xor_sync(0xffffffffu, aq, o);
-            bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    if (bad) atomicAdd(&nbad, 1);
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        double sq = 0.0, sa = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const double v = red[lane + 32 * k];
+            sq += v;
+            sa += fabs(v);
         }
+        for (int o = 16; o > 0; o >>= 1) {
+            sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        }
+        __syncwarp();
         if (lane == 0) {
-            atomicAdd(status + 0, q);
-            atomicAdd(status + 1, aq);
-            if (bad > 0) atomicAdd(status + 2, bad);
+            atomicAdd(status + 0, sq);
+            atomicAdd(status + 1, sa);
         }
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && nbad > 0) atomicAdd(status + 2, static_cast<double>(nbad));
 }
 
-// Exclusive scan of cnt[0..N) into off[0..N]; one block per segment (blockIdx.x = 0 / 1).
+// Exclusive scan of cnt[0..N) into off[0..N]; one block per segment (blockIdx.x = 0 / 1).  Thread t owns
+// the contiguous run [t K, (t + 1) K) with K a multiple of 4 (16-byte vector loads and stores): a first
+// pass sums the run, one block-wide scan of the run sums gives its offset, a second pass (L1/L2 hits)
+// writes the offsets.  Two memory round trips whatever N, instead of one per 16K counters.
 static __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cnt0, int* __restrict__ off0, int n0,
                                                const int* __restrict__ cnt1, int* __restrict__ off1, int n1) {
     const int* cnt = blockIdx.x == 0 ? cnt0 : cnt1;
@@ -137,117 +220,105 @@ static __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cn
     const int N = blockIdx.x == 0 ? n0 : n1;
     __shared__ int wsum[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int carry = 0;
-    constexpr int ITEMS = 16;   // 16K counters per round: the ~3e4 cell counters of a 1e5-particle plan in 2 rounds
-    for (int base = 0; base < N; base += blockDim.x * ITEMS) {
-        int v[ITEMS], s = 0;
-        const int i0 = base + threadIdx.x * ITEMS;
-        if (i0 + ITEMS <= N) {   // whole 64-byte runs: vector loads (the arrays are cudaMalloc-aligned)
-            const int4* c4 = reinterpret_cast<const int4*>(cnt + i0);
-#pragma unroll
-            for (int q = 0; q < ITEMS / 4; ++q) {
-                const int4 t = c4[q];
-                v[4 * q] = t.x;
-                v[4 * q + 1] = t.y;
-                v[4 * q + 2] = t.z;
-                v[4 * q + 3] = t.w;
-            }
+    const int K = ((N + blockDim.x - 1) / blockDim.x + 3) & ~3;
+    const int i0 = threadIdx.x * K, i1 = min(i0 + K, N);
+    int s = 0;
+#pragma unroll 4
+    for (int i = i0; i < i1; i += 4) {
+        if (i + 4 <= i1) {   // the arrays are cudaMalloc-aligned (or 16-byte aligned carves) and i % 4 == 0
+            const int4 t = *reinterpret_cast<const int4*>(cnt + i);
+            s += (t.x + t.y) + (t.z + t.w);
         } else {
-#pragma unroll
-            for (int k = 0; k < ITEMS; ++k) v[k] = (i0 + k < N) ? cnt[i0 + k] : 0;
+            for (int k = i; k < i1; ++k) s += cnt[k];
         }
+    }
+    int x = s;
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) s += v[k];
-        int x = s;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < nw ? wsum[lane] : 0;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
         }
-        if (lane == 31) wsum[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            int w = lane < nw ? wsum[lane] : 0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            wsum[lane] = w;
-        }
-        __syncthreads();
-        int e = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - s;
-        if (i0 + ITEMS <= N) {
-            int4* o4 = reinterpret_cast<int4*>(off + i0);
-#pragma unroll
-            for (int q = 0; q < ITEMS / 4; ++q) {
-                int4 t;
-                t.x = e;
-                e += v[4 * q];
-                t.y = e;
-                e += v[4 * q + 1];
-                t.z = e;
-                e += v[4 * q + 2];
-                t.w = e;
-                e += v[4 * q + 3];
-                o4[q] = t;
-            }
-        } else {
-#pragma unroll
-            for (int k = 0; k < ITEMS; ++k) {
-                if (i0 + k < N) off[i0 + k] = e;
-                e += v[k];
-            }
-        }
-        const int total = wsum[nw - 1];
-        __syncthreads();
-        carry += total;
+        wsum[lane] = w;
     }
-    if (threadIdx.x == 0) off[N] = carry;
+    __syncthreads();
+    int e = (warp > 0 ? wsum[warp - 1] : 0) + x - s;
+#pragma unroll 4
+    for (int i = i0; i < i1; i += 4) {
+        if (i + 4 <= i1) {
+            const int4 t = *reinterpret_cast<const int4*>(cnt + i);
+            int4 o;
+            o.x = e;
+            o.y = e + t.x;
+            o.z = o.y + t.y;
+            o.w = o.z + t.z;
+            e = o.w + t.w;
+            *reinterpret_cast<int4*>(off + i) = o;
+        } else {
+            for (int k = i; k < i1; ++k) {
+                off[k] = e;
+                e += cnt[k];
+            }
+        }
+    }
+    if (threadIdx.x == 0) off[N] = wsum[nw - 1];
 }
 
 // Sorted records.  Spreading side (tile order): {z0, z1, z2, rho}, {packed offsets in tile, original index}.
 // Real-space side (cell order): {local x, y, z, rho}, {cell id, original index}.
 template <typename real>
-__global__ void k_scatter(const double* __restrict__ x, const double* __restrict__ rho, Geom g,
-                          const int* __restrict__ key_rank, const int* __restrict__ tile_off,
-                          const int* __restrict__ cell_off, Vec4<real>* __restrict__ sp_rec,
-                          int2* __restrict__ sp_idx, Vec4<real>* __restrict__ sr_rec, int2* __restrict__ sr_idx,
-                          Vec4<real>* __restrict__ sr_lo, float4* __restrict__ sr_f32) {
+__global__ void __launch_bounds__(256) k_scatter(const double* __restrict__ x, const double* __restrict__ rho, Geom g,
+                                                 const int* __restrict__ key_rank, const int* __restrict__ tile_off,
+                                                 const int* __restrict__ cell_off, Vec4<real>* __restrict__ sp_rec,
+                                                 int2* __restrict__ sp_idx, Vec4<real>* __restrict__ sr_rec,
+                                                 int2* __restrict__ sr_idx, Vec4<real>* __restrict__ sr_lo,
+                                                 float4* __restrict__ sr_f32) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
-    const Located r = locate(x + 3 * static_cast<size_t>(i), g);
     double q = rho[i];
-    if (!isfinite(q)) q = 0.0;
+    if ((__double2hiint(q) & 0x7ff00000) == 0x7ff00000) q = 0.0;
     const int4 kr = reinterpret_cast<const int4*>(key_rank)[i];
     const int ps = tile_off[kr.x] + kr.y;
     const int pc = cell_off[kr.z] + kr.w;
-    Vec4<real> a;
-    a.x = static_cast<real>(r.z[0]);
-    a.y = static_cast<real>(r.z[1]);
-    a.z = static_cast<real>(r.z[2]);
-    a.w = static_cast<real>(q);
-    sp_rec[ps] = a;
-    const int pack = (r.lw[0] % g.T) | ((r.lw[1] % g.T) << 8) | ((r.lw[2] % g.T) << 16);
-    sp_idx[ps] = make_int2(pack, i);
-    Vec4<real> b;
-    b.x = static_cast<real>(r.loc[0]);
-    b.y = static_cast<real>(r.loc[1]);
-    b.z = static_cast<real>(r.loc[2]);
-    b.w = static_cast<real>(q);
-    sr_rec[pc] = b;
-    sr_idx[pc] = make_int2(cell_of(r, g), i);
-    if (sr_lo) {   // float32 records carry the rounding residue (float-float local coordinates)
-        Vec4<real> c;
-        c.x = static_cast<real>(r.loc[0] - static_cast<double>(b.x));
-        c.y = static_cast<real>(r.loc[1] - static_cast<double>(b.y));
-        c.z = static_cast<real>(r.loc[2] - static_cast<double>(b.z));
-        c.w = static_cast<real>(r.cell[2]);   // z cell index, exact in float
-        sr_lo[pc] = c;
+    if constexpr (std::is_same<real, float>::value) {
+        // float32 records: the float-float locate of k_prep<true>
+        const LocatedF r = locate_ff(x + 3 * static_cast<size_t>(i), g);
+        const float qf = static_cast<float>(q);
+        sp_rec[ps] = Vec4<float>{r.z[0], r.z[1], r.z[2], qf};
+        sp_idx[ps] = make_int2((r.lw[0] % g.T) | ((r.lw[1] % g.T) << 8) | ((r.lw[2] % g.T) << 16), i);
+        sr_rec[pc] = Vec4<float>{r.loc[0].h, r.loc[1].h, r.loc[2].h, qf};
+        sr_idx[pc] = make_int2(kr.z, i);
+        // rounding residue of the local coordinates (float-float) and the z cell index (exact in float)
+        sr_lo[pc] = Vec4<float>{r.loc[0].l, r.loc[1].l, r.loc[2].l, static_cast<float>(r.cell[2])};
+    } else {
+        const Located r = locate(x + 3 * static_cast<size_t>(i), g);
+        Vec4<real> a;
+        a.x = static_cast<real>(r.z[0]);
+        a.y = static_cast<real>(r.z[1]);
+        a.z = static_cast<real>(r.z[2]);
+        a.w = static_cast<real>(q);
+        sp_rec[ps] = a;
+        const int pack = (r.lw[0] % g.T) | ((r.lw[1] % g.T) << 8) | ((r.lw[2] % g.T) << 16);
+        sp_idx[ps] = make_int2(pack, i);
+        Vec4<real> b;
+        b.x = static_cast<real>(r.loc[0]);
+        b.y = static_cast<real>(r.loc[1]);
+        b.z = static_cast<real>(r.loc[2]);
+        b.w = static_cast<real>(q);
+        sr_rec[pc] = b;
+        sr_idx[pc] = make_int2(cell_of(r, g), i);
+        if (sr_f32)    // float64 records get a float32 copy for the cutoff pre-test of the real-space sum
+            sr_f32[pc] = make_float4(static_cast<float>(r.loc[0]), static_cast<float>(r.loc[1]),
+                                     static_cast<float>(r.loc[2]), static_cast<float>(r.cell[2]));
     }
-    if (sr_f32)    // float64 records get a float32 copy for the cutoff pre-test of the real-space sum
-        sr_f32[pc] = make_float4(static_cast<float>(r.loc[0]), static_cast<float>(r.loc[1]),
-                                 static_cast<float>(r.loc[2]), static_cast<float>(r.cell[2]));
 }
 
 // P window weights at one coordinate z by Horner (coefficients c[a*(deg+1) + k], monomials in z).
@@ -367,9 +438,13 @@ __global__ void __launch_bounds__(spread_threads<P, spread_tile<real>()>()) k_sp
 // Sum of every tile slab covering grid point l (periodic).  Point l lies in tile t = l / T at
 // offset o = l % T; the tiles t - j (mod nt) cover it at slab offset e = o + j T for every j with
 // e < E = T + P - 1 (per axis).  Empty tiles write no slab and are skipped.
-template <typename real>
-__global__ void k_halo(const real* __restrict__ scratch, const int* __restrict__ tile_off, Geom g,
-                       real* __restrict__ grid) {
+// NI > 0: every axis has at most NI overlapping slabs (NI = ceil(E / T)); the enumeration is unrolled
+// and every slab value is loaded unconditionally (empty tiles never wrote theirs, so their values are
+// discarded by a select), so the ~NI^3 loads of a point are independent and in flight together
+// instead of one L2 round trip (tile_off, then the slab) after another.  NI = 0: run-time loops.
+template <typename real, int NI>
+__global__ void __launch_bounds__(256) k_halo(const real* __restrict__ scratch, const int* __restrict__ tile_off, Geom g,
+                                              real* __restrict__ grid) {
     const int my = g.m[1], mz = g.m[2], T = g.T, E = g.T + g.P - 1;
     const int ntx = g.nt[0], nty = g.nt[1], ntz = g.nt[2];
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
@@ -379,20 +454,48 @@ __global__ void k_halo(const real* __restrict__ scratch, const int* __restrict__
     const int olx = lx - tlx * T, oly = ly - tly * T, olz = lz - tlz * T;
     const size_t slab = static_cast<size_t>(E) * E * E;
     real s = real(0);
-    int tx = tlx;
-    for (int ex = olx; ex < E; ex += T) {
-        int ty = tly;
-        for (int ey = oly; ey < E; ey += T) {
-            int tz = tlz;
-            for (int ez = olz; ez < E; ez += T) {
-                const int tile = (tx * nty + ty) * ntz + tz;
-                if (tile_off[tile] != tile_off[tile + 1])
-                    s += scratch[static_cast<size_t>(tile) * slab + (ex * E + ey) * E + ez];
-                tz = tz == 0 ? ntz - 1 : tz - 1;
-            }
-            ty = ty == 0 ? nty - 1 : ty - 1;
+    if constexpr (NI > 0) {
+        int txs[NI], tys[NI], tzs[NI];
+#pragma unroll
+        for (int a = 0; a < NI; ++a) {   // tile a steps back along each axis (periodic)
+            txs[a] = ((tlx - a) % ntx + ntx) % ntx;   // grids of fewer than NI tiles wrap more than once
+            tys[a] = ((tly - a) % nty + nty) % nty;
+            tzs[a] = ((tlz - a) % ntz + ntz) % ntz;
         }
-        tx = tx == 0 ? ntx - 1 : tx - 1;
+#pragma unroll
+        for (int a = 0; a < NI; ++a) {
+            const int ex = olx + a * T;
+#pragma unroll
+            for (int b = 0; b < NI; ++b) {
+                const int ey = oly + b * T;
+#pragma unroll
+                for (int c = 0; c < NI; ++c) {
+                    const int ez = olz + c * T;
+                    if (ex < E && ey < E && ez < E) {
+                        const int tile = (txs[a] * nty + tys[b]) * ntz + tzs[c];
+                        const int2 range = make_int2(tile_off[tile], tile_off[tile + 1]);
+                        const real v = scratch[static_cast<size_t>(tile) * slab + (ex * E + ey) * E + ez];
+                        s += range.x != range.y ? v : real(0);
+                    }
+                }
+            }
+        }
+    } else {
+        int tx = tlx;
+        for (int ex = olx; ex < E; ex += T) {
+            int ty = tly;
+            for (int ey = oly; ey < E; ey += T) {
+                int tz = tlz;
+                for (int ez = olz; ez < E; ez += T) {
+                    const int tile = (tx * nty + ty) * ntz + tz;
+                    if (tile_off[tile] != tile_off[tile + 1])
+                        s += scratch[static_cast<size_t>(tile) * slab + (ex * E + ey) * E + ez];
+                    tz = tz == 0 ? ntz - 1 : tz - 1;
+                }
+                ty = ty == 0 ? nty - 1 : ty - 1;
+            }
+            tx = tx == 0 ? ntx - 1 : tx - 1;
+        }
     }
     grid[id] = s;
 }
@@ -751,8 +854,8 @@ __global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<float>
     constexpr int NSH = 2 * kShortMaxR + 1;
     __shared__ float sh_hi[3][NSH], sh_lo[3][NSH];   // cell shifts (k - R) w_d, hi and lo parts
     __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
-    __shared__ float stx[kShortWarps][kShortMaxT][4];          // target position (hi parts) and charge
-    __shared__ float stl[kShortWarps][kShortMaxT][4];          // lo parts of the position
+    __shared__ __align__(16) float stx[kShortWarps][kShortMaxT][4];   // target position (hi parts) and charge
+    __shared__ __align__(16) float stl[kShortWarps][kShortMaxT][4];   // lo parts of the position
     const int R = g.reach;
     for (int k = threadIdx.x; k < 3 * (2 * R + 1); k += blockDim.x) {
         const int d = k / (2 * R + 1), i = k % (2 * R + 1);
@@ -800,9 +903,9 @@ __global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<float>
             while (pos[r + 1] <= p) ++r;
             const int4 rg = rng[r];
             const int j = rg.x + (p - pos[r]);
-            float sfx, sfy, sfz, szc;
+            float sfx, sfy, sfz, szc, sq;
             const Vec4<float> a = rec[j];
-            sfx = a.x; sfy = a.y; sfz = a.z;
+            sfx = a.x; sfy = a.y; sfz = a.z; sq = a.w;
             szc = lo[j].w;
             const int4 col = scol[rg.w];
             const int ix = col.x + R, iy = col.y + R, iz = rg.z + (static_cast<int>(szc) - rg.y) + R;
@@ -812,23 +915,23 @@ __global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<float>
 #pragma unroll
             for (int t = 0; t < kShortMaxT; ++t) {
                 if (t >= nt) break;   // nt is warp-uniform
-                float tx, ty, tz;
-                tx = stx[warp][t][0]; ty = stx[warp][t][1]; tz = stx[warp][t][2];
-                const float dxf = tx - px, dyf = ty - py, dzf = tz - pz;
+                const float4 tt = *reinterpret_cast<const float4*>(stx[warp][t]);   // broadcast
+                const float dxf = tt.x - px, dyf = tt.y - py, dzf = tt.z - pz;
                 const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
                 if (r2f < kp.rc2f && r2f > 0.f) {
                     if (!loaded) {
                         loaded = true;
                         const Vec4<float> l = lo[j];
-                        qj = rec[j].w;
+                        qj = sq;
                         ex = l.x + sh_lo[0][ix];
                         ey = l.y + sh_lo[1][iy];
                         ez = l.z + sh_lo[2][iz];
                     }
+                    const float4 tl = *reinterpret_cast<const float4*>(stl[warp][t]);
                     float ddx, ddy, ddz;
-                    ddx = dxf + (stl[warp][t][0] - ex);
-                    ddy = dyf + (stl[warp][t][1] - ey);
-                    ddz = dzf + (stl[warp][t][2] - ez);
+                    ddx = dxf + (tl.x - ex);
+                    ddy = dyf + (tl.y - ey);
+                    ddz = dzf + (tl.z - ez);
                     const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
                     if (r2 < kp.rc2 && r2 > 0.f) {
                         const float u = fma(r2, kp.two_over_rc2, float(-1));
@@ -1048,11 +1151,15 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<double>
 }
 
 // ---- energy ------------------------------------------------------------------------------------
-// phi += phi_sr, F += F_sr (the real-space sum computed on the second stream), and per-block partial
-// sums of rho phi for the energy.
-static __global__ void k_combine_energy(double* __restrict__ phi, double* __restrict__ f,
-                                        const double* __restrict__ phi_sr, const double* __restrict__ f_sr,
-                                        const double* __restrict__ rho, int n, double* __restrict__ part) {
+// phi += phi_sr, F += F_sr and E = 1/2 sum rho phi.  Block partial sums go to part[]; the last block to
+// finish (ticket counter `done`, zeroed before the evaluation) adds them in a fixed order and writes E,
+// so the energy needs no second launch and does not depend on the block schedule.
+static __global__ void __launch_bounds__(256) k_combine_energy(double* __restrict__ phi, double* __restrict__ f,
+                                                               const double* __restrict__ phi_sr,
+                                                               const double* __restrict__ f_sr,
+                                                               const double* __restrict__ rho, int n,
+                                                               double* __restrict__ part, unsigned* __restrict__ done,
+                                                               double* __restrict__ energy) {
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double q = rho[i];
@@ -1061,32 +1168,34 @@ static __global__ void k_combine_energy(double* __restrict__ phi, double* __rest
         f[3 * static_cast<size_t>(i) + 0] += f_sr[3 * static_cast<size_t>(i) + 0];
         f[3 * static_cast<size_t>(i) + 1] += f_sr[3 * static_cast<size_t>(i) + 1];
         f[3 * static_cast<size_t>(i) + 2] += f_sr[3 * static_cast<size_t>(i) + 2];
-        s += (isfinite(q) ? q : 0.0) * p;
+        s += ((__double2hiint(q) & 0x7ff00000) != 0x7ff00000 ? q : 0.0) * p;
     }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __shared__ double red[32];
+    __shared__ double red[8];
+    __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
-    if (warp == 0) {
-        s = lane < (blockDim.x >> 5) ? red[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) part[blockIdx.x] = s;
-    }
-}
-
-static __global__ void k_energy_final(const double* __restrict__ part, int np, double* __restrict__ energy) {
-    double s = 0.0;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) s += part[i];
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    __shared__ double red[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) red[warp] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < (blockDim.x >> 5); ++w) t += red[w];
-        energy[0] = 0.5 * t;
+        for (int w = 0; w < 8; ++w) t += red[w];
+        part[blockIdx.x] = t;
+        __threadfence();
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    double t = 0.0;
+    for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += __ldcg(part + b);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double e = 0.0;
+        for (int w = 0; w < 8; ++w) e += red[w];
+        energy[0] = 0.5 * e;
     }
 }
 

@@ -95,7 +95,12 @@ cudaError_t LaunchFF::spread(int ntiles, const Geom& g, const float4* rec_h, con
 
 cudaError_t LaunchFF::halo(const float2* scratch, const int* tile_off, const Geom& g, double* grid, cudaStream_t s) {
     const int mm = g.m[0] * g.m[1] * g.m[2];
-    k_halo_ff<<<(mm + 255) / 256, 256, 0, s>>>(scratch, tile_off, g, grid);
+    const int nz = (g.T + g.P - 1 + g.T - 1) / g.T, hb = (mm + 255) / 256;   // overlapping slabs per axis
+    if (nz <= 4) k_halo_ff<4><<<hb, 256, 0, s>>>(scratch, tile_off, g, grid);
+    else if (nz <= 6) k_halo_ff<6><<<hb, 256, 0, s>>>(scratch, tile_off, g, grid);
+    else if (nz <= 8) k_halo_ff<8><<<hb, 256, 0, s>>>(scratch, tile_off, g, grid);
+    else if (nz <= 16) k_halo_ff<16><<<hb, 256, 0, s>>>(scratch, tile_off, g, grid);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

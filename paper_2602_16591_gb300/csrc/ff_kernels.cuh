@@ -142,8 +142,9 @@ __global__ void __launch_bounds__(spread_threads<P, kTile64>()) k_spread_ff(cons
 }
 
 // Halo sum of the float-float slabs (same enumeration as k_halo) into the float64 grid.
-static __global__ void k_halo_ff(const float2* __restrict__ scratch, const int* __restrict__ tile_off, Geom g,
-                                 double* __restrict__ grid) {
+template <int NZ>
+__global__ void __launch_bounds__(256) k_halo_ff(const float2* __restrict__ scratch, const int* __restrict__ tile_off, Geom g,
+                                                 double* __restrict__ grid) {
     const int my = g.m[1], mz = g.m[2], T = g.T, E = g.T + g.P - 1;
     const int ntx = g.nt[0], nty = g.nt[1], ntz = g.nt[2];
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
@@ -152,20 +153,32 @@ static __global__ void k_halo_ff(const float2* __restrict__ scratch, const int* 
     const int tlx = lx / T, tly = ly / T, tlz = lz / T;
     const int olx = lx - tlx * T, oly = ly - tly * T, olz = lz - tlz * T;
     const size_t slab = static_cast<size_t>(E) * E * E;
+    // the NZ slabs along z (at most ceil(E / T)) are unrolled and loaded unconditionally (values of
+    // empty tiles, which never wrote their slab, are discarded by a select): independent loads
+    int tzs[NZ];
+#pragma unroll
+    for (int c = 0; c < NZ; ++c) tzs[c] = ((tlz - c) % ntz + ntz) % ntz;
     ff s{0.f, 0.f};
     int tx = tlx;
     for (int ex = olx; ex < E; ex += T) {
         int ty = tly;
         for (int ey = oly; ey < E; ey += T) {
-            int tz = tlz;
-            for (int ez = olz; ez < E; ez += T) {
-                const int tile = (tx * nty + ty) * ntz + tz;
-                if (tile_off[tile] != tile_off[tile + 1]) {
-                    const float2 v = scratch[static_cast<size_t>(tile) * slab + (ex * E + ey) * E + ez];
-                    s = ff_add(s, ff{v.x, v.y});
+            float2 v[NZ];
+            bool use[NZ];
+#pragma unroll
+            for (int c = 0; c < NZ; ++c) {
+                const int ez = olz + c * T;
+                use[c] = false;
+                v[c] = make_float2(0.f, 0.f);
+                if (ez < E) {
+                    const int tile = (tx * nty + ty) * ntz + tzs[c];
+                    use[c] = tile_off[tile] != tile_off[tile + 1];
+                    v[c] = scratch[static_cast<size_t>(tile) * slab + (ex * E + ey) * E + ez];
                 }
-                tz = tz == 0 ? ntz - 1 : tz - 1;
             }
+#pragma unroll
+            for (int c = 0; c < NZ; ++c)
+                if (use[c]) s = ff_add(s, ff{v[c].x, v[c].y});
             ty = ty == 0 ? nty - 1 : ty - 1;
         }
         tx = tx == 0 ? ntx - 1 : tx - 1;

@@ -148,7 +148,7 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
     g.self = 0.0;
 
     const int tb = 256, nb = static_cast<int>((n + tb - 1) / tb);
-    pswf::k_prep<<<nb, tb, 0, s>>>(x, rho, g, key_rank, tile_cnt, cell_cnt, status);
+    pswf::k_prep<false><<<nb, tb, 0, s>>>(x, rho, g, key_rank, tile_cnt, cell_cnt, status);
     pswf::k_scan<<<2, 1024, 0, s>>>(tile_cnt, tile_off, static_cast<int>(ntiles), cell_cnt, cell_off, 1);
     pswf::k_scatter<double><<<nb, tb, 0, s>>>(x, rho, g, key_rank, tile_off, cell_off, sp_rec, sp_idx, sr_rec,
                                               sr_idx, nullptr, nullptr);
@@ -157,7 +157,7 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
     e = pswf::Launch<double>::spread(P, static_cast<int>(ntiles), sp_rec, sp_idx, tile_off, coef, p->deg_w, slab, s);
     if (e != cudaSuccess) return fail_static(EWALD_ECUDA, std::string("spread launch: ") + cudaGetErrorString(e));
     const int mm = m * m * m;
-    pswf::k_halo<double><<<(mm + 255) / 256, 256, 0, s>>>(slab, tile_off, g, grid);
+    pswf::k_halo<double, 0><<<(mm + 255) / 256, 256, 0, s>>>(slab, tile_off, g, grid);
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail_static(EWALD_ECUDA, std::string("halo launch: ") + cudaGetErrorString(e));
     return EWALD_OK;
