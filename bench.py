@@ -164,13 +164,34 @@ def algorithmic_flops(stage, p, n, pairs):
     return None
 
 
+# device.cuh section (first line prefix) holding each stage's kernel; the float-float kernels live in
+# ff_kernels.cuh
+SECTION_OF = {"short": "// ---- real-space sum", "interp": "// ---- Alg. 2 step 5", "spread": "// ---- Alg. 2 step 1:",
+              "halo": "// ---- Alg. 2 step 1 (continued)"}
+
+
+def source_digest(stage, precision):
+    """sha1 prefix of the source a stage's kernel is compiled from (its device.cuh section)."""
+    csrc = os.path.join(ROOT, "paper_2602_16591_gb300", "csrc")
+    if precision == "ff":
+        text = open(os.path.join(csrc, "ff_kernels.cuh")).read()
+    else:
+        text = open(os.path.join(csrc, "device.cuh")).read()
+        marker = SECTION_OF.get(stage)
+        if marker is None or marker not in text:
+            return None
+        i = text.index(marker)
+        j = text.find("\n// ---- ", i + 1)
+        text = text[i:j if j >= 0 else len(text)]
+    return hashlib.sha1(text.encode()).hexdigest()[:12]
+
+
 def traffic_for(stage, n, p, precision):
-    """Per-launch DRAM bytes from the committed ncu summary, if taken on the current kernels."""
+    """Per-launch DRAM bytes from the committed ncu summary, if taken on the current kernel source."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.txt")
-    src = os.path.join(ROOT, "paper_2602_16591_gb300", "csrc", "device.cuh")
     if not os.path.exists(path):
         return None
-    digest = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+    digest = source_digest(stage, precision)
     for line in open(path):
         f = line.split()
         if len(f) >= 6 and not line.startswith("#") and f[0] == stage and int(f[1]) == n and int(f[2]) == p.P \

@@ -383,10 +383,13 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
         const int ni = (g.T + g.P - 1 + g.T - 1) / g.T;   // overlapping slabs per axis
         const auto* sc = static_cast<const real*>(p->scratch);
         auto* ga = static_cast<real*>(p->grid_a);
+        // float32 plans (tile edge 8): 32 x 8 blocks over (z, y), grid (m_z / 32, m_y / 8, m_x); otherwise 1-D
+        const dim3 hrow((g.m[2] + 31) / 32, (g.m[1] + 7) / 8, g.m[0]), hblk(32, 8);
         const int hb = (mm + 255) / 256;
-        if (ni <= 2) pswf::k_halo<real, 2><<<hb, 256, 0, s>>>(sc, p->tile_off, g, ga);
-        else if (ni == 3) pswf::k_halo<real, 3><<<hb, 256, 0, s>>>(sc, p->tile_off, g, ga);
-        else if (ni == 4) pswf::k_halo<real, 4><<<hb, 256, 0, s>>>(sc, p->tile_off, g, ga);
+        const bool rows = sizeof(real) == 4 && g.T == pswf::kTile32;
+        if (rows && ni <= 2) pswf::k_halo<real, 2><<<hrow, hblk, 0, s>>>(sc, p->tile_off, g, ga);
+        else if (rows && ni == 3) pswf::k_halo<real, 3><<<hrow, hblk, 0, s>>>(sc, p->tile_off, g, ga);
+        else if (rows && ni == 4) pswf::k_halo<real, 4><<<hrow, hblk, 0, s>>>(sc, p->tile_off, g, ga);
         else pswf::k_halo<real, 0><<<hb, 256, 0, s>>>(sc, p->tile_off, g, ga);
     }
     PSWF_CUDA(cudaGetLastError());

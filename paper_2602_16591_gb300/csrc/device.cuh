@@ -209,10 +209,7 @@ __global__ void __launch_bounds__(256) k_prep(const double* __restrict__ x, cons
     if (threadIdx.x == 0 && nbad > 0) atomicAdd(status + 2, static_cast<double>(nbad));
 }
 
-// Exclusive scan of cnt[0..N) into off[0..N]; one block per segment (blockIdx.x = 0 / 1).  Thread t owns
-// the contiguous run [t K, (t + 1) K) with K a multiple of 4 (16-byte vector loads and stores): a first
-// pass sums the run, one block-wide scan of the run sums gives its offset, a second pass (L1/L2 hits)
-// writes the offsets.  Two memory round trips whatever N, instead of one per 16K counters.
+// Exclusive scan of cnt[0..N) into off[0..N]; one block per segment (blockIdx.x = 0 / 1).
 static __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cnt0, int* __restrict__ off0, int n0,
                                                const int* __restrict__ cnt1, int* __restrict__ off1, int n1) {
     const int* cnt = blockIdx.x == 0 ? cnt0 : cnt1;
@@ -220,56 +217,73 @@ static __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cn
     const int N = blockIdx.x == 0 ? n0 : n1;
     __shared__ int wsum[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int K = ((N + blockDim.x - 1) / blockDim.x + 3) & ~3;
-    const int i0 = threadIdx.x * K, i1 = min(i0 + K, N);
-    int s = 0;
-#pragma unroll 4
-    for (int i = i0; i < i1; i += 4) {
-        if (i + 4 <= i1) {   // the arrays are cudaMalloc-aligned (or 16-byte aligned carves) and i % 4 == 0
-            const int4 t = *reinterpret_cast<const int4*>(cnt + i);
-            s += (t.x + t.y) + (t.z + t.w);
-        } else {
-            for (int k = i; k < i1; ++k) s += cnt[k];
-        }
-    }
-    int x = s;
+    int carry = 0;
+    constexpr int ITEMS = 16;   // 16K counters per round: the ~3e4 cell counters of a 1e5-particle plan in 2 rounds
+    for (int base = 0; base < N; base += blockDim.x * ITEMS) {
+        int v[ITEMS], s = 0;
+        const int i0 = base + threadIdx.x * ITEMS;
+        if (i0 + ITEMS <= N) {   // whole 64-byte runs: vector loads (the arrays are cudaMalloc-aligned)
+            const int4* c4 = reinterpret_cast<const int4*>(cnt + i0);
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        int w = lane < nw ? wsum[lane] : 0;
+            for (int q = 0; q < ITEMS / 4; ++q) {
+                const int4 t = c4[q];
+                v[4 * q] = t.x;
+                v[4 * q + 1] = t.y;
+                v[4 * q + 2] = t.z;
+                v[4 * q + 3] = t.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < ITEMS; ++k) v[k] = (i0 + k < N) ? cnt[i0 + k] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) s += v[k];
+        int x = s;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+            const int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        wsum[lane] = w;
-    }
-    __syncthreads();
-    int e = (warp > 0 ? wsum[warp - 1] : 0) + x - s;
-#pragma unroll 4
-    for (int i = i0; i < i1; i += 4) {
-        if (i + 4 <= i1) {
-            const int4 t = *reinterpret_cast<const int4*>(cnt + i);
-            int4 o;
-            o.x = e;
-            o.y = e + t.x;
-            o.z = o.y + t.y;
-            o.w = o.z + t.z;
-            e = o.w + t.w;
-            *reinterpret_cast<int4*>(off + i) = o;
+        if (lane == 31) wsum[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        int e = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - s;
+        if (i0 + ITEMS <= N) {
+            int4* o4 = reinterpret_cast<int4*>(off + i0);
+#pragma unroll
+            for (int q = 0; q < ITEMS / 4; ++q) {
+                int4 t;
+                t.x = e;
+                e += v[4 * q];
+                t.y = e;
+                e += v[4 * q + 1];
+                t.z = e;
+                e += v[4 * q + 2];
+                t.w = e;
+                e += v[4 * q + 3];
+                o4[q] = t;
+            }
         } else {
-            for (int k = i; k < i1; ++k) {
-                off[k] = e;
-                e += cnt[k];
+#pragma unroll
+            for (int k = 0; k < ITEMS; ++k) {
+                if (i0 + k < N) off[i0 + k] = e;
+                e += v[k];
             }
         }
+        const int total = wsum[nw - 1];
+        __syncthreads();
+        carry += total;
     }
-    if (threadIdx.x == 0) off[N] = wsum[nw - 1];
+    if (threadIdx.x == 0) off[N] = carry;
 }
 
 // Sorted records.  Spreading side (tile order): {z0, z1, z2, rho}, {packed offsets in tile, original index}.
@@ -296,8 +310,9 @@ __global__ void __launch_bounds__(256) k_scatter(const double* __restrict__ x, c
         sp_idx[ps] = make_int2((r.lw[0] % g.T) | ((r.lw[1] % g.T) << 8) | ((r.lw[2] % g.T) << 16), i);
         sr_rec[pc] = Vec4<float>{r.loc[0].h, r.loc[1].h, r.loc[2].h, qf};
         sr_idx[pc] = make_int2(kr.z, i);
-        // rounding residue of the local coordinates (float-float) and the z cell index (exact in float)
-        sr_lo[pc] = Vec4<float>{r.loc[0].l, r.loc[1].l, r.loc[2].l, static_cast<float>(r.cell[2])};
+        // rounding residue of the local coordinates (float-float) and the z cell index (its int bits: the
+        // real-space kernel reads it back without a conversion instruction)
+        sr_lo[pc] = Vec4<float>{r.loc[0].l, r.loc[1].l, r.loc[2].l, __int_as_float(r.cell[2])};
     } else {
         const Located r = locate(x + 3 * static_cast<size_t>(i), g);
         Vec4<real> a;
@@ -317,7 +332,7 @@ __global__ void __launch_bounds__(256) k_scatter(const double* __restrict__ x, c
         sr_idx[pc] = make_int2(cell_of(r, g), i);
         if (sr_f32)    // float64 records get a float32 copy for the cutoff pre-test of the real-space sum
             sr_f32[pc] = make_float4(static_cast<float>(r.loc[0]), static_cast<float>(r.loc[1]),
-                                     static_cast<float>(r.loc[2]), static_cast<float>(r.cell[2]));
+                                     static_cast<float>(r.loc[2]), __int_as_float(r.cell[2]));
     }
 }
 
@@ -438,29 +453,39 @@ __global__ void __launch_bounds__(spread_threads<P, spread_tile<real>()>()) k_sp
 // Sum of every tile slab covering grid point l (periodic).  Point l lies in tile t = l / T at
 // offset o = l % T; the tiles t - j (mod nt) cover it at slab offset e = o + j T for every j with
 // e < E = T + P - 1 (per axis).  Empty tiles write no slab and are skipped.
-// NI > 0: every axis has at most NI overlapping slabs (NI = ceil(E / T)); the enumeration is unrolled
-// and every slab value is loaded unconditionally (empty tiles never wrote theirs, so their values are
-// discarded by a select), so the ~NI^3 loads of a point are independent and in flight together
-// instead of one L2 round trip (tile_off, then the slab) after another.  NI = 0: run-time loops.
+// ---- Alg. 2 step 1 (continued): halo sum of the tile slabs into the periodic grid -----------------
+// NI > 0 (float32 plans, tile edge T = 8 at compile time): every axis has at most NI overlapping slabs
+// (NI = ceil(E / T)); the enumeration is unrolled and every slab value is loaded unconditionally
+// (empty tiles never wrote theirs, so their values are discarded by a select), so the ~NI^3 loads of a
+// point are independent and in flight together.  Blocks of 32 x 8 points (z, y), grid
+// (m_z / 32, m_y / 8, m_x): no integer division in the indexing.  NI = 0: run-time tile edge and loops (float64 plans, static path),
+// one thread per point of a 1-D grid.
 template <typename real, int NI>
 __global__ void __launch_bounds__(256) k_halo(const real* __restrict__ scratch, const int* __restrict__ tile_off, Geom g,
                                               real* __restrict__ grid) {
-    const int my = g.m[1], mz = g.m[2], T = g.T, E = g.T + g.P - 1;
+    const int my = g.m[1], mz = g.m[2], E = g.T + g.P - 1;
     const int ntx = g.nt[0], nty = g.nt[1], ntz = g.nt[2];
-    const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= g.m[0] * my * mz) return;
-    const int lz = id % mz, ly = (id / mz) % my, lx = id / (mz * my);
-    const int tlx = lx / T, tly = ly / T, tlz = lz / T;
-    const int olx = lx - tlx * T, oly = ly - tly * T, olz = lz - tlz * T;
     const size_t slab = static_cast<size_t>(E) * E * E;
     real s = real(0);
     if constexpr (NI > 0) {
+        constexpr int T = kTile32;
+        const int lz = blockIdx.x * blockDim.x + threadIdx.x, ly = blockIdx.y * blockDim.y + threadIdx.y;
+        const int lx = blockIdx.z;
+        if (lz >= mz || ly >= my) return;
+        const int tlx = lx / T, tly = ly / T, tlz = lz / T;   // shifts (T is a power of two)
+        const int olx = lx % T, oly = ly % T, olz = lz % T;
         int txs[NI], tys[NI], tzs[NI];
 #pragma unroll
-        for (int a = 0; a < NI; ++a) {   // tile a steps back along each axis (periodic)
-            txs[a] = ((tlx - a) % ntx + ntx) % ntx;   // grids of fewer than NI tiles wrap more than once
-            tys[a] = ((tly - a) % nty + nty) % nty;
-            tzs[a] = ((tlz - a) % ntz + ntz) % ntz;
+        for (int a = 0; a < NI; ++a) {   // tile a steps back along each axis (periodic; tiny grids wrap repeatedly)
+            int t = tlx - a;
+            while (t < 0) t += ntx;
+            txs[a] = t;
+            t = tly - a;
+            while (t < 0) t += nty;
+            tys[a] = t;
+            t = tlz - a;
+            while (t < 0) t += ntz;
+            tzs[a] = t;
         }
 #pragma unroll
         for (int a = 0; a < NI; ++a) {
@@ -480,7 +505,14 @@ __global__ void __launch_bounds__(256) k_halo(const real* __restrict__ scratch, 
                 }
             }
         }
+        grid[(static_cast<size_t>(lx) * my + ly) * mz + lz] = s;
     } else {
+        const int T = g.T;
+        const int id = blockIdx.x * blockDim.x + threadIdx.x;
+        if (id >= g.m[0] * my * mz) return;
+        const int lz = id % mz, ly = (id / mz) % my, lx = id / (mz * my);
+        const int tlx = lx / T, tly = ly / T, tlz = lz / T;
+        const int olx = lx - tlx * T, oly = ly - tly * T, olz = lz - tlz * T;
         int tx = tlx;
         for (int ex = olx; ex < E; ex += T) {
             int ty = tly;
@@ -496,8 +528,8 @@ __global__ void __launch_bounds__(256) k_halo(const real* __restrict__ scratch, 
             }
             tx = tx == 0 ? ntx - 1 : tx - 1;
         }
+        grid[id] = s;
     }
-    grid[id] = s;
 }
 
 // ---- Alg. 2 step 3: diagonal scaling on the R2C half spectrum ------------------------------------
@@ -908,7 +940,7 @@ __global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<float>
             sfx = a.x; sfy = a.y; sfz = a.z; sq = a.w;
             szc = lo[j].w;
             const int4 col = scol[rg.w];
-            const int ix = col.x + R, iy = col.y + R, iz = rg.z + (static_cast<int>(szc) - rg.y) + R;
+            const int ix = col.x + R, iy = col.y + R, iz = rg.z + (__float_as_int(szc) - rg.y) + R;
             const float px = sfx + sh_hi[0][ix], py = sfy + sh_hi[1][iy], pz = sfz + sh_hi[2][iz];
             bool loaded = false;
             float qj = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
@@ -1089,7 +1121,7 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<double>
                     sfx = f.x; sfy = f.y; sfz = f.z;
                     szc = f.w;
                     const int4 col = scol[rg.w];
-                    const int ix = col.x + R, iy = col.y + R, iz = rg.z + (static_cast<int>(szc) - rg.y) + R;
+                    const int ix = col.x + R, iy = col.y + R, iz = rg.z + (__float_as_int(szc) - rg.y) + R;
                     const float px = sfx + sh_hi[0][ix], py = sfy + sh_hi[1][iy], pz = sfz + sh_hi[2][iz];
 #pragma unroll
                     for (int t = 0; t < MT; ++t) {

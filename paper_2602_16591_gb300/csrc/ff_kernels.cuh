@@ -157,7 +157,11 @@ __global__ void __launch_bounds__(256) k_halo_ff(const float2* __restrict__ scra
     // empty tiles, which never wrote their slab, are discarded by a select): independent loads
     int tzs[NZ];
 #pragma unroll
-    for (int c = 0; c < NZ; ++c) tzs[c] = ((tlz - c) % ntz + ntz) % ntz;
+    for (int c = 0; c < NZ; ++c) {   // tiny grids wrap repeatedly
+        int t = tlz - c;
+        while (t < 0) t += ntz;
+        tzs[c] = t;
+    }
     ff s{0.f, 0.f};
     int tx = tlx;
     for (int ex = olx; ex < E; ex += T) {
