@@ -315,7 +315,8 @@ cudaError_t launch_short_d(ewald_plan p, const pswf::Vec4<real>* sr_rec, const p
     // float32 pairs are cheap: the direct kernel; float64 pairs: the two-phase (queued) kernel
     if constexpr (sizeof(real) == 4)
         pswf::k_short<D><<<blocks, 32 * pswf::kShortWarps, smem, s>>>(
-            sr_rec, p->sr_idx, sr_lo, p->cell_off, p->sr_cols, p->n_cols, p->sr_rcap, g, kp, phi, f);
+            sr_rec, p->sr_idx, sr_lo, p->cell_off, p->sr_cols, p->n_cols, p->sr_rcap, g, kp,
+            reinterpret_cast<float*>(phi), reinterpret_cast<float*>(f));   // float results in the float64 buffers
     else
         pswf::k_short_q<D><<<blocks, 32 * pswf::kShortWarps, smem, s>>>(
             sr_rec, p->sr_idx, p->sr_f32, p->cell_off, p->sr_cols, p->n_cols, p->sr_rcap, g, kp, phi, f);
@@ -441,7 +442,8 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     PSWF_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
     PSWF_CUDA(cudaStreamWaitEvent(s, p->ev_join2, 0));
     p->mark(8, false, s);
-    pswf::k_combine_energy<<<p->epart_blocks, 256, 0, s>>>(phi, f, p->phi_sr, p->f_sr, rho, n, p->epart,
+    pswf::k_combine_energy<real><<<p->epart_blocks, 256, 0, s>>>(phi, f, reinterpret_cast<const real*>(p->phi_sr),
+                                                                 reinterpret_cast<const real*>(p->f_sr), rho, n, p->epart,
                                                            reinterpret_cast<unsigned*>(p->status + 3), p->energy_d);
     PSWF_CUDA(cudaGetLastError());
     p->mark(8, true, s);
@@ -523,7 +525,7 @@ int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* ph
     PSWF_CUDA(cudaStreamWaitEvent(s, p->ev_join, 0));
     PSWF_CUDA(cudaStreamWaitEvent(s, p->ev_join2, 0));
     p->mark(8, false, s);
-    pswf::k_combine_energy<<<p->epart_blocks, 256, 0, s>>>(phi, f, p->phi_sr, p->f_sr, rho, n, p->epart,
+    pswf::k_combine_energy<double><<<p->epart_blocks, 256, 0, s>>>(phi, f, p->phi_sr, p->f_sr, rho, n, p->epart,
                                                            reinterpret_cast<unsigned*>(p->status + 3), p->energy_d);
     PSWF_CUDA(cudaGetLastError());
     p->mark(8, true, s);

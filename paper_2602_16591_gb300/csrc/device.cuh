@@ -882,7 +882,7 @@ __global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<float>
                                                             const Vec4<float>* __restrict__ lo,
                                                             const int* __restrict__ cell_off, const int4* __restrict__ cols,
                                                             int ncols, int rcap, Geom g, const __grid_constant__ ShortParams<float, D> kp,
-                                                            double* __restrict__ phi_out, double* __restrict__ f_out) {
+                                                            float* __restrict__ phi_out, float* __restrict__ f_out) {
     constexpr int NSH = 2 * kShortMaxR + 1;
     __shared__ float sh_hi[3][NSH], sh_lo[3][NSH];   // cell shifts (k - R) w_d, hi and lo parts
     __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
@@ -1003,13 +1003,13 @@ __global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<float>
                 mine[3] = acc[t][3];
             }
         }
-        if (lane < nt) {   // float64 conversions once per pass, lane-parallel
+        if (lane < nt) {   // float32 results; k_combine_energy widens them with full warps
             const int oi = idx[t0 + lane].y;
-            const double qi = static_cast<double>(stx[warp][lane][3]);
-            phi_out[oi] = static_cast<double>(mine[0]);
-            f_out[3 * static_cast<size_t>(oi) + 0] = qi * static_cast<double>(mine[1]);
-            f_out[3 * static_cast<size_t>(oi) + 1] = qi * static_cast<double>(mine[2]);
-            f_out[3 * static_cast<size_t>(oi) + 2] = qi * static_cast<double>(mine[3]);
+            const float qi = stx[warp][lane][3];
+            phi_out[oi] = mine[0];
+            f_out[3 * static_cast<size_t>(oi) + 0] = qi * mine[1];
+            f_out[3 * static_cast<size_t>(oi) + 1] = qi * mine[2];
+            f_out[3 * static_cast<size_t>(oi) + 2] = qi * mine[3];
         }
     }
 }
@@ -1185,21 +1185,22 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<double>
 // ---- energy ------------------------------------------------------------------------------------
 // phi += phi_sr, F += F_sr and E = 1/2 sum rho phi.  Block partial sums go to part[]; the last block to
 // finish (ticket counter `done`, zeroed before the evaluation) adds them in a fixed order and writes E,
-// so the energy needs no second launch and does not depend on the block schedule.
-static __global__ void __launch_bounds__(256) k_combine_energy(double* __restrict__ phi, double* __restrict__ f,
-                                                               const double* __restrict__ phi_sr,
-                                                               const double* __restrict__ f_sr,
+// so the energy needs no second launch and does not depend on the block schedule.  SR: the type of the
+// real-space results (float for float32 plans: k_short leaves the widening to these full warps).
+template <typename SR>
+__global__ void __launch_bounds__(256) k_combine_energy(double* __restrict__ phi, double* __restrict__ f,
+                                                        const SR* __restrict__ phi_sr, const SR* __restrict__ f_sr,
                                                                const double* __restrict__ rho, int n,
                                                                double* __restrict__ part, unsigned* __restrict__ done,
                                                                double* __restrict__ energy) {
     double s = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double q = rho[i];
-        const double p = phi[i] + phi_sr[i];
+        const double p = phi[i] + static_cast<double>(phi_sr[i]);
         phi[i] = p;
-        f[3 * static_cast<size_t>(i) + 0] += f_sr[3 * static_cast<size_t>(i) + 0];
-        f[3 * static_cast<size_t>(i) + 1] += f_sr[3 * static_cast<size_t>(i) + 1];
-        f[3 * static_cast<size_t>(i) + 2] += f_sr[3 * static_cast<size_t>(i) + 2];
+        f[3 * static_cast<size_t>(i) + 0] += static_cast<double>(f_sr[3 * static_cast<size_t>(i) + 0]);
+        f[3 * static_cast<size_t>(i) + 1] += static_cast<double>(f_sr[3 * static_cast<size_t>(i) + 1]);
+        f[3 * static_cast<size_t>(i) + 2] += static_cast<double>(f_sr[3 * static_cast<size_t>(i) + 2]);
         s += ((__double2hiint(q) & 0x7ff00000) != 0x7ff00000 ? q : 0.0) * p;
     }
     __shared__ double red[8];
