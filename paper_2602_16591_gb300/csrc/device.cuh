@@ -12,7 +12,8 @@
 //   k_interp   Alg. 2 step 5 and eq. force: phi^far, grad phi^far; writes phi - self, F
 //   k_short    real-space sum of the residual R (eq. R) over the cell list (second stream, concurrent
 //              with spread..interp), into separate phi/F buffers
-//   k_combine_energy  phi += phi_sr, F += F_sr, E = 1/2 sum rho phi (Remark on energy), two-pass reduction
+//   k_combine_energy  phi += phi_sr, F += F_sr, E = 1/2 sum rho phi (Remark on energy); its last block
+//              adds the block sums
 #pragma once
 
 #include <cstdint>
