@@ -405,8 +405,8 @@ def run_ours(args, rank, world, local_rank):
             "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
                     "d2h_bytes_per_step": 32 * n + 8},
             # own kernels per step: prep, scan, scatter, real-space, spread, halo, scale, (float-float:
-            # grid conversion,) interpolation, combine, energy; cuFFT's kernels are not counted
-            "gpu_launches": (11 if prec_tag == "ff" else 10) * args.steps,
+            # grid conversion,) interpolation, combine + energy; cuFFT's kernels are not counted
+            "gpu_launches": (10 if prec_tag == "ff" else 9) * args.steps,
             "stages_serial_ms": stages_serial, "clocks": clocks, "stages_ms": stages, "variants": variants,
             "batched": batch,
         }
