@@ -164,6 +164,67 @@ def algorithmic_flops(stage, p, n, pairs):
     return None
 
 
+def hbm_peak():
+    """Measured copy bandwidth (GB/s) from MEASURED_PEAKS.json, else the fallback figure."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, ValueError, KeyError, TypeError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def algorithmic_bytes(stage, p, n, precision):
+    """Algorithmic bytes of one launch (minimum data a stage must move); definitions in the design doc."""
+    grid = [int(v) for v in p.grid]
+    m3 = grid[0] * grid[1] * grid[2]
+    word = 4 if precision == "f32" else 8                    # grid value (float-float grids: float2)
+    rec = {"f32": 24, "f64": 40, "ff": 40}[precision]       # sorted spreading record + index per particle
+    if stage == "sort":
+        out = {"f32": 64, "f64": 96, "ff": 84}[precision]
+        return n * (32 + 32 + out)                          # x, rho in; keys out and back; records out
+    if stage == "spread":
+        return n * rec + m3 * word
+    if stage == "halo":
+        E = p.tile + p.P - 1
+        ntiles = m3 // (p.tile ** 3)
+        return ntiles * E ** 3 * word + m3 * word           # tile slabs in, grid out
+    if stage == "scale":
+        nspec = grid[0] * grid[1] * (grid[2] // 2 + 1)
+        return nspec * 2 * (8 if precision == "f32" else 16)
+    if stage == "interp":
+        return n * rec + m3 * word + n * 32                 # records and grid in, phi and F out
+    if stage == "short":
+        return n * ({"f32": 32, "f64": 48, "ff": 36}[precision] + (16 if precision == "f32" else 32))
+    if stage == "energy":
+        return n * (88 if precision == "f32" else 104)
+    return None
+
+
+def stage_rooflines(stages_serial, p, n, pairs, precision):
+    """Per-stage achieved bandwidth and flop rate against the HBM and ALU peaks (serialised stage times)."""
+    try:
+        hbm, hbm_src = hbm_peak()
+        alu = FP64_PEAK_TFLOPS if precision == "f64" else FP32_PEAK_TFLOPS
+        out = []
+        for st in ("sort", "spread", "halo", "scale", "interp", "short", "energy"):
+            t = stages_serial.get(st)
+            if not t or t <= 0:
+                continue
+            b = algorithmic_bytes(st, p, n, precision)
+            fl = algorithmic_flops(st, p, n, pairs)
+            row = {"stage": st, "us": 1000.0 * t}
+            if b:
+                gbs = b / (t / 1000.0) / 1e9
+                row.update({"bytes": b, "GB/s": gbs, "frac_hbm": gbs / hbm})
+            if fl:
+                tf = fl / (t / 1000.0) / 1e12
+                row.update({"flops": fl, "TFLOP/s": tf, "frac_alu": tf / alu})
+            out.append(row)
+        return {"hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src, "alu_peak_tflops": alu, "stages": out}
+    except Exception as e:   # reporting only: never fail the bench line
+        return {"error": repr(e)}
+
+
 # device.cuh section (first line prefix) holding each stage's kernel; the float-float kernels live in
 # ff_kernels.cuh
 SECTION_OF = {"short": "// ---- real-space sum", "interp": "// ---- Alg. 2 step 5", "spread": "// ---- Alg. 2 step 1:",
@@ -407,7 +468,9 @@ def run_ours(args, rank, world, local_rank):
             # own kernels per step: prep, scan, scatter, real-space, spread, halo, scale, (float-float:
             # grid conversion,) interpolation, combine + energy; cuFFT's kernels are not counted
             "gpu_launches": (10 if prec_tag == "ff" else 9) * args.steps,
-            "stages_serial_ms": stages_serial, "clocks": clocks, "stages_ms": stages, "variants": variants,
+            "stages_serial_ms": stages_serial,
+            "stage_rooflines": stage_rooflines(stages_serial, p, n, pairs, prec_tag),
+            "clocks": clocks, "stages_ms": stages, "variants": variants,
             "batched": batch,
         }
         print(json.dumps(line), flush=True)
