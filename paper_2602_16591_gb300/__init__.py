@@ -147,6 +147,16 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.c_void_p)
 
 
+def _out(a, shape):
+    """A caller's float64 output array (written in place), or a new one when a is None."""
+    if a is None:
+        return np.empty(shape)
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or a.shape != shape \
+            or not a.flags.c_contiguous or not a.flags.writeable:
+        raise ValueError("output must be a writeable C-contiguous float64 array of shape %s" % (shape,))
+    return a
+
+
 def pswf_eval(c, x):
     """The library planner's psi_0^c, its derivative, chi_0 and lambda_0 (host)."""
     x = _f64(x).ravel()
@@ -239,12 +249,13 @@ class Plan:
                                ctypes.byref(e) if energy else None, self._stream()))
         return phi, force, (e.value if energy else None)
 
-    def eval_host(self, x, rho):
-        """Same evaluation from host (NumPy) buffers; copies run inside the library call."""
+    def eval_host(self, x, rho, phi=None, force=None):
+        """Same evaluation from host (NumPy) buffers; copies run inside the library call.  phi (n,) and
+        force (n,3) may be caller-owned float64 arrays (page-locked ones make the copies back faster)."""
         x = _f64(x, (self.n, 3))
         rho = _f64(rho, (self.n,))
-        phi = np.empty(self.n)
-        F = np.empty((self.n, 3))
+        phi = _out(phi, (self.n,))
+        F = _out(force, (self.n, 3))
         e = ctypes.c_double(0.0)
         _check(_lib.ewald_eval_host(self._h, _ptr(x), _ptr(rho), _ptr(phi), _ptr(F), ctypes.byref(e),
                                     self._stream()))

@@ -210,3 +210,17 @@ def test_box_api_with_equal_edges_is_the_cube():
         a = pe.plan_params(1.3, 20_000, 1e-7, precision=prec).as_dict()
         b = pe.plan_params((1.3, 1.3, 1.3), 20_000, 1e-7, precision=prec).as_dict()
         assert a == b and a["deg_g"] == 0
+
+
+def test_eval_host_output_arrays_are_checked():
+    """Caller-owned outputs of Plan.eval_host: float64, C-contiguous, writeable, exact shape (host only)."""
+    a = np.empty((7, 3))
+    assert pe._out(a, (7, 3)) is a
+    assert pe._out(None, (7,)).shape == (7,)
+    for bad in (np.empty((7, 3), dtype=np.float32), np.empty((3, 7)).T, np.empty(7), [0.0] * 21):
+        with pytest.raises(ValueError):
+            pe._out(bad, (7, 3))
+    ro = np.empty((7, 3))
+    ro.flags.writeable = False
+    with pytest.raises(ValueError):
+        pe._out(ro, (7, 3))
