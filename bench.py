@@ -56,7 +56,7 @@ import os, sys, time, json
 sys.path.insert(0, %r)
 import numpy as np
 from oracle import exact
-from paper_2602_16591_gb300.workloads import uniform_neutral
+from workloads import uniform_neutral
 x, rho, L = uniform_neutral(%d, seed=%d)
 tg = np.linspace(0, len(x) - 1, %d).astype(np.int64)
 t = time.perf_counter()
@@ -153,14 +153,15 @@ class ClockSampler:
 
 # --------------------------------------------------------------------- work models --
 def algorithmic_flops(stage, p, n, pairs):
-    """Algorithmic flops of one launch (FMA = 2 flops); definitions in the design doc."""
+    """Algorithmic flops of one launch (FMA = 2 flops): window Horner + tensor-product stencil for
+    spread / interp, 100 flop per pair inside r_c for the real-space sum (rsqrt, two radial Horners)."""
     P, dw, dr = p.P, p.deg_w, p.deg_r
     if stage == "spread":
         return n * 2 * (P ** 3 + P ** 2 + 3 * P * (dw + 1))
     if stage == "interp":
         return n * 2 * (2 * P ** 3 + 6 * P ** 2 + 6 * P * (dw + 1))
     if stage == "short":
-        return pairs * 2 * (10 + 2 * (dr + 1))
+        return pairs * 100
     return None
 
 
@@ -174,7 +175,7 @@ def hbm_peak():
 
 
 def algorithmic_bytes(stage, p, n, precision):
-    """Algorithmic bytes of one launch (minimum data a stage must move); definitions in the design doc."""
+    """Algorithmic bytes of one launch: the minimum data a stage must read and write once."""
     grid = [int(v) for v in p.grid]
     m3 = grid[0] * grid[1] * grid[2]
     word = 4 if precision == "f32" else 8                    # grid value (float-float grids: float2)
@@ -283,7 +284,7 @@ def run_ours(args, rank, world, local_rank):
     import torch
 
     import paper_2602_16591_gb300 as pe
-    from paper_2602_16591_gb300.workloads import uniform_neutral
+    from workloads import uniform_neutral
 
     torch.cuda.set_device(local_rank)
     dist = None
@@ -413,7 +414,7 @@ def run_ours(args, rank, world, local_rank):
 
     if not args.no_variants:
         # cuboid box (Remark on cuboid domains): the headline density in a 1 x 1 x 2 box, twice the particles
-        from paper_2602_16591_gb300.workloads import uniform_neutral_box
+        from workloads import uniform_neutral_box
         cb = (1.0, 1.0, 2.0)
         cxn, crn, _ = uniform_neutral_box(2 * n, cb, seed=rank)
         cxr = (torch.tensor(cxn, device="cuda"), torch.tensor(crn, device="cuda"))
@@ -428,7 +429,7 @@ def run_ours(args, rank, world, local_rank):
     batch = None
     if not args.no_variants:
         # batched workload: 256 independent systems, n log-uniform in [500, 20000], L = (n/100)^(1/3)
-        from paper_2602_16591_gb300.workloads import batched_systems
+        from workloads import batched_systems
         systems = batched_systems(nsys=256, seed=rank)
         bx = torch.tensor(np.concatenate([sy[0] for sy in systems]), device="cuda")
         brho = torch.tensor(np.concatenate([sy[1] for sy in systems]), device="cuda")

@@ -13,12 +13,16 @@ split     PSWF mollifier, split function Phi, residual R, mollifier transform
 exact     the converged Ewald sum (Sec. 3.1, Alg. 1 with converged k-range plus
           the real-space sum and self term), brute-force lattice sums.
 alg2      Alg. 2 (fast Fourier-space sum) restated step by step with exact psi.
-params    Alg. 3 parameter selection (Sec. 6) with the readings listed in the design doc.
-models    closed-form error models and bounds (Sec. 5).
+params    Alg. 3 parameter selection (Sec. 6) as printed, with the readings it needs
+          (relative tolerance, Lambert-W branches, instantiation after rounding).
 
 Parity status: every public function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` (identities, library special cases, the NaCl Madelung
-constant, brute-force lattice sums, split independence).  The error models in
-``models`` are approximations by nature and are compared with measured errors
-only within the factor the paper reports.
+constant, brute-force lattice sums, split independence, the paper's Table 3).
+The closed-form error models of Sec. 5 are approximations by nature; the tests
+compare them with measured errors only within the factor the paper reports.
+
+Nothing here imports the CUDA library's package.  Callers take their seeded inputs
+from the top-level ``workloads`` module, which holds no arithmetic of the method and
+does not load the library either.
 """

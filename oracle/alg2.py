@@ -15,11 +15,14 @@ window half-width alpha = P h / 2 (Sec. 6.3, eq. alpha and the relation alpha = 
             The factor h^-3 converts the continuous transform of Sec. 4.3 into the
             coefficient seen by an unnormalised m^3-point DFT (Poisson summation with
             c_k = phihat/V of eq. fcoeffs, times m^3); Alg. 2 as printed leaves it implicit.
-            S(k) = 0 also for |k| >= m/2 (the cube corners of I_m and the sphere
-            |k| = m/2 itself, which holds the Nyquist axis modes): Prop. 1 bounds the
-            split error by the modes outside this ball, and deconvolving where
-            phihat ~ psi(1)^3 (corners) or ~psi(1) (Nyquist) amplifies rounding by up to
-            ~exp(3 c_w - c_s) (``ball=False`` keeps the full cube for comparison).
+            Retained modes: k in I_m strictly inside the mollifier's band,
+            |w| < c_s/r_c (eq. csrc; |k| < c_s L/(2 pi r_c) for a cube), with the unpaired
+            Nyquist planes k_d = -m_d/2 of an even m_d dropped.  Prop. 1 bounds the split
+            error by the modes outside this band, and deconvolving where phihat ~ psi(1)^3
+            (cube corners) or at an aliased Nyquist plane amplifies rounding by up to
+            ~exp(3 c_w - c_s).  When eq. csrc holds exactly (instantiated plans) the band is
+            the open ball |k| < m/2.  ``modes="cube"`` keeps the whole cube I_m of Alg. 2 as
+            printed, for comparison.
 4. IFFT     b_l = sum_k bhat_k e^{-2 pi i k.l/m}                          (Alg. 2 step 4)
 5. interp   phi_i^far = sum_l b_l phitilde(x_i - h l)                     (Alg. 2 step 5)
             grad phi_i^far = sum_l b_l grad phitilde(x_i - h l)           (Remark 'force', eq. force)
@@ -30,11 +33,14 @@ FFTs are NumPy's complex FFTs, and k runs over I_m = {-m/2, ..., m/2-1}.
 
 Cuboid boxes (Remark on cuboid domains, Sec. 6.1): L and m may be given per axis; then h_d = L_d/m_d,
 alpha_d = P h_d/2 (the window support is P points on every axis), w_d = 2 pi k_d/L_d, V = prod L_d,
-and the retained modes are the ellipsoid 0 < |w| < pi min_d m_d/L_d.
+and the band |w| < c_s/r_c is the ellipsoid 0 < |w| < pi min_d m_d/L_d once r_c is
+instantiated from the coarsest axis (eq. csrc).
 
 Parity status: pinned (tests/test_oracle_alg2.py) against the converged Ewald sum
 of ``exact`` (its difference is the method's own error, compared with the error
-models of Sec. 5) and by a single-charge DFT identity.
+models of Sec. 5), by a single-charge DFT identity, and (tests/test_oracle_table3.py)
+by the paper's Table 3: the smallest (m, P) that reach each tolerance in its n = 100,
+r_c = 0.1, c_s = log(1/eps) experiment.
 """
 import numpy as np
 
@@ -44,8 +50,10 @@ from .exact import wrap, realspace
 
 
 class Alg2:
-    def __init__(self, L, m, P, cs, cw, rc, ball=True):
-        self.ball = bool(ball)
+    def __init__(self, L, m, P, cs, cw, rc, modes="band"):
+        if modes not in ("band", "cube"):
+            raise ValueError("modes must be 'band' or 'cube'")
+        self.modes = modes
         self.Lv = np.broadcast_to(np.asarray(L, dtype=np.float64), (3,)).copy()
         self.mv = np.broadcast_to(np.asarray(m, dtype=np.int64), (3,)).copy()
         self.P = int(P)
@@ -103,32 +111,31 @@ class Alg2:
         return al * self.win.cos_transform(w * al) / (self.win.psi0 * self.hv[axis])
 
     def scaling(self):
-        """S(k) on the full index grid (S(0) = 0)."""
+        """S(k) on the full index grid (S(0) = 0; zero outside the retained modes)."""
         ph = [self.window_ft(d) for d in range(3)]
         den = (ph[0][:, None, None] * ph[1][None, :, None] * ph[2][None, None, :]) ** 2
+        ks = [self.kgrid(d) for d in range(3)]
+        KX, KY, KZ = np.meshgrid(*ks, indexing='ij')
         cube = np.all(self.Lv == self.Lv[0]) and np.all(self.mv == self.mv[0])
+        S = np.zeros(KX.shape)
         if cube:
-            m, L = self.m, self.L
-            k = self.kgrid()
-            KX, KY, KZ = np.meshgrid(k, k, k, indexing='ij')
-            k2 = (KX ** 2 + KY ** 2 + KZ ** 2)
-            S = np.zeros(k2.shape)
+            L = self.L
+            k2 = KX ** 2 + KY ** 2 + KZ ** 2
             nz = k2 > 0
             uk, inv = np.unique(k2[nz], return_inverse=True)
-            Mh = self.split.Mhat_k2(uk, L)[inv]
-            S[nz] = Mh / (L ** 3) / den[nz]
-            if self.ball:
-                S[4 * k2 >= m * m] = 0.0
-            return S
-        KX, KY, KZ = np.meshgrid(*(self.kgrid(d) for d in range(3)), indexing='ij')
-        w2 = (2.0 * np.pi) ** 2 * ((KX / self.Lv[0]) ** 2 + (KY / self.Lv[1]) ** 2 + (KZ / self.Lv[2]) ** 2)
-        S = np.zeros(w2.shape)
-        nz = w2 > 0
-        uw, inv = np.unique(w2[nz], return_inverse=True)
-        S[nz] = self.split.Mhat_w2(uw)[inv] / float(np.prod(self.Lv)) / den[nz]
-        if self.ball:
-            wmax = np.pi * np.min(self.mv / self.Lv)
-            S[w2 >= wmax * wmax] = 0.0
+            S[nz] = self.split.Mhat_k2(uk, L)[inv] / (L ** 3) / den[nz]
+            w2 = (2.0 * np.pi / L) ** 2 * k2
+        else:
+            w2 = (2.0 * np.pi) ** 2 * ((KX / self.Lv[0]) ** 2 + (KY / self.Lv[1]) ** 2 + (KZ / self.Lv[2]) ** 2)
+            nz = w2 > 0
+            uw, inv = np.unique(w2[nz], return_inverse=True)
+            S[nz] = self.split.Mhat_w2(uw)[inv] / float(np.prod(self.Lv)) / den[nz]
+        if self.modes == "band":
+            wb = self.cs / self.rc                       # eq. csrc: the mollifier's bandlimit
+            S[w2 >= wb * wb * (1.0 - 1e-12)] = 0.0       # (a band edge at exactly m/2 counts as outside)
+            for d, K in enumerate((KX, KY, KZ)):
+                if self.mv[d] % 2 == 0:
+                    S[K == -(self.mv[d] // 2)] = 0.0
         return S
 
     def fft(self, a):

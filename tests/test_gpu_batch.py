@@ -8,9 +8,11 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-import paper_2602_16591_gb300 as pe  # noqa: E402
+from conftest import require_library  # noqa: E402
+
+pe = require_library()
 from oracle import exact  # noqa: E402
-from paper_2602_16591_gb300.workloads import batched_systems  # noqa: E402
+from workloads import batched_systems  # noqa: E402
 
 
 def _rel(a, b):

@@ -10,7 +10,9 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-import paper_2602_16591_gb300 as pe  # noqa: E402
+from conftest import require_library  # noqa: E402
+
+pe = require_library()
 from oracle import exact  # noqa: E402
 from oracle.alg2 import Alg2  # noqa: E402
 

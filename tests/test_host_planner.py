@@ -10,11 +10,13 @@ import numpy as np
 import pytest
 from scipy.special import lambertw
 
-import paper_2602_16591_gb300 as pe
+from conftest import require_library
 from oracle import params as oparams
 from oracle.alg2 import Alg2
 from oracle.pswf import PSWF
 from oracle.split import PSWFSplit
+
+pe = require_library()
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -62,27 +64,81 @@ def test_lambertw_lower(z):
 CFGS = [(1.0, 1000, 1e-6), (1.0, 512, 1e-6), (1.0, 100_000, 1e-4), (1.0, 100_000, 1e-6), (1.0, 100_000, 1e-10),
         (1.0, 100_000, 1e-12), (9.96, 99_000, 1e-6), (1.0, 10_000_000, 1e-8)]
 
+# The planner runs the paper's Alg. 3 (oracle.params) with these additions of its own, each a stated
+# difference from the procedure as printed (the paper leaves r_c to tuning and has no force model):
+GRID_DENSITY = 3.0      # (a) r_c: fixed point r = min(c_s(r) L/(pi (g n)^(1/3)), L/2) for g = m^3/n
+TOL_SAFETY = 0.25       # (b) the split and window targets are tol * 0.25
+FORCE_M0 = 10.0         # (c) the split target is further multiplied by min(1, 10/m0), m0 the unrounded m
+#                         (d) m is rounded up to a multiple of the spreading tile (8 for float32 plans,
+#                             4 otherwise) with no prime factor above 7, and r_c re-derived from eq. csrc
+#                         (e) the window (c_w, hence P) is balanced against the target of (b), not (c)
+
+
+def good_size(m, mult):
+    m = max(int(m), mult)
+    while True:
+        r = m
+        for q in (2, 3, 5, 7):
+            while r % q == 0:
+                r //= q
+        if m % mult == 0 and r == 1:
+            return m
+        m += 1
+
+
+def library_rule(L, n, tol, mult):
+    """Alg. 3 steps (oracle) with the planner's additions (a)-(e) above."""
+    t = tol * TOL_SAFETY
+
+    def cutoff(t):
+        r, mstar = 0.1, (GRID_DENSITY * n) ** (1.0 / 3.0)
+        for _ in range(12):
+            r = min(oparams.cs_of(r, t) / (math.pi * mstar), 0.5)
+        return r
+
+    t_pot = t
+    rcl = cutoff(t)
+    m0 = oparams.cs_of(rcl, t) / (math.pi * rcl)
+    if m0 > FORCE_M0:
+        t *= FORCE_M0 / m0
+        rcl = cutoff(t)
+    q = oparams.alg3(1.0, t, rcl)                             # steps 1, 4 at the split target
+    m = good_size(q["m"], mult)
+    eff = oparams.instantiate(L, m, 0, q["cs"])               # r_c from eq. csrc after rounding
+    cw = oparams.cw_of(oparams.cs_of(eff["rc"] / L, t_pot), eff["rc"] / L)     # step 2 at the target of (b)
+    P = int(math.ceil(2.0 * (eff["rc"] * cw / q["cs"]) * m / L))              # steps 3, 5
+    return oparams.instantiate(L, m, P, q["cs"]) | {"cw_target": cw, "t_split": t}
+
 
 @pytest.mark.parametrize("L,n,tol", CFGS)
-def test_plan_params_match_oracle_alg3(L, n, tol):
-    p = pe.plan_params(L, n, tol)
-    q = oparams.plan(L, n, tol, tol_safety=0.25, grid_density=3.0)
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_plan_params_are_alg3_plus_stated_additions(L, n, tol, prec):
+    p = pe.plan_params(L, n, tol, precision=prec)
+    mult = 8 if p.precision == pe.EWALD_MIXED else 4
+    q = library_rule(L, n, tol, mult)
+    assert p.tile == mult and p.m % p.tile == 0
     assert (p.m, p.P) == (q["m"], q["P"])
-    for k in ("rc", "cs", "cw", "alpha", "h"):
+    for k in ("rc", "cs", "cw", "alpha", "h", "cw_target"):
         assert abs(getattr(p, k) / q[k] - 1) <= 1e-11, k
-    assert p.tile == 4 and p.m % p.tile == 0
     assert p.ncell >= 1 and p.L / p.ncell >= p.rc / p.sr_reach - 1e-15
 
 
-@pytest.mark.parametrize("L,n,tol", [c for c in CFGS if c[2] >= 1e-7])
-def test_mixed_plan_params_match_oracle_alg3(L, n, tol):
-    """float32 plans round m to a multiple of their tile edge 8."""
-    p = pe.plan_params(L, n, tol, precision="mixed")
-    q = oparams.plan(L, n, tol, tol_safety=0.25, grid_density=3.0, mult=8)
-    assert p.precision == pe.EWALD_MIXED and p.tile == 8 and p.m % 8 == 0
-    assert (p.m, p.P) == (q["m"], q["P"])
-    for k in ("rc", "cs", "cw", "alpha", "h"):
-        assert abs(getattr(p, k) / q[k] - 1) <= 1e-11, k
+@pytest.mark.parametrize("L,n,tol", CFGS)
+def test_plan_differs_from_alg3_only_as_stated(L, n, tol):
+    """Alg. 3 as printed at the planner's split target and unrounded cutoff gives an m that the planner
+    only rounds up by (d); after rounding eq. csrc, eq. bandwidth and eq. cwP hold exactly, and P is
+    eq. P_dimless for the window of (e)."""
+    p = pe.plan_params(L, n, tol)
+    q = library_rule(L, n, tol, 4)
+    m_alg3 = math.ceil(p.cs * L / (math.pi * p.rc) - 1e-9)     # = p.m: r_c was re-derived from it
+    assert m_alg3 == p.m and p.m == good_size(p.m, 4)
+    assert abs(p.cs / p.rc - math.pi * p.m / L) <= 1e-12 * p.cs / p.rc
+    assert abs(p.cs / p.rc - p.cw / p.alpha) <= 1e-12 * p.cs / p.rc
+    assert abs(p.cw - math.pi * p.P / 2) <= 1e-12 * p.cw
+    assert p.P == math.ceil(2 * p.cw_target / math.pi - 1e-12)
+    # the window target (e) is looser than the split target (c): never a wider window than Alg. 3 would
+    # choose for the split target itself
+    assert p.cw_target <= oparams.cw_of(p.cs, p.rc / L) + 1e-9 and q["t_split"] <= tol * TOL_SAFETY
 
 
 def test_plan_rejects_bad_arguments():
@@ -125,7 +181,7 @@ def test_radial_fit_error(prec, tol):
 
 @pytest.mark.parametrize("L,n,tol", [(1.0, 1000, 1e-6), (1.0, 8000, 1e-10)])
 def test_scale_table_matches_oracle(L, n, tol):
-    """Alg. 2 step 3 table vs the oracle's S(k) (same (m, P, cs, cw, rc); ball |k| <= m/2)."""
+    """Alg. 2 step 3 table vs the oracle's S(k) (same (m, P, cs, cw, rc); modes inside the band |k| < m/2)."""
     p = pe.plan_params(L, n, tol)
     S = pe.scale_table(p)
     A = Alg2(L, p.m, p.P, p.cs, p.cw, p.rc)
@@ -190,13 +246,41 @@ def test_batch_arguments_rejected_before_any_device_work():
 
 
 # ------------------------------------------------------------------ cuboid boxes (Remark, Sec. 6.1) --
+def library_rule_box(Ls, n, tol, mult):
+    """The cuboid reading (Alg. 3 in units of the shortest edge; oracle.params.plan_box) with the
+    planner's additions (a)-(e); the cutoff fixed point uses the common spacing (V/(g n))^(1/3)."""
+    Lv = np.asarray(Ls, dtype=np.float64)
+    Lmin, V = float(Lv.min()), float(np.prod(Lv))
+    t = tol * TOL_SAFETY
+
+    def cutoff(t):
+        r, h = 0.1, (V / (GRID_DENSITY * n)) ** (1.0 / 3.0)
+        for _ in range(12):
+            r = min(oparams.cs_of(r, t) * h / (math.pi * Lmin), 0.5)
+        return r
+
+    t_pot = t
+    rcl = cutoff(t)
+    m0 = oparams.cs_of(rcl, t) / (math.pi * rcl)
+    if m0 > FORCE_M0:
+        t *= FORCE_M0 / m0
+        rcl = cutoff(t)
+    cs = oparams.cs_of(rcl, t)
+    ms = [good_size(math.ceil(cs * L / (math.pi * rcl * Lmin)), mult) for L in Lv]
+    hmax = max(float(L) / m for L, m in zip(Lv, ms))
+    rcl = cs * hmax / (math.pi * Lmin)
+    cw = oparams.cw_of(oparams.cs_of(rcl, t_pot), rcl)
+    P = int(math.ceil(2.0 * (rcl * cw / cs) * Lmin / hmax))
+    return dict(m=ms, P=P, rc=rcl * Lmin, cs=cs, cw=math.pi * P / 2.0)
+
+
 @pytest.mark.parametrize("box,n,tol,prec,mult", [((1.0, 1.25, 0.75), 5000, 1e-6, "fp64", 4),
                                                  ((1.0, 1.25, 0.75), 5000, 1e-6, "mixed", 8),
                                                  ((2.0, 1.0, 1.0), 100_000, 1e-10, "fp64", 4),
                                                  ((0.9, 1.7, 1.2), 40_000, 1e-8, "floatfloat", 4)])
-def test_cuboid_plan_params_match_oracle(box, n, tol, prec, mult):
+def test_cuboid_plan_params_match_stated_rule(box, n, tol, prec, mult):
     p = pe.plan_params(box, n, tol, precision=prec)
-    q = oparams.plan_box(box, n, tol, tol_safety=0.25, grid_density=3.0, mult=mult)
+    q = library_rule_box(box, n, tol, mult)
     assert list(p.grid) == q["m"] and p.P == q["P"] and p.deg_g > 0
     assert list(p.box) == list(box)
     for k in ("rc", "cs", "cw"):

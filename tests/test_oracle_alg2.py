@@ -8,7 +8,7 @@ from scipy.special import lambertw
 from oracle import exact, params
 from oracle.alg2 import Alg2
 from oracle.pswf import PSWF
-from paper_2602_16591_gb300.workloads import uniform_alternating, uniform_neutral
+from workloads import uniform_alternating, uniform_neutral
 
 
 def _rel(a, b):
@@ -33,27 +33,46 @@ def test_single_charge_dft_is_window_transform():
 
 
 @pytest.mark.parametrize("tol", [1e-4, 1e-6, 1e-8])
-def test_alg2_meets_tolerance(tol):
-    """E8: the fast method with Alg. 3 parameters meets the requested relative tolerance."""
+@pytest.mark.parametrize("rc", [0.2, 0.3])
+def test_alg2_meets_tolerance(tol, rc):
+    """Alg. 3 as printed (with the relative-tolerance reading) gives an error close to tol (Remark after
+    Alg. 3): potential and energy within 2 tol of the converged sum.  The paper has no force model;
+    the forces are bounded loosely here and pinned exactly elsewhere (gradient = -F)."""
     x, rho, L = uniform_alternating(1000, seed=0)
-    p = params.plan(L, len(x), tol, tol_safety=0.25)
+    p = params.plan(L, tol, rc)
     ref = exact.pswf_exact(x, rho, L)
     A = Alg2(L, p["m"], p["P"], p["cs"], p["cw"], p["rc"])
     out = A.total(x, rho)
-    assert _rel(out[0], ref[0]) <= 2 * tol
-    assert _rel(out[3], ref[3]) <= 2 * tol
-    assert abs(out[2] - ref[2]) <= 2 * tol * abs(ref[2])
+    assert 0.3 * tol <= _rel(out[0], ref[0]) <= 2 * tol     # near tol, not far below it
+    assert abs(out[2] - ref[2]) <= 4 * tol * abs(ref[2])
+    assert _rel(out[3], ref[3]) <= 10 * tol
 
 
-def test_cube_corners_are_unstable_ball_is_not():
-    """Deconvolving the corners of I_m amplifies rounding (reading recorded in the design doc)."""
+@pytest.mark.parametrize("tol", [1e-3, 1e-4])
+def test_cube_of_alg2_agrees_with_band_where_stable(tol):
+    """Alg. 2 as printed scales every mode of the cube I_m.  Where that is numerically stable (loose
+    tolerances) it agrees with the band-limited reading within the tolerance, and both meet it."""
     x, rho, L = uniform_neutral(1500, seed=1)
-    p = params.plan(L, len(x), 1e-8, tol_safety=0.25)
     ref = exact.pswf_exact(x, rho, L)
-    cube = Alg2(L, p["m"], p["P"], p["cs"], p["cw"], p["rc"], ball=False).total(x, rho)
-    ball = Alg2(L, p["m"], p["P"], p["cs"], p["cw"], p["rc"], ball=True).total(x, rho)
-    assert _rel(ball[0], ref[0]) <= 2e-8
-    assert _rel(cube[0], ref[0]) > 1e3 * _rel(ball[0], ref[0])
+    for rc in (0.15, 0.25):
+        p = params.plan(L, tol, rc)
+        cube = Alg2(L, p["m"], p["P"], p["cs"], p["cw"], p["rc"], modes="cube").total(x, rho)
+        band = Alg2(L, p["m"], p["P"], p["cs"], p["cw"], p["rc"]).total(x, rho)
+        assert _rel(cube[0], ref[0]) <= 2 * tol
+        assert _rel(band[0], ref[0]) <= 2 * tol
+        assert _rel(cube[0], band[0]) <= 2 * tol
+
+
+def test_cube_corners_are_unstable_band_is_not():
+    """Deconvolving the corners of I_m amplifies rounding: the whole cube of Alg. 2 as printed loses
+    every digit at tol 1e-8, the modes inside the mollifier's band do not."""
+    x, rho, L = uniform_neutral(1500, seed=1)
+    p = params.plan(L, 1e-8, 0.2)
+    ref = exact.pswf_exact(x, rho, L)
+    cube = Alg2(L, p["m"], p["P"], p["cs"], p["cw"], p["rc"], modes="cube").total(x, rho)
+    band = Alg2(L, p["m"], p["P"], p["cs"], p["cw"], p["rc"], modes="band").total(x, rho)
+    assert _rel(band[0], ref[0]) <= 2e-8
+    assert _rel(cube[0], ref[0]) > 1e3 * _rel(band[0], ref[0])
 
 
 def test_error_models_match_measured_split_error():
@@ -102,33 +121,29 @@ def test_params_lambert_equations():
 
 
 def test_params_structure():
-    for n, tol in [(1000, 1e-6), (100_000, 1e-6), (100_000, 1e-10), (10_000_000, 1e-8)]:
-        p = params.plan(1.0, n, tol)
-        m = p["m"]
-        r = m
-        for q in (2, 3, 5, 7):
-            while r % q == 0:
-                r //= q
-        assert r == 1 and m % 4 == 0
-        assert abs(p["cs"] / p["rc"] - math.pi * m / p["L"]) < 1e-9 * p["cs"] / p["rc"]
-        assert abs(p["cs"] / p["rc"] - p["cw"] / p["alpha"]) < 1e-9 * p["cs"] / p["rc"]
-        assert p["P"] == math.ceil(2 * p["cw_target"] / math.pi - 1e-12)
-        assert p["rc"] <= 0.5 * p["L"]
+    """Alg. 3 steps 3-5 and the instantiation reading: eq. csrc and eq. bandwidth hold exactly after
+    rounding, P follows eq. P_dimless from the unrounded window, c_w = pi P/2 (eq. cwP)."""
+    for tol, rc in [(1e-4, 0.1), (1e-6, 0.05), (1e-10, 0.2), (1e-8, 0.026)]:
+        q = params.alg3(1.0, tol, rc)
+        assert q["m"] == math.ceil(q["cs"] / (math.pi * rc))
+        assert q["P"] == math.ceil(2 * q["alpha"] * q["m"])
+        assert abs(q["alpha"] - rc * q["cw"] / q["cs"]) < 1e-15
+        p = params.plan(1.0, tol, rc)
+        assert p["m"] % 2 == 0 and q["m"] <= p["m"] <= q["m"] + 1
+        assert abs(p["cs"] / p["rc"] - math.pi * p["m"] / p["L"]) < 1e-12 * p["cs"] / p["rc"]
+        assert abs(p["cs"] / p["rc"] - p["cw"] / p["alpha"]) < 1e-12 * p["cs"] / p["rc"]
+        assert p["P"] == math.ceil(2 * (rc * q["cw"] / q["cs"]) * p["m"] - 1e-12)
+        assert p["rc"] <= rc and abs(p["cw"] - math.pi * p["P"] / 2) < 1e-15
 
 
-def test_kappa_against_direct_sum():
-    K = 40
-    r = np.arange(-K, K + 1)
-    k2 = (r[:, None, None] ** 2 + r[None, :, None] ** 2 + r[None, None, :] ** 2).ravel()
-    k2 = k2[(k2 > 0) & (k2 <= K * K)].astype(float)
-    direct = np.sum(1.0 / k2 ** 2) + 4 * math.pi / K
-    assert abs(direct / math.pi ** 2 / params.KAPPA - 1) < 2e-3
-
-
-def test_lambertw_branches():
-    z = -2 * params.KAPPA * 1e-12 / params.A_W ** 2
-    w = float(np.real(lambertw(z, -1)))
-    assert w < -1 and abs(w * math.exp(w) / z - 1) < 1e-12
+def test_alg3_worked_numbers():
+    """Numbers the paper states about Alg. 3: A_s/A_w = 4 sqrt(5)/pi^(3/2) ~ 1.61 (Sec. 6.3), and with
+    c_s = log(1/eps) and r_c = 0.1 (Table 3's setting) steps 4-5 give the bandlimit-sized m, i.e. within
+    a few modes of the smallest m Table 3 reports (42 at 1e-6, 72 at 1e-10)."""
+    assert abs(params.A_S / params.A_W - 4 * math.sqrt(5) / math.pi ** 1.5) < 0.01
+    for eps, m_table in ((1e-6, 42), (1e-10, 72)):
+        q = params.alg3(1.0, eps, 0.1, cs=math.log(1 / eps))
+        assert m_table <= q["m"] <= m_table + 3
 
 
 # ------------------------------------------------------------------ cuboid boxes (Remark, Sec. 6.1) --
@@ -140,7 +155,7 @@ def test_cuboid_alg2_supercell_equals_cube():
     x = rng.random((60, 3))
     q = rng.uniform(-1, 1, 60)
     q -= q.mean()
-    p = op.plan(1.0, 60, 1e-6, grid_density=8.0)
+    p = op.plan(1.0, 1e-6, 0.35)
     A = Alg2(1.0, p["m"], p["P"], p["cs"], p["cw"], p["rc"])
     phi, grad, E, F = A.total(x, q)
     B = Alg2((1.0, 1.0, 2.0), (p["m"], p["m"], 2 * p["m"]), p["P"], p["cs"], p["cw"], p["rc"])
@@ -154,26 +169,26 @@ def test_cuboid_alg2_supercell_equals_cube():
 
 @pytest.mark.parametrize("tol", [1e-4, 1e-6, 1e-8])
 def test_cuboid_alg2_meets_tolerance(tol):
-    """The cuboid plan rule (oracle params.plan_box) meets tol against the converged cuboid sum."""
+    """Alg. 3 for a cuboid (reading: units of the shortest edge) meets tol against the converged sum."""
     from oracle import params as op
     Lv = (1.0, 1.25, 0.75)
     rng = np.random.default_rng(8)
     x = rng.random((400, 3)) * np.array(Lv)
     q = rng.uniform(-1, 1, 400)
     q -= q.mean()
-    p = op.plan_box(Lv, 400, tol, grid_density=3.0, tol_safety=0.25)
+    p = op.plan_box(Lv, tol, 0.3)
     assert len(set(p["m"])) >= 2          # a genuinely anisotropic grid
     A = Alg2(Lv, p["m"], p["P"], p["cs"], p["cw"], p["rc"])
     phi, grad, E, F = A.total(x, q)
     ref = exact.pswf_exact(x, q, Lv)
     rel = lambda a, b: np.linalg.norm(a - b) / np.linalg.norm(b)  # noqa: E731
-    assert rel(phi, ref[0]) <= tol
-    assert rel(F, ref[3]) <= 2 * tol
+    assert rel(phi, ref[0]) <= 2 * tol
+    assert rel(F, ref[3]) <= 10 * tol
 
 
 def test_cuboid_plan_reduces_to_cube():
     from oracle import params as op
     for tol in (1e-4, 1e-8):
-        a = op.plan(1.3, 5000, tol, grid_density=3.0, tol_safety=0.25)
-        b = op.plan_box((1.3, 1.3, 1.3), 5000, tol, grid_density=3.0, tol_safety=0.25)
+        a = op.plan(1.3, tol, 0.2)
+        b = op.plan_box((1.3, 1.3, 1.3), tol, 0.2)
         assert b["m"] == [a["m"]] * 3 and b["P"] == a["P"] and b["rc"] == a["rc"]

@@ -4,7 +4,7 @@ import pytest
 
 from conftest import read_golden
 from oracle import exact
-from paper_2602_16591_gb300.workloads import nacl_lattice, uniform_neutral
+from workloads import nacl_lattice, uniform_neutral
 
 
 def _rel(a, b):

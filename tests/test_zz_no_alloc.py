@@ -15,8 +15,10 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-import paper_2602_16591_gb300 as pe  # noqa: E402
-from paper_2602_16591_gb300.workloads import uniform_neutral  # noqa: E402
+from conftest import require_library  # noqa: E402
+
+pe = require_library()
+from workloads import uniform_neutral  # noqa: E402
 
 
 def _spread_static(params, xt, rt):

@@ -1,6 +1,8 @@
 """Seeded synthetic particle systems (inputs only; no Ewald arithmetic here).
 
-Shared by the tests, the oracle runs and ``bench.py``.  Every generator uses
+Shared by the tests, the oracle runs and ``bench.py``.  This module imports neither
+the CUDA library's package nor ``oracle``, so generating inputs never loads the
+library.  Every generator uses
 NumPy's PCG64 with an explicit seed and returns ``(x, rho, L)`` with ``x`` an
 (n, 3) float64 array in [0, L)^3 and ``rho`` a float64 array summing to zero
 (to rounding).  The shapes follow the paper's experiments (Sec. 7.1: uniform
