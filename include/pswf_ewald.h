@@ -252,20 +252,28 @@ int ewald_scale_table(const ewald_params* p, double* S);
  * Spreads n = p->n charges (Alg. 2 step 1, float64 arithmetic) onto the
  * caller's grid: x (n,3) and rho (n) float64 DEVICE pointers as in ewald_eval,
  * grid an m^3 float64 DEVICE array (z fastest) that receives a_l.  p holds the
- * parameters of ewald_plan_params / ewald_plan_query (any precision; the
- * window degree p->deg_w is used as given).  Asynchronous on `stream`.
+ * parameters of ewald_plan_params / ewald_plan_query for an EWALD_FP64 or
+ * EWALD_FLOATFLOAT plan (tile 4; parameters of an EWALD_MIXED plan, tile 8,
+ * are rejected with their own message); the window degree p->deg_w is used as
+ * given.  The result equals the spread grid of ewald_eval for the same plan
+ * bit for bit.  Asynchronous on `stream`.  The inputs are not checked: a
+ * non-finite position spreads its charge at the origin and a non-finite
+ * charge spreads nothing, without an error code (ewald_eval reports both).
  *
  * Scratch: a fixed 64 MiB array in the library's device image (every GPU that
  * loads the library holds it until the process exits).  Problems needing more
- * (roughly 120 n bytes plus 8 (m/4)^3 (P+3)^3 bytes) return EWALD_ETOOBIG.
+ * (about 104 n bytes plus 8 (m/4)^3 (P+3)^3 bytes plus 8 KB) return EWALD_ETOOBIG.
  * No cudaMalloc, cudaFree or other allocating call is made.  The first call on
  * each device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  All
- * calls share the one array and it keeps the previous call's contents (the
+ * that device current; make that first call before any stream capture.  The
+ * fitted window table stays in the array: a call with the same (c_w, P, deg_w)
+ * as the previous one on that device skips the host fit and the table copy.
+ * All calls share the one array and it keeps the previous call's contents (the
  * entry point clears what must start at zero), so calls whose GPU work
  * overlaps -- on different streams or host threads -- race and must be
  * serialised by the caller.  Errors: EWALD_EINVAL (NULL pointer, parameters
- * not from the planner), EWALD_ETOOBIG (scratch limit), EWALD_ECUDA. */
+ * not from the planner or of a tile-8 plan), EWALD_ETOOBIG (scratch limit),
+ * EWALD_ECUDA. */
 int ewald_spread_static(const ewald_params* p, const double* x, const double* rho, double* grid, void* stream);
 
 const char* ewald_error_string(int code);

@@ -165,6 +165,7 @@ struct ewald_plan_s {
     size_t m3 = 0, nspec = 0;   // grid points, half-spectrum modes
     // workspace
     int* key_rank = nullptr;
+    int* perm = nullptr;       // bin lists of the stable counting sort (tile order, then cell order)
     int* tile_cnt = nullptr;
     int* tile_off = nullptr;
     int* cell_cnt = nullptr;
@@ -238,7 +239,7 @@ struct ewald_plan_s {
     }
 
     ~ewald_plan_s() {
-        void* bufs[] = {key_rank, zeroed, tile_off, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, sr_lo, sr_f32, sr_cz, grid_ff, sr_cols, scratch,
+        void* bufs[] = {key_rank, perm, zeroed, tile_off, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, sr_lo, sr_f32, sr_cz, grid_ff, sr_cols, scratch,
                         grid_a, grid_b, spec, wcoef, dwcoef, p1c, qc, iw, mtab, gcoef, phi_int, f_int, epart,
                         energy_d, x_stage, rho_stage};
         for (void* b : bufs)
@@ -340,6 +341,14 @@ cudaError_t launch_short(ewald_plan p, const pswf::Vec4<real>* sr_rec, const psw
     return launch_short_d<real, 60>(p, sr_rec, sr_lo, phi, f, s);
 }
 
+// Input-order ranks inside every tile and cell (k_place, k_rerank), after the counting scan.
+cudaError_t stable_ranks(ewald_plan p, cudaStream_t s) {
+    const int n = p->g.n, tb = 256, nb = (n + tb - 1) / tb;
+    pswf::k_place<<<nb, tb, 0, s>>>(p->key_rank, n, p->tile_off, p->cell_off, p->perm);
+    pswf::k_rerank<<<dim3(nb, 2), tb, 0, s>>>(p->key_rank, n, p->tile_off, p->cell_off, p->perm);
+    return cudaGetLastError();
+}
+
 template <typename real, typename cplx>
 int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, double* f, cudaStream_t s) {
     using pswf::Vec4;
@@ -352,6 +361,7 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     PSWF_CUDA(cudaGetLastError());
     pswf::k_scan<<<2, 1024, 0, s>>>(p->tile_cnt, p->tile_off, p->ntiles, p->cell_cnt, p->cell_off, p->ncells);
     PSWF_CUDA(cudaGetLastError());
+    PSWF_CUDA(stable_ranks(p, s));
     auto* sp_rec = static_cast<Vec4<real>*>(p->sp_rec);
     auto* sr_rec = static_cast<Vec4<real>*>(p->sr_rec);
     auto* sr_lo = static_cast<Vec4<real>*>(p->sr_lo);
@@ -464,6 +474,7 @@ int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* ph
     PSWF_CUDA(cudaGetLastError());
     pswf::k_scan<<<2, 1024, 0, s>>>(p->tile_cnt, p->tile_off, p->ntiles, p->cell_cnt, p->cell_off, p->ncells);
     PSWF_CUDA(cudaGetLastError());
+    PSWF_CUDA(stable_ranks(p, s));
     auto* sp_h = static_cast<float4*>(p->sp_rec);
     auto* sp_l = sp_h + nn;
     auto* sr_h = static_cast<float4*>(p->sr_rec);
@@ -737,6 +748,7 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
     const size_t m3 = p->m3, nspec = p->nspec;
     struct A { void** ptr; size_t bytes; } allocs[] = {
         {reinterpret_cast<void**>(&p->key_rank), sizeof(int4) * n},
+        {reinterpret_cast<void**>(&p->perm), sizeof(int) * 2 * n},
         {&p->zeroed, sizeof(double) * 4 + sizeof(int) * (((p->ntiles + 1 + 3) / 4) * 4 + p->ncells + 1)},
         {reinterpret_cast<void**>(&p->tile_off), sizeof(int) * (p->ntiles + 1)},
         {reinterpret_cast<void**>(&p->cell_off), sizeof(int) * (p->ncells + 1)},

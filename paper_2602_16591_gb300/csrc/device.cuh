@@ -287,6 +287,43 @@ static __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cn
     if (threadIdx.x == 0) off[N] = carry;
 }
 
+// ---- stable order inside tiles and cells (counting sort, deterministic ranks) --------------------
+// k_prep's atomic ranks depend on the schedule, and so would every sum over the particles of a tile
+// or cell (spreading, the real-space sum).  k_place lists each bin's particles at their atomic
+// positions (perm: tile order in [0, n), cell order in [n, 2n)); k_rerank then replaces every atomic
+// rank by the number of particles of the same bin with a smaller input index, so the scatter writes
+// each bin in input order and an evaluation is bitwise repeatable.  The rank loop of k_rerank reads
+// the bin's list once per position; consecutive positions mostly share a bin, so the loads are warp
+// broadcasts (a bin of b particles costs b^2 / 32 warp loads).
+static __global__ void __launch_bounds__(256) k_place(const int* __restrict__ key_rank, int n,
+                                                      const int* __restrict__ tile_off,
+                                                      const int* __restrict__ cell_off, int* __restrict__ perm) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int4 kr = reinterpret_cast<const int4*>(key_rank)[i];
+    perm[tile_off[kr.x] + kr.y] = i;
+    perm[static_cast<size_t>(n) + cell_off[kr.z] + kr.w] = i;
+}
+
+// blockIdx.y = 0: tile ranks (key_rank .x/.y), 1: cell ranks (.z/.w).  Each thread owns one position
+// of the bin lists; it writes only the rank word of its own particle.
+static __global__ void __launch_bounds__(256) k_rerank(int* __restrict__ key_rank, int n,
+                                                       const int* __restrict__ tile_off,
+                                                       const int* __restrict__ cell_off,
+                                                       const int* __restrict__ perm) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int kind = blockIdx.y;
+    const int* list = perm + (kind ? static_cast<size_t>(n) : 0);
+    const int* off = kind ? cell_off : tile_off;
+    const int i = list[p];
+    const int key = key_rank[4 * static_cast<size_t>(i) + 2 * kind];
+    const int s = off[key], e = off[key + 1];
+    int r = 0;
+    for (int q = s; q < e; ++q) r += list[q] < i ? 1 : 0;
+    key_rank[4 * static_cast<size_t>(i) + 2 * kind + 1] = r;
+}
+
 // Sorted records.  Spreading side (tile order): {z0, z1, z2, rho}, {packed offsets in tile, original index}.
 // Real-space side (cell order): {local x, y, z, rho}, {cell id, original index}.
 template <typename real>
@@ -877,18 +914,37 @@ struct ShortParams {
     float rc2f;
 };
 
-// float32 plans.  7 resident blocks per SM (<= 73 registers; measured best).
+// float32 plans.  One warp per target cell; targets in passes of up to kShortMT.  Two stages per chunk
+// of 32 candidates of the cell's neighbourhood:
+//   test    each lane takes one candidate and tests it against every target of the pass in float32 on
+//           the high parts of the coordinates, with the cutoff enlarged by 1e-4 (rc2f); each passing
+//           (candidate, target) pair is appended to the warp's pair queue in shared memory (warp scan of
+//           the per-lane counts: the order is fixed by the candidate order, not by the schedule);
+//   drain   whenever 32 or more pairs wait (and once more at the end), each lane evaluates one queued
+//           pair in full: float-float displacement, exact cutoff test, R and -R'/r by Horner, and adds
+//           the result to its own slot of that target's accumulators in shared memory (a lane owns its
+//           slots, so no atomics are needed and the order of the additions is fixed).
+// The pair arithmetic thus runs in full warps whatever the fraction of candidates inside the cutoff
+// (~25% of a cell's neighbourhood at reach 2), and targets cost nothing beyond their own pairs and one
+// reduction.  Queue entries: {record index, target | shift indices << 8}.
+constexpr int kShortMT = 4;                   // targets per pass
+constexpr int kShortQ = 256;                  // queue ring (>= 32 left over + 32 * kShortMT per chunk)
+static_assert(kShortQ >= 32 + 32 * kShortMT && (kShortQ & (kShortQ - 1)) == 0, "queue ring size");
+
 template <int D>
-__global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<float>* __restrict__ rec, const int2* __restrict__ idx,
+__global__ void __launch_bounds__(32 * kShortWarps) k_short(const Vec4<float>* __restrict__ rec, const int2* __restrict__ idx,
                                                             const Vec4<float>* __restrict__ lo,
                                                             const int* __restrict__ cell_off, const int4* __restrict__ cols,
                                                             int ncols, int rcap, Geom g, const __grid_constant__ ShortParams<float, D> kp,
                                                             float* __restrict__ phi_out, float* __restrict__ f_out) {
-    constexpr int NSH = 2 * kShortMaxR + 1;
+    constexpr int NSH = 2 * kShortMaxR + 1, MT = kShortMT, QM = kShortQ - 1;
+    static_assert(NSH <= 16, "queue entries pack 4-bit shift indices");
     __shared__ float sh_hi[3][NSH], sh_lo[3][NSH];   // cell shifts (k - R) w_d, hi and lo parts
     __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
-    __shared__ __align__(16) float stx[kShortWarps][kShortMaxT][4];   // target position (hi parts) and charge
-    __shared__ __align__(16) float stl[kShortWarps][kShortMaxT][4];   // lo parts of the position
+    __shared__ __align__(16) float4 sth[kShortWarps][MT];        // target position (hi parts) and charge
+    __shared__ __align__(16) float4 stl[kShortWarps][MT];        // lo parts of the target position
+    __shared__ __align__(16) float4 sacc[kShortWarps][MT][32];   // per-lane partial {phi, grad} per target
+    __shared__ int2 que[kShortWarps][kShortQ];
     const int R = g.reach;
     for (int k = threadIdx.x; k < 3 * (2 * R + 1); k += blockDim.x) {
         const int d = k / (2 * R + 1), i = k % (2 * R + 1);
@@ -907,110 +963,130 @@ __global__ void __launch_bounds__(32 * kShortWarps, 7) k_short(const Vec4<float>
     extern __shared__ __align__(16) unsigned char short_dyn[];
     int4* rng = reinterpret_cast<int4*>(short_dyn) + warp * rcap;
     int* pos = reinterpret_cast<int*>(reinterpret_cast<int4*>(short_dyn) + kShortWarps * rcap) + warp * (rcap + 1);
+    int2* q = que[warp];
 
     const int total = short_ranges(scol, ncols, cell_off, g.ncell, cx, cy, cz, lane, rcap, rng, pos);
 
-    for (int t0 = tb; t0 < te; t0 += kShortMaxT) {
-        const int nt = min(kShortMaxT, te - t0);
-        // targets: exact parts and float32 test copies in shared memory (broadcast reads)
+    for (int t0 = tb; t0 < te; t0 += MT) {
+        const int nt = min(MT, te - t0);
         __syncwarp();
         if (lane < nt) {
             const Vec4<float> a = rec[t0 + lane];
-            stx[warp][lane][0] = a.x;
-            stx[warp][lane][1] = a.y;
-            stx[warp][lane][2] = a.z;
-            stx[warp][lane][3] = a.w;
             const Vec4<float> l = lo[t0 + lane];
-            stl[warp][lane][0] = l.x;
-            stl[warp][lane][1] = l.y;
-            stl[warp][lane][2] = l.z;
+            sth[warp][lane] = make_float4(a.x, a.y, a.z, a.w);
+            stl[warp][lane] = make_float4(l.x, l.y, l.z, 0.f);
         }
+#pragma unroll
+        for (int t = 0; t < MT; ++t) sacc[warp][t][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
         __syncwarp();
-        float acc[kShortMaxT][4];
+        float tx[MT], ty[MT], tz[MT];
 #pragma unroll
-        for (int t = 0; t < kShortMaxT; ++t) acc[t][0] = acc[t][1] = acc[t][2] = acc[t][3] = 0.f;
-        int r = 0;
-        for (int s0 = 0; s0 < total; s0 += 32) {
-            const int p = s0 + lane;
-            if (p >= total) continue;
-            while (pos[r + 1] <= p) ++r;
-            const int4 rg = rng[r];
-            const int j = rg.x + (p - pos[r]);
-            float sfx, sfy, sfz, szc, sq;
-            const Vec4<float> a = rec[j];
-            sfx = a.x; sfy = a.y; sfz = a.z; sq = a.w;
-            szc = lo[j].w;
-            const int4 col = scol[rg.w];
-            const int ix = col.x + R, iy = col.y + R, iz = rg.z + (__float_as_int(szc) - rg.y) + R;
-            const float px = sfx + sh_hi[0][ix], py = sfy + sh_hi[1][iy], pz = sfz + sh_hi[2][iz];
-            bool loaded = false;
-            float qj = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+        for (int t = 0; t < MT; ++t) {
+            const float4 v = sth[warp][t < nt ? t : 0];
+            tx[t] = v.x;
+            ty[t] = v.y;
+            tz[t] = v.z;
+        }
+        int head = 0, tail = 0, r = 0;   // queue pointers (warp-uniform), range cursor of this lane
+        for (int s0 = 0;; s0 += 32) {
+            const bool fin = s0 >= total;
+            if (!fin) {
+                // test: candidate p against the targets of the pass (float32 on the high parts)
+                const int p = s0 + lane;
+                unsigned mask = 0u;
+                int j = 0, code = 0;
+                if (p < total) {
+                    while (pos[r + 1] <= p) ++r;
+                    const int4 rg = rng[r];
+                    j = rg.x + (p - pos[r]);
+                    const Vec4<float> a = rec[j];
+                    const int czj = __float_as_int(lo[j].w);
+                    const int4 col = scol[rg.w];
+                    const int ix = col.x + R, iy = col.y + R, iz = rg.z + (czj - rg.y) + R;
+                    code = (ix << 8) | (iy << 12) | (iz << 16);
+                    const float px = a.x + sh_hi[0][ix], py = a.y + sh_hi[1][iy], pz = a.z + sh_hi[2][iz];
 #pragma unroll
-            for (int t = 0; t < kShortMaxT; ++t) {
-                if (t >= nt) break;   // nt is warp-uniform
-                const float4 tt = *reinterpret_cast<const float4*>(stx[warp][t]);   // broadcast
-                const float dxf = tt.x - px, dyf = tt.y - py, dzf = tt.z - pz;
-                const float r2f = dxf * dxf + dyf * dyf + dzf * dzf;
-                if (r2f < kp.rc2f && r2f > 0.f) {
-                    if (!loaded) {
-                        loaded = true;
-                        const Vec4<float> l = lo[j];
-                        qj = sq;
-                        ex = l.x + sh_lo[0][ix];
-                        ey = l.y + sh_lo[1][iy];
-                        ez = l.z + sh_lo[2][iz];
-                    }
-                    const float4 tl = *reinterpret_cast<const float4*>(stl[warp][t]);
-                    float ddx, ddy, ddz;
-                    ddx = dxf + (tl.x - ex);
-                    ddy = dyf + (tl.y - ey);
-                    ddz = dzf + (tl.z - ez);
-                    const float r2 = ddx * ddx + ddy * ddy + ddz * ddz;
-                    if (r2 < kp.rc2 && r2 > 0.f) {
-                        const float u = fma(r2, kp.two_over_rc2, float(-1));
-                        float p1 = kp.p1[D], qq = kp.q[D];
-#pragma unroll
-                        for (int kk = D - 1; kk >= 0; --kk) {
-                            p1 = fma(p1, u, kp.p1[kk]);
-                            qq = fma(qq, u, kp.q[kk]);
-                        }
-                        const float ri = rsqrtf(r2);
-                        acc[t][0] = fma(qj, ri - p1, acc[t][0]);
-                        const float cf = qj * fma(ri * ri, ri, qq);
-                        acc[t][1] = fma(cf, ddx, acc[t][1]);
-                        acc[t][2] = fma(cf, ddy, acc[t][2]);
-                        acc[t][3] = fma(cf, ddz, acc[t][3]);
+                    for (int t = 0; t < MT; ++t) {
+                        if (t >= nt) break;   // warp-uniform
+                        const float dx = tx[t] - px, dy = ty[t] - py, dz = tz[t] - pz;
+                        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < kp.rc2f) mask |= 1u << t;
                     }
                 }
-            }
-        }
-        // reduce each target's partial sums over the lanes; lane t writes target t
+                // append this lane's pairs after those of the lanes below it
+                const int cnt = __popc(mask);
+                int incl = cnt;
 #pragma unroll
-        for (int t = 0; t < kShortMaxT; ++t) {
-#pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                float x = acc[t][v];
-                for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-                acc[t][v] = x;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                int slot = tail + incl - cnt;
+                while (mask) {
+                    const int t = __ffs(mask) - 1;
+                    mask &= mask - 1u;
+                    q[slot & QM] = make_int2(j, code | t);
+                    ++slot;
+                }
+                tail += __shfl_sync(0xffffffffu, incl, 31);
+                __syncwarp();
             }
-        }
-        float mine[4] = {0.f, 0.f, 0.f, 0.f};
+            // drain: one queued pair per lane, full warps (the final round takes what is left)
+            while (tail - head >= 32 || (fin && tail > head)) {
+                const int k = head + lane;
+                const bool act = k < tail;
+                const int2 e = q[(act ? k : head) & QM];
+                const int t = e.y & 0xff, ix = (e.y >> 8) & 15, iy = (e.y >> 12) & 15, iz = (e.y >> 16) & 15;
+                const Vec4<float> a = rec[e.x];
+                const Vec4<float> l = lo[e.x];
+                const float4 th = sth[warp][t], tl = stl[warp][t];
+                // d = (hi_t - (hi_j + s_hi)) + ((lo_t - lo_j) - s_lo): a close pair across a cell face keeps
+                // its relative precision
+                const float ddx = (th.x - (a.x + sh_hi[0][ix])) + ((tl.x - l.x) - sh_lo[0][ix]);
+                const float ddy = (th.y - (a.y + sh_hi[1][iy])) + ((tl.y - l.y) - sh_lo[1][iy]);
+                const float ddz = (th.z - (a.z + sh_hi[2][iz])) + ((tl.z - l.z) - sh_lo[2][iz]);
+                const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+                const bool in = act && r2 < kp.rc2 && r2 > 0.f;
+                const float u = fmaf(r2, kp.two_over_rc2, float(-1));
+                float p1 = kp.p1[D], qq = kp.q[D];
 #pragma unroll
-        for (int t = 0; t < kShortMaxT; ++t) {
-            if (lane == t) {
-                mine[0] = acc[t][0];
-                mine[1] = acc[t][1];
-                mine[2] = acc[t][2];
-                mine[3] = acc[t][3];
+                for (int kk = D - 1; kk >= 0; --kk) {
+                    p1 = fmaf(p1, u, kp.p1[kk]);
+                    qq = fmaf(qq, u, kp.q[kk]);
+                }
+                const float ri = rsqrtf(in ? r2 : 1.f);
+                const float qj = in ? a.w : 0.f;
+                const float cf = qj * fmaf(ri * ri, ri, qq);
+                if (act) {
+                    float4 s = sacc[warp][t][lane];
+                    s.x = fmaf(qj, ri - p1, s.x);
+                    s.y = fmaf(cf, ddx, s.y);
+                    s.z = fmaf(cf, ddy, s.z);
+                    s.w = fmaf(cf, ddz, s.w);
+                    sacc[warp][t][lane] = s;
+                }
+                head += min(32, tail - head);
             }
+            if (fin) break;
         }
-        if (lane < nt) {   // float32 results; k_combine_energy widens them with full warps
-            const int oi = idx[t0 + lane].y;
-            const float qi = stx[warp][lane][3];
-            phi_out[oi] = mine[0];
-            f_out[3 * static_cast<size_t>(oi) + 0] = qi * mine[1];
-            f_out[3 * static_cast<size_t>(oi) + 1] = qi * mine[2];
-            f_out[3 * static_cast<size_t>(oi) + 2] = qi * mine[3];
+        __syncwarp();
+        // per target: sum the 32 lanes' slots; lane 0 writes (float32 results, widened by k_combine_energy)
+        for (int t = 0; t < nt; ++t) {
+            float4 s = sacc[warp][t][lane];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
+                s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+                s.z += __shfl_xor_sync(0xffffffffu, s.z, o);
+                s.w += __shfl_xor_sync(0xffffffffu, s.w, o);
+            }
+            if (lane == 0) {
+                const int oi = idx[t0 + t].y;
+                const float qi = sth[warp][t].w;
+                phi_out[oi] = s.x;
+                f_out[3 * static_cast<size_t>(oi) + 0] = qi * s.y;
+                f_out[3 * static_cast<size_t>(oi) + 1] = qi * s.z;
+                f_out[3 * static_cast<size_t>(oi) + 2] = qi * s.w;
+            }
         }
     }
 }

@@ -34,6 +34,16 @@ constexpr int kMaxDevices = 64;
 std::mutex g_addr_mu;
 void* g_addr[kMaxDevices] = {nullptr};
 
+// The window table sits at the start of the array (offset 0, sized for the largest P and degree) and
+// stays there between calls: a call whose (c_w, P, deg_w) equal the table already in place on this
+// device neither refits the window on the host nor copies it.
+struct TableKey {
+    bool valid = false;
+    double cw = 0.0;
+    int P = 0, deg_w = 0;
+};
+TableKey g_table[kMaxDevices];
+
 int fail_static(int code, const std::string& msg) {
     pswf::record_error(msg);   // reported by ewald_last_error()
     return code;
@@ -47,6 +57,9 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
                                    void* stream) {
     if (!p || !x || !rho || !grid) return fail_static(EWALD_EINVAL, "NULL argument");
     if (p->n < 1 || p->n > (int64_t(1) << 30)) return fail_static(EWALD_EINVAL, "particle count out of range");
+    if (p->tile == pswf::kTile32)
+        return fail_static(EWALD_EINVAL, "parameters of a float32 (EWALD_MIXED, tile 8) plan: ewald_spread_static "
+                                         "takes the parameters of EWALD_FP64 or EWALD_FLOATFLOAT plans (tile 4)");
     if (p->P < pswf::kPMin || p->P > pswf::kPMax || p->tile != pswf::kTile64 || p->m % p->tile != 0 ||
         p->deg_w < 1 || p->deg_w > pswf::kDegWMax || !(p->L > 0) || !(p->alpha > 0))
         return fail_static(EWALD_EINVAL, "parameters do not come from ewald_plan_params");
@@ -58,16 +71,17 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
     const int64_t n = p->n;
     const int m = p->m, P = p->P, T = p->tile, nt = m / T, E = T + P - 1;
     const size_t ntiles = size_t(nt) * nt * nt;
+    const size_t need_coef = align256(sizeof(double) * pswf::kPMax * (pswf::kDegWMax + 1));   // fixed slot
     const size_t need_key = align256(sizeof(int4) * n);
+    const size_t need_perm = align256(sizeof(int) * 2 * n);
     const size_t need_tcnt = align256(sizeof(int) * (ntiles + 1));
     const size_t need_ccnt = align256(sizeof(int) * 2);
     const size_t need_status = align256(sizeof(double) * 4);
     const size_t need_rec = align256(sizeof(pswf::Vec4<double>) * n);
     const size_t need_idx = align256(sizeof(int2) * n);
     const size_t need_slab = align256(sizeof(double) * ntiles * size_t(E) * E * E);
-    const size_t need_coef = align256(sizeof(double) * P * (p->deg_w + 1));
-    const size_t need = need_key + 2 * need_tcnt + 2 * need_ccnt + need_status + 2 * need_rec + 2 * need_idx +
-                        need_slab + need_coef;
+    const size_t need = need_coef + need_key + need_perm + 2 * need_tcnt + 2 * need_ccnt + need_status +
+                        2 * need_rec + 2 * need_idx + need_slab;
     if (need > kStaticScratchBytes)
         return fail_static(EWALD_ETOOBIG, "ewald_spread_static needs " + std::to_string(need) +
                                               " bytes of scratch; its static array holds " +
@@ -96,7 +110,9 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
         cur += b;
         return r;
     };
+    double* coef = reinterpret_cast<double*>(take(need_coef));
     int* key_rank = reinterpret_cast<int*>(take(need_key));
+    int* perm = reinterpret_cast<int*>(take(need_perm));
     int* tile_cnt = reinterpret_cast<int*>(take(need_tcnt));
     int* tile_off = reinterpret_cast<int*>(take(need_tcnt));
     int* cell_cnt = reinterpret_cast<int*>(take(need_ccnt));
@@ -107,19 +123,26 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
     int2* sp_idx = reinterpret_cast<int2*>(take(need_idx));
     int2* sr_idx = reinterpret_cast<int2*>(take(need_idx));
     double* slab = reinterpret_cast<double*>(take(need_slab));
-    double* coef = reinterpret_cast<double*>(take(need_coef));
 
-    // ---- window polynomial table (host fit, copied into the static array)
-    std::vector<double> wc;
-    try {
-        const pswf::Prolate pw(p->cw);
-        wc = pswf::fit_window(pw, P, p->deg_w, false, nullptr);
-    } catch (const std::exception& e) {
-        return fail_static(EWALD_EINVAL, e.what());
-    }
+    // ---- window polynomial table (host fit, copied into the static array unless already there)
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(coef, wc.data(), sizeof(double) * wc.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return fail_static(EWALD_ECUDA, "window table copy failed");
+    {
+        std::lock_guard<std::mutex> lk(g_addr_mu);
+        TableKey& tk = g_table[dev];
+        if (!(tk.valid && tk.cw == p->cw && tk.P == P && tk.deg_w == p->deg_w)) {
+            std::vector<double> wc;
+            try {
+                const pswf::Prolate pw(p->cw);
+                wc = pswf::fit_window(pw, P, p->deg_w, false, nullptr);
+            } catch (const std::exception& e) {
+                return fail_static(EWALD_EINVAL, e.what());
+            }
+            tk.valid = false;
+            if (cudaMemcpyAsync(coef, wc.data(), sizeof(double) * wc.size(), cudaMemcpyHostToDevice, s) != cudaSuccess)
+                return fail_static(EWALD_ECUDA, "window table copy failed");
+            tk = TableKey{true, p->cw, P, p->deg_w};
+        }
+    }
 
     // the array keeps the previous call's contents: counters must start at zero
     if (cudaMemsetAsync(tile_cnt, 0, sizeof(int) * ntiles, s) != cudaSuccess ||
@@ -150,6 +173,10 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
     const int tb = 256, nb = static_cast<int>((n + tb - 1) / tb);
     pswf::k_prep<false><<<nb, tb, 0, s>>>(x, rho, g, key_rank, tile_cnt, cell_cnt, status);
     pswf::k_scan<<<2, 1024, 0, s>>>(tile_cnt, tile_off, static_cast<int>(ntiles), cell_cnt, cell_off, 1);
+    // input order inside every tile (the regular pipeline's stable ranks; the single real-space cell of
+    // this entry point is never read, so its ranks stay as placed)
+    pswf::k_place<<<nb, tb, 0, s>>>(key_rank, static_cast<int>(n), tile_off, cell_off, perm);
+    pswf::k_rerank<<<dim3(nb, 1), tb, 0, s>>>(key_rank, static_cast<int>(n), tile_off, cell_off, perm);
     pswf::k_scatter<double><<<nb, tb, 0, s>>>(x, rho, g, key_rank, tile_off, cell_off, sp_rec, sp_idx, sr_rec,
                                               sr_idx, nullptr, nullptr);
     cudaError_t e = cudaGetLastError();

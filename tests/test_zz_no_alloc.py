@@ -34,17 +34,30 @@ def _spread_static(params, xt, rt):
 
 
 def test_static_spread_matches_pipeline_on_consecutive_calls():
-    # two calls in a row on different systems (different n, grid and tile counts)
-    for seed, n in ((21, 3000), (22, 5200)):
+    # consecutive calls on different systems, the second one smaller (fewer particles, fewer tiles), the
+    # third back at the first's parameters: leftovers of an earlier call in the shared array (counters,
+    # slabs, the cached window table) would show.  Same kernels and the same stable order as the
+    # pipeline, so the grids agree bit for bit.
+    cases = [(21, 5200, 1e-8), (22, 900, 1e-6), (21, 5200, 1e-8)]
+    for seed, n, tol in cases:
         x, rho, L = uniform_neutral(n, seed=seed)
         xt = torch.tensor(x, device="cuda")
         rt = torch.tensor(rho, device="cuda")
-        plan = pe.Plan(L, n, 1e-8, precision="fp64")
+        plan = pe.Plan(L, n, tol, precision="fp64")
         plan.eval(xt, rt)
         ref = plan.debug_grid(0)
         got = _spread_static(plan.params, xt, rt)
         assert np.all(np.isfinite(got))
-        assert np.max(np.abs(got - ref)) <= 50 * plan.params.fit_tol * np.max(np.abs(ref))
+        assert np.array_equal(got, ref), np.max(np.abs(got - ref))
+
+
+def test_static_spread_rejects_float32_plan_parameters():
+    p = pe.plan_params(1.0, 1000, 1e-6, precision="mixed")
+    assert p.tile == 8
+    dummy = ctypes.c_void_p(16)                    # never dereferenced: the parameter check comes first
+    code = pe.lib.ewald_spread_static(ctypes.byref(p), dummy, dummy, dummy, None)
+    assert code == pe.EWALD_EINVAL
+    assert b"tile 8" in pe.lib.ewald_last_error()
 
 
 def test_static_spread_rejects_problems_beyond_its_scratch():
