@@ -49,48 +49,95 @@ def workload_config(n, tol, precision):
 
 
 # ------------------------------------------------------------------ oracle timing (CPU) --
-def oracle_sample(n, targets, seed=0):
-    """Time the FP64 converged Ewald sum (oracle) for `targets` of the n-particle system."""
-    code = r"""
-import os, sys, time, json
-sys.path.insert(0, %r)
-import numpy as np
-from oracle import exact
-from workloads import uniform_neutral
-x, rho, L = uniform_neutral(%d, seed=%d)
-tg = np.linspace(0, len(x) - 1, %d).astype(np.int64)
-t = time.perf_counter()
-exact.pswf_exact(x, rho, L, targets=tg)
-print(json.dumps({"seconds": time.perf_counter() - t}))
-""" % (ROOT, n, seed, targets)
-    env = dict(os.environ)
-    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = "1"
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+# The oracle runs as it stands in worker processes started with "spawn" (the parent may already hold a
+# CUDA context), one per host core, each with one BLAS/OpenMP thread.
+
+def _oracle_exact_sample(args):
+    """Worker: the converged PSWF Ewald sum (O-exact) of the n-particle system for the given targets."""
+    n, targets, seed = args
+    import numpy as np
+    from oracle import exact
+    from workloads import uniform_neutral
+    x, rho, L = uniform_neutral(n, seed=seed)
+    t = time.perf_counter()
+    exact.pswf_exact(x, rho, L, targets=np.asarray(targets, dtype=np.int64))
+    return time.perf_counter() - t
+
+
+def _oracle_alg2_sample(args):
+    """Worker: Alg. 2 restated on the CPU (O-alg2) with a plan's parameters: spread and FFTs over all n,
+    potential and forces at the given targets (real-space sum included)."""
+    n, seed, prm, targets = args
+    import numpy as np
+    from oracle.alg2 import Alg2
+    from workloads import uniform_neutral
+    x, rho, L = uniform_neutral(n, seed=seed)
+    A = Alg2(L, prm["m"], prm["P"], prm["cs"], prm["cw"], prm["rc"])
+    t = time.perf_counter()
+    A.total(x, rho, targets=np.asarray(targets, dtype=np.int64))
+    return time.perf_counter() - t
+
+
+class OraclePool:
+    """A pool of `cores` spawned worker processes running the oracle on the host cores."""
+
+    def __init__(self, cores=None):
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        self.cores = int(cores or os.cpu_count() or 1)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        self.ex = ProcessPoolExecutor(self.cores, mp_context=mp.get_context("spawn"))
+
+    def exact_round(self, n, per_worker, seed=0):
+        """Every core evaluates its own `per_worker` targets (structure factor included); wall seconds."""
+        step = max(1, n // (self.cores * per_worker))
+        jobs = [(n, [(w * per_worker + k) * step % n for k in range(per_worker)], seed) for w in range(self.cores)]
+        t = time.perf_counter()
+        list(self.ex.map(_oracle_exact_sample, jobs))
+        return time.perf_counter() - t
+
+    def alg2(self, n, prm, targets, seed=0):
+        return self.ex.submit(_oracle_alg2_sample, (n, seed, prm, list(targets))).result()
+
+    def close(self):
+        self.ex.shutdown()
+
+
+def host_cpu():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
     n = args.n
+    pool = OraclePool()
     times = []
     for k in range(args.warmup + args.steps):
-        s = oracle_sample(n, REF_TARGETS, seed=0)
+        s = pool.exact_round(n, REF_TARGETS)
         if k >= args.warmup:
             times.append(s)
+    pool.close()
     t = sum(times) / len(times)
-    value = REF_TARGETS / t
-    sample = "phi+F at %d of %d particles per step (oracle: FP64 PSWF Ewald, c_s=34, r_c=L/2, " \
-             "all-source structure factor, k-sphere |k|<=14)" % (REF_TARGETS, n)
+    value = pool.cores * REF_TARGETS / t
+    sample = ("phi+F at %d targets per core per step, %d cores in parallel, of the %d-particle system (oracle: "
+              "FP64 converged PSWF Ewald sum, c_s=34, r_c=L/2, all-source structure factor, k-sphere |k|<=14)"
+              % (REF_TARGETS, pool.cores, n))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * t, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": workload_config(n, args.tol, args.precision),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.cores, "kind": "oracle", "sample": sample,
+                         "cpu": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -278,6 +325,66 @@ def aggregate_value(n_per_rank, world, ms_max):
     return world * n_per_rank / (ms_max / 1000.0)
 
 
+# ------------------------------------------------------------------ stored oracle values --
+GOLDEN = {100_000: "uniform1e5_seed0.txt", 10_000_000: "uniform1e7_seed0.txt"}
+VARIANTS = ((1e-4, "mixed"), (1e-6, "fp64"), (1e-8, "mixed"), (1e-10, "mixed"), (1e-10, "fp64"), (1e-12, "mixed"))
+LARGE_N, LARGE_TOL, LARGE_DENSITIES = 10_000_000, 1e-8, (1.0, 4.0, 13.0)
+LARGE_SCRATCH_GB = 60.0          # plans whose workspace would exceed this are reported, not run
+CPU_TARGETS = 16                 # O-exact targets per host core in the CPU baseline
+
+
+def read_golden(n):
+    """Stored oracle values (targets, phi, F, E or None) of uniform_neutral(n, seed=0), when committed.
+    They are written by tests/golden/make_reference_values.py, which calls only the oracle."""
+    name = GOLDEN.get(n)
+    path = os.path.join(ROOT, "tests", "golden", name) if name else None
+    if not path or not os.path.exists(path):
+        return None
+    import numpy as np
+    E, rows = None, []
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            f = line.split()
+            if f[0] == "E":
+                E = float(f[1])
+            else:
+                rows.append([float(v) for v in f])
+    a = np.array(rows)
+    return a[:, 0].astype(np.int64), a[:, 1], a[:, 2:5], E
+
+
+def result_errors(phi, F, E, gold):
+    """Errors of one evaluation against the stored oracle values: relative l2 of phi and of F over the
+    stored targets, relative energy error (when stored), worst particle relative to the RMS."""
+    if gold is None:
+        return None
+    import numpy as np
+    tg, rphi, rF, rE = gold
+    import torch
+    ti = torch.as_tensor(tg, device=phi.device)
+    p = phi[ti].double().cpu().numpy()
+    f = F[ti].double().cpu().numpy()
+    rel = lambda a, r: float(np.linalg.norm(a - r) / np.linalg.norm(r))   # noqa: E731
+    out = {"err_phi": rel(p, rphi), "err_F": rel(f, rF),
+           "err_E": abs(E - rE) / abs(rE) if (rE is not None and E is not None) else None,
+           "worst_phi": float(np.max(np.abs(p - rphi)) / np.sqrt(np.mean(rphi ** 2))),
+           "worst_F": float(np.max(np.linalg.norm(f - rF, axis=1)) / np.sqrt(np.mean(np.sum(rF ** 2, axis=1)))),
+           "targets": int(len(tg)), "reference": "stored oracle values (converged PSWF Ewald sum)"}
+    return out
+
+
+def plan_workspace_gb(p, n):
+    """Device workspace of a plan (the tile slabs dominate), in GB."""
+    word = 4 if p.precision == 1 else 8
+    grid = [int(v) for v in p.grid]
+    m3 = grid[0] * grid[1] * grid[2]
+    E = p.tile + p.P - 1
+    ntiles = m3 // p.tile ** 3
+    return (ntiles * E ** 3 * word + 4 * m3 * word + n * 400) / 1e9
+
+
 # ------------------------------------------------------------------------- main run --
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -305,6 +412,7 @@ def run_ours(args, rank, world, local_rank):
     rho = torch.tensor(rho_np, device="cuda")
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    gold = read_golden(n) if rank == 0 else None
 
     def timed(plan, steps, warmup, profile=False, xr=None, serial=False):
         xx, rr = (x, rho) if xr is None else xr
@@ -335,6 +443,15 @@ def run_ours(args, rank, world, local_rank):
         plan.check()
         return ms / steps, stages
 
+    def errors_of(plan, g, xr=None):
+        """One more evaluation of the timed plan (with the energy) against the stored oracle values."""
+        if g is None:
+            return None
+        xx, rr = (x, rho) if xr is None else xr
+        phi, F, E = plan.eval(xx, rr)
+        torch.cuda.synchronize()
+        return result_errors(phi, F, E, g)
+
     gpu_index = local_rank
     cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
     if cvd:
@@ -354,6 +471,7 @@ def run_ours(args, rank, world, local_rank):
     _, stages = timed(plan, min(60, args.steps), 2, profile=True)
     ms = reduce_max(ms_local)
     value = aggregate_value(n, world, ms)
+    headline_err = errors_of(plan, gold)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     xh = torch.empty((n, 3), dtype=torch.float64, pin_memory=True).numpy()
@@ -397,19 +515,22 @@ def run_ours(args, rank, world, local_rank):
         roofline = {"bound": "alu", "kernel": dom, "timing": "stage events with the stages serialised (ewald_profile 2)",
                     "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                     "frac": ach / peak, "traffic": traffic_for(dom, n, p, prec_tag),
+                    "flops_per_launch": fl, "count": "100 flop per pair inside r_c" if dom == "short" else
+                    "window Horner + tensor-product stencil per particle",
                     "peak_source": "nominal GB300 FP64 1.25 TFLOP/s" if prec_tag == "f64"
                     else "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz"}
 
     variants = []
     if not args.no_variants:
-        for tol, prec in ((1e-6, "fp64"), (1e-8, "mixed"), (1e-10, "mixed"), (1e-10, "fp64"), (1e-12, "mixed")):
+        for tol, prec in VARIANTS:
             vp = pe.Plan(L, n, tol, precision=prec, **popts)
             vms, vst = timed(vp, min(60, max(5, args.steps // 3)), 2, profile=True)
             vms = reduce_max(vms)
             variants.append({"tol": tol, "precision": prec,
                              "path": pe.PATH_NAMES[vp.params.precision],
                              "m": vp.params.m, "P": vp.params.P, "ms_per_step": vms,
-                             "value": world * n / (vms / 1000.0), "stages_ms": vst})
+                             "value": world * n / (vms / 1000.0), "stages_ms": vst,
+                             "errors": errors_of(vp, gold)})
             del vp
 
     if not args.no_variants:
@@ -435,7 +556,9 @@ def run_ours(args, rank, world, local_rank):
         brho = torch.tensor(np.concatenate([sy[1] for sy in systems]), device="cuda")
         bLs = np.array([sy[2] for sy in systems])
         bns = np.array([len(sy[1]) for sy in systems], dtype=np.int64)
+        t0 = time.perf_counter()
         bp = pe.BatchPlan(bLs, bns, 1e-6, precision="mixed")
+        plan_s = time.perf_counter() - t0
         bphi = torch.empty(len(brho), dtype=torch.float64, device="cuda")
         bF = torch.empty(len(brho), 3, dtype=torch.float64, device="cuda")
         for _ in range(3):
@@ -453,17 +576,33 @@ def run_ours(args, rank, world, local_rank):
         bms = reduce_max(a.elapsed_time(b) / reps)
         N = int(bns.sum())
         batch = {"workload": "256 independent systems, n log-uniform in [500, 20000] (total %d), L = (n/100)^(1/3), "
-                             "rel tol 1e-6, mixed; one captured graph per call, energies copied back" % N,
+                             "rel tol 1e-6, mixed; one call per step, energies copied back" % N,
                  "ms_per_step": bms, "value": world * N / (bms / 1000.0), "unit": UNIT,
-                 "systems_per_s": world * 256 / (bms / 1000.0)}
-        del bp
+                 "systems_per_s": world * 256 / (bms / 1000.0), "plan_seconds": plan_s}
+        del bp, bx, brho, bphi, bF
+
+    large = None
+    if not args.no_large:
+        large = run_large(pe, torch, np, timed, errors_of, reduce_max, world, rank)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        s = oracle_sample(n, 48)
-        cpu = {"value": 48 / s, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "phi+F at 48 of %d particles (FP64 converged PSWF Ewald sum incl. the all-source "
-                         "structure factor), %.1f s, single thread" % (n, s)}
+        pool = OraclePool()
+        pool.exact_round(n, 1)                         # start-up (imports, first structure factor)
+        s = pool.exact_round(n, CPU_TARGETS)
+        tg = np.linspace(0, n - 1, 256).astype(np.int64)
+        prm = {"m": p.m, "P": p.P, "cs": p.cs, "cw": p.cw, "rc": p.rc}
+        s2 = pool.alg2(n, prm, tg)
+        pool.close()
+        cv = pool.cores * CPU_TARGETS / s
+        cpu = {"value": cv, "unit": UNIT, "cores": pool.cores, "per_core": cv / pool.cores, "kind": "oracle",
+               "cpu": host_cpu(),
+               "sample": "O-exact (FP64 converged PSWF Ewald sum incl. the all-source structure factor): phi+F at "
+                         "%d targets of the %d-particle system on each of %d cores in parallel, %.1f s wall"
+                         % (CPU_TARGETS, n, pool.cores, s),
+               "o_alg2": {"value": 256 / s2, "unit": UNIT, "cores": 1, "seconds": s2,
+                          "sample": "Alg. 2 restated on the CPU with the headline plan (m=%d, P=%d): spread and "
+                                    "FFTs over all %d particles, phi+F at 256 targets, one process" % (p.m, p.P, n)}}
 
     if rank == 0:
         line = {
@@ -472,21 +611,61 @@ def run_ours(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": prec_tag, "data": "synthetic",
             "config": dict(workload_config(n, args.tol, args.precision), m=p.m, P=p.P, rc=p.rc, cs=p.cs, cw=p.cw,
                            deg_w=p.deg_w, deg_r=p.deg_r, tile=p.tile, plan=dict(popts)),
+            "errors": headline_err,
             "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": world * n / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 32 * n,
                     "d2h_bytes_per_step": 32 * n + 8, "host_buffers": "page-locked inputs, results " + e2e_outputs},
-            # own kernels per step: prep, scan, scatter, real-space, spread, halo, scale, (float-float:
-            # grid conversion,) interpolation, combine + energy; cuFFT's kernels are not counted
-            "gpu_launches": (10 if prec_tag == "ff" else 9) * args.steps,
+            # own kernels per step: prep, scan, place, rerank, scatter, real-space, spread, halo, scale,
+            # (float-float: grid conversion,) interpolation, combine + energy; cuFFT's kernels are not counted
+            "gpu_launches": (12 if prec_tag == "ff" else 11) * args.steps,
             "stages_serial_ms": stages_serial,
             "stage_rooflines": stage_rooflines(stages_serial, p, n, pairs, prec_tag),
             "clocks": clocks, "stages_ms": stages, "variants": variants,
-            "batched": batch,
+            "batched": batch, "large": large,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def run_large(pe, torch, np, timed, errors_of, reduce_max, world, rank):
+    """The large configuration: n = 1e7 uniform neutral charges, tol 1e-8, grid densities 1, 4, 13 (m up to
+    512), float64 grid + FFT with float64 particles vs float-float particles (the MIXED path at this tol).
+    Inputs exceed L2 (320 MB), so no flush is needed.  Per-stage rooflines from serialised stage events."""
+    from workloads import uniform_neutral
+    xn, rn, L = uniform_neutral(LARGE_N, seed=rank)
+    xr = (torch.tensor(xn, device="cuda"), torch.tensor(rn, device="cuda"))
+    del xn, rn
+    gold = read_golden(LARGE_N) if rank == 0 else None
+    runs = []
+    for g in LARGE_DENSITIES:
+        for prec in ("fp64", "mixed"):
+            q = pe.plan_params(L, LARGE_N, LARGE_TOL, precision=prec, grid_density=g)
+            gb = plan_workspace_gb(q, LARGE_N)
+            row = {"grid_density": g, "precision": prec, "path": pe.PATH_NAMES[q.precision], "m": q.m, "P": q.P,
+                   "tile": q.tile, "rc": q.rc, "workspace_gb": gb}
+            if gb > LARGE_SCRATCH_GB:
+                row["skipped"] = "workspace %.0f GB above the bench's %.0f GB bound" % (gb, LARGE_SCRATCH_GB)
+                runs.append(row)
+                continue
+            lp = pe.Plan(L, LARGE_N, LARGE_TOL, precision=prec, grid_density=g, autotune=0)
+            lms, _ = timed(lp, 3, 2, xr=xr)
+            _, lst = timed(lp, 2, 1, xr=xr, profile=True, serial=True)
+            lms = reduce_max(lms)
+            tag = pe.PATH_NAMES[lp.params.precision]
+            row.update({"ms_per_step": lms, "value": world * LARGE_N / (lms / 1000.0), "stages_serial_ms": lst,
+                        "stage_rooflines": stage_rooflines(lst, lp.params, LARGE_N,
+                                                           LARGE_N * (LARGE_N - 1) * 4.0 / 3.0 * np.pi * q.rc ** 3,
+                                                           tag),
+                        "errors": errors_of(lp, gold, xr)})
+            runs.append(row)
+            del lp
+            torch.cuda.empty_cache()
+    return {"workload": "n=%d uniform neutral charges, rho~U[-1,1] minus mean, L=1, rel tol %g; grid densities "
+                        "%s; fp64 = float64 particles, grid and FFT; mixed = float-float particles (float32 "
+                        "pipes, ~48 bits) with float64 grid and FFT" % (LARGE_N, LARGE_TOL, list(LARGE_DENSITIES)),
+            "unit": UNIT, "runs": runs}
 
 
 def main():
@@ -503,6 +682,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="plan with the default grid density")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true", help="skip the n = 1e7 configuration")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.steps is None:

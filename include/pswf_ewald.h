@@ -64,15 +64,18 @@ typedef struct ewald_opts {
                              measured optimum of the GB300 kernels for n ~ 1e5) */
     double tol_safety;    /* the plan is sized for tol * tol_safety (default 0.25; forces have no
                              error model in the paper and measure ~2-5x the potential error) */
-    int    sr_reach;      /* cells per cutoff radius in the real-space cell list, 1..4;
-                             0 (default) picks it for ~3 particles per cell */
+    int    sr_reach;      /* cells per cutoff radius in the real-space cell list, 1..4 (along x and
+                             y; EWALD_MIXED plans keep 4 along z); 0 (default): 1 for EWALD_MIXED
+                             plans, otherwise ~3 particles per cell (~1.5 for float-float) */
     int    window_extra;  /* window support added to the Alg. 3 value of P (default 0) */
-    int    autotune;      /* 1: ewald_plan_create times the candidate grid densities
-                             {1.5, 2, 3, 4, 6, 8, 12} (distinct m only) on a synthetic uniform
+    int    autotune;      /* 1: ewald_plan_create times candidate plans on a synthetic uniform
                              system of n alternating unit charges in the plan's box and keeps
-                             the fastest plan; grid_density is then ignored.  The cutoff, and
-                             with it the balance between the real-space sum and Alg. 2, is what
-                             the paper leaves to measurement (Sec. 6.2.2).  0 (default): off. */
+                             the fastest: first the grid densities {1.5, 2, 3, 4, 6, 8, 12}
+                             (distinct m only; grid_density is then ignored), then, at the
+                             fastest density, the real-space cell shapes sr_reach = 1..4 (only
+                             when sr_reach is 0).  The cutoff, and with it the balance between
+                             the real-space sum and Alg. 2, is what the paper leaves to
+                             measurement (Sec. 6.2.2).  0 (default): off. */
 } ewald_opts;
 
 /* ---- derived parameters (Alg. 3 and the library's readings of it) ------ */
@@ -106,6 +109,9 @@ typedef struct ewald_params {
     int    grid[3];    /* FFT grid points per axis (each a multiple of tile, prime factors <= 7) */
     int    cells[3];   /* real-space cells per axis */
     int    deg_g;      /* cuboids: degree of the in-band mollifier transform polynomial (scaling) */
+    int    sr_reach_z; /* real-space cells per cutoff radius along z (cells of edge >= rc / sr_reach
+                          along x, y and >= rc / sr_reach_z along z): 4 for EWALD_MIXED plans, whose
+                          real-space kernel walks z windows of columns; sr_reach otherwise */
 } ewald_params;
 
 typedef struct ewald_plan_s* ewald_plan;   /* opaque, owned by the library */

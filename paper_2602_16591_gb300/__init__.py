@@ -34,7 +34,8 @@ class ewald_params(ctypes.Structure):
                 ("L", "rc", "cs", "cw", "cw_target", "alpha", "h", "lambda_s", "lambda_w", "self_coeff",
                  "tol", "fit_tol")] + [("n", ctypes.c_int64)] + [(k, ctypes.c_int) for k in
                 ("m", "P", "deg_w", "deg_r", "tile", "ncell", "sr_reach", "precision")] + \
-        [("box", ctypes.c_double * 3), ("grid", ctypes.c_int * 3), ("cells", ctypes.c_int * 3), ("deg_g", ctypes.c_int)]
+        [("box", ctypes.c_double * 3), ("grid", ctypes.c_int * 3), ("cells", ctypes.c_int * 3), ("deg_g", ctypes.c_int),
+         ("sr_reach_z", ctypes.c_int)]
 
     def as_dict(self):
         out = {}

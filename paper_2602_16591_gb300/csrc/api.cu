@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "batch.cuh"
 #include "device.cuh"
 #include "launch.h"
 #include "planner.h"
@@ -185,6 +186,7 @@ struct ewald_plan_s {
     void* grid_a = nullptr;
     void* grid_b = nullptr;
     void* spec = nullptr;
+    bool pooled_grids = false;   // grid_a, grid_b, spec belong to a fused batch's pool (not freed here)
     void* wcoef = nullptr;
     void* dwcoef = nullptr;
     void* p1c = nullptr;
@@ -223,6 +225,24 @@ struct ewald_plan_s {
     double* bout_d = nullptr;                   // per system {sum rho, sum |rho|, non-finite, energy}
     double* bout_h = nullptr;                   // pinned
     const double** bsrc_d = nullptr;            // per system {status, energy} device pointers
+    // fused float32 batches (batch.cuh): one launch per stage over all systems, cuFFT batched per grid size
+    bool fused = false;
+    int bD = 0, bP = 0;                          // radial degree bucket and window support of the batch
+    void* bsys_d = nullptr;                      // BatchSysF[nsys]
+    void* bkp_d = nullptr;                       // ShortParams<float, bD>[nsys]
+    int* bstart_d = nullptr;                     // kBStages rows of nsys + 1 block offsets
+    std::vector<int> btotal;                     // blocks of every stage
+    size_t bspread_smem = 0, binterp_smem = 0, bshort_smem = 0;
+    struct FftGroup {
+        int m = 0, count = 0;
+        float* a = nullptr;
+        float* b = nullptr;
+        float2* spec = nullptr;
+        cufftHandle fwd = 0, inv = 0;
+    };
+    std::vector<FftGroup> fgroups;
+    cudaStream_t bs_short = nullptr;
+    cudaEvent_t bfork = nullptr, bjoin = nullptr;
     bool profiling = false;
     bool serial = false;   // profiling mode 2: real-space sum and Alg. 2 serialised on the caller's stream
     std::vector<std::vector<cudaEvent_t>> prof;   // begin/end event of every stage per recorded evaluation
@@ -240,8 +260,8 @@ struct ewald_plan_s {
 
     ~ewald_plan_s() {
         void* bufs[] = {key_rank, perm, zeroed, tile_off, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, sr_lo, sr_f32, sr_cz, grid_ff, sr_cols, scratch,
-                        grid_a, grid_b, spec, wcoef, dwcoef, p1c, qc, iw, mtab, gcoef, phi_int, f_int, epart,
-                        energy_d, x_stage, rho_stage};
+                        pooled_grids ? nullptr : grid_a, pooled_grids ? nullptr : grid_b, pooled_grids ? nullptr : spec,
+                        wcoef, dwcoef, p1c, qc, iw, mtab, gcoef, phi_int, f_int, epart, energy_d, x_stage, rho_stage};
         for (void* b : bufs)
             if (b) cudaFree(b);
         if (status_h) cudaFreeHost(status_h);
@@ -263,6 +283,19 @@ struct ewald_plan_s {
         if (bout_d) cudaFree(bout_d);
         if (bout_h) cudaFreeHost(bout_h);
         if (bsrc_d) cudaFree(bsrc_d);
+        if (bsys_d) cudaFree(bsys_d);
+        if (bkp_d) cudaFree(bkp_d);
+        if (bstart_d) cudaFree(bstart_d);
+        for (auto& fg : fgroups) {
+            if (fg.fwd) cufftDestroy(fg.fwd);
+            if (fg.inv) cufftDestroy(fg.inv);
+            if (fg.a) cudaFree(fg.a);
+            if (fg.b) cudaFree(fg.b);
+            if (fg.spec) cudaFree(fg.spec);
+        }
+        if (bs_short) cudaStreamDestroy(bs_short);
+        if (bfork) cudaEventDestroy(bfork);
+        if (bjoin) cudaEventDestroy(bjoin);
     }
 };
 
@@ -313,14 +346,17 @@ cudaError_t launch_short_d(ewald_plan p, const pswf::Vec4<real>* sr_rec, const p
     const int ncells = g.ncell[0] * g.ncell[1] * g.ncell[2];
     const size_t smem = pswf::short_dyn_smem(p->sr_rcap);
     const int blocks = (ncells + pswf::kShortWarps - 1) / pswf::kShortWarps;
-    // float32 pairs are cheap: the direct kernel; float64 pairs: the two-phase (queued) kernel
-    if constexpr (sizeof(real) == 4)
-        pswf::k_short<D><<<blocks, 32 * pswf::kShortWarps, smem, s>>>(
-            sr_rec, p->sr_idx, sr_lo, p->cell_off, p->sr_cols, p->n_cols, p->sr_rcap, g, kp,
+    // float32 pairs are cheap: one target at a time, full-warp masked pairs over the target's own
+    // neighbourhood; float64 pairs: the two-phase (queued) kernel over cells
+    if constexpr (sizeof(real) == 4) {
+        const int per_block = pswf::kShortWarps * pswf::kShortTPW;
+        pswf::k_short<D><<<(g.n + per_block - 1) / per_block, 32 * pswf::kShortWarps, smem, s>>>(
+            sr_rec, p->sr_idx, sr_lo, p->cell_off, p->sr_rcap, g, kp,
             reinterpret_cast<float*>(phi), reinterpret_cast<float*>(f));   // float results in the float64 buffers
-    else
+    } else {
         pswf::k_short_q<D><<<blocks, 32 * pswf::kShortWarps, smem, s>>>(
             sr_rec, p->sr_idx, p->sr_f32, p->cell_off, p->sr_cols, p->n_cols, p->sr_rcap, g, kp, phi, f);
+    }
     return cudaGetLastError();
 }
 
@@ -641,6 +677,35 @@ int plan_autotune(const double* box, int64_t n, double tol, const ewald_opts& o,
     }
     ewald_plan best = nullptr;
     float best_ms = 0.f;
+    double best_gd = base.grid_density;
+    // times one candidate (warm-up + 3 evaluations); keeps it when it is the fastest so far
+    auto try_candidate = [&](const ewald_opts& c) -> int {
+        ewald_plan cand = nullptr;
+        if (plan_create_impl(box, n, tol, &c, &cand) != EWALD_OK) return EWALD_OK;   // not a usable shape
+        int rc = eval_device(cand, xd, rd, nullptr, nullptr, st);   // warm-up
+        float ms = 0.f;
+        if (rc == EWALD_OK) {
+            cudaEventRecord(e0, st);
+            for (int k = 0; k < 3 && rc == EWALD_OK; ++k) rc = eval_device(cand, xd, rd, nullptr, nullptr, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                rc = EWALD_ECUDA;
+        }
+        if (rc != EWALD_OK) {
+            delete cand;
+            return rc;
+        }
+        if (!best || ms < best_ms) {
+            delete best;
+            best = cand;
+            best_ms = ms;
+            best_gd = c.grid_density;
+        } else {
+            delete cand;
+        }
+        return EWALD_OK;
+    };
+    // stage 1: grid density g = m^3/n (the cutoff; Sec. 6.2.2 leaves r_c to runtime measurements)
     std::vector<int64_t> seen_m;   // grid sizes tried (m_x m_y m_z)
     for (const double gd : {1.5, 2.0, 3.0, 4.0, 6.0, 8.0, 12.0}) {
         ewald_opts c = base;
@@ -654,28 +719,28 @@ int plan_autotune(const double* box, int64_t n, double tol, const ewald_opts& o,
         }
         if (std::find(seen_m.begin(), seen_m.end(), m) != seen_m.end()) continue;
         seen_m.push_back(m);
-        ewald_plan cand = nullptr;
-        if (plan_create_impl(box, n, tol, &c, &cand) != EWALD_OK) continue;
-        int rc = eval_device(cand, xd, rd, nullptr, nullptr, st);   // warm-up
-        float ms = 0.f;
-        if (rc == EWALD_OK) {
-            cudaEventRecord(e0, st);
-            for (int k = 0; k < 3 && rc == EWALD_OK; ++k) rc = eval_device(cand, xd, rd, nullptr, nullptr, st);
-            cudaEventRecord(e1, st);
-            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
-                rc = EWALD_ECUDA;
-        }
+        const int rc = try_candidate(c);
         if (rc != EWALD_OK) {
-            delete cand;
+            delete best;
             cleanup();
             return rc;
         }
-        if (!best || ms < best_ms) {
-            delete best;
-            best = cand;
-            best_ms = ms;
-        } else {
-            delete cand;
+    }
+    // stage 2: the real-space cell shape (cells of edge r_c / reach) at the chosen density, unless the
+    // caller fixed the reach
+    if (best && base.sr_reach == 0) {
+        const int r0 = best->hp.p.sr_reach;
+        for (const int reach : {1, 2, 3, 4}) {
+            if (reach == r0) continue;
+            ewald_opts c = base;
+            c.grid_density = best_gd;
+            c.sr_reach = reach;
+            const int rc = try_candidate(c);
+            if (rc != EWALD_OK) {
+                delete best;
+                cleanup();
+                return rc;
+            }
         }
     }
     cleanup();
@@ -713,6 +778,7 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
     g.P = q.P;
     g.T = q.tile;
     g.reach = q.sr_reach;
+    g.reachz = q.sr_reach_z;
     g.degw = q.deg_w;
     g.degr = q.deg_r;
     for (int d = 0; d < 3; ++d) {
@@ -794,21 +860,21 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
         // real-space columns: (dx, dy) within reach and, for each, the largest |dz| keeping the box
         // distance between target and source cell below rc
         std::vector<int4> cols;
-        const int R = g.reach;
+        const int R = g.reach, Rz = g.reachz;
         // box distance between cells offset by (dx, dy, dz): sum_d (max(|d| - 1, 0) w_d)^2
         auto gap = [&](int k, int d) { return (k == 0 ? 0 : std::abs(k) - 1) * g.cellw[d]; };
-        const double lim = g.rc * g.rc;
+        const double lim = g.rc * g.rc * (1.0 + 2e-4);   // a superset of what the kernels' float32 tests admit
         for (int dx = -R; dx <= R; ++dx)
             for (int dy = -R; dy <= R; ++dy) {
                 const double gxy = gap(dx, 0) * gap(dx, 0) + gap(dy, 1) * gap(dy, 1);
                 if (gxy >= lim) continue;
                 int dzmax = 0;
-                while (dzmax < R && gxy + gap(dzmax + 1, 2) * gap(dzmax + 1, 2) < lim) ++dzmax;
+                while (dzmax < Rz && gxy + gap(dzmax + 1, 2) * gap(dzmax + 1, 2) < lim) ++dzmax;
                 cols.push_back(make_int4(dx, dy, dzmax, 0));
             }
         p->n_cols = static_cast<int>(cols.size());
         // every column's z-run splits into at most ceil((2R+1)/nc) + 1 contiguous pieces
-        const int pieces = (2 * R + 1 + g.ncell[2] - 1) / g.ncell[2] + 1;
+        const int pieces = (2 * Rz + 1 + g.ncell[2] - 1) / g.ncell[2] + 1;
         p->sr_rcap = p->n_cols * pieces;
         if (p->sr_rcap > pswf::kShortMaxRanges) {
             delete p;
@@ -896,6 +962,187 @@ __global__ void k_batch_gather(const double* const* __restrict__ src, int nsys, 
     out[4 * b + 1] = st[1];
     out[4 * b + 2] = st[2];
     out[4 * b + 3] = en[0];
+}
+
+// Radial polynomials of every member, padded with leading zeros to the batch's degree bucket D.
+template <int D>
+std::vector<unsigned char> batch_kps(const std::vector<ewald_plan_s*>& members) {
+    std::vector<unsigned char> out(sizeof(pswf::ShortParams<float, D>) * members.size());
+    for (size_t i = 0; i < members.size(); ++i) {
+        pswf::ShortParams<float, D> kp{};
+        const ewald_plan_s* m = members[i];
+        for (int k = 0; k <= D; ++k) {
+            kp.p1[k] = static_cast<float>(k < static_cast<int>(m->hp.p1c.size()) ? m->hp.p1c[k] : 0.0);
+            kp.q[k] = static_cast<float>(k < static_cast<int>(m->hp.qc.size()) ? m->hp.qc[k] : 0.0);
+        }
+        kp.rc2 = static_cast<float>(m->g.rc * m->g.rc);
+        kp.two_over_rc2 = static_cast<float>(2.0 / (m->g.rc * m->g.rc));
+        kp.rc2f = static_cast<float>(m->g.rc * m->g.rc * (1.0 + 1e-4));
+        std::memcpy(out.data() + i * sizeof(kp), &kp, sizeof(kp));
+    }
+    return out;
+}
+
+// Fused evaluation (batch.cuh) for batches of float32 systems sharing the window support: descriptors,
+// per-stage block tables, and for every grid size one pool of contiguous grids with batched cuFFT plans
+// (the members' own grids are replaced by slices of the pool).  Batches it does not cover keep the
+// captured graph of per-system pipelines.
+int setup_fused(ewald_plan p) {
+    const int ns = static_cast<int>(p->members.size());
+    const int P = p->members[0]->g.P;
+    int dmax = 0, degw = 0, rcap = 0;
+    for (const ewald_plan_s* m : p->members) {
+        if (m->fp64 || m->ff || m->hp.p.deg_g != 0 || m->g.P != P || m->g.T != pswf::kTile32) return EWALD_OK;
+        dmax = std::max(dmax, m->g.degr);
+        degw = std::max(degw, m->g.degw);
+        rcap = std::max(rcap, m->sr_rcap);
+    }
+    const int D = dmax <= 8 ? 8 : dmax <= 10 ? 10 : dmax == 11 ? 11 : dmax <= 12 ? 12 : dmax <= 16 ? 16 : 0;
+    if (D == 0 || !pswf::batch_f32_supports(P, D)) return EWALD_OK;
+    // grid pools and batched cuFFT plans per grid size
+    std::map<int, std::vector<int>> bym;
+    for (int i = 0; i < ns; ++i) bym[p->members[i]->g.m[0]].push_back(i);
+    for (const auto& kv : bym) {
+        ewald_plan_s::FftGroup fg;
+        fg.m = kv.first;
+        fg.count = static_cast<int>(kv.second.size());
+        const size_t m3 = static_cast<size_t>(fg.m) * fg.m * fg.m, nsp = static_cast<size_t>(fg.m) * fg.m * (fg.m / 2 + 1);
+        if (cudaMalloc(reinterpret_cast<void**>(&fg.a), sizeof(float) * m3 * fg.count) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void**>(&fg.b), sizeof(float) * m3 * fg.count) != cudaSuccess ||
+            cudaMalloc(reinterpret_cast<void**>(&fg.spec), sizeof(float2) * nsp * fg.count) != cudaSuccess) {
+            cudaGetLastError();
+            p->fgroups.push_back(fg);
+            return fail(EWALD_ENOMEM, "fused batch: grid pool allocation failed");
+        }
+        int nn[3] = {fg.m, fg.m, fg.m};
+        const bool ok = cufftPlanMany(&fg.fwd, 3, nn, nullptr, 1, static_cast<int>(m3), nullptr, 1,
+                                      static_cast<int>(nsp), CUFFT_R2C, fg.count) == CUFFT_SUCCESS &&
+                        cufftPlanMany(&fg.inv, 3, nn, nullptr, 1, static_cast<int>(nsp), nullptr, 1,
+                                      static_cast<int>(m3), CUFFT_C2R, fg.count) == CUFFT_SUCCESS;
+        p->fgroups.push_back(fg);
+        if (!ok) return fail(EWALD_ECUFFT, "fused batch: batched cuFFT plan creation failed");
+        for (int k = 0; k < fg.count; ++k) {
+            ewald_plan_s* m = p->members[kv.second[k]];
+            cudaFree(m->grid_a);
+            cudaFree(m->grid_b);
+            cudaFree(m->spec);
+            m->grid_a = fg.a + k * m3;
+            m->grid_b = fg.b + k * m3;
+            m->spec = fg.spec + k * nsp;
+            m->pooled_grids = true;
+        }
+    }
+    // descriptors and block tables
+    std::vector<pswf::BatchSysF> sys(ns);
+    std::vector<int> start(static_cast<size_t>(pswf::kBStages) * (ns + 1), 0);
+    p->btotal.assign(pswf::kBStages, 0);
+    const int per_short = pswf::kShortWarps * pswf::kShortTPW;
+    for (int i = 0; i < ns; ++i) {
+        ewald_plan_s* m = p->members[i];
+        pswf::BatchSysF& b = sys[i];
+        b.g = m->g;
+        b.sc = scale_params<float>(m);
+        b.inv_alpha = pswf::Vec4<float>{static_cast<float>(2.0 * m->g.m[0] / (P * m->g.L[0])),
+                                        static_cast<float>(2.0 * m->g.m[1] / (P * m->g.L[1])),
+                                        static_cast<float>(2.0 * m->g.m[2] / (P * m->g.L[2])), 0.f};
+        b.key_rank = m->key_rank;
+        b.perm = m->perm;
+        b.tile_cnt = m->tile_cnt;
+        b.tile_off = m->tile_off;
+        b.cell_cnt = m->cell_cnt;
+        b.cell_off = m->cell_off;
+        b.status = m->status;
+        b.zeroed = static_cast<int*>(m->zeroed);
+        b.sp_rec = static_cast<pswf::Vec4<float>*>(m->sp_rec);
+        b.sp_idx = m->sp_idx;
+        b.sr_rec = static_cast<pswf::Vec4<float>*>(m->sr_rec);
+        b.sr_idx = m->sr_idx;
+        b.sr_lo = static_cast<pswf::Vec4<float>*>(m->sr_lo);
+        b.scratch = static_cast<float*>(m->scratch);
+        b.grid_a = static_cast<float*>(m->grid_a);
+        b.grid_b = static_cast<float*>(m->grid_b);
+        b.spec = static_cast<float2*>(m->spec);
+        b.wcoef = static_cast<const float*>(m->wcoef);
+        b.dwcoef = static_cast<const float*>(m->dwcoef);
+        b.phi_sr = reinterpret_cast<float*>(m->phi_sr);
+        b.f_sr = reinterpret_cast<float*>(m->f_sr);
+        b.epart = m->epart;
+        b.energy = m->energy_d;
+        b.off = p->offsets[i];
+        b.zeroed_ints = static_cast<int>(m->zeroed_bytes / sizeof(int));
+        b.ntiles = m->ntiles;
+        b.ncells = m->ncells;
+        b.m3 = static_cast<int>(m->m3);
+        b.nspec = static_cast<int>(m->nspec);
+        b.rcap = m->sr_rcap;
+        b.degw = m->g.degw;
+        const int n = m->g.n, nb = (n + 255) / 256;
+        b.eblocks = std::min(256, std::max(1, nb));
+        const int blocks[pswf::kBStages] = {(b.zeroed_ints + 255) / 256, nb, 2, nb, 2 * nb, nb,
+                                            (n + per_short - 1) / per_short, b.ntiles, (b.m3 + 255) / 256,
+                                            (b.nspec + 255) / 256, b.ntiles, b.eblocks};
+        for (int st = 0; st < pswf::kBStages; ++st) {
+            start[st * (ns + 1) + i + 1] = start[st * (ns + 1) + i] + blocks[st];
+        }
+    }
+    for (int st = 0; st < pswf::kBStages; ++st) p->btotal[st] = start[st * (ns + 1) + ns];
+    std::vector<unsigned char> kps;
+    switch (D) {
+        case 8: kps = batch_kps<8>(p->members); break;
+        case 10: kps = batch_kps<10>(p->members); break;
+        case 11: kps = batch_kps<11>(p->members); break;
+        case 12: kps = batch_kps<12>(p->members); break;
+        default: kps = batch_kps<16>(p->members); break;
+    }
+    if (cudaMalloc(&p->bsys_d, sizeof(pswf::BatchSysF) * ns) != cudaSuccess ||
+        cudaMalloc(&p->bkp_d, kps.size()) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&p->bstart_d), sizeof(int) * start.size()) != cudaSuccess ||
+        cudaMemcpy(p->bsys_d, sys.data(), sizeof(pswf::BatchSysF) * ns, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->bkp_d, kps.data(), kps.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->bstart_d, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(EWALD_ENOMEM, "fused batch: descriptor allocation failed");
+    }
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&p->bs_short, cudaStreamNonBlocking, lo) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->bfork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->bjoin, cudaEventDisableTiming) != cudaSuccess)
+        return fail(EWALD_ECUDA, "fused batch: stream or event creation failed");
+    p->bspread_smem = pswf::Launch<float>::spread_smem(P, degw);
+    p->binterp_smem = pswf::Launch<float>::interp_smem(P, degw);
+    p->bshort_smem = pswf::short_dyn_smem(rcap);
+    p->bD = D;
+    p->bP = P;
+    p->fused = true;
+    return EWALD_OK;
+}
+
+int run_fused(ewald_plan p, const double* x, const double* rho, double* phi, double* f, cudaStream_t s) {
+    std::vector<pswf::BatchFftF> ff;
+    for (const auto& fg : p->fgroups) ff.push_back(pswf::BatchFftF{fg.count, fg.fwd, fg.inv, fg.a, fg.b, fg.spec});
+    pswf::BatchRunF r{};
+    r.sys = static_cast<const pswf::BatchSysF*>(p->bsys_d);
+    r.kps = p->bkp_d;
+    r.start = p->bstart_d;
+    r.total = p->btotal.data();
+    r.nsys = static_cast<int>(p->members.size());
+    r.P = p->bP;
+    r.D = p->bD;
+    r.spread_smem = p->bspread_smem;
+    r.interp_smem = p->binterp_smem;
+    r.short_smem = p->bshort_smem;
+    r.ffts = ff.data();
+    r.nfft = static_cast<int>(ff.size());
+    r.x = x;
+    r.rho = rho;
+    r.phi = phi;
+    r.f = f;
+    std::lock_guard<std::mutex> lk(fft_cache().mu);   // cuFFT handles are bound to the stream per call
+    PSWF_CUDA(pswf::batch_f32_run(r, s, p->bs_short, p->bfork, p->bjoin));
+    k_batch_gather<<<(r.nsys + 127) / 128, 128, 0, s>>>(p->bsrc_d, r.nsys, p->bout_d);
+    PSWF_CUDA(cudaGetLastError());
+    return EWALD_OK;
 }
 
 // Captures every member's pipeline into one graph: the origin stream forks to one stream per system,
@@ -1129,6 +1376,11 @@ int ewald_plan_batch_create(int nsys, const double* L, const int64_t* n, double 
         delete p;
         return fail(EWALD_ENOMEM, "batch plan: stream, event or buffer allocation failed");
     }
+    const int frc = setup_fused(p);
+    if (frc != EWALD_OK) {
+        delete p;
+        return frc;
+    }
     *out = p;
     return EWALD_OK;
 }
@@ -1146,10 +1398,14 @@ int ewald_eval_batch(ewald_plan plan, const int64_t* offsets, const double* x, c
     if ((rc = check_ptr_device(x, "x")) || (rc = check_ptr_device(rho, "rho")) ||
         (rc = check_ptr_device(phi, "phi")) || (rc = check_ptr_device(force, "force")))
         return rc;
-    if (!plan->bexec || plan->bkey[0] != x || plan->bkey[1] != rho || plan->bkey[2] != phi || plan->bkey[3] != force)
-        if ((rc = capture_batch(plan, x, rho, phi, force))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    PSWF_CUDA(cudaGraphLaunch(plan->bexec, s));
+    if (plan->fused && phi && force) {
+        if ((rc = run_fused(plan, x, rho, phi, force, s))) return rc;
+    } else {
+        if (!plan->bexec || plan->bkey[0] != x || plan->bkey[1] != rho || plan->bkey[2] != phi || plan->bkey[3] != force)
+            if ((rc = capture_batch(plan, x, rho, phi, force))) return rc;
+        PSWF_CUDA(cudaGraphLaunch(plan->bexec, s));
+    }
     PSWF_CUDA(cudaMemcpyAsync(plan->bout_h, plan->bout_d, sizeof(double) * 4 * ns, cudaMemcpyDeviceToHost, s));
     PSWF_CUDA(cudaStreamSynchronize(s));
     for (int b = 0; b < ns; ++b) {

@@ -31,6 +31,7 @@ template <typename real> struct alignas(4 * sizeof(real)) Vec4 { real x, y, z, w
 // describe cuboid boxes (Remark on cuboid domains, Sec. 6.1); a cube has three equal entries.
 struct Geom {
     int n, P, T, reach, degw, degr;
+    int reachz;   // real-space cells per cutoff radius along z (reach along x and y)
     int m[3], nt[3], ncell[3];
     double L[3], invL[3], invh[3], cellw[3], invcellw[3];
     double rc, self;
@@ -154,10 +155,10 @@ __device__ inline int cell_of(const Loc& r, const Geom& g) {
 // FFLOC: locate in float-float (float32 plans) instead of float64; k_scatter of the same plan must use
 // the same routine (the keys and ranks written here place its records).
 template <bool FFLOC>
-__global__ void __launch_bounds__(256) k_prep(const double* __restrict__ x, const double* __restrict__ rho, Geom g,
+__device__ __forceinline__ void k_prep_body(int bx, const double* __restrict__ x, const double* __restrict__ rho, Geom g,
                                               int* __restrict__ key_rank, int* __restrict__ tile_cnt,
                                               int* __restrict__ cell_cnt, double* __restrict__ status) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bx * blockDim.x + threadIdx.x;
     double q = 0.0;
     int bad = 0;
     if (i < g.n) {
@@ -210,12 +211,19 @@ __global__ void __launch_bounds__(256) k_prep(const double* __restrict__ x, cons
     if (threadIdx.x == 0 && nbad > 0) atomicAdd(status + 2, static_cast<double>(nbad));
 }
 
+template <bool FFLOC>
+__global__ void __launch_bounds__(256) k_prep(const double* __restrict__ x, const double* __restrict__ rho, Geom g,
+                                              int* __restrict__ key_rank, int* __restrict__ tile_cnt,
+                                              int* __restrict__ cell_cnt, double* __restrict__ status) {
+    k_prep_body<FFLOC>(blockIdx.x, x, rho, g, key_rank, tile_cnt, cell_cnt, status);
+}
+
 // Exclusive scan of cnt[0..N) into off[0..N]; one block per segment (blockIdx.x = 0 / 1).
-static __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cnt0, int* __restrict__ off0, int n0,
+__device__ __forceinline__ void k_scan_body(int bx, const int* __restrict__ cnt0, int* __restrict__ off0, int n0,
                                                const int* __restrict__ cnt1, int* __restrict__ off1, int n1) {
-    const int* cnt = blockIdx.x == 0 ? cnt0 : cnt1;
-    int* off = blockIdx.x == 0 ? off0 : off1;
-    const int N = blockIdx.x == 0 ? n0 : n1;
+    const int* cnt = bx == 0 ? cnt0 : cnt1;
+    int* off = bx == 0 ? off0 : off1;
+    const int N = bx == 0 ? n0 : n1;
     __shared__ int wsum[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int carry = 0;
@@ -287,6 +295,11 @@ static __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cn
     if (threadIdx.x == 0) off[N] = carry;
 }
 
+static __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cnt0, int* __restrict__ off0, int n0,
+                                               const int* __restrict__ cnt1, int* __restrict__ off1, int n1) {
+    k_scan_body(blockIdx.x, cnt0, off0, n0, cnt1, off1, n1);
+}
+
 // ---- stable order inside tiles and cells (counting sort, deterministic ranks) --------------------
 // k_prep's atomic ranks depend on the schedule, and so would every sum over the particles of a tile
 // or cell (spreading, the real-space sum).  k_place lists each bin's particles at their atomic
@@ -295,25 +308,31 @@ static __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cn
 // each bin in input order and an evaluation is bitwise repeatable.  The rank loop of k_rerank reads
 // the bin's list once per position; consecutive positions mostly share a bin, so the loads are warp
 // broadcasts (a bin of b particles costs b^2 / 32 warp loads).
-static __global__ void __launch_bounds__(256) k_place(const int* __restrict__ key_rank, int n,
+__device__ __forceinline__ void k_place_body(int bx, const int* __restrict__ key_rank, int n,
                                                       const int* __restrict__ tile_off,
                                                       const int* __restrict__ cell_off, int* __restrict__ perm) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bx * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int4 kr = reinterpret_cast<const int4*>(key_rank)[i];
     perm[tile_off[kr.x] + kr.y] = i;
     perm[static_cast<size_t>(n) + cell_off[kr.z] + kr.w] = i;
 }
 
+static __global__ void __launch_bounds__(256) k_place(const int* __restrict__ key_rank, int n,
+                                                      const int* __restrict__ tile_off,
+                                                      const int* __restrict__ cell_off, int* __restrict__ perm) {
+    k_place_body(blockIdx.x, key_rank, n, tile_off, cell_off, perm);
+}
+
 // blockIdx.y = 0: tile ranks (key_rank .x/.y), 1: cell ranks (.z/.w).  Each thread owns one position
 // of the bin lists; it writes only the rank word of its own particle.
-static __global__ void __launch_bounds__(256) k_rerank(int* __restrict__ key_rank, int n,
+__device__ __forceinline__ void k_rerank_body(int bx, int by, int* __restrict__ key_rank, int n,
                                                        const int* __restrict__ tile_off,
                                                        const int* __restrict__ cell_off,
                                                        const int* __restrict__ perm) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const int p = bx * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    const int kind = blockIdx.y;
+    const int kind = by;
     const int* list = perm + (kind ? static_cast<size_t>(n) : 0);
     const int* off = kind ? cell_off : tile_off;
     const int i = list[p];
@@ -324,16 +343,23 @@ static __global__ void __launch_bounds__(256) k_rerank(int* __restrict__ key_ran
     key_rank[4 * static_cast<size_t>(i) + 2 * kind + 1] = r;
 }
 
+static __global__ void __launch_bounds__(256) k_rerank(int* __restrict__ key_rank, int n,
+                                                       const int* __restrict__ tile_off,
+                                                       const int* __restrict__ cell_off,
+                                                       const int* __restrict__ perm) {
+    k_rerank_body(blockIdx.x, blockIdx.y, key_rank, n, tile_off, cell_off, perm);
+}
+
 // Sorted records.  Spreading side (tile order): {z0, z1, z2, rho}, {packed offsets in tile, original index}.
 // Real-space side (cell order): {local x, y, z, rho}, {cell id, original index}.
 template <typename real>
-__global__ void __launch_bounds__(256) k_scatter(const double* __restrict__ x, const double* __restrict__ rho, Geom g,
+__device__ __forceinline__ void k_scatter_body(int bx, const double* __restrict__ x, const double* __restrict__ rho, Geom g,
                                                  const int* __restrict__ key_rank, const int* __restrict__ tile_off,
                                                  const int* __restrict__ cell_off, Vec4<real>* __restrict__ sp_rec,
                                                  int2* __restrict__ sp_idx, Vec4<real>* __restrict__ sr_rec,
                                                  int2* __restrict__ sr_idx, Vec4<real>* __restrict__ sr_lo,
                                                  float4* __restrict__ sr_f32) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = bx * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     double q = rho[i];
     if ((__double2hiint(q) & 0x7ff00000) == 0x7ff00000) q = 0.0;
@@ -347,7 +373,7 @@ __global__ void __launch_bounds__(256) k_scatter(const double* __restrict__ x, c
         sp_rec[ps] = Vec4<float>{r.z[0], r.z[1], r.z[2], qf};
         sp_idx[ps] = make_int2((r.lw[0] % g.T) | ((r.lw[1] % g.T) << 8) | ((r.lw[2] % g.T) << 16), i);
         sr_rec[pc] = Vec4<float>{r.loc[0].h, r.loc[1].h, r.loc[2].h, qf};
-        sr_idx[pc] = make_int2(kr.z, i);
+        sr_idx[pc] = make_int2(r.cell[0] | (r.cell[1] << 10) | (r.cell[2] << 20), i);   // packed cell (< 1024 per axis)
         // rounding residue of the local coordinates (float-float) and the z cell index (its int bits: the
         // real-space kernel reads it back without a conversion instruction)
         sr_lo[pc] = Vec4<float>{r.loc[0].l, r.loc[1].l, r.loc[2].l, __int_as_float(r.cell[2])};
@@ -374,6 +400,16 @@ __global__ void __launch_bounds__(256) k_scatter(const double* __restrict__ x, c
     }
 }
 
+template <typename real>
+__global__ void __launch_bounds__(256) k_scatter(const double* __restrict__ x, const double* __restrict__ rho, Geom g,
+                                                 const int* __restrict__ key_rank, const int* __restrict__ tile_off,
+                                                 const int* __restrict__ cell_off, Vec4<real>* __restrict__ sp_rec,
+                                                 int2* __restrict__ sp_idx, Vec4<real>* __restrict__ sr_rec,
+                                                 int2* __restrict__ sr_idx, Vec4<real>* __restrict__ sr_lo,
+                                                 float4* __restrict__ sr_f32) {
+    k_scatter_body<real>(blockIdx.x, x, rho, g, key_rank, tile_off, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, sr_lo, sr_f32);
+}
+
 // P window weights at one coordinate z by Horner (coefficients c[a*(deg+1) + k], monomials in z).
 template <typename real, int P>
 __device__ __forceinline__ void window_weights(const real* __restrict__ c, int deg, real z, real (&w)[P]) {
@@ -396,11 +432,11 @@ template <int P, int T>
 constexpr int spread_threads() { return (((T + P - 1) * (T + P - 1) + 31) / 32) * 32; }
 
 template <typename real, int P>
-__global__ void __launch_bounds__(spread_threads<P, spread_tile<real>()>()) k_spread(const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
+__device__ __forceinline__ void k_spread_body(int bx, const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
                                                  const int* __restrict__ tile_off, const real* __restrict__ wcoef,
                                                  int degw, real* __restrict__ scratch) {
     constexpr int T = spread_tile<real>(), E = T + P - 1, CH = kSpreadChunk;
-    const int tile = blockIdx.x;
+    const int tile = bx;
     const int beg = tile_off[tile], end = tile_off[tile + 1];
     if (beg == end) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -488,6 +524,13 @@ __global__ void __launch_bounds__(spread_threads<P, spread_tile<real>()>()) k_sp
     }
 }
 
+template <typename real, int P>
+__global__ void __launch_bounds__(spread_threads<P, spread_tile<real>()>()) k_spread(const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
+                                                 const int* __restrict__ tile_off, const real* __restrict__ wcoef,
+                                                 int degw, real* __restrict__ scratch) {
+    k_spread_body<real, P>(blockIdx.x, rec, idx, tile_off, wcoef, degw, scratch);
+}
+
 // Sum of every tile slab covering grid point l (periodic).  Point l lies in tile t = l / T at
 // offset o = l % T; the tiles t - j (mod nt) cover it at slab offset e = o + j T for every j with
 // e < E = T + P - 1 (per axis).  Empty tiles write no slab and are skipped.
@@ -499,7 +542,7 @@ __global__ void __launch_bounds__(spread_threads<P, spread_tile<real>()>()) k_sp
 // (m_z / 32, m_y / 8, m_x): no integer division in the indexing.  NI = 0: run-time tile edge and loops (float64 plans, static path),
 // one thread per point of a 1-D grid.
 template <typename real, int NI>
-__global__ void __launch_bounds__(256) k_halo(const real* __restrict__ scratch, const int* __restrict__ tile_off, Geom g,
+__device__ __forceinline__ void k_halo_body(int bx, int by, const real* __restrict__ scratch, const int* __restrict__ tile_off, Geom g,
                                               real* __restrict__ grid) {
     const int my = g.m[1], mz = g.m[2], E = g.T + g.P - 1;
     const int ntx = g.nt[0], nty = g.nt[1], ntz = g.nt[2];
@@ -507,7 +550,7 @@ __global__ void __launch_bounds__(256) k_halo(const real* __restrict__ scratch, 
     real s = real(0);
     if constexpr (NI > 0) {
         constexpr int T = kTile32;
-        const int lz = blockIdx.x * blockDim.x + threadIdx.x, ly = blockIdx.y * blockDim.y + threadIdx.y;
+        const int lz = bx * blockDim.x + threadIdx.x, ly = by * blockDim.y + threadIdx.y;
         const int lx = blockIdx.z;
         if (lz >= mz || ly >= my) return;
         const int tlx = lx / T, tly = ly / T, tlz = lz / T;   // shifts (T is a power of two)
@@ -546,7 +589,7 @@ __global__ void __launch_bounds__(256) k_halo(const real* __restrict__ scratch, 
         grid[(static_cast<size_t>(lx) * my + ly) * mz + lz] = s;
     } else {
         const int T = g.T;
-        const int id = blockIdx.x * blockDim.x + threadIdx.x;
+        const int id = bx * blockDim.x + threadIdx.x;
         if (id >= g.m[0] * my * mz) return;
         const int lz = id % mz, ly = (id / mz) % my, lx = id / (mz * my);
         const int tlx = lx / T, tly = ly / T, tlz = lz / T;
@@ -570,6 +613,12 @@ __global__ void __launch_bounds__(256) k_halo(const real* __restrict__ scratch, 
     }
 }
 
+template <typename real, int NI>
+__global__ void __launch_bounds__(256) k_halo(const real* __restrict__ scratch, const int* __restrict__ tile_off, Geom g,
+                                              real* __restrict__ grid) {
+    k_halo_body<real, NI>(blockIdx.x, blockIdx.y, scratch, tile_off, g, grid);
+}
+
 // ---- Alg. 2 step 3: diagonal scaling on the R2C half spectrum ------------------------------------
 // Cube: S = mtab[|k|^2] iw[kx] iw[ky] iw[kz] on the open ball |k| < m/2 (host table over integer |k|^2).
 // Cuboid: |omega|^2 = sum_d (2 pi k_d / L_d)^2 is not an integer function, so
@@ -588,9 +637,9 @@ struct ScaleParams {
 };
 
 template <typename real, typename cplx>
-__global__ void k_scale(cplx* __restrict__ spec, ScaleParams<real> sp) {
+__device__ __forceinline__ void k_scale_body(int bx, cplx* __restrict__ spec, ScaleParams<real> sp) {
     const int mx = sp.m[0], my = sp.m[1], mz = sp.m[2], mh = mz / 2 + 1;
-    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    const int id = bx * blockDim.x + threadIdx.x;
     if (id >= mx * my * mh) return;
     const int iz = id % mh, iy = (id / mh) % my, ix = id / (mh * my);
     const int kx = ix < mx / 2 ? ix : ix - mx, ky = iy < my / 2 ? iy : iy - my, kz = iz;
@@ -616,6 +665,11 @@ __global__ void k_scale(cplx* __restrict__ spec, ScaleParams<real> sp) {
     spec[id] = v;
 }
 
+template <typename real, typename cplx>
+__global__ void k_scale(cplx* __restrict__ spec, ScaleParams<real> sp) {
+    k_scale_body<real, cplx>(blockIdx.x, spec, sp);
+}
+
 // ---- Alg. 2 step 5 with eq. force: interpolation of phi and grad phi ------------------------------
 // One CTA per tile: the tile's extended block of the grid b (E^3 values) is staged in shared memory.
 // Each warp takes batches of NB particles: all 32 lanes first evaluate the 6 P window weights
@@ -632,7 +686,7 @@ template <> struct InterpCfg<float> { static constexpr int NB = 8, NWARP = 4; };
 template <> struct InterpCfg<double> { static constexpr int NB = 8, NWARP = 4; };
 
 template <typename real, int P>
-__global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, const Vec4<real>* __restrict__ rec,
+__device__ __forceinline__ void k_interp_body(int bx, const real* __restrict__ grid, const Vec4<real>* __restrict__ rec,
                                                 const int2* __restrict__ idx, const int* __restrict__ tile_off,
                                                 const real* __restrict__ wcoef, const real* __restrict__ dwcoef,
                                                 Geom g, Vec4<real> inv_alpha, double* __restrict__ phi_out,
@@ -640,7 +694,7 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
     constexpr int T = spread_tile<real>(), E = T + P - 1;
     constexpr int NB = InterpCfg<real>::NB, NWARP = InterpCfg<real>::NWARP;
     constexpr int NQ = (P * P + 31) / 32;
-    const int tile = blockIdx.x;
+    const int tile = bx;
     const int beg = tile_off[tile], end = tile_off[tile + 1];
     if (beg == end) return;
     const int mx = g.m[0], my = g.m[1], mz = g.m[2], degw = g.degw;
@@ -769,6 +823,15 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
             f_out[3 * static_cast<size_t>(i) + 2] = -q * static_cast<double>(mgz);
         }
     }
+}
+
+template <typename real, int P>
+__global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, const Vec4<real>* __restrict__ rec,
+                                                const int2* __restrict__ idx, const int* __restrict__ tile_off,
+                                                const real* __restrict__ wcoef, const real* __restrict__ dwcoef,
+                                                Geom g, Vec4<real> inv_alpha, double* __restrict__ phi_out,
+                                                double* __restrict__ f_out) {
+    k_interp_body<real, P>(blockIdx.x, grid, rec, idx, tile_off, wcoef, dwcoef, g, inv_alpha, phi_out, f_out);
 }
 
 // ---- real-space sum of R over the cell list (Sec. 3.1.1) -----------------------------------------
@@ -914,181 +977,198 @@ struct ShortParams {
     float rc2f;
 };
 
-// float32 plans.  One warp per target cell; targets in passes of up to kShortMT.  Two stages per chunk
-// of 32 candidates of the cell's neighbourhood:
-//   test    each lane takes one candidate and tests it against every target of the pass in float32 on
-//           the high parts of the coordinates, with the cutoff enlarged by 1e-4 (rc2f); each passing
-//           (candidate, target) pair is appended to the warp's pair queue in shared memory (warp scan of
-//           the per-lane counts: the order is fixed by the candidate order, not by the schedule);
-//   drain   whenever 32 or more pairs wait (and once more at the end), each lane evaluates one queued
-//           pair in full: float-float displacement, exact cutoff test, R and -R'/r by Horner, and adds
-//           the result to its own slot of that target's accumulators in shared memory (a lane owns its
-//           slots, so no atomics are needed and the order of the additions is fixed).
-// The pair arithmetic thus runs in full warps whatever the fraction of candidates inside the cutoff
-// (~25% of a cell's neighbourhood at reach 2), and targets cost nothing beyond their own pairs and one
-// reduction.  Queue entries: {record index, target | shift indices << 8}.
-constexpr int kShortMT = 4;                   // targets per pass
-constexpr int kShortQ = 256;                  // queue ring (>= 32 left over + 32 * kShortMT per chunk)
-static_assert(kShortQ >= 32 + 32 * kShortMT && (kShortQ & (kShortQ - 1)) == 0, "queue ring size");
+// Source ranges of ONE target for the float32 real-space sum: every column (dx, dy) of the reach whose
+// x-y box distance from the target point is below the cutoff contributes the run of z cells that can
+// hold points within the cutoff of the target (its z window, from the target's own position), split
+// into contiguous pieces at the periodic wrap.  Lanes take one column each.  rng[r] = {first particle,
+// first z cell, dz of that cell, ix | iy << 4}, pos[r] = offset of piece r in the candidate stream,
+// pos[nr] = total, returned (warp-uniform).  Columns whose pieces would overflow cap are dropped (the
+// host sizes cap for the worst case, so none are).
+// v in (-2 n, 2 n) -> [0, n): periodic cell index
+__device__ __forceinline__ int wrap_cells(int v, int n) {
+    v += v < 0 ? n : 0;
+    v += v < 0 ? n : 0;
+    v -= v >= n ? n : 0;
+    v -= v >= n ? n : 0;
+    return v;
+}
+
+struct CellGridF {   // what target_ranges needs of the cell grid, in registers
+    int R, Rz, ncx, ncy, nc;   // reach along x, y and along z; cells per axis
+    float wx, wy, iwz;
+};
+
+__device__ __forceinline__ int target_ranges(const int* __restrict__ cell_off, const CellGridF cg, int cx, int cy,
+                                             int cz, float tx, float ty, float tz, float rc2f, int lane, int cap,
+                                             int4* rng, int* pos) {
+    const int R = cg.R, Rz = cg.Rz, W = 2 * R + 1;
+    const int ncx = cg.ncx, ncy = cg.ncy, nc = cg.nc;
+    const float wx = cg.wx, wy = cg.wy, iwz = cg.iwz;
+    int nr = 0;
+    for (int k0 = 0; k0 < W * W; k0 += 32) {
+        const int k = k0 + lane;
+        int npc = 0, zlo = 0, zhi = -1, base = 0, dx = 0, dy = 0;
+        if (k < W * W) {
+            dx = k / W - R;
+            dy = k % W - R;
+            const float gx = dx > 0 ? dx * wx - tx : (dx < 0 ? tx - (dx + 1) * wx : 0.f);
+            const float gy = dy > 0 ? dy * wy - ty : (dy < 0 ? ty - (dy + 1) * wy : 0.f);
+            const float d2 = gx * gx + gy * gy;
+            if (d2 < rc2f) {
+                const float hz = sqrtf(rc2f - d2);
+                zlo = max(-Rz, static_cast<int>(floorf((tz - hz) * iwz)));
+                zhi = min(Rz, static_cast<int>(floorf((tz + hz) * iwz)));
+                base = (wrap_cells(cx + dx, ncx) * ncy + wrap_cells(cy + dy, ncy)) * nc;
+                for (int d = zlo; d <= zhi;) {
+                    const int zw = wrap_cells(cz + d, nc);
+                    d += min(zhi - d + 1, nc - zw);
+                    ++npc;
+                }
+            }
+        }
+        int incl = npc;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        int slot = nr + incl - npc;
+        for (int d = zlo; d <= zhi;) {
+            const int zw = wrap_cells(cz + d, nc);
+            const int len = min(zhi - d + 1, nc - zw);
+            if (slot < cap) {
+                const int a = cell_off[base + zw], b = cell_off[base + zw + len];
+                rng[slot] = make_int4(a, zw, d, (dx + R) | ((dy + R) << 4));
+                pos[slot] = b - a;
+            }
+            ++slot;
+            d += len;
+        }
+        nr += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    nr = min(nr, cap);
+    __syncwarp();
+    int total = 0;
+    for (int r0 = 0; r0 < nr; r0 += 32) {
+        const int r = r0 + lane;
+        const int len = r < nr ? pos[r] : 0;
+        int incl = len;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        __syncwarp();
+        if (r < nr) pos[r] = total + incl - len;
+        total += __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+    }
+    if (lane == 0) pos[nr] = total;
+    __syncwarp();
+    return total;
+}
+
+// float32 plans.  Each warp takes kShortTPW consecutive targets (cell order) one at a time: the lanes
+// first build the target's own neighbourhood (target_ranges: z windows per column from the target's
+// position, ~40% of the candidates inside the cutoff at reach 2, against ~25% for a whole cell's
+// neighbourhood), then take 32 candidates at a time and evaluate every pair in full warps with the
+// cutoff as a mask (no divergent branch), accumulating in registers; one warp reduction per target.
+//   R(r) = 1/r - P1(u),  -R'(r)/r = 1/r^3 + Q(u),  u = 2 r^2/rc^2 - 1   (host-fitted polynomials)
+// Displacements are float-float: positions are (hi, lo) pairs relative to their cell and the cell shift
+// d w is split the same way, d = (hi_t - (hi_j + s_hi)) + ((lo_t - lo_j) - s_lo), so a close pair
+// across a cell face keeps its relative precision.
+constexpr int kShortTPW = 4;   // targets per warp
 
 template <int D>
-__global__ void __launch_bounds__(32 * kShortWarps) k_short(const Vec4<float>* __restrict__ rec, const int2* __restrict__ idx,
+__device__ __forceinline__ void k_short_body(int bx, const Vec4<float>* __restrict__ rec, const int2* __restrict__ idx,
                                                             const Vec4<float>* __restrict__ lo,
-                                                            const int* __restrict__ cell_off, const int4* __restrict__ cols,
-                                                            int ncols, int rcap, Geom g, const __grid_constant__ ShortParams<float, D> kp,
+                                                            const int* __restrict__ cell_off, int rcap, Geom g,
+                                                            const ShortParams<float, D>& kp,
                                                             float* __restrict__ phi_out, float* __restrict__ f_out) {
-    constexpr int NSH = 2 * kShortMaxR + 1, MT = kShortMT, QM = kShortQ - 1;
-    static_assert(NSH <= 16, "queue entries pack 4-bit shift indices");
+    constexpr int NSH = 2 * kShortMaxR + 1;
     __shared__ float sh_hi[3][NSH], sh_lo[3][NSH];   // cell shifts (k - R) w_d, hi and lo parts
-    __shared__ int4 scol[(2 * kShortMaxR + 1) * (2 * kShortMaxR + 1)];
-    __shared__ __align__(16) float4 sth[kShortWarps][MT];        // target position (hi parts) and charge
-    __shared__ __align__(16) float4 stl[kShortWarps][MT];        // lo parts of the target position
-    __shared__ __align__(16) float4 sacc[kShortWarps][MT][32];   // per-lane partial {phi, grad} per target
-    __shared__ int2 que[kShortWarps][kShortQ];
-    const int R = g.reach;
-    for (int k = threadIdx.x; k < 3 * (2 * R + 1); k += blockDim.x) {
-        const int d = k / (2 * R + 1), i = k % (2 * R + 1);
-        const double o = (i - R) * g.cellw[d];
+    const int R = g.reach, Rz = g.reachz;
+    for (int k = threadIdx.x; k < 3 * NSH; k += blockDim.x) {
+        const int d = k / NSH, i = k % NSH, rd = d == 2 ? Rz : R;
+        const double o = (i - rd) * g.cellw[d];
         sh_hi[d][i] = static_cast<float>(o);
         sh_lo[d][i] = static_cast<float>(o - static_cast<double>(sh_hi[d][i]));
     }
-    for (int k = threadIdx.x; k < ncols; k += blockDim.x) scol[k] = cols[k];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c = blockIdx.x * kShortWarps + warp;
-    if (c >= g.ncell[0] * g.ncell[1] * g.ncell[2]) return;
-    const int tb = cell_off[c], te = cell_off[c + 1];
-    if (tb == te) return;
-    const int cz = c % g.ncell[2], cy = (c / g.ncell[2]) % g.ncell[1], cx = c / (g.ncell[2] * g.ncell[1]);
     extern __shared__ __align__(16) unsigned char short_dyn[];
     int4* rng = reinterpret_cast<int4*>(short_dyn) + warp * rcap;
     int* pos = reinterpret_cast<int*>(reinterpret_cast<int4*>(short_dyn) + kShortWarps * rcap) + warp * (rcap + 1);
-    int2* q = que[warp];
-
-    const int total = short_ranges(scol, ncols, cell_off, g.ncell, cx, cy, cz, lane, rcap, rng, pos);
-
-    for (int t0 = tb; t0 < te; t0 += MT) {
-        const int nt = min(MT, te - t0);
-        __syncwarp();
-        if (lane < nt) {
-            const Vec4<float> a = rec[t0 + lane];
-            const Vec4<float> l = lo[t0 + lane];
-            sth[warp][lane] = make_float4(a.x, a.y, a.z, a.w);
-            stl[warp][lane] = make_float4(l.x, l.y, l.z, 0.f);
+    const int t0 = (bx * kShortWarps + warp) * kShortTPW;
+    const CellGridF cg{R, Rz, g.ncell[0], g.ncell[1], g.ncell[2], static_cast<float>(g.cellw[0]),
+                       static_cast<float>(g.cellw[1]), static_cast<float>(g.invcellw[2])};
+    for (int ti = t0; ti < min(t0 + kShortTPW, g.n); ++ti) {
+        const Vec4<float> th = rec[ti];                 // same address in every lane: one broadcast load
+        const Vec4<float> tl = lo[ti];
+        const int c = idx[ti].x;   // packed cell coordinates
+        const int cx = c & 1023, cy = (c >> 10) & 1023, cz = c >> 20;
+        const int total = target_ranges(cell_off, cg, cx, cy, cz, th.x, th.y, th.z, kp.rc2f, lane, rcap, rng, pos);
+        float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+        int r = 0;
+        for (int s0 = 0; s0 < total; s0 += 32) {   // warp-uniform trip count
+            const int p = s0 + lane;
+            const bool act = p < total;
+            int j = ti, ix = R, iy = R, iz = Rz;
+            if (act) {
+                while (pos[r + 1] <= p) ++r;
+                const int4 rg = rng[r];
+                j = rg.x + (p - pos[r]);
+                ix = rg.w & 15;
+                iy = rg.w >> 4;
+                iz = rg.z + (__float_as_int(lo[j].w) - rg.y) + Rz;
+            }
+            const Vec4<float> a = rec[j];
+            const Vec4<float> l = lo[j];
+            const float ddx = (th.x - (a.x + sh_hi[0][ix])) + ((tl.x - l.x) - sh_lo[0][ix]);
+            const float ddy = (th.y - (a.y + sh_hi[1][iy])) + ((tl.y - l.y) - sh_lo[1][iy]);
+            const float ddz = (th.z - (a.z + sh_hi[2][iz])) + ((tl.z - l.z) - sh_lo[2][iz]);
+            const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
+            const bool in = act && r2 < kp.rc2 && r2 > 0.f;
+            const float u = fmaf(r2, kp.two_over_rc2, float(-1));
+            float p1 = kp.p1[D], qq = kp.q[D];
+#pragma unroll
+            for (int kk = D - 1; kk >= 0; --kk) {
+                p1 = fmaf(p1, u, kp.p1[kk]);
+                qq = fmaf(qq, u, kp.q[kk]);
+            }
+            const float ri = rsqrtf(in ? r2 : 1.f);
+            const float qj = in ? a.w : 0.f;
+            const float cf = qj * fmaf(ri * ri, ri, qq);
+            ph = fmaf(qj, ri - p1, ph);
+            gx = fmaf(cf, ddx, gx);
+            gy = fmaf(cf, ddy, gy);
+            gz = fmaf(cf, ddz, gz);
         }
 #pragma unroll
-        for (int t = 0; t < MT; ++t) sacc[warp][t][lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-        __syncwarp();
-        float tx[MT], ty[MT], tz[MT];
-#pragma unroll
-        for (int t = 0; t < MT; ++t) {
-            const float4 v = sth[warp][t < nt ? t : 0];
-            tx[t] = v.x;
-            ty[t] = v.y;
-            tz[t] = v.z;
+        for (int o = 16; o > 0; o >>= 1) {
+            ph += __shfl_xor_sync(0xffffffffu, ph, o);
+            gx += __shfl_xor_sync(0xffffffffu, gx, o);
+            gy += __shfl_xor_sync(0xffffffffu, gy, o);
+            gz += __shfl_xor_sync(0xffffffffu, gz, o);
         }
-        int head = 0, tail = 0, r = 0;   // queue pointers (warp-uniform), range cursor of this lane
-        for (int s0 = 0;; s0 += 32) {
-            const bool fin = s0 >= total;
-            if (!fin) {
-                // test: candidate p against the targets of the pass (float32 on the high parts)
-                const int p = s0 + lane;
-                unsigned mask = 0u;
-                int j = 0, code = 0;
-                if (p < total) {
-                    while (pos[r + 1] <= p) ++r;
-                    const int4 rg = rng[r];
-                    j = rg.x + (p - pos[r]);
-                    const Vec4<float> a = rec[j];
-                    const int czj = __float_as_int(lo[j].w);
-                    const int4 col = scol[rg.w];
-                    const int ix = col.x + R, iy = col.y + R, iz = rg.z + (czj - rg.y) + R;
-                    code = (ix << 8) | (iy << 12) | (iz << 16);
-                    const float px = a.x + sh_hi[0][ix], py = a.y + sh_hi[1][iy], pz = a.z + sh_hi[2][iz];
-#pragma unroll
-                    for (int t = 0; t < MT; ++t) {
-                        if (t >= nt) break;   // warp-uniform
-                        const float dx = tx[t] - px, dy = ty[t] - py, dz = tz[t] - pz;
-                        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < kp.rc2f) mask |= 1u << t;
-                    }
-                }
-                // append this lane's pairs after those of the lanes below it
-                const int cnt = __popc(mask);
-                int incl = cnt;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                int slot = tail + incl - cnt;
-                while (mask) {
-                    const int t = __ffs(mask) - 1;
-                    mask &= mask - 1u;
-                    q[slot & QM] = make_int2(j, code | t);
-                    ++slot;
-                }
-                tail += __shfl_sync(0xffffffffu, incl, 31);
-                __syncwarp();
-            }
-            // drain: one queued pair per lane, full warps (the final round takes what is left)
-            while (tail - head >= 32 || (fin && tail > head)) {
-                const int k = head + lane;
-                const bool act = k < tail;
-                const int2 e = q[(act ? k : head) & QM];
-                const int t = e.y & 0xff, ix = (e.y >> 8) & 15, iy = (e.y >> 12) & 15, iz = (e.y >> 16) & 15;
-                const Vec4<float> a = rec[e.x];
-                const Vec4<float> l = lo[e.x];
-                const float4 th = sth[warp][t], tl = stl[warp][t];
-                // d = (hi_t - (hi_j + s_hi)) + ((lo_t - lo_j) - s_lo): a close pair across a cell face keeps
-                // its relative precision
-                const float ddx = (th.x - (a.x + sh_hi[0][ix])) + ((tl.x - l.x) - sh_lo[0][ix]);
-                const float ddy = (th.y - (a.y + sh_hi[1][iy])) + ((tl.y - l.y) - sh_lo[1][iy]);
-                const float ddz = (th.z - (a.z + sh_hi[2][iz])) + ((tl.z - l.z) - sh_lo[2][iz]);
-                const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
-                const bool in = act && r2 < kp.rc2 && r2 > 0.f;
-                const float u = fmaf(r2, kp.two_over_rc2, float(-1));
-                float p1 = kp.p1[D], qq = kp.q[D];
-#pragma unroll
-                for (int kk = D - 1; kk >= 0; --kk) {
-                    p1 = fmaf(p1, u, kp.p1[kk]);
-                    qq = fmaf(qq, u, kp.q[kk]);
-                }
-                const float ri = rsqrtf(in ? r2 : 1.f);
-                const float qj = in ? a.w : 0.f;
-                const float cf = qj * fmaf(ri * ri, ri, qq);
-                if (act) {
-                    float4 s = sacc[warp][t][lane];
-                    s.x = fmaf(qj, ri - p1, s.x);
-                    s.y = fmaf(cf, ddx, s.y);
-                    s.z = fmaf(cf, ddy, s.z);
-                    s.w = fmaf(cf, ddz, s.w);
-                    sacc[warp][t][lane] = s;
-                }
-                head += min(32, tail - head);
-            }
-            if (fin) break;
+        if (lane == 0) {   // float32 results; k_combine_energy widens them with full warps
+            const int oi = idx[ti].y;
+            phi_out[oi] = ph;
+            f_out[3 * static_cast<size_t>(oi) + 0] = th.w * gx;
+            f_out[3 * static_cast<size_t>(oi) + 1] = th.w * gy;
+            f_out[3 * static_cast<size_t>(oi) + 2] = th.w * gz;
         }
         __syncwarp();
-        // per target: sum the 32 lanes' slots; lane 0 writes (float32 results, widened by k_combine_energy)
-        for (int t = 0; t < nt; ++t) {
-            float4 s = sacc[warp][t][lane];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-                s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
-                s.z += __shfl_xor_sync(0xffffffffu, s.z, o);
-                s.w += __shfl_xor_sync(0xffffffffu, s.w, o);
-            }
-            if (lane == 0) {
-                const int oi = idx[t0 + t].y;
-                const float qi = sth[warp][t].w;
-                phi_out[oi] = s.x;
-                f_out[3 * static_cast<size_t>(oi) + 0] = qi * s.y;
-                f_out[3 * static_cast<size_t>(oi) + 1] = qi * s.z;
-                f_out[3 * static_cast<size_t>(oi) + 2] = qi * s.w;
-            }
-        }
     }
+}
+
+template <int D>
+__global__ void __launch_bounds__(32 * kShortWarps, 8) k_short(const Vec4<float>* __restrict__ rec, const int2* __restrict__ idx,
+                                                            const Vec4<float>* __restrict__ lo,
+                                                            const int* __restrict__ cell_off, int rcap, Geom g,
+                                                            const __grid_constant__ ShortParams<float, D> kp,
+                                                            float* __restrict__ phi_out, float* __restrict__ f_out) {
+    k_short_body<D>(blockIdx.x, rec, idx, lo, cell_off, rcap, g, kp, phi_out, f_out);
 }
 
 // Two-phase form of k_short (float64 plans): the float32 cutoff scan fills per-target pair queues, full
@@ -1109,10 +1189,10 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<double>
     __shared__ float stl[kShortWarps][MT][4];         // float32 copy of the target (cutoff pre-test)
     __shared__ int2 sq[kShortWarps][MT][kShortQCap];  // {source, ix | iy << 4 | iz << 8}
     __shared__ int sqlen[kShortWarps][MT];
-    const int R = g.reach;
-    for (int k = threadIdx.x; k < 3 * (2 * R + 1); k += blockDim.x) {
-        const int d = k / (2 * R + 1), i = k % (2 * R + 1);
-        const double o = (i - R) * g.cellw[d];
+    const int R = g.reach, Rz = g.reachz;
+    for (int k = threadIdx.x; k < 3 * NSH; k += blockDim.x) {
+        const int d = k / NSH, i = k % NSH, rd = d == 2 ? Rz : R;
+        const double o = (i - rd) * g.cellw[d];
         sh_d[d][i] = o;
         sh_hi[d][i] = static_cast<float>(o);
     }
@@ -1198,7 +1278,7 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<double>
                     sfx = f.x; sfy = f.y; sfz = f.z;
                     szc = f.w;
                     const int4 col = scol[rg.w];
-                    const int ix = col.x + R, iy = col.y + R, iz = rg.z + (__float_as_int(szc) - rg.y) + R;
+                    const int ix = col.x + R, iy = col.y + R, iz = rg.z + (__float_as_int(szc) - rg.y) + Rz;
                     const float px = sfx + sh_hi[0][ix], py = sfy + sh_hi[1][iy], pz = sfz + sh_hi[2][iz];
 #pragma unroll
                     for (int t = 0; t < MT; ++t) {
@@ -1265,13 +1345,13 @@ __global__ void __launch_bounds__(32 * kShortWarps) k_short_q(const Vec4<double>
 // so the energy needs no second launch and does not depend on the block schedule.  SR: the type of the
 // real-space results (float for float32 plans: k_short leaves the widening to these full warps).
 template <typename SR>
-__global__ void __launch_bounds__(256) k_combine_energy(double* __restrict__ phi, double* __restrict__ f,
+__device__ __forceinline__ void k_combine_energy_body(int bx, int nbx, double* __restrict__ phi, double* __restrict__ f,
                                                         const SR* __restrict__ phi_sr, const SR* __restrict__ f_sr,
                                                                const double* __restrict__ rho, int n,
                                                                double* __restrict__ part, unsigned* __restrict__ done,
                                                                double* __restrict__ energy) {
     double s = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = bx * blockDim.x + threadIdx.x; i < n; i += nbx * blockDim.x) {
         const double q = rho[i];
         const double p = phi[i] + static_cast<double>(phi_sr[i]);
         phi[i] = p;
@@ -1289,15 +1369,15 @@ __global__ void __launch_bounds__(256) k_combine_energy(double* __restrict__ phi
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < 8; ++w) t += red[w];
-        part[blockIdx.x] = t;
+        part[bx] = t;
         __threadfence();
-        last = atomicAdd(done, 1u) == gridDim.x - 1;
+        last = atomicAdd(done, 1u) == nbx - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
     double t = 0.0;
-    for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) t += __ldcg(part + b);
+    for (int b = threadIdx.x; b < nbx; b += blockDim.x) t += __ldcg(part + b);
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     __syncthreads();
     if (lane == 0) red[warp] = t;
@@ -1307,6 +1387,15 @@ __global__ void __launch_bounds__(256) k_combine_energy(double* __restrict__ phi
         for (int w = 0; w < 8; ++w) e += red[w];
         energy[0] = 0.5 * e;
     }
+}
+
+template <typename SR>
+__global__ void __launch_bounds__(256) k_combine_energy(double* __restrict__ phi, double* __restrict__ f,
+                                                        const SR* __restrict__ phi_sr, const SR* __restrict__ f_sr,
+                                                               const double* __restrict__ rho, int n,
+                                                               double* __restrict__ part, unsigned* __restrict__ done,
+                                                               double* __restrict__ energy) {
+    k_combine_energy_body<SR>(blockIdx.x, gridDim.x, phi, f, phi_sr, f_sr, rho, n, part, done, energy);
 }
 
 }  // namespace pswf

@@ -392,10 +392,10 @@ __global__ void __launch_bounds__(32 * kShortWarps, 6) k_short_ff(const float4* 
     __shared__ float4 sth[kShortWarps][MT], stl[kShortWarps][MT];
     __shared__ int2 sq[kShortWarps][MT][kShortQCap];   // {source, ix | iy << 4 | iz << 8}
     __shared__ int sqlen[kShortWarps][MT];
-    const int R = g.reach;
-    for (int k = threadIdx.x; k < 3 * (2 * R + 1); k += blockDim.x) {
-        const int d = k / (2 * R + 1), i = k % (2 * R + 1);
-        split_ff((i - R) * g.cellw[d], sh_hi[d][i], sh_lo[d][i]);
+    const int R = g.reach, Rz = g.reachz;
+    for (int k = threadIdx.x; k < 3 * NSH; k += blockDim.x) {
+        const int d = k / NSH, i = k % NSH, rd = d == 2 ? Rz : R;
+        split_ff((i - rd) * g.cellw[d], sh_hi[d][i], sh_lo[d][i]);
     }
     for (int k = threadIdx.x; k < ncols; k += blockDim.x) scol[k] = cols[k];
     __syncthreads();
@@ -489,7 +489,7 @@ __global__ void __launch_bounds__(32 * kShortWarps, 6) k_short_ff(const float4* 
                     const int j = rg.x + (p - pos[r]);
                     const float4 sh = rec_h[j];
                     const int4 col = scol[rg.w];
-                    const int ix = col.x + R, iy = col.y + R, iz = rg.z + (cz_of[j] - rg.y) + R;
+                    const int ix = col.x + R, iy = col.y + R, iz = rg.z + (cz_of[j] - rg.y) + Rz;
                     const float px = sh.x + sh_hi[0][ix], py = sh.y + sh_hi[1][iy], pz = sh.z + sh_hi[2][iz];
 #pragma unroll
                     for (int t = 0; t < MT; ++t) {

@@ -537,18 +537,27 @@ HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opt
     // float32 products cannot reach tol < 1e-7; below it MIXED runs the float-float kernels
     p.precision = precision;
     p.tile = tile;
-    // real-space cells of edge >= rc / reach; the automatic reach aims at ~3 particles per cell, or
-    // ~1.5 for float-float plans, whose pairs cost ~15x a float32 pair: finer cells approximate the
+    // real-space cells of edge >= rc / reach.  float32 plans: columns of edge >= rc / reach in x and y
+    // (reach 1 by default) cut into cells of edge >= rc / 4 along z, which the float32 kernel walks as
+    // z windows per target.  Otherwise cubic cells; the automatic reach aims at ~3 particles per cell,
+    // or ~1.5 for float-float plans, whose pairs cost ~15x a float32 pair: finer cells approximate the
     // cutoff sphere better (fewer candidates per pair) and fit the kernel's 4 targets per pass
     int reach = o.sr_reach;
     if (reach <= 0) {
-        const double per_cell = precision == EWALD_FLOATFLOAT ? 1.5 : 3.0;
-        reach = static_cast<int>(std::lround(rcl * std::cbrt(static_cast<double>(n) / per_cell)));
-        reach = std::max(1, std::min(reach, 4));
+        if (precision == EWALD_MIXED) {
+            reach = 1;
+        } else {
+            const double per_cell = precision == EWALD_FLOATFLOAT ? 1.5 : 3.0;
+            reach = static_cast<int>(std::lround(rcl * std::cbrt(static_cast<double>(n) / per_cell)));
+            reach = std::max(1, std::min(reach, 4));
+        }
     }
+    const int reach_z = precision == EWALD_MIXED ? 4 : reach;
     p.sr_reach = reach;
-    for (int d = 0; d < 3; ++d) {   // cells of edge L_d / ncell_d >= rc / reach on every axis
-        int nc = static_cast<int>(std::floor(reach * (box[d] / L) / rcl));
+    p.sr_reach_z = reach_z;
+    for (int d = 0; d < 3; ++d) {   // cells of edge L_d / ncell_d >= rc / reach_d on every axis
+        const int rd = d == 2 ? reach_z : reach;
+        int nc = static_cast<int>(std::floor(rd * (box[d] / L) / rcl));
         p.cells[d] = std::max(1, std::min(nc, 1024));
     }
     p.ncell = p.cells[0];

@@ -1,5 +1,6 @@
-"""Grid-density autotuning at plan creation (ewald_opts.autotune): the tuned plan is one of the
-candidate plans, meets the accuracy bar and is not slower than the default plan."""
+"""Autotuning at plan creation (ewald_opts.autotune): grid density, then the real-space cell reach.
+The tuned plan is one of the candidate plans, meets the accuracy bar and is not slower than the
+default plan."""
 import numpy as np
 import pytest
 
@@ -45,7 +46,7 @@ def test_autotuned_plan(tol, prec):
     tuned = pe.Plan(L, n, tol, precision=prec, autotune=True)
     default = pe.Plan(L, n, tol, precision=prec)
     ms = {pe.plan_params(L, n, tol, precision=prec, grid_density=g).m for g in CANDIDATES}
-    assert tuned.params.m in ms
+    assert tuned.params.m in ms and 1 <= tuned.params.sr_reach <= 4
     phi, F, E = tuned.eval(xt, rt)
     phi, F = phi.cpu().numpy(), F.cpu().numpy()
     assert _rel(phi[tg], ref[0]) <= 2 * tol

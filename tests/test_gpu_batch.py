@@ -125,3 +125,29 @@ def test_full_batch_workload():
         o = bp.offsets
         assert _rel(phi[o[b]:o[b + 1]][tg], ref[0]) <= 2e-6
         assert _rel(F[o[b]:o[b + 1]][tg], ref[3]) <= 2e-6
+
+
+def test_sharded_shares_equal_the_whole_batch_bitwise():
+    """The two shares of a batch split for two GPUs (ShardedBatchPlan, evaluated one after the other on
+    this GPU) give exactly the results of the whole batch in one BatchPlan: systems share nothing and
+    every evaluation is deterministic, so the split is invisible in the bits."""
+    from paper_2602_16591_gb300 import shard
+    systems = batched_systems(nsys=12, seed=4, nmin=500, nmax=3000)
+    Ls = np.array([s[2] for s in systems])
+    ns = np.array([len(s[1]) for s in systems], dtype=np.int64)
+    x = torch.tensor(np.concatenate([s[0] for s in systems]), device="cuda")
+    rho = torch.tensor(np.concatenate([s[1] for s in systems]), device="cuda")
+    phi, F, E = pe.BatchPlan(Ls, ns, 1e-6, precision="mixed").eval(x, rho)
+    phi, F = phi.cpu().numpy(), F.cpu().numpy()
+    results = {}
+    for r in range(2):
+        sp = shard.ShardedBatchPlan(Ls, ns, 1e-6, rank=r, world=2, precision="mixed")
+        assert sp.share[r]
+        for i, res in zip(sp.share[r], sp.eval_local(x, rho)):
+            results[i] = res
+    assert sorted(results) == list(range(len(systems)))
+    off = np.concatenate([[0], np.cumsum(ns)])
+    for i in range(len(systems)):
+        assert np.array_equal(results[i][0], phi[off[i]:off[i + 1]])
+        assert np.array_equal(results[i][1], F[off[i]:off[i + 1]])
+        assert results[i][2] == E[i]

@@ -60,6 +60,32 @@ def test_water_autograd_forces_by_finite_differences(water):
         assert abs(fd - g[i, d]) <= 1e-5 * max(1.0, np.max(np.abs(g)))
 
 
+def test_water_autograd_forces_float32_path(water):
+    """The water box's headline form (tol 1e-6, float32 path): the autograd gradient of E (-F of the
+    float32 path) against central differences of the FP64 energy (tol 1e-10, the reference gradient);
+    the float32 gradient must carry no more than the path's force error (2 tol of max |F|)."""
+    x, q, L, tg, ref = water
+    plan = pe.Plan(L, len(q), 1e-6, precision="mixed")
+    assert plan.params.precision == pe.EWALD_MIXED
+    exact_plan = pe.Plan(L, len(q), 1e-10, precision="fp64")
+    xt = torch.tensor(x, device="cuda", requires_grad=True)
+    qt = torch.tensor(q, device="cuda")
+    E = pe.energy(xt, qt, plan)
+    E.backward()
+    g = xt.grad.cpu().numpy()
+    gmax = np.max(np.abs(g))
+    h = 1e-4
+    for i, d in [(0, 0), (2, 1), (33_003, 2), (98_997, 0), (61_000, 1)]:
+        xp = x.copy()
+        xm = x.copy()
+        xp[i, d] += h
+        xm[i, d] -= h
+        Ep = exact_plan.eval(torch.tensor(xp, device="cuda"), qt)[2]
+        Em = exact_plan.eval(torch.tensor(xm, device="cuda"), qt)[2]
+        fd = (Ep - Em) / (2 * h)
+        assert abs(fd - g[i, d]) <= 2e-6 * gmax + 1e-5, (i, d, fd, g[i, d])
+
+
 def test_large_system_1e7_tol_1e8():
     """n = 1e7 uniform neutral charges, tol 1e-8: sampled targets against the oracle, sum F = 0."""
     n = 10_000_000

@@ -121,6 +121,8 @@ def test_plan_params_are_alg3_plus_stated_additions(L, n, tol, prec):
     for k in ("rc", "cs", "cw", "alpha", "h", "cw_target"):
         assert abs(getattr(p, k) / q[k] - 1) <= 1e-11, k
     assert p.ncell >= 1 and p.L / p.ncell >= p.rc / p.sr_reach - 1e-15
+    assert p.L / p.cells[2] >= p.rc / p.sr_reach_z - 1e-15
+    assert p.sr_reach_z == (4 if p.precision == pe.EWALD_MIXED else p.sr_reach)
 
 
 @pytest.mark.parametrize("L,n,tol", CFGS)
@@ -285,8 +287,8 @@ def test_cuboid_plan_params_match_stated_rule(box, n, tol, prec, mult):
     assert list(p.box) == list(box)
     for k in ("rc", "cs", "cw"):
         assert abs(getattr(p, k) / q[k] - 1) <= 1e-11, k
-    for d in range(3):   # cells of edge >= rc / reach on every axis
-        assert box[d] / p.cells[d] >= p.rc / p.sr_reach - 1e-15
+    for d in range(3):   # cells of edge >= rc / reach on every axis (z: rc / sr_reach_z)
+        assert box[d] / p.cells[d] >= p.rc / (p.sr_reach_z if d == 2 else p.sr_reach) - 1e-15
 
 
 def test_box_api_with_equal_edges_is_the_cube():

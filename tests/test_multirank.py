@@ -70,3 +70,94 @@ def test_stage_roofline_report():
         assert 0 < r.get("frac_hbm", 1e-9) < 1 and 0 < r.get("frac_alu", 1e-9) < 1
     # a broken input never raises: the bench line must still print
     assert "error" in bench.stage_rooflines(stages, None, n, 6.1e6, "f32")
+
+
+# ------------------------------------------------ one batch of independent systems over two ranks --
+def _oracle_evaluator(systems):
+    """Evaluates the listed systems of a batch on the CPU with the converged oracle (a stand-in for the
+    GPU evaluation: deterministic, so a split batch must reproduce the single-rank results bit for bit)."""
+    from oracle import exact
+
+    def evaluate(indices):
+        out = []
+        for i in indices:
+            x, rho, L = systems[i]
+            phi, _, E, F = exact.pswf_exact(x, rho, L, cs=20.0, rc_frac=0.45)
+            out.append((phi, F, E))
+        return out
+    return evaluate
+
+
+def _small_batch():
+    from workloads import batched_systems
+    return batched_systems(nsys=7, seed=3, nmin=20, nmax=90)
+
+
+def _shard_worker(rank, world, port, out):
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    sys.path.insert(0, os.path.join(root, "tests"))
+    from conftest import require_library
+    require_library()
+    from paper_2602_16591_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    systems = _small_batch()
+    ns = [len(s[1]) for s in systems]
+    costs = shard.batch_costs([s[2] for s in systems], ns, 1e-6)
+    calls = []
+    ev = _oracle_evaluator(systems)
+
+    def evaluate(indices):
+        calls.append(list(indices))
+        return ev(indices)
+    phi, F, E = shard.evaluate_sharded(evaluate, ns, costs, rank, world)
+    out[rank] = (phi.tobytes(), F.tobytes(), E.tobytes(), calls)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_batch_split_over_two_ranks_reproduces_single_rank():
+    """A batch split over two gloo ranks (no exchange while evaluating; results gathered on the host)
+    gives every rank the single-rank phi, F and E bit for bit, each system evaluated exactly once."""
+    from conftest import require_library
+    require_library()
+    import numpy as np
+    from paper_2602_16591_gb300 import shard
+    systems = _small_batch()
+    ns = [len(s[1]) for s in systems]
+    costs = shard.batch_costs([s[2] for s in systems], ns, 1e-6)
+    ref = shard.evaluate_sharded(_oracle_evaluator(systems), ns, costs, 0, 1)
+    world = 2
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_shard_worker, args=(world, port, out), nprocs=world, start_method="spawn", join=True)
+    for r in range(world):
+        assert out[r][0] == ref[0].tobytes() and out[r][1] == ref[1].tobytes() and out[r][2] == ref[2].tobytes()
+    done = sorted(i for r in range(world) for c in out[r][3] for i in c)
+    assert done == list(range(len(systems)))            # every system once, on exactly one rank
+    assert all(len(out[r][3]) == 1 and out[r][3][0] for r in range(world))
+
+
+def test_shard_assignment_balances_cost():
+    """Longest-processing-time packing: deterministic, complete, and within 4/3 of the optimum bound."""
+    from conftest import require_library
+    require_library()
+    import numpy as np
+    from paper_2602_16591_gb300 import shard
+    from workloads import batched_systems
+    systems = batched_systems(nsys=256, seed=0)
+    ns = [len(s[1]) for s in systems]
+    costs = shard.batch_costs([s[2] for s in systems], ns, 1e-6, precision="mixed")
+    for world in (2, 4, 8):
+        share = shard.assign(costs, world)
+        assert share == shard.assign(costs, world)
+        assert sorted(i for s in share for i in s) == list(range(256))
+        loads = [sum(costs[i] for i in s) for s in share]
+        bound = max(sum(costs) / world, max(costs))
+        assert max(loads) <= 4.0 / 3.0 * bound
+    # the model grows with n and with the window support
+    assert costs[int(np.argmax(ns))] == max(costs)
