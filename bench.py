@@ -233,9 +233,7 @@ def algorithmic_bytes(stage, p, n, precision):
     if stage == "spread":
         return n * rec + m3 * word
     if stage == "halo":
-        E = p.tile + p.P - 1
-        ntiles = m3 // (p.tile ** 3)
-        return ntiles * E ** 3 * word + m3 * word           # tile slabs in, grid out
+        return slab_values(p) * word + m3 * word            # tile slabs in, grid out
     if stage == "scale":
         nspec = grid[0] * grid[1] * (grid[2] // 2 + 1)
         return nspec * 2 * (8 if precision == "f32" else 16)
@@ -375,14 +373,23 @@ def result_errors(phi, F, E, gold):
     return out
 
 
+def slab_values(p):
+    """Tile-slab values of a plan: a head of T x-planes per tile and a tail of E - T planes per x-chain of
+    K tiles (K the largest divisor of the x tile count with K T <= 32), E x E values per plane."""
+    grid = [int(v) for v in p.grid]
+    T, E = p.tile, p.tile + p.P - 1
+    nt = [g // T for g in grid]
+    K = max(k for k in range(1, 32 // T + 1) if nt[0] % k == 0)
+    ntiles = nt[0] * nt[1] * nt[2]
+    return ntiles * T * E * E + (ntiles // K) * (E - T) * E * E
+
+
 def plan_workspace_gb(p, n):
     """Device workspace of a plan (the tile slabs dominate), in GB."""
     word = 4 if p.precision == 1 else 8
     grid = [int(v) for v in p.grid]
     m3 = grid[0] * grid[1] * grid[2]
-    E = p.tile + p.P - 1
-    ntiles = m3 // p.tile ** 3
-    return (ntiles * E ** 3 * word + 4 * m3 * word + n * 400) / 1e9
+    return (slab_values(p) * word + 4 * m3 * word + n * 400) / 1e9
 
 
 # ------------------------------------------------------------------------- main run --
@@ -549,16 +556,25 @@ def run_ours(args, rank, world, local_rank):
 
     batch = None
     if not args.no_variants:
-        # batched workload: 256 independent systems, n log-uniform in [500, 20000], L = (n/100)^(1/3)
+        # batched workload: 256 independent systems, n log-uniform in [500, 20000], L = (n/100)^(1/3).  With
+        # several ranks the ONE batch is split over them (cost-model bin packing, no exchange while
+        # evaluating; the timed region covers each rank's own share, max over ranks)
         from workloads import batched_systems
-        systems = batched_systems(nsys=256, seed=rank)
-        bx = torch.tensor(np.concatenate([sy[0] for sy in systems]), device="cuda")
-        brho = torch.tensor(np.concatenate([sy[1] for sy in systems]), device="cuda")
+        from paper_2602_16591_gb300 import shard
+        systems = batched_systems(nsys=256, seed=0)
         bLs = np.array([sy[2] for sy in systems])
         bns = np.array([len(sy[1]) for sy in systems], dtype=np.int64)
         t0 = time.perf_counter()
-        bp = pe.BatchPlan(bLs, bns, 1e-6, precision="mixed")
+        if world > 1:
+            sp = shard.ShardedBatchPlan(bLs, bns, 1e-6, rank=rank, world=world, precision="mixed")
+            mine = sp.share[rank]
+            bp = sp.plan
+        else:
+            mine = list(range(len(systems)))
+            bp = pe.BatchPlan(bLs, bns, 1e-6, precision="mixed")
         plan_s = time.perf_counter() - t0
+        bx = torch.tensor(np.concatenate([systems[i][0] for i in mine]), device="cuda")
+        brho = torch.tensor(np.concatenate([systems[i][1] for i in mine]), device="cuda")
         bphi = torch.empty(len(brho), dtype=torch.float64, device="cuda")
         bF = torch.empty(len(brho), 3, dtype=torch.float64, device="cuda")
         for _ in range(3):
@@ -577,8 +593,10 @@ def run_ours(args, rank, world, local_rank):
         N = int(bns.sum())
         batch = {"workload": "256 independent systems, n log-uniform in [500, 20000] (total %d), L = (n/100)^(1/3), "
                              "rel tol 1e-6, mixed; one call per step, energies copied back" % N,
-                 "ms_per_step": bms, "value": world * N / (bms / 1000.0), "unit": UNIT,
-                 "systems_per_s": world * 256 / (bms / 1000.0), "plan_seconds": plan_s}
+                 "ms_per_step": bms, "value": N / (bms / 1000.0), "unit": UNIT,
+                 "systems_per_s": 256 / (bms / 1000.0), "plan_seconds": plan_s,
+                 "scaling": "strong" if world > 1 else None,
+                 "sharding": "one batch split over %d ranks by cost (shard.py)" % world if world > 1 else None}
         del bp, bx, brho, bphi, bF
 
     large = None

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <future>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <tuple>
@@ -42,10 +43,45 @@ int fail(int code, const std::string& msg) {
         if (r_ != CUFFT_SUCCESS) return fail(EWALD_ECUFFT, std::string(#call) + " failed: " + std::to_string(r_)); \
     } while (0)
 
+// Device memory of batch members comes from one pool owned by the batch (a few large cudaMalloc calls
+// instead of ~35 per system); other plans allocate directly.  The pool in use is thread-local and set
+// only while a batch creates its members.
+struct DevicePool {
+    std::vector<void*> chunks;
+    char* cur = nullptr;
+    size_t left = 0;
+    cudaError_t alloc(void** p, size_t bytes) {
+        bytes = (bytes + 255) & ~static_cast<size_t>(255);
+        if (bytes > left) {
+            const size_t sz = std::max(bytes, static_cast<size_t>(256) << 20);
+            void* c = nullptr;
+            const cudaError_t e = cudaMalloc(&c, sz);
+            if (e != cudaSuccess) return e;
+            chunks.push_back(c);
+            cur = static_cast<char*>(c);
+            left = sz;
+        }
+        *p = cur;
+        cur += bytes;
+        left -= bytes;
+        return cudaSuccess;
+    }
+    ~DevicePool() {
+        for (void* c : chunks) cudaFree(c);
+    }
+};
+thread_local DevicePool* t_pool = nullptr;
+
+cudaError_t dmalloc(void** p, size_t bytes) { return t_pool ? t_pool->alloc(p, bytes) : cudaMalloc(p, bytes); }
+template <typename T>
+cudaError_t dmalloc(T** p, size_t bytes) {
+    return dmalloc(reinterpret_cast<void**>(p), bytes);
+}
+
 template <typename T>
 int upload(T** dst, const std::vector<double>& src) {
     std::vector<T> tmp(src.begin(), src.end());
-    if (cudaMalloc(dst, sizeof(T) * (tmp.empty() ? 1 : tmp.size())) != cudaSuccess)
+    if (dmalloc(dst, sizeof(T) * (tmp.empty() ? 1 : tmp.size())) != cudaSuccess)
         return fail(EWALD_ENOMEM, "cudaMalloc of a table failed");
     if (!tmp.empty() && cudaMemcpy(*dst, tmp.data(), sizeof(T) * tmp.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(EWALD_ECUDA, "table upload failed");
@@ -59,7 +95,7 @@ int upload_ff(float** dst, const std::vector<double>& src) {
         tmp[i] = static_cast<float>(src[i]);
         tmp[src.size() + i] = static_cast<float>(src[i] - static_cast<double>(tmp[i]));
     }
-    if (cudaMalloc(dst, sizeof(float) * (tmp.empty() ? 1 : tmp.size())) != cudaSuccess)
+    if (dmalloc(dst, sizeof(float) * (tmp.empty() ? 1 : tmp.size())) != cudaSuccess)
         return fail(EWALD_ENOMEM, "cudaMalloc of a table failed");
     if (!tmp.empty() && cudaMemcpy(*dst, tmp.data(), sizeof(float) * tmp.size(), cudaMemcpyHostToDevice) != cudaSuccess)
         return fail(EWALD_ECUDA, "table upload failed");
@@ -187,6 +223,8 @@ struct ewald_plan_s {
     void* grid_b = nullptr;
     void* spec = nullptr;
     bool pooled_grids = false;   // grid_a, grid_b, spec belong to a fused batch's pool (not freed here)
+    bool pooled = false;         // every device buffer comes from a batch's DevicePool (not freed here)
+    std::unique_ptr<DevicePool> pool;   // batch plans: the members' device memory
     void* wcoef = nullptr;
     void* dwcoef = nullptr;
     void* p1c = nullptr;
@@ -230,8 +268,8 @@ struct ewald_plan_s {
     int bD = 0, bP = 0;                          // radial degree bucket and window support of the batch
     void* bsys_d = nullptr;                      // BatchSysF[nsys]
     void* bkp_d = nullptr;                       // ShortParams<float, bD>[nsys]
-    int* bstart_d = nullptr;                     // kBStages rows of nsys + 1 block offsets
-    std::vector<int> btotal;                     // blocks of every stage
+    int2* bmap_d = nullptr;                      // {system, local block} for every block of every stage
+    std::vector<int> btotal, bmoff;              // blocks of every stage, offset of its segment in bmap_d
     size_t bspread_smem = 0, binterp_smem = 0, bshort_smem = 0;
     struct FftGroup {
         int m = 0, count = 0;
@@ -263,20 +301,22 @@ struct ewald_plan_s {
                         pooled_grids ? nullptr : grid_a, pooled_grids ? nullptr : grid_b, pooled_grids ? nullptr : spec,
                         wcoef, dwcoef, p1c, qc, iw, mtab, gcoef, phi_int, f_int, epart, energy_d, x_stage, rho_stage};
         for (void* b : bufs)
-            if (b) cudaFree(b);
+            if (b && !pooled) cudaFree(b);
         if (status_h) cudaFreeHost(status_h);
         clear_prof();
-        if (phi_sr) cudaFree(phi_sr);
-        if (f_sr) cudaFree(f_sr);
+        if (phi_sr && !pooled) cudaFree(phi_sr);
+        if (f_sr && !pooled) cudaFree(f_sr);
         if (ev_fork) cudaEventDestroy(ev_fork);
         if (ev_join) cudaEventDestroy(ev_join);
         if (ev_join2) cudaEventDestroy(ev_join2);
         if (s_short) cudaStreamDestroy(s_short);
         if (s_alg2) cudaStreamDestroy(s_alg2);
-        if (fft_work) cudaFree(fft_work);
+        if (fft_work && !pooled) cudaFree(fft_work);
         for (ewald_plan_s* m : members) delete m;
-        for (cudaStream_t st : bstreams) cudaStreamDestroy(st);
-        for (cudaEvent_t e : bevents) cudaEventDestroy(e);
+        for (cudaStream_t st : bstreams)
+            if (st) cudaStreamDestroy(st);
+        for (cudaEvent_t e : bevents)
+            if (e) cudaEventDestroy(e);
         if (bstart) cudaEventDestroy(bstart);
         if (bcap) cudaStreamDestroy(bcap);
         if (bexec) cudaGraphExecDestroy(bexec);
@@ -285,7 +325,7 @@ struct ewald_plan_s {
         if (bsrc_d) cudaFree(bsrc_d);
         if (bsys_d) cudaFree(bsys_d);
         if (bkp_d) cudaFree(bkp_d);
-        if (bstart_d) cudaFree(bstart_d);
+        if (bmap_d) cudaFree(bmap_d);
         for (auto& fg : fgroups) {
             if (fg.fwd) cufftDestroy(fg.fwd);
             if (fg.inv) cufftDestroy(fg.inv);
@@ -422,7 +462,9 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     // Alg. 2 step 1
     p->mark(1, false, s);
     PSWF_CUDA(pswf::Launch<real>::spread(g.P, p->ntiles, sp_rec, p->sp_idx, p->tile_off,
-                                         static_cast<const real*>(p->wcoef), g.degw, static_cast<real*>(p->scratch), s));
+                                         static_cast<const real*>(p->wcoef), g.degw,
+                                         pswf::SpreadChain{g.K, g.nt[1] * g.nt[2], p->ntiles},
+                                         static_cast<real*>(p->scratch), s));
     p->mark(1, true, s);
     p->mark(2, false, s);
     const int mm = static_cast<int>(p->m3);
@@ -625,6 +667,22 @@ namespace {
 int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts* opts, ewald_plan* out,
                      const pswf::HostPlan* pre = nullptr);
 
+// The forked streams and events of a plan's evaluation (real-space sum and Alg. 2 run concurrently).
+int member_streams(ewald_plan p) {
+    if (p->s_short) return EWALD_OK;
+    int prio_lo = 0, prio_hi = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+    if (cudaStreamCreateWithPriority(&p->s_short, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&p->s_alg2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(EWALD_ECUDA, "stream/event creation failed");
+    }
+    return EWALD_OK;
+}
+
 // Synthetic tuning system: n uniform points in the box (xorshift64*), charges +1, -1, ... (the last
 // one 0 for odd n), neutral.
 void tuning_system(const double* box, int64_t n, std::vector<double>& x, std::vector<double>& rho) {
@@ -757,6 +815,7 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
     if (n > (int64_t(1) << 30)) return fail(EWALD_ETOOBIG, "n beyond 2^30 particles");
     ewald_plan p = new (std::nothrow) ewald_plan_s();
     if (!p) return fail(EWALD_ENOMEM, "host allocation failed");
+    p->pooled = t_pool != nullptr;   // set before the first allocation: a failure frees nothing of the pool
     try {
         const ewald_opts o = opts ? *opts : pswf::default_opts();
         p->hp = pre ? *pre : pswf::make_plan_box(box, n, tol, o);
@@ -803,6 +862,13 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
     g.rc = q.rc;
     g.self = q.self_coeff;
     p->ntiles = g.nt[0] * g.nt[1] * g.nt[2];
+    // x-chains of the spreading: the largest divisor of the x tile count with K T <= 32
+    g.K = 1;
+    for (int k = 32 / g.T; k >= 1; --k)
+        if (g.nt[0] % k == 0) {
+            g.K = k;
+            break;
+        }
     p->ncells = g.ncell[0] * g.ncell[1] * g.ncell[2];
     p->m3 = static_cast<size_t>(g.m[0]) * g.m[1] * g.m[2];
     p->nspec = static_cast<size_t>(g.m[0]) * g.m[1] * (g.m[2] / 2 + 1);
@@ -822,7 +888,8 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
         {reinterpret_cast<void**>(&p->sp_idx), sizeof(int2) * n},
         {&p->sr_rec, 4 * rs * n},
         {reinterpret_cast<void**>(&p->sr_idx), sizeof(int2) * n},
-        {&p->scratch, rs * static_cast<size_t>(p->ntiles) * E * E * E},
+        {&p->scratch, rs * (static_cast<size_t>(p->ntiles) * g.T * E * E +
+                            static_cast<size_t>(p->ntiles / g.K) * (E - g.T) * E * E)},
         {&p->grid_a, rs * m3},
         {&p->grid_b, rs * m3},
         {&p->spec, 2 * rs * nspec},
@@ -836,7 +903,7 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
         {reinterpret_cast<void**>(&p->rho_stage), sizeof(double) * n},
     };
     for (auto& a : allocs) {
-        if (cudaMalloc(a.ptr, a.bytes) != cudaSuccess) {
+        if (dmalloc(a.ptr, a.bytes) != cudaSuccess) {
             cudaGetLastError();
             delete p;
             return fail(EWALD_ENOMEM, "device allocation failed (" + std::to_string(a.bytes) + " bytes)");
@@ -848,10 +915,10 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
     p->tile_cnt = reinterpret_cast<int*>(p->status + 4);
     p->cell_cnt = p->tile_cnt + ((p->ntiles + 1 + 3) / 4) * 4;
     p->zeroed_bytes = sizeof(double) * 4 + sizeof(int) * (((p->ntiles + 1 + 3) / 4) * 4 + p->ncells + 1);
-    if ((!p->fp64 && cudaMalloc(&p->sr_lo, 4 * sizeof(float) * n) != cudaSuccess) ||
-        (p->fp64 && !p->ff && cudaMalloc(reinterpret_cast<void**>(&p->sr_f32), sizeof(float4) * n) != cudaSuccess) ||
-        (p->ff && cudaMalloc(reinterpret_cast<void**>(&p->sr_cz), sizeof(int) * n) != cudaSuccess) ||
-        (p->ff && cudaMalloc(&p->grid_ff, sizeof(float2) * m3) != cudaSuccess)) {
+    if ((!p->fp64 && dmalloc(&p->sr_lo, 4 * sizeof(float) * n) != cudaSuccess) ||
+        (p->fp64 && !p->ff && dmalloc(&p->sr_f32, sizeof(float4) * n) != cudaSuccess) ||
+        (p->ff && dmalloc(&p->sr_cz, sizeof(int) * n) != cudaSuccess) ||
+        (p->ff && dmalloc(&p->grid_ff, sizeof(float2) * m3) != cudaSuccess)) {
         cudaGetLastError();
         delete p;
         return fail(EWALD_ENOMEM, "device allocation failed (real-space residues)");
@@ -880,27 +947,25 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
             delete p;
             return fail(EWALD_EINVAL, "real-space neighbourhood has too many cell ranges for the kernel");
         }
-        if (cudaMalloc(reinterpret_cast<void**>(&p->sr_cols), sizeof(int4) * cols.size()) != cudaSuccess ||
+        if (dmalloc(&p->sr_cols, sizeof(int4) * cols.size()) != cudaSuccess ||
             cudaMemcpy(p->sr_cols, cols.data(), sizeof(int4) * cols.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
             cudaGetLastError();
             delete p;
             return fail(EWALD_ENOMEM, "device allocation of the real-space columns failed");
         }
     }
-    int prio_lo = 0, prio_hi = 0;
-    cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
-    if (cudaStreamCreateWithPriority(&p->s_short, cudaStreamNonBlocking, prio_lo) != cudaSuccess ||
-        cudaStreamCreateWithPriority(&p->s_alg2, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_join2, cudaEventDisableTiming) != cudaSuccess) {
-        cudaGetLastError();
-        delete p;
-        return fail(EWALD_ECUDA, "stream/event creation failed");
-    }
-    if (cudaMallocHost(reinterpret_cast<void**>(&p->status_h), sizeof(double) * 4) != cudaSuccess) {
-        delete p;
-        return fail(EWALD_ENOMEM, "pinned host allocation failed");
+    // batch members (pre != nullptr) get their streams and events only when a batch graph is captured
+    // (member_streams), and never evaluate on their own, so they need no pinned status buffer
+    if (!pre) {
+        const int rcs = member_streams(p);
+        if (rcs != EWALD_OK) {
+            delete p;
+            return rcs;
+        }
+        if (cudaMallocHost(reinterpret_cast<void**>(&p->status_h), sizeof(double) * 4) != cudaSuccess) {
+            delete p;
+            return fail(EWALD_ENOMEM, "pinned host allocation failed");
+        }
     }
     int rc = EWALD_OK;
     if (p->ff) {
@@ -943,7 +1008,7 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
         delete p;
         return rc;
     }
-    if (cudaMalloc(&p->fft_work, std::max<size_t>(std::max(wf, wi), 256)) != cudaSuccess) {
+    if (dmalloc(&p->fft_work, std::max<size_t>(std::max(wf, wi), 256)) != cudaSuccess) {
         cudaGetLastError();
         delete p;
         return fail(EWALD_ENOMEM, "device allocation of the cuFFT work area failed");
@@ -1023,9 +1088,11 @@ int setup_fused(ewald_plan p) {
         if (!ok) return fail(EWALD_ECUFFT, "fused batch: batched cuFFT plan creation failed");
         for (int k = 0; k < fg.count; ++k) {
             ewald_plan_s* m = p->members[kv.second[k]];
-            cudaFree(m->grid_a);
-            cudaFree(m->grid_b);
-            cudaFree(m->spec);
+            if (!m->pooled) {   // pooled members' grids stay in the batch pool (released with it)
+                cudaFree(m->grid_a);
+                cudaFree(m->grid_b);
+                cudaFree(m->spec);
+            }
             m->grid_a = fg.a + k * m3;
             m->grid_b = fg.b + k * m3;
             m->spec = fg.spec + k * nsp;
@@ -1079,13 +1146,21 @@ int setup_fused(ewald_plan p) {
         const int n = m->g.n, nb = (n + 255) / 256;
         b.eblocks = std::min(256, std::max(1, nb));
         const int blocks[pswf::kBStages] = {(b.zeroed_ints + 255) / 256, nb, 2, nb, 2 * nb, nb,
-                                            (n + per_short - 1) / per_short, b.ntiles, (b.m3 + 255) / 256,
+                                            (n + per_short - 1) / per_short, b.ntiles / m->g.K, (b.m3 + 255) / 256,
                                             (b.nspec + 255) / 256, b.ntiles, b.eblocks};
         for (int st = 0; st < pswf::kBStages; ++st) {
             start[st * (ns + 1) + i + 1] = start[st * (ns + 1) + i] + blocks[st];
         }
     }
     for (int st = 0; st < pswf::kBStages; ++st) p->btotal[st] = start[st * (ns + 1) + ns];
+    // block maps: every block of every stage -> {system, local block}
+    p->bmoff.assign(pswf::kBStages + 1, 0);
+    for (int st = 0; st < pswf::kBStages; ++st) p->bmoff[st + 1] = p->bmoff[st] + p->btotal[st];
+    std::vector<int2> bmap(static_cast<size_t>(p->bmoff[pswf::kBStages]));
+    for (int st = 0; st < pswf::kBStages; ++st)
+        for (int i = 0; i < ns; ++i)
+            for (int k = start[st * (ns + 1) + i]; k < start[st * (ns + 1) + i + 1]; ++k)
+                bmap[p->bmoff[st] + k] = make_int2(i, k - start[st * (ns + 1) + i]);
     std::vector<unsigned char> kps;
     switch (D) {
         case 8: kps = batch_kps<8>(p->members); break;
@@ -1096,10 +1171,10 @@ int setup_fused(ewald_plan p) {
     }
     if (cudaMalloc(&p->bsys_d, sizeof(pswf::BatchSysF) * ns) != cudaSuccess ||
         cudaMalloc(&p->bkp_d, kps.size()) != cudaSuccess ||
-        cudaMalloc(reinterpret_cast<void**>(&p->bstart_d), sizeof(int) * start.size()) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&p->bmap_d), sizeof(int2) * std::max<size_t>(bmap.size(), 1)) != cudaSuccess ||
         cudaMemcpy(p->bsys_d, sys.data(), sizeof(pswf::BatchSysF) * ns, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->bkp_d, kps.data(), kps.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(p->bstart_d, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(p->bmap_d, bmap.data(), sizeof(int2) * bmap.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
         cudaGetLastError();
         return fail(EWALD_ENOMEM, "fused batch: descriptor allocation failed");
     }
@@ -1124,7 +1199,8 @@ int run_fused(ewald_plan p, const double* x, const double* rho, double* phi, dou
     pswf::BatchRunF r{};
     r.sys = static_cast<const pswf::BatchSysF*>(p->bsys_d);
     r.kps = p->bkp_d;
-    r.start = p->bstart_d;
+    r.map = p->bmap_d;
+    r.moff = p->bmoff.data();
     r.total = p->btotal.data();
     r.nsys = static_cast<int>(p->members.size());
     r.P = p->bP;
@@ -1149,6 +1225,12 @@ int run_fused(ewald_plan p, const double* x, const double* rho, double* phi, dou
 // each runs eval_device (which forks further to the member's own real-space / Alg. 2 streams), and the
 // origin joins them all before the gather.
 int capture_batch(ewald_plan p, const double* x, const double* rho, double* phi, double* f) {
+    for (ewald_plan_s* m : p->members)
+        if (const int rs = member_streams(m)) return rs;
+    for (size_t b = 0; b < p->bstreams.size(); ++b)
+        if (!p->bstreams[b] && (cudaStreamCreateWithFlags(&p->bstreams[b], cudaStreamNonBlocking) != cudaSuccess ||
+                                cudaEventCreateWithFlags(&p->bevents[b], cudaEventDisableTiming) != cudaSuccess))
+            return fail(EWALD_ECUDA, "batch capture: stream or event creation failed");
     if (p->bexec) {
         cudaGraphExecDestroy(p->bexec);
         p->bexec = nullptr;
@@ -1340,28 +1422,35 @@ int ewald_plan_batch_create(int nsys, const double* L, const int64_t* n, double 
             delete p;
             return fail(codes[b], "system " + std::to_string(b) + ": " + errs[b]);
         }
+    p->pool.reset(new (std::nothrow) DevicePool());
+    if (!p->pool) {
+        delete p;
+        return fail(EWALD_ENOMEM, "host allocation failed");
+    }
+    t_pool = p->pool.get();   // the members' device buffers come from the batch's pool
     for (int b = 0; b < nsys; ++b) {
         ewald_plan m = nullptr;
         const double box[3] = {L[b], L[b], L[b]};
         const int rc = plan_create_impl(box, n[b], tol, &o, &m, &hps[b]);
         if (rc != EWALD_OK) {
+            t_pool = nullptr;
             const std::string why = g_last_error;
             delete p;
             return fail(rc, "system " + std::to_string(b) + ": " + why);
         }
+        m->pooled = true;
         p->members.push_back(m);
         p->offsets.push_back(p->offsets.back() + n[b]);
     }
+    t_pool = nullptr;
     p->hp = p->members[0]->hp;
     p->g = p->members[0]->g;
     cudaGetDevice(&p->device);
     p->bstreams.assign(nsys, nullptr);
     p->bevents.assign(nsys, nullptr);
+    // per-system capture streams are created with the graph (capture_batch), not here
     bool ok = cudaStreamCreateWithFlags(&p->bcap, cudaStreamNonBlocking) == cudaSuccess &&
               cudaEventCreateWithFlags(&p->bstart, cudaEventDisableTiming) == cudaSuccess;
-    for (int b = 0; b < nsys && ok; ++b)
-        ok = cudaStreamCreateWithFlags(&p->bstreams[b], cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&p->bevents[b], cudaEventDisableTiming) == cudaSuccess;
     std::vector<const double*> src(2 * static_cast<size_t>(nsys));
     for (int b = 0; b < nsys; ++b) {
         src[2 * b] = p->members[b]->status;

@@ -23,7 +23,7 @@ cudaError_t short_d(const BatchRunF& r, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     kern<<<r.total[kBShort], 32 * kShortWarps, r.short_smem, s>>>(
-        r.sys, static_cast<const ShortParams<float, D>*>(r.kps), r.start + kBShort * (r.nsys + 1), r.nsys);
+        r.sys, static_cast<const ShortParams<float, D>*>(r.kps), r.map + r.moff[kBShort]);
     return cudaGetLastError();
 }
 
@@ -34,7 +34,7 @@ cudaError_t spread_p(const BatchRunF& r, cudaStream_t s) {
                                          static_cast<int>(r.spread_smem));
     if (e != cudaSuccess) return e;
     kern<<<r.total[kBSpread], spread_threads<P, kTile32>(), r.spread_smem, s>>>(
-        r.sys, r.start + kBSpread * (r.nsys + 1), r.nsys);
+        r.sys, r.map + r.moff[kBSpread]);
     return cudaGetLastError();
 }
 
@@ -45,7 +45,7 @@ cudaError_t interp_p(const BatchRunF& r, cudaStream_t s) {
                                          static_cast<int>(r.interp_smem));
     if (e != cudaSuccess) return e;
     kern<<<r.total[kBInterp], 32 * InterpCfg<float>::NWARP, r.interp_smem, s>>>(
-        r.sys, r.start + kBInterp * (r.nsys + 1), r.nsys, r.phi, r.f);
+        r.sys, r.map + r.moff[kBInterp], r.phi, r.f);
     return cudaGetLastError();
 }
 
@@ -70,15 +70,14 @@ bool batch_f32_supports(int P, int D) {
 
 cudaError_t batch_f32_run(const BatchRunF& r, cudaStream_t s, cudaStream_t s_short, cudaEvent_t fork,
                           cudaEvent_t join) {
-    const int ns = r.nsys, row = ns + 1;
-    auto st = [&](int stage) { return r.start + stage * row; };
+    auto st = [&](int stage) { return r.map + r.moff[stage]; };
     // sort: zero the counters, count, scan, stable ranks, records
-    kb_zero<<<r.total[kBZero], 256, 0, s>>>(r.sys, st(kBZero), ns);
-    kb_prep<<<r.total[kBPrep], 256, 0, s>>>(r.sys, st(kBPrep), ns, r.x, r.rho);
-    kb_scan<<<r.total[kBScan], 1024, 0, s>>>(r.sys, st(kBScan), ns);
-    kb_place<<<r.total[kBPlace], 256, 0, s>>>(r.sys, st(kBPlace), ns);
-    kb_rerank<<<r.total[kBRerank], 256, 0, s>>>(r.sys, st(kBRerank), ns);
-    kb_scatter<<<r.total[kBScatter], 256, 0, s>>>(r.sys, st(kBScatter), ns, r.x, r.rho);
+    kb_zero<<<r.total[kBZero], 256, 0, s>>>(r.sys, st(kBZero));
+    kb_prep<<<r.total[kBPrep], 256, 0, s>>>(r.sys, st(kBPrep), r.x, r.rho);
+    kb_scan<<<r.total[kBScan], 1024, 0, s>>>(r.sys, st(kBScan));
+    kb_place<<<r.total[kBPlace], 256, 0, s>>>(r.sys, st(kBPlace));
+    kb_rerank<<<r.total[kBRerank], 256, 0, s>>>(r.sys, st(kBRerank));
+    kb_scatter<<<r.total[kBScatter], 256, 0, s>>>(r.sys, st(kBScatter), r.x, r.rho);
     PSWF_TRY(cudaGetLastError());
     // real-space sum on the second stream
     PSWF_TRY(cudaEventRecord(fork, s));
@@ -101,14 +100,14 @@ cudaError_t batch_f32_run(const BatchRunF& r, cudaStream_t s, cudaStream_t s_sho
         default: break;
     }
     PSWF_TRY(e);
-    kb_halo<<<r.total[kBHalo], 256, 0, s>>>(r.sys, st(kBHalo), ns);
+    kb_halo<<<r.total[kBHalo], 256, 0, s>>>(r.sys, st(kBHalo));
     PSWF_TRY(cudaGetLastError());
     for (int k = 0; k < r.nfft; ++k) {
         const cufftHandle h = static_cast<cufftHandle>(r.ffts[k].handle_fwd);
         if (cufftSetStream(h, s) != CUFFT_SUCCESS || cufftExecR2C(h, r.ffts[k].a, reinterpret_cast<cufftComplex*>(r.ffts[k].spec)) != CUFFT_SUCCESS)
             return cudaErrorLaunchFailure;
     }
-    kb_scale<<<r.total[kBScale], 256, 0, s>>>(r.sys, st(kBScale), ns);
+    kb_scale<<<r.total[kBScale], 256, 0, s>>>(r.sys, st(kBScale));
     PSWF_TRY(cudaGetLastError());
     for (int k = 0; k < r.nfft; ++k) {
         const cufftHandle h = static_cast<cufftHandle>(r.ffts[k].handle_inv);
@@ -125,7 +124,7 @@ cudaError_t batch_f32_run(const BatchRunF& r, cudaStream_t s, cudaStream_t s_sho
     PSWF_TRY(e);
     // join, then phi += real-space phi, F += real-space F, per-system energies
     PSWF_TRY(cudaStreamWaitEvent(s, join, 0));
-    kb_combine<<<r.total[kBCombine], 256, 0, s>>>(r.sys, st(kBCombine), ns, r.phi, r.f, r.rho);
+    kb_combine<<<r.total[kBCombine], 256, 0, s>>>(r.sys, st(kBCombine), r.phi, r.f, r.rho);
     return cudaGetLastError();
 }
 

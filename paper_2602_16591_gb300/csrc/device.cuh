@@ -32,6 +32,7 @@ template <typename real> struct alignas(4 * sizeof(real)) Vec4 { real x, y, z, w
 struct Geom {
     int n, P, T, reach, degw, degr;
     int reachz;   // real-space cells per cutoff radius along z (reach along x and y)
+    int K;        // spreading tiles per x-chain (a divisor of nt[0]; k_spread)
     int m[3], nt[3], ncell[3];
     double L[3], invL[3], invh[3], cellw[3], invcellw[3];
     double rc, self;
@@ -428,17 +429,23 @@ __device__ __forceinline__ void window_weights(const real* __restrict__ c, int d
 // block is written to a per-tile scratch slab; k_halo sums overlapping slabs (no atomics anywhere).
 constexpr int kSpreadChunk = 64;
 
+// x-chains of the spreading: one CTA walks K consecutive tiles along x (nyz = nt_y nt_z tiles per
+// x plane of tiles) and keeps its register columns across them, so only T planes per tile (the
+// tile's head) plus E - T planes per chain (its tail) reach the slab buffer, instead of E planes per
+// tile.  Slab layout: heads [tile][a < T][y < E][z < E], then tails [chain][a < E - T][y][z].
+struct SpreadChain {
+    int K, nyz, ntiles;
+};
+
 template <int P, int T>
 constexpr int spread_threads() { return (((T + P - 1) * (T + P - 1) + 31) / 32) * 32; }
 
 template <typename real, int P>
 __device__ __forceinline__ void k_spread_body(int bx, const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
                                                  const int* __restrict__ tile_off, const real* __restrict__ wcoef,
-                                                 int degw, real* __restrict__ scratch) {
+                                                 int degw, SpreadChain ch, real* __restrict__ scratch) {
     constexpr int T = spread_tile<real>(), E = T + P - 1, CH = kSpreadChunk;
-    const int tile = bx;
-    const int beg = tile_off[tile], end = tile_off[tile + 1];
-    if (beg == end) return;
+    const int qx = bx / ch.nyz, rem = bx - qx * ch.nyz;   // this chain: tiles (qx K + k, rem)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     // weight rows padded to whole 16-byte vectors so a thread reads a particle's P x-weights with
     // PP / VW broadcast vector loads instead of P scalar ones
@@ -456,7 +463,12 @@ __device__ __forceinline__ void k_spread_body(int bx, const Vec4<real>* __restri
     real acc[E];
 #pragma unroll
     for (int a = 0; a < E; ++a) acc[a] = real(0);
+    real* heads = scratch;
+    real* tails = scratch + static_cast<size_t>(ch.ntiles) * T * E * E;
 
+    for (int k = 0; k < ch.K; ++k) {
+    const int tile = (qx * ch.K + k) * ch.nyz + rem;
+    const int beg = tile_off[tile], end = tile_off[tile + 1];
     for (int base = beg; base < end; base += CH) {
         const int cnt = min(CH, end - base);
         __syncthreads();
@@ -517,51 +529,79 @@ __device__ __forceinline__ void k_spread_body(int bx, const Vec4<real>* __restri
             }
         }
     }
+    // planes [0, T) of this tile are complete along x within the chain (later tiles start T further):
+    // write them as the tile's head and carry the remaining E - T planes to the next tile
     if (own) {
-        real* out = scratch + static_cast<size_t>(tile) * E * E * E;
+        real* out = heads + static_cast<size_t>(tile) * T * E * E;
 #pragma unroll
-        for (int a = 0; a < E; ++a) out[a * E * E + col] = acc[a];
+        for (int a = 0; a < T; ++a) out[a * E * E + col] = acc[a];
+#pragma unroll
+        for (int a = 0; a < E; ++a) acc[a] = a + T < E ? acc[a + T] : real(0);
+    }
+    }
+    if (own) {   // the chain's tail: planes that belong to the tiles after the chain
+        real* out = tails + static_cast<size_t>(bx) * (E - T) * E * E;
+#pragma unroll
+        for (int a = 0; a < E - T; ++a) out[a * E * E + col] = acc[a];
     }
 }
 
 template <typename real, int P>
 __global__ void __launch_bounds__(spread_threads<P, spread_tile<real>()>()) k_spread(const Vec4<real>* __restrict__ rec, const int2* __restrict__ idx,
                                                  const int* __restrict__ tile_off, const real* __restrict__ wcoef,
-                                                 int degw, real* __restrict__ scratch) {
-    k_spread_body<real, P>(blockIdx.x, rec, idx, tile_off, wcoef, degw, scratch);
+                                                 int degw, SpreadChain ch, real* __restrict__ scratch) {
+    k_spread_body<real, P>(blockIdx.x, rec, idx, tile_off, wcoef, degw, ch, scratch);
 }
 
-// Sum of every tile slab covering grid point l (periodic).  Point l lies in tile t = l / T at
-// offset o = l % T; the tiles t - j (mod nt) cover it at slab offset e = o + j T for every j with
-// e < E = T + P - 1 (per axis).  Empty tiles write no slab and are skipped.
 // ---- Alg. 2 step 1 (continued): halo sum of the tile slabs into the periodic grid -----------------
-// NI > 0 (float32 plans, tile edge T = 8 at compile time): every axis has at most NI overlapping slabs
-// (NI = ceil(E / T)); the enumeration is unrolled and every slab value is loaded unconditionally
-// (empty tiles never wrote theirs, so their values are discarded by a select), so the ~NI^3 loads of a
-// point are independent and in flight together.  Blocks of 32 x 8 points (z, y), grid
-// (m_z / 32, m_y / 8, m_x): no integer division in the indexing.  NI = 0: run-time tile edge and loops (float64 plans, static path),
-// one thread per point of a 1-D grid.
+// Grid point l gets, from every tile column (t_y, t_z) overlapping it in y and z (ceil(E / T) per axis,
+// periodic), the head of its own x tile at plane l_x mod T and the tails of the x-chains that end
+// before l_x and still reach it (at most one unless the chain is shorter than E - T).  Every slab value
+// is read by exactly one grid point per overlapping column.  NI > 0 (float32 plans, tile edge 8 at
+// compile time, NI = ceil(E / T)): the y-z enumeration is unrolled, blocks of 32 x 8 points (z, y) and
+// grid (m_z / 32, m_y / 8, m_x).  NI = 0: run-time tile edge, one thread per point of a 1-D grid.
 template <typename real, int NI>
-__device__ __forceinline__ void k_halo_body(int bx, int by, const real* __restrict__ scratch, const int* __restrict__ tile_off, Geom g,
-                                              real* __restrict__ grid) {
-    const int my = g.m[1], mz = g.m[2], E = g.T + g.P - 1;
-    const int ntx = g.nt[0], nty = g.nt[1], ntz = g.nt[2];
-    const size_t slab = static_cast<size_t>(E) * E * E;
-    real s = real(0);
-    if constexpr (NI > 0) {
-        constexpr int T = kTile32;
-        const int lz = bx * blockDim.x + threadIdx.x, ly = by * blockDim.y + threadIdx.y;
-        const int lx = blockIdx.z;
+__device__ __forceinline__ void k_halo_body(int bx, int by, const real* __restrict__ scratch, const int* __restrict__ tile_off,
+                                            Geom g, real* __restrict__ grid) {
+    (void)tile_off;
+    const int my = g.m[1], mz = g.m[2], P = g.P;
+    const int nty = g.nt[1], ntz = g.nt[2], K = g.K, nchx = g.nt[0] / g.K;
+    const int T = NI > 0 ? kTile32 : g.T, E = T + P - 1, ET = E - T;
+    const size_t plane = static_cast<size_t>(E) * E;
+    const real* heads = scratch;
+    const real* tails = scratch + static_cast<size_t>(g.nt[0]) * nty * ntz * T * plane;
+    int lx, ly, lz;
+    if constexpr (NI > 0) {   // 32 x 8 blocks over (z, y), blockIdx.z = x
+        lz = bx * 32 + static_cast<int>(threadIdx.x);
+        ly = by * 8 + static_cast<int>(threadIdx.y);
+        lx = blockIdx.z;
         if (lz >= mz || ly >= my) return;
-        const int tlx = lx / T, tly = ly / T, tlz = lz / T;   // shifts (T is a power of two)
-        const int olx = lx % T, oly = ly % T, olz = lz % T;
-        int txs[NI], tys[NI], tzs[NI];
+    } else {
+        const int id = bx * blockDim.x + threadIdx.x;
+        if (id >= g.m[0] * my * mz) return;
+        lz = id % mz;
+        ly = (id / mz) % my;
+        lx = id / (mz * my);
+    }
+    const int tlx = lx / T, tly = ly / T, tlz = lz / T;
+    const int olx = lx - tlx * T, oly = ly - tly * T, olz = lz - tlz * T;
+    const int qc = tlx / K;   // the chain holding lx; the tails of the chains before it reach into lx
+    real s = real(0);
+    auto add_column = [&](int tyz, int ey, int ez) {
+        s += heads[(static_cast<size_t>(tlx) * nty * ntz + tyz) * T * plane + olx * plane + ey * E + ez];
+        for (int j = 1;; ++j) {
+            const int e = lx - (qc - j + 1) * K * T;   // plane of chain qc - j's tail at lx
+            if (e >= ET) break;
+            int q = (qc - j) % nchx;
+            q += q < 0 ? nchx : 0;
+            s += tails[(static_cast<size_t>(q) * nty * ntz + tyz) * ET * plane + e * plane + ey * E + ez];
+        }
+    };
+    if constexpr (NI > 0) {
+        int tys[NI], tzs[NI];
 #pragma unroll
-        for (int a = 0; a < NI; ++a) {   // tile a steps back along each axis (periodic; tiny grids wrap repeatedly)
-            int t = tlx - a;
-            while (t < 0) t += ntx;
-            txs[a] = t;
-            t = tly - a;
+        for (int a = 0; a < NI; ++a) {   // tiny grids wrap repeatedly
+            int t = tly - a;
             while (t < 0) t += nty;
             tys[a] = t;
             t = tlz - a;
@@ -569,47 +609,26 @@ __device__ __forceinline__ void k_halo_body(int bx, int by, const real* __restri
             tzs[a] = t;
         }
 #pragma unroll
-        for (int a = 0; a < NI; ++a) {
-            const int ex = olx + a * T;
+        for (int b = 0; b < NI; ++b) {
+            const int ey = oly + b * T;
 #pragma unroll
-            for (int b = 0; b < NI; ++b) {
-                const int ey = oly + b * T;
-#pragma unroll
-                for (int c = 0; c < NI; ++c) {
-                    const int ez = olz + c * T;
-                    if (ex < E && ey < E && ez < E) {
-                        const int tile = (txs[a] * nty + tys[b]) * ntz + tzs[c];
-                        const int2 range = make_int2(tile_off[tile], tile_off[tile + 1]);
-                        const real v = scratch[static_cast<size_t>(tile) * slab + (ex * E + ey) * E + ez];
-                        s += range.x != range.y ? v : real(0);
-                    }
-                }
+            for (int c = 0; c < NI; ++c) {
+                const int ez = olz + c * T;
+                if (ey < E && ez < E) add_column(tys[b] * ntz + tzs[c], ey, ez);
             }
         }
         grid[(static_cast<size_t>(lx) * my + ly) * mz + lz] = s;
     } else {
-        const int T = g.T;
-        const int id = bx * blockDim.x + threadIdx.x;
-        if (id >= g.m[0] * my * mz) return;
-        const int lz = id % mz, ly = (id / mz) % my, lx = id / (mz * my);
-        const int tlx = lx / T, tly = ly / T, tlz = lz / T;
-        const int olx = lx - tlx * T, oly = ly - tly * T, olz = lz - tlz * T;
-        int tx = tlx;
-        for (int ex = olx; ex < E; ex += T) {
-            int ty = tly;
-            for (int ey = oly; ey < E; ey += T) {
-                int tz = tlz;
-                for (int ez = olz; ez < E; ez += T) {
-                    const int tile = (tx * nty + ty) * ntz + tz;
-                    if (tile_off[tile] != tile_off[tile + 1])
-                        s += scratch[static_cast<size_t>(tile) * slab + (ex * E + ey) * E + ez];
-                    tz = tz == 0 ? ntz - 1 : tz - 1;
-                }
-                ty = ty == 0 ? nty - 1 : ty - 1;
+        int ty = tly;
+        for (int ey = oly; ey < E; ey += T) {
+            int tz = tlz;
+            for (int ez = olz; ez < E; ez += T) {
+                add_column(ty * ntz + tz, ey, ez);
+                tz = tz == 0 ? ntz - 1 : tz - 1;
             }
-            tx = tx == 0 ? ntx - 1 : tx - 1;
+            ty = ty == 0 ? nty - 1 : ty - 1;
         }
-        grid[id] = s;
+        grid[(static_cast<size_t>(lx) * my + ly) * mz + lz] = s;
     }
 }
 
@@ -682,7 +701,7 @@ __global__ void k_scale(cplx* __restrict__ spec, ScaleParams<real> sp) {
 template <int P, int E>
 constexpr int interp_plane() { return E * E + (((P - E * E) % 32) + 32) % 32; }
 template <typename real> struct InterpCfg;
-template <> struct InterpCfg<float> { static constexpr int NB = 8, NWARP = 4; };
+template <> struct InterpCfg<float> { static constexpr int NB = 8, NWARP = 8; };
 template <> struct InterpCfg<double> { static constexpr int NB = 8, NWARP = 4; };
 
 template <typename real, int P>
@@ -826,7 +845,7 @@ __device__ __forceinline__ void k_interp_body(int bx, const real* __restrict__ g
 }
 
 template <typename real, int P>
-__global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, const Vec4<real>* __restrict__ rec,
+__global__ void __launch_bounds__(32 * InterpCfg<real>::NWARP) k_interp(const real* __restrict__ grid, const Vec4<real>* __restrict__ rec,
                                                 const int2* __restrict__ idx, const int* __restrict__ tile_off,
                                                 const real* __restrict__ wcoef, const real* __restrict__ dwcoef,
                                                 Geom g, Vec4<real> inv_alpha, double* __restrict__ phi_out,
@@ -835,17 +854,17 @@ __global__ void __launch_bounds__(128) k_interp(const real* __restrict__ grid, c
 }
 
 // ---- real-space sum of R over the cell list (Sec. 3.1.1) -----------------------------------------
-// Real-space sum over a cell list of cubic cells of edge w >= rc/R ("reach" R).  For a target cell
-// c, the source cells within reach form columns (dx, dy) with a z-run dz in [-dzmax, dzmax] that
-// keeps the box distance below rc (host table).  Cells are stored z-fastest, so each z-run is one
-// or two contiguous particle ranges (more when the box has fewer than 2R+1 cells per axis and the
-// run wraps onto itself: every wrapped piece is a different periodic image).
+// Real-space sum over a cell list of cells of edge >= rc/R along x and y and >= rc/Rz along z (Rz = R
+// for float64 and float-float plans, 4 for float32 plans).  Cells are stored z-fastest, so a run of cells
+// along z in one (x, y) column is one contiguous particle range, or several where the run wraps around
+// the periodic box (every wrapped piece is a different periodic image).
 //
-// One warp per target cell.  The warp flattens the cell's ranges into one stream of candidate
-// sources; lanes take 32 consecutive candidates at a time (coalesced loads) and test each against
-// every target of the cell (held in shared memory, up to kShortMaxT per pass, accumulated in
-// registers per lane).  Candidates pass a float32 test against a slightly enlarged cutoff and are
-// then evaluated in the plan's precision:
+// float64 / float-float plans (k_short_q, k_short_ff): one warp per target cell; the source cells within
+// reach form columns (dx, dy) with a z-run dz in [-dzmax, dzmax] keeping the box distance below rc (host
+// table); the warp flattens the ranges into one candidate stream, tests 32 candidates at a time against
+// the cell's targets in float32 and queues passing pairs for full-warp evaluation.
+// float32 plans (k_short): one target at a time, over its own neighbourhood (target_ranges).
+// Pairs are evaluated in the plan's precision:
 //   R(r) = 1/r - P1(u),  -R'(r)/r = 1/r^3 + Q(u),  u = 2 r^2/rc^2 - 1   (host-fitted polynomials).
 // In float32 the displacement is float-float: positions are (hi, lo) pairs relative to their cell and
 // the cell shift d w is split the same way, d = (hi_i - (hi_j + s_hi)) + ((lo_i - s_lo) - lo_j), so a
@@ -1090,7 +1109,9 @@ __device__ __forceinline__ void k_short_body(int bx, const Vec4<float>* __restri
     const int R = g.reach, Rz = g.reachz;
     for (int k = threadIdx.x; k < 3 * NSH; k += blockDim.x) {
         const int d = k / NSH, i = k % NSH, rd = d == 2 ? Rz : R;
-        const double o = (i - rd) * g.cellw[d];
+        // static indices only: in the fused batch g is a copy in registers, not a kernel parameter
+        const double w = d == 0 ? g.cellw[0] : (d == 1 ? g.cellw[1] : g.cellw[2]);
+        const double o = (i - rd) * w;
         sh_hi[d][i] = static_cast<float>(o);
         sh_lo[d][i] = static_cast<float>(o - static_cast<double>(sh_hi[d][i]));
     }
@@ -1163,7 +1184,7 @@ __device__ __forceinline__ void k_short_body(int bx, const Vec4<float>* __restri
 }
 
 template <int D>
-__global__ void __launch_bounds__(32 * kShortWarps, 8) k_short(const Vec4<float>* __restrict__ rec, const int2* __restrict__ idx,
+__global__ void __launch_bounds__(32 * kShortWarps) k_short(const Vec4<float>* __restrict__ rec, const int2* __restrict__ idx,
                                                             const Vec4<float>* __restrict__ lo,
                                                             const int* __restrict__ cell_off, int rcap, Geom g,
                                                             const __grid_constant__ ShortParams<float, D> kp,

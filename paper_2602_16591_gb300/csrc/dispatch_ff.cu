@@ -30,7 +30,8 @@ cudaError_t spread_p(int ntiles, const Geom& g, const float4* rh, const float4* 
     auto kern = k_spread_ff<P>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    kern<<<ntiles, spread_threads<P, kTile64>(), smem, s>>>(rh, rl, idx, tile_off, wc, g.degw, kf, scratch);
+    const SpreadChain ch{g.K, g.nt[1] * g.nt[2], ntiles};
+    kern<<<ntiles / g.K, spread_threads<P, kTile64>(), smem, s>>>(rh, rl, idx, tile_off, wc, g.degw, kf, ch, scratch);
     return cudaGetLastError();
 }
 

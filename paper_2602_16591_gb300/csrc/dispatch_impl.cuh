@@ -8,13 +8,13 @@ namespace {
 
 template <int P>
 cudaError_t spread_p(int ntiles, const Vec4<real_t>* rec, const int2* idx, const int* tile_off, const real_t* wcoef,
-                     int degw, real_t* scratch, cudaStream_t s) {
+                     int degw, SpreadChain ch, real_t* scratch, cudaStream_t s) {
     const int threads = spread_threads<P, spread_tile<real_t>()>();
     const size_t smem = Launch<real_t>::spread_smem(P, degw);
     auto kern = k_spread<real_t, P>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
-    kern<<<ntiles, threads, smem, s>>>(rec, idx, tile_off, wcoef, degw, scratch);
+    kern<<<ntiles / ch.K, threads, smem, s>>>(rec, idx, tile_off, wcoef, degw, ch, scratch);
     return cudaGetLastError();
 }
 
@@ -55,9 +55,9 @@ size_t Launch<real_t>::interp_smem(int P, int degw) {
 
 template <>
 cudaError_t Launch<real_t>::spread(int P, int ntiles, const Vec4<real_t>* rec, const int2* idx, const int* tile_off,
-                                 const real_t* wcoef, int degw, real_t* scratch, cudaStream_t s) {
+                                 const real_t* wcoef, int degw, SpreadChain ch, real_t* scratch, cudaStream_t s) {
     switch (P) {
-#define X(p) case p: return spread_p<p>(ntiles, rec, idx, tile_off, wcoef, degw, scratch, s);
+#define X(p) case p: return spread_p<p>(ntiles, rec, idx, tile_off, wcoef, degw, ch, scratch, s);
         PSWF_P_CASES(X)
 #undef X
         default: return cudaErrorInvalidValue;

@@ -74,11 +74,9 @@ __global__ void __launch_bounds__(spread_threads<P, kTile64>()) k_spread_ff(cons
                                                                    const int2* __restrict__ idx,
                                                                    const int* __restrict__ tile_off,
                                                                    const float* __restrict__ wc, int degw, int kf,
-                                                                   float2* __restrict__ scratch) {
+                                                                   SpreadChain ch, float2* __restrict__ scratch) {
     constexpr int T = kTile64, E = T + P - 1, CH = kSpreadFFChunk;
-    const int tile = blockIdx.x;
-    const int beg = tile_off[tile], end = tile_off[tile + 1];
-    if (beg == end) return;
+    const int qx = blockIdx.x / ch.nyz, rem = blockIdx.x - qx * ch.nyz;   // chain: tiles (qx K + k, rem)
     const int nc = P * (degw + 1);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ff* sw = reinterpret_cast<ff*>(smem_raw);                        // CH * 3 * P
@@ -93,6 +91,11 @@ __global__ void __launch_bounds__(spread_threads<P, kTile64>()) k_spread_ff(cons
     ff acc[E];
 #pragma unroll
     for (int a = 0; a < E; ++a) acc[a] = ff{0.f, 0.f};
+    float2* heads = scratch;
+    float2* tails = scratch + static_cast<size_t>(ch.ntiles) * T * E * E;
+    for (int k = 0; k < ch.K; ++k) {
+    const int tile = (qx * ch.K + k) * ch.nyz + rem;
+    const int beg = tile_off[tile], end = tile_off[tile + 1];
     for (int base = beg; base < end; base += CH) {
         const int cnt = min(CH, end - base);
         __syncthreads();
@@ -131,30 +134,44 @@ __global__ void __launch_bounds__(spread_threads<P, kTile64>()) k_spread_ff(cons
             }
         }
     }
-    if (own) {
-        float2* out = scratch + static_cast<size_t>(tile) * E * E * E;
+    if (own) {   // the tile's head (complete along x within the chain); carry the rest
+        float2* out = heads + static_cast<size_t>(tile) * T * E * E;
 #pragma unroll
-        for (int a = 0; a < E; ++a) {
+        for (int a = 0; a < T; ++a) {
+            const ff v = ff_norm(acc[a]);
+            out[a * E * E + col] = make_float2(v.h, v.l);
+        }
+#pragma unroll
+        for (int a = 0; a < E; ++a) acc[a] = a + T < E ? acc[a + T] : ff{0.f, 0.f};
+    }
+    }
+    if (own) {   // the chain's tail
+        float2* out = tails + static_cast<size_t>(blockIdx.x) * (E - T) * E * E;
+#pragma unroll
+        for (int a = 0; a < E - T; ++a) {
             const ff v = ff_norm(acc[a]);
             out[a * E * E + col] = make_float2(v.h, v.l);
         }
     }
 }
 
-// Halo sum of the float-float slabs (same enumeration as k_halo) into the float64 grid.
+// Halo sum of the float-float slabs (heads and x-chain tails, the enumeration of k_halo) into the
+// float64 grid; the NZ overlapping z tiles are unrolled so their loads are in flight together.
 template <int NZ>
 __global__ void __launch_bounds__(256) k_halo_ff(const float2* __restrict__ scratch, const int* __restrict__ tile_off, Geom g,
                                                  double* __restrict__ grid) {
-    const int my = g.m[1], mz = g.m[2], T = g.T, E = g.T + g.P - 1;
-    const int ntx = g.nt[0], nty = g.nt[1], ntz = g.nt[2];
+    (void)tile_off;
+    const int my = g.m[1], mz = g.m[2], T = g.T, E = g.T + g.P - 1, ET = E - T;
+    const int nty = g.nt[1], ntz = g.nt[2], K = g.K, nchx = g.nt[0] / g.K;
     const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= g.m[0] * my * mz) return;
     const int lz = id % mz, ly = (id / mz) % my, lx = id / (mz * my);
     const int tlx = lx / T, tly = ly / T, tlz = lz / T;
     const int olx = lx - tlx * T, oly = ly - tly * T, olz = lz - tlz * T;
-    const size_t slab = static_cast<size_t>(E) * E * E;
-    // the NZ slabs along z (at most ceil(E / T)) are unrolled and loaded unconditionally (values of
-    // empty tiles, which never wrote their slab, are discarded by a select): independent loads
+    const size_t plane = static_cast<size_t>(E) * E;
+    const float2* heads = scratch;
+    const float2* tails = scratch + static_cast<size_t>(g.nt[0]) * nty * ntz * T * plane;
+    const int qc = tlx / K;
     int tzs[NZ];
 #pragma unroll
     for (int c = 0; c < NZ; ++c) {   // tiny grids wrap repeatedly
@@ -163,29 +180,36 @@ __global__ void __launch_bounds__(256) k_halo_ff(const float2* __restrict__ scra
         tzs[c] = t;
     }
     ff s{0.f, 0.f};
-    int tx = tlx;
-    for (int ex = olx; ex < E; ex += T) {
-        int ty = tly;
-        for (int ey = oly; ey < E; ey += T) {
-            float2 v[NZ];
-            bool use[NZ];
+    int ty = tly;
+    for (int ey = oly; ey < E; ey += T) {
+        float2 v[NZ];
+#pragma unroll
+        for (int c = 0; c < NZ; ++c) {
+            const int ez = olz + c * T;
+            v[c] = make_float2(0.f, 0.f);
+            if (ez < E)
+                v[c] = heads[(static_cast<size_t>(tlx) * nty * ntz + ty * ntz + tzs[c]) * T * plane + olx * plane +
+                             ey * E + ez];
+        }
+#pragma unroll
+        for (int c = 0; c < NZ; ++c)
+            if (olz + c * T < E) s = ff_add(s, ff{v[c].x, v[c].y});
+        for (int j = 1;; ++j) {   // tails of the chains before this one that reach lx
+            const int e = lx - (qc - j + 1) * K * T;
+            if (e >= ET) break;
+            int q = (qc - j) % nchx;
+            q += q < 0 ? nchx : 0;
 #pragma unroll
             for (int c = 0; c < NZ; ++c) {
                 const int ez = olz + c * T;
-                use[c] = false;
-                v[c] = make_float2(0.f, 0.f);
                 if (ez < E) {
-                    const int tile = (tx * nty + ty) * ntz + tzs[c];
-                    use[c] = tile_off[tile] != tile_off[tile + 1];
-                    v[c] = scratch[static_cast<size_t>(tile) * slab + (ex * E + ey) * E + ez];
+                    const float2 w = tails[(static_cast<size_t>(q) * nty * ntz + ty * ntz + tzs[c]) * ET * plane +
+                                           e * plane + ey * E + ez];
+                    s = ff_add(s, ff{w.x, w.y});
                 }
             }
-#pragma unroll
-            for (int c = 0; c < NZ; ++c)
-                if (use[c]) s = ff_add(s, ff{v[c].x, v[c].y});
-            ty = ty == 0 ? nty - 1 : ty - 1;
         }
-        tx = tx == 0 ? ntx - 1 : tx - 1;
+        ty = ty == 0 ? nty - 1 : ty - 1;
     }
     grid[id] = ff_to_double(s);
 }

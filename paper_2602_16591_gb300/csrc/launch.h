@@ -13,8 +13,9 @@ template <typename real>
 struct Launch {
     static size_t spread_smem(int P, int degw);
     static size_t interp_smem(int P, int degw);
+    // ch: x-chains of ch.K tiles (grid of ntiles / ch.K blocks), slab layout of k_spread
     static cudaError_t spread(int P, int ntiles, const Vec4<real>* rec, const int2* idx, const int* tile_off,
-                              const real* wcoef, int degw, real* scratch, cudaStream_t s);
+                              const real* wcoef, int degw, SpreadChain ch, real* scratch, cudaStream_t s);
     static cudaError_t interp(int P, int ntiles, const real* grid, const Vec4<real>* rec, const int2* idx,
                               const int* tile_off, const real* wcoef, const real* dwcoef, const Geom& g,
                               Vec4<real> inv_alpha, double* phi, double* f, cudaStream_t s);

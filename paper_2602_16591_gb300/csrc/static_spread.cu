@@ -79,7 +79,14 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
     const size_t need_status = align256(sizeof(double) * 4);
     const size_t need_rec = align256(sizeof(pswf::Vec4<double>) * n);
     const size_t need_idx = align256(sizeof(int2) * n);
-    const size_t need_slab = align256(sizeof(double) * ntiles * size_t(E) * E * E);
+    int K = 1;   // x-chains of the spreading (as in the plans): largest divisor of nt with K T <= 32
+    for (int k = 32 / T; k >= 1; --k)
+        if (nt % k == 0) {
+            K = k;
+            break;
+        }
+    const size_t need_slab = align256(sizeof(double) * (ntiles * size_t(T) * E * E +
+                                                        (ntiles / K) * size_t(E - T) * E * E));
     const size_t need = need_coef + need_key + need_perm + 2 * need_tcnt + 2 * need_ccnt + need_status +
                         2 * need_rec + 2 * need_idx + need_slab;
     if (need > kStaticScratchBytes)
@@ -155,6 +162,8 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
     g.P = P;
     g.T = T;
     g.reach = 1;
+    g.reachz = 1;
+    g.K = K;
     g.degw = p->deg_w;
     g.degr = 0;
     for (int d = 0; d < 3; ++d) {
@@ -181,7 +190,8 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
                                               sr_idx, nullptr, nullptr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail_static(EWALD_ECUDA, std::string("sort launch: ") + cudaGetErrorString(e));
-    e = pswf::Launch<double>::spread(P, static_cast<int>(ntiles), sp_rec, sp_idx, tile_off, coef, p->deg_w, slab, s);
+    e = pswf::Launch<double>::spread(P, static_cast<int>(ntiles), sp_rec, sp_idx, tile_off, coef, p->deg_w,
+                                     pswf::SpreadChain{K, nt * nt, static_cast<int>(ntiles)}, slab, s);
     if (e != cudaSuccess) return fail_static(EWALD_ECUDA, std::string("spread launch: ") + cudaGetErrorString(e));
     const int mm = m * m * m;
     pswf::k_halo<double, 0><<<(mm + 255) / 256, 256, 0, s>>>(slab, tile_off, g, grid);

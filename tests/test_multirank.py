@@ -53,7 +53,7 @@ def test_stage_roofline_report():
     import bench
 
     class Params:
-        P, deg_w, deg_r, tile, grid = 12, 8, 11, 8, (96, 96, 96)
+        P, deg_w, deg_r, tile, grid, precision = 12, 8, 11, 8, (96, 96, 96), 1
 
     n = 100_000
     stages = {"sort": 0.04, "spread": 0.07, "halo": 0.033, "scale": 0.008, "interp": 0.105, "short": 0.16,
@@ -64,8 +64,9 @@ def test_stage_roofline_report():
     # spreading: records in, grid out; P^3 + P^2 + 3 P (d_w + 1) multiply-adds per particle
     assert rows["spread"]["bytes"] == n * 24 + 96 ** 3 * 4
     assert rows["spread"]["flops"] == n * 2 * (12 ** 3 + 12 ** 2 + 3 * 12 * 9)
-    # halo: 12^3 tiles of 19^3 slab values in, the grid out
-    assert rows["halo"]["bytes"] == 12 ** 3 * 19 ** 3 * 4 + 96 ** 3 * 4
+    # halo: x-chains of K = 4 tiles: heads of 8 x 19^2 values per tile, tails of 11 x 19^2 per chain in,
+    # the grid out
+    assert rows["halo"]["bytes"] == (12 ** 3 * 8 * 19 ** 2 + 12 ** 3 // 4 * 11 * 19 ** 2) * 4 + 96 ** 3 * 4
     for r in rows.values():
         assert 0 < r.get("frac_hbm", 1e-9) < 1 and 0 < r.get("frac_alu", 1e-9) < 1
     # a broken input never raises: the bench line must still print
