@@ -57,6 +57,7 @@ def realspace(x, rho, L, split, rcut, targets=None, chunk=64):
         shifts = np.array([(a, b, c) for a in rngs[0] for b in rngs[1] for c in rngs[2]], dtype=np.float64) * Lv
     phi = np.zeros(len(tgt))
     grad = np.zeros((len(tgt), 3))
+    chunk = max(1, min(chunk, (1 << 24) // max(len(x), 1)))   # memory only: ~0.4 GB per (t, n, 3) array
     for s in range(0, len(tgt), chunk):
         ti = tgt[s:s + chunk]
         d0 = x[ti, None, :] - x[None, :, :]

@@ -28,7 +28,9 @@ def _nvcc():
 def _compile(src, verbose_ptxas=False):
     os.makedirs(BUILD, exist_ok=True)
     obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
-    cmd = [_nvcc(), "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include"),
+    # host code: no contraction of a*b+c into fma, so that x86-64 and AArch64 hosts round alike
+    cmd = [_nvcc(), "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=off",
+           "-I" + os.path.join(ROOT, "include"),
            "-I" + CSRC, "-c", os.path.join(CSRC, src), "-o", obj] + ARCH
     if src.endswith(".cu"):
         cmd += ["--expt-relaxed-constexpr", "-Xcudafe", "--diag_suppress=177"]

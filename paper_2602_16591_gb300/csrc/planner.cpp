@@ -21,6 +21,68 @@ namespace {
 
 constexpr double kPi = 3.14159265358979323846;
 
+// ---------------------------------------------------------- double-double ----
+// Unevaluated sums hi + lo of two doubles (about 32 significant digits) from plain IEEE double
+// operations: Knuth's error-free two-sum, the fma residual of a product, and one Newton correction
+// for quotients and square roots.  The same operations give the same bits on every IEEE-754 host,
+// unlike long double (80-bit on x86-64, 128-bit software arithmetic on AArch64).
+struct DD {
+    double hi = 0, lo = 0;
+};
+
+inline DD two_sum(double a, double b) {
+    const double s = a + b, bb = s - a;
+    return {s, (a - (s - bb)) + (b - bb)};
+}
+inline DD fast_two_sum(double a, double b) {   // |a| >= |b| (or a == 0)
+    const double s = a + b;
+    return {s, b - (s - a)};
+}
+inline DD dd(double a) { return {a, 0.0}; }
+inline DD operator+(DD a, DD b) {
+    DD s = two_sum(a.hi, b.hi);
+    const DD t = two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return fast_two_sum(s.hi, s.lo);
+}
+inline DD operator-(DD a) { return {-a.hi, -a.lo}; }
+inline DD operator-(DD a, DD b) { return a + (-b); }
+inline DD operator*(DD a, DD b) {
+    const double p = a.hi * b.hi;
+    double e = std::fma(a.hi, b.hi, -p);
+    e += a.hi * b.lo + a.lo * b.hi;
+    return fast_two_sum(p, e);
+}
+inline DD operator*(DD a, double b) {
+    const double p = a.hi * b;
+    double e = std::fma(a.hi, b, -p);
+    e += a.lo * b;
+    return fast_two_sum(p, e);
+}
+inline DD operator/(DD a, double b) {
+    const double q1 = a.hi / b;
+    const double p = q1 * b, pe = std::fma(q1, b, -p);   // q1 b = p + pe exactly
+    DD r = two_sum(a.hi, -p);
+    r.lo += a.lo - pe;
+    return fast_two_sum(q1, (r.hi + r.lo) / b);
+}
+inline DD operator/(DD a, DD b) {
+    const double q1 = a.hi / b.hi;
+    const DD r = a - b * q1;
+    const double q2 = r.hi / b.hi;
+    const DD r2 = r - b * q2;
+    return fast_two_sum(q1, q2) + dd(r2.hi / b.hi);
+}
+inline DD dd_sqrt(DD a) {   // a >= 0
+    if (!(a.hi > 0)) return dd(0.0);
+    const double x = std::sqrt(a.hi);
+    const DD r = a - DD{x * x, std::fma(x, x, -x * x)};
+    return fast_two_sum(x, (r.hi + r.lo) / (2.0 * x));
+}
+inline double to_double(DD a) { return a.hi + a.lo; }
+
 // Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_N.
 void gauss_legendre(int N, std::vector<double>& x, std::vector<double>& w) {
     x.assign(N, 0.0);
@@ -160,47 +222,42 @@ double Prolate::psi(double x) const {
     return s;
 }
 
-long double Prolate::psi_ld(long double x) const {
+double Prolate::dpsi(double x) const {
+    // P'_{n+1} = P'_{n-1} + (2n+1) P_n, alongside the three-term recurrence of P_n
     const int nmax = 2 * static_cast<int>(a.size()) - 2;
-    long double p0 = 1.0L, p1 = x, s = a[0];
+    double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0, s = 0.0;   // P_{n-1}, P_n, P'_{n-1}, P'_n at n = 1
     for (int n = 1; n < nmax; ++n) {
-        long double p2 = ((2.0L * n + 1.0L) * x * p1 - n * p0) / (n + 1.0L);
+        const double p2 = ((2.0 * n + 1.0) * x * p1 - n * p0) / (n + 1.0);
+        const double d2 = d0 + (2.0 * n + 1.0) * p1;
+        if ((n + 1) % 2 == 0) s += a[(n + 1) / 2] * d2;
         p0 = p1;
         p1 = p2;
-        if ((n + 1) % 2 == 0) s += a[(n + 1) / 2] * p1;
+        d0 = d1;
+        d1 = d2;
     }
-    return s;
+    return s;   // the P_0 term has zero derivative
 }
 
-double Prolate::dpsi(double x) const {
-    // P'_{n+1} = P'_{n-1} + (2n+1) P_n
-    const int nmax = 2 * static_cast<int>(a.size()) - 2;
-    std::vector<double> P(nmax + 1), D(nmax + 1);
-    P[0] = 1.0;
-    D[0] = 0.0;
-    if (nmax >= 1) { P[1] = x; D[1] = 1.0; }
-    for (int n = 1; n < nmax; ++n) {
-        P[n + 1] = ((2.0 * n + 1.0) * x * P[n] - n * P[n - 1]) / (n + 1.0);
-        D[n + 1] = D[n - 1] + (2.0 * n + 1.0) * P[n];
+void Prolate::psi_int0_dd(double xhi, double xlo, double* psi_out, double* int0_out) const {
+    // psi(x) = sum_i a_i P_{2i}(x) and int_0^x psi = a_0 x + sum_{i>=1} a_i (P_{2i+1} - P_{2i-1})(x) / (4i+1)
+    // (int_0^x P_n = (P_{n+1} - P_{n-1}) / (2n+1)), both from one run of the Legendre recurrence
+    const int K = static_cast<int>(a.size());
+    const DD x{xhi, xlo};
+    DD p0 = dd(1.0), p1 = x, sp = dd(a[0]), si = x * a[0];
+    for (int n = 1; n <= 2 * K - 2; ++n) {
+        const DD p2 = (x * p1 * (2.0 * n + 1.0) - p0 * static_cast<double>(n)) / (n + 1.0);   // P_{n+1}
+        if (n % 2 == 1) {
+            if ((n + 1) / 2 < K) sp = sp + p2 * a[(n + 1) / 2];
+        } else {
+            si = si + (p2 - p0) * a[n / 2] / (2.0 * n + 1.0);
+        }
+        p0 = p1;
+        p1 = p2;
     }
-    double s = 0;
-    for (size_t i = 0; i < a.size(); ++i) s += a[i] * D[2 * i];
-    return s;
-}
-
-long double Prolate::int0_ld(long double x) const {
-    // int_0^x P_0 = x; int_0^x P_n = (P_{n+1}(x) - P_{n-1}(x)) / (2n+1) for n >= 1
-    const int nmax = 2 * static_cast<int>(a.size());
-    std::vector<long double> P(nmax + 1);
-    P[0] = 1.0L;
-    P[1] = x;
-    for (int n = 1; n < nmax; ++n) P[n + 1] = ((2.0L * n + 1.0L) * x * P[n] - n * P[n - 1]) / (n + 1.0L);
-    long double s = a[0] * x;
-    for (size_t i = 1; i < a.size(); ++i) {
-        const int n = 2 * static_cast<int>(i);
-        s += a[i] * (P[n + 1] - P[n - 1]) / (2.0L * n + 1.0L);
-    }
-    return s;
+    psi_out[0] = sp.hi;
+    psi_out[1] = sp.lo;
+    int0_out[0] = si.hi;
+    int0_out[1] = si.lo;
 }
 
 double Prolate::cos_transform(double omega) const {
@@ -296,33 +353,37 @@ ewald_opts default_opts() {
 // ------------------------------------------------------------------- fits ---
 namespace {
 
-// Chebyshev interpolant of f at deg+1 first-kind nodes on [-1, 1], converted to monomials.
+// Chebyshev interpolant of f at deg+1 first-kind nodes on [-1, 1], converted to monomials.  The
+// coefficient sums and the conversion (whose T_k coefficients reach 2^(k-1)) run in double-double.
 template <class F>
 std::vector<double> cheb_monomial_fit(F f, int deg) {
     const int N = deg + 1;
-    std::vector<long double> fv(N), ch(N, 0.0L);
+    std::vector<double> fv(N);
+    std::vector<DD> ch(N);
     for (int j = 0; j < N; ++j) fv[j] = f(std::cos(kPi * (j + 0.5) / N));
     for (int k = 0; k < N; ++k) {
-        long double s = 0;
-        for (int j = 0; j < N; ++j) s += fv[j] * std::cos(kPi * k * (j + 0.5) / N);
-        ch[k] = s * (k == 0 ? 1.0L : 2.0L) / N;
+        DD s;
+        for (int j = 0; j < N; ++j) s = s + dd(fv[j]) * std::cos(kPi * k * (j + 0.5) / N);
+        ch[k] = s * (k == 0 ? 1.0 : 2.0) / static_cast<double>(N);
     }
-    // monomial coefficients of T_k by the recurrence T_{k+1} = 2 z T_k - T_{k-1}
-    std::vector<long double> tm1(N, 0.0L), t0(N, 0.0L), mono(N, 0.0L);
-    t0[0] = 1.0L;
+    // monomial coefficients of T_k by the recurrence T_{k+1} = 2 z T_k - T_{k-1} (exact integers)
+    std::vector<DD> tm1(N), t0(N), mono(N);
+    t0[0] = dd(1.0);
     for (int k = 0; k < N; ++k) {
-        for (int i = 0; i < N; ++i) mono[i] += ch[k] * t0[i];
-        std::vector<long double> t1(N, 0.0L);
-        for (int i = 0; i + 1 < N; ++i) t1[i + 1] += 2.0L * t0[i];
-        for (int i = 0; i < N; ++i) t1[i] -= (k == 0 ? 0.0L : tm1[i]);
+        for (int i = 0; i < N; ++i) mono[i] = mono[i] + ch[k] * t0[i];
+        std::vector<DD> t1(N);
         if (k == 0) {                      // T_1 = z
-            std::fill(t1.begin(), t1.end(), 0.0L);
-            if (N > 1) t1[1] = 1.0L;
+            if (N > 1) t1[1] = dd(1.0);
+        } else {
+            for (int i = 0; i + 1 < N; ++i) t1[i + 1] = t0[i] * 2.0;
+            for (int i = 0; i < N; ++i) t1[i] = t1[i] - tm1[i];
         }
         tm1 = t0;
         t0 = t1;
     }
-    return std::vector<double>(mono.begin(), mono.end());
+    std::vector<double> out(N);
+    for (int i = 0; i < N; ++i) out[i] = to_double(mono[i]);
+    return out;
 }
 
 template <class F>
@@ -353,29 +414,58 @@ std::vector<double> fit_window(const Prolate& pw, int P, int deg, bool deriv, do
     return out;
 }
 
-std::vector<double> fit_radial(const Prolate& ps, double rc_d, int deg, int which, double* rel_err) {
-    const long double norm = 2.0L / (static_cast<long double>(ps.lambda) * ps.psi0);
-    const long double rc = rc_d;
-    auto f = [&](double u) -> double {
-        const long double x = std::sqrt((static_cast<long double>(u) + 1.0L) / 2.0L);
-        const long double Phi = norm * ps.int0_ld(x);
-        if (which == 0) return static_cast<double>(Phi / (x * rc));                 // P1
-        const long double dPhi = norm * ps.psi_ld(x);
-        return static_cast<double>((dPhi * x - Phi) / (x * x * x) / (rc * rc * rc));  // Q
-    };
-    auto c = cheb_monomial_fit(f, deg);
+// P1(u) = Phi(x) / (x r_c) and Q(u) = (x Phi'(x) - Phi(x)) / (x^3 r_c^3), x = r / r_c = sqrt((u + 1)/2),
+// with Phi(x) = 2 / (lambda_0 psi(0)) int_0^x psi (eq. Phi_cs).  Q's numerator is O(x^3) while both of
+// its terms are O(x): double-double keeps the digits that the subtraction cancels.
+RadialFitter::RadialFitter(const Prolate& ps, double rc) : ps_(ps), rc_(rc) {}
+
+void RadialFitter::values(double u, double* p1, double* q) const {
+    const DD norm = dd(2.0) / (dd(ps_.lambda) * ps_.psi0);
+    const DD x = dd_sqrt(two_sum(u, 1.0) * 0.5);
+    double pv[2], iv[2];
+    ps_.psi_int0_dd(x.hi, x.lo, pv, iv);
+    const DD Phi = norm * DD{iv[0], iv[1]};
+    const DD rc = dd(rc_);
+    if (p1) *p1 = to_double(Phi / (x * rc));
+    if (q) {
+        const DD dPhi = norm * DD{pv[0], pv[1]};
+        *q = to_double((dPhi * x - Phi) / (x * x * x) / (rc * rc * rc));
+    }
+}
+
+double RadialFitter::value(double u, int which) const {
+    double v = 0;
+    values(u, which == 0 ? &v : nullptr, which == 0 ? nullptr : &v);
+    return v;
+}
+
+std::vector<double> RadialFitter::fit(int deg, int which, double* rel_err) {
+    auto c = cheb_monomial_fit([&](double u) { return value(u, which); }, deg);
     if (rel_err) {
-        // error measured away from u = -1, where the sampled form itself loses digits in FP64
-        double e = 0, s = 0;
-        for (int i = 0; i <= 1000; ++i) {
-            const double u = -1.0 + 1e-4 + (2.0 - 1e-4) * i / 1000.0;
-            const double v = f(u);
-            s = std::max(s, std::fabs(v));
-            e = std::max(e, std::fabs(horner(c.data(), deg, u) - v));
+        // error measured away from u = -1, where x -> 0 and both functions approach finite limits
+        // that the sampled form reaches only through the cancellation; both functions are sampled
+        // at the check points on first use
+        constexpr int kCheck = 1000;
+        auto check_u = [](int i) { return -1.0 + 1e-4 + (2.0 - 1e-4) * i / kCheck; };
+        if (check_[0].empty()) {
+            check_[0].resize(kCheck + 1);
+            check_[1].resize(kCheck + 1);
+            for (int i = 0; i <= kCheck; ++i) values(check_u(i), &check_[0][i], &check_[1][i]);
         }
-        *rel_err = e / s;
+        const std::vector<double>& v = check_[which];
+        double e = 0, sm = 0;
+        for (int i = 0; i <= kCheck; ++i) {
+            sm = std::max(sm, std::fabs(v[i]));
+            e = std::max(e, std::fabs(horner(c.data(), deg, check_u(i)) - v[i]));
+        }
+        *rel_err = e / sm;
     }
     return c;
+}
+
+std::vector<double> fit_radial(const Prolate& ps, double rc, int deg, int which, double* rel_err) {
+    RadialFitter f(ps, rc);
+    return f.fit(deg, which, rel_err);
 }
 
 void scale_tables(const ewald_params& p, const Prolate& ps, const Prolate& pw, std::vector<double>& iw,
@@ -589,10 +679,11 @@ HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opt
     // ---- radial polynomials in u = 2 r^2/rc^2 - 1
     {
         bool ok = false;
+        RadialFitter rf(ps, p.rc);
         for (int deg = 4; deg <= kDegRMax && !ok; ++deg) {
             double e1 = 0, e2 = 0;
-            auto c1 = fit_radial(ps, p.rc, deg, 0, &e1);
-            auto c2 = fit_radial(ps, p.rc, deg, 1, &e2);
+            auto c1 = rf.fit(deg, 0, &e1);
+            auto c2 = rf.fit(deg, 1, &e2);
             if (e1 <= p.fit_tol && e2 <= p.fit_tol) {
                 ok = true;
                 p.deg_r = deg;

@@ -18,8 +18,8 @@ struct Prolate {
     explicit Prolate(double c);
     double psi(double x) const;
     double dpsi(double x) const;
-    long double int0_ld(long double x) const;     // int_0^x psi, long double
-    long double psi_ld(long double x) const;
+    // psi(x) and int_0^x psi in double-double (x = xhi + xlo; each result as {hi, lo})
+    void psi_int0_dd(double xhi, double xlo, double* psi, double* int0) const;
     double cos_transform(double omega) const;     // int_{-1}^{1} psi(u) cos(omega u) du
 };
 
@@ -52,6 +52,21 @@ constexpr int kDegWMax = 40, kDegRMax = 60;
 
 std::vector<double> fit_window(const Prolate& pw, int P, int deg, bool deriv, double* max_err);
 std::vector<double> fit_radial(const Prolate& ps, double rc, int deg, int which, double* rel_err);
+
+// The two radial functions sampled once for a degree search: fit(deg, which, &rel_err) equals
+// fit_radial(ps, rc, deg, which, &rel_err) and reuses the error-check samples across degrees.
+class RadialFitter {
+public:
+    RadialFitter(const Prolate& ps, double rc);
+    std::vector<double> fit(int deg, int which, double* rel_err);
+    double value(double u, int which) const;   // P1 (which = 0) or Q (which = 1) at u = 2 r^2/rc^2 - 1
+    void values(double u, double* p1, double* q) const;   // both (either pointer may be NULL)
+
+private:
+    const Prolate& ps_;
+    double rc_;
+    std::vector<double> check_[2];   // both functions at the error-check points (filled on first use)
+};
 void scale_tables(const ewald_params& p, const Prolate& ps, const Prolate& pw, std::vector<double>& iw,
                   std::vector<double>& mtab);
 
