@@ -301,6 +301,88 @@ static __global__ void __launch_bounds__(1024) k_scan(const int* __restrict__ cn
     k_scan_body(blockIdx.x, cnt0, off0, n0, cnt1, off1, n1);
 }
 
+// Multi-block form of k_scan for long counter arrays (the ~1e6 tiles and cells of the 1e7-particle
+// plans), in three launches without inter-block waits: k_scan_sums (one block per kScanChunk counters
+// of either segment: its sum), k_scan over the block sums (their exclusive offsets, two blocks), and
+// k_scan_apply (every block scans its chunk again from its offset).  Blocks [0, nb0) cover segment 0.
+constexpr int kScanItems = 16, kScanChunk = 1024 * kScanItems;
+
+// exclusive scan of the chunk cnt[i0 .. i0 + kScanChunk) of a length-N array from carry (written to off
+// when off != nullptr); returns the chunk's total.  1024 threads.
+__device__ __forceinline__ int scan_chunk(const int* __restrict__ cnt, int* __restrict__ off, int N, int base,
+                                          int carry) {
+    __shared__ int wsum[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int v[kScanItems], s = 0;
+    const int i0 = base + threadIdx.x * kScanItems;
+    if (i0 + kScanItems <= N) {   // 64-byte runs (chunk starts are multiples of 16K counters)
+        const int4* c4 = reinterpret_cast<const int4*>(cnt + i0);
+#pragma unroll
+        for (int q = 0; q < kScanItems / 4; ++q) {
+            const int4 t = c4[q];
+            v[4 * q] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) v[k] = (i0 + k < N) ? cnt[i0 + k] : 0;
+    }
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) s += v[k];
+    int x = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    const int total = wsum[31];
+    if (off) {
+        int e = carry + (warp > 0 ? wsum[warp - 1] : 0) + x - s;
+#pragma unroll
+        for (int k = 0; k < kScanItems; ++k) {
+            if (i0 + k < N) off[i0 + k] = e;
+            e += v[k];
+        }
+    }
+    __syncthreads();   // wsum is reused by the caller's next chunk
+    return total;
+}
+
+static __global__ void __launch_bounds__(1024) k_scan_sums(const int* __restrict__ cnt0, int n0, int nb0,
+                                                           const int* __restrict__ cnt1, int n1,
+                                                           int* __restrict__ bsum0, int* __restrict__ bsum1) {
+    const int b = blockIdx.x, seg = b >= nb0, lb = seg ? b - nb0 : b;
+    const int t = scan_chunk(seg ? cnt1 : cnt0, nullptr, seg ? n1 : n0, lb * kScanChunk, 0);
+    if (threadIdx.x == 0) (seg ? bsum1 : bsum0)[lb] = t;
+}
+
+// boff0[0 .. nb0] and boff1[0 .. nb1]: exclusive block offsets of the two segments (k_scan of the sums)
+static __global__ void __launch_bounds__(1024) k_scan_apply(const int* __restrict__ cnt0, int* __restrict__ off0, int n0,
+                                                            int nb0, const int* __restrict__ cnt1, int* __restrict__ off1,
+                                                            int n1, const int* __restrict__ boff0,
+                                                            const int* __restrict__ boff1) {
+    const int b = blockIdx.x, seg = b >= nb0, lb = seg ? b - nb0 : b;
+    const int* boff = seg ? boff1 : boff0;
+    const int N = seg ? n1 : n0;
+    int* off = seg ? off1 : off0;
+    scan_chunk(seg ? cnt1 : cnt0, off, N, lb * kScanChunk, boff[lb]);
+    if (lb == 0 && threadIdx.x == 0) off[N] = boff[(N + kScanChunk - 1) / kScanChunk];
+}
+
 // ---- stable order inside tiles and cells (counting sort, deterministic ranks) --------------------
 // k_prep's atomic ranks depend on the schedule, and so would every sum over the particles of a tile
 // or cell (spreading, the real-space sum).  k_place lists each bin's particles at their atomic
@@ -704,6 +786,52 @@ template <typename real> struct InterpCfg;
 template <> struct InterpCfg<float> { static constexpr int NB = 8, NWARP = 8; };
 template <> struct InterpCfg<double> { static constexpr int NB = 8, NWARP = 4; };
 
+// Stages the tile's extended block of the grid, x in [tx T, tx T + E) (and y, z alike, periodic), as
+// G[y SP + x E + z].  The block's E^2 z-rows are contiguous in the grid unless they cross the periodic
+// end, and every row starts on a 16-byte boundary (z0 = tz T, T multiple of 16 / sizeof(real), m_z a
+// multiple of T, the grid 256-byte aligned): NV lanes load one row in 16-byte vectors (the last vector
+// may read up to VW - 1 values past the row, still inside the grid), 32 / NV rows per warp step.  Tiles
+// whose rows wrap (the last ones along z, or E > m) load element by element.
+template <typename real, int T, int E, int SP, int NWARP>
+__device__ __forceinline__ void stage_block(const real* __restrict__ grid, int mx, int my, int mz, int tx, int ty,
+                                            int tz, int lane, int warp, real* __restrict__ G) {
+    constexpr int VW = 16 / static_cast<int>(sizeof(real)), NV = (E + VW - 1) / VW, RPW = 32 / NV;
+    using V = typename std::conditional<sizeof(real) == 4, float4, double2>::type;
+    static_assert((T * sizeof(real)) % 16 == 0, "tile rows must start on 16-byte boundaries");
+    auto wrap = [](int v, int m) {
+        while (v >= m) v -= m;   // v < 2 m except for blocks wider than the grid
+        return v;
+    };
+    const int z0 = tz * T;
+    if (z0 + NV * VW <= mz && E <= mx && E <= my) {
+        const int rl = lane / NV, k = lane - rl * NV;   // row of the warp step, vector in the row
+        for (int r0 = warp * RPW; r0 < E * E; r0 += NWARP * RPW) {
+            const int row = r0 + rl;
+            if (rl < RPW && row < E * E) {
+                const int ex = row / E, ey = row - ex * E;
+                const int gx = wrap(tx * T + ex, mx), gy = wrap(ty * T + ey, my);
+                const V v = reinterpret_cast<const V*>(grid + (static_cast<size_t>(gx) * my + gy) * mz + z0)[k];
+                real* dst = G + ey * SP + ex * E + k * VW;
+                if constexpr (sizeof(real) == 4) {
+                    dst[0] = v.x;
+                    if (k * VW + 1 < E) dst[1] = v.y;
+                    if (k * VW + 2 < E) dst[2] = v.z;
+                    if (k * VW + 3 < E) dst[3] = v.w;
+                } else {
+                    dst[0] = v.x;
+                    if (k * VW + 1 < E) dst[1] = v.y;
+                }
+            }
+        }
+    } else {
+        for (int e = warp * 32 + lane; e < E * E * E; e += NWARP * 32) {
+            const int ez = e % E, ey = (e / E) % E, ex = e / (E * E);
+            const int gx = wrap(tx * T + ex, mx), gy = wrap(ty * T + ey, my), gz = wrap(z0 + ez, mz);
+            G[ey * SP + ex * E + ez] = grid[(static_cast<size_t>(gx) * my + gy) * mz + gz];
+        }
+    }
+}
+
 template <typename real, int P>
 __device__ __forceinline__ void k_interp_body(int bx, const real* __restrict__ grid, const Vec4<real>* __restrict__ rec,
                                                 const int2* __restrict__ idx, const int* __restrict__ tile_off,
@@ -731,21 +859,9 @@ __device__ __forceinline__ void k_interp_body(int bx, const real* __restrict__ g
         sc[i] = wcoef[i];
         sd[i] = dwcoef[i];
     }
-    for (int e = threadIdx.x; e < E * E * E; e += blockDim.x) {
-        const int ez = e % E, ey = (e / E) % E, ex = e / (E * E);
-        int gx = tx * T + ex, gy = ty * T + ey, gz = tz * T + ez;
-        gx -= gx >= mx ? mx : 0;
-        gy -= gy >= my ? my : 0;
-        gz -= gz >= mz ? mz : 0;
-        if (gx >= mx || gy >= my || gz >= mz) {   // extended block wider than the grid (small m)
-            gx %= mx;
-            gy %= my;
-            gz %= mz;
-        }
-        G[ey * SP + ex * E + ez] = grid[(static_cast<size_t>(gx) * my + gy) * mz + gz];
-    }
-    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    stage_block<real, T, E, SP, NWARP>(grid, mx, my, mz, tx, ty, tz, lane, warp, G);
+    __syncthreads();
     real* ww = sw + warp * NB * 6 * PP;
     for (int b0 = beg + warp * NB; b0 < end; b0 += NWARP * NB) {
         const int cnt = min(NB, end - b0);

@@ -262,17 +262,41 @@ __global__ void __launch_bounds__(32 * kInterpFFWarps) k_interp_ff(const float2*
         sdh[i] = dwc[i];
     }
     __shared__ int sxo[NWARP][P], syo[NWARP][P], szo[NWARP][P];   // unstaged: wrapped grid offsets
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if constexpr (STAGED) {
-        for (int e = threadIdx.x; e < E * E * E; e += blockDim.x) {
-            const int ez = e % E, ey = (e / E) % E, ex = e / (E * E);
-            const int gx = (tx * T + ex) % mx, gy = (ty * T + ey) % my, gz = (tz * T + ez) % mz;
-            const float2 v = grid[(static_cast<size_t>(gx) * my + gy) * mz + gz];
-            G[e] = ff{v.x, v.y};
+        // z-rows of the block in 16-byte vectors (two float2 values) where they do not cross the periodic
+        // end (rows start on 32-byte boundaries: z0 = 4 tz, m_z a multiple of 4); element-wise otherwise
+        constexpr int NV = (E + 1) / 2, RPW = 32 / NV;
+        const int z0 = tz * T;
+        auto wrap = [](int v, int m) {
+            while (v >= m) v -= m;
+            return v;
+        };
+        if (z0 + 2 * NV <= mz) {
+            const int rl = lane / NV, k = lane - rl * NV;
+            for (int r0 = warp * RPW; r0 < E * E; r0 += NWARP * RPW) {
+                const int row = r0 + rl;   // ex E + ey
+                if (rl < RPW && row < E * E) {
+                    const int ex = row / E, ey = row - ex * E;
+                    const int gx = wrap(tx * T + ex, mx), gy = wrap(ty * T + ey, my);
+                    const float4 v =
+                        reinterpret_cast<const float4*>(grid + (static_cast<size_t>(gx) * my + gy) * mz + z0)[k];
+                    ff* dst = G + row * E + 2 * k;
+                    dst[0] = ff{v.x, v.y};
+                    if (2 * k + 1 < E) dst[1] = ff{v.z, v.w};
+                }
+            }
+        } else {
+            for (int e = threadIdx.x; e < E * E * E; e += blockDim.x) {
+                const int ez = e % E, ey = (e / E) % E, ex = e / (E * E);
+                const int gx = wrap(tx * T + ex, mx), gy = wrap(ty * T + ey, my), gz = wrap(z0 + ez, mz);
+                const float2 v = grid[(static_cast<size_t>(gx) * my + gy) * mz + gz];
+                G[e] = ff{v.x, v.y};
+            }
         }
     }
     __syncthreads();
 
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     ff* ww = sw + warp * NB * 6 * P;
     for (int b0 = beg + warp * NB; b0 < end; b0 += NWARP * NB) {
         const int cnt = min(NB, end - b0);

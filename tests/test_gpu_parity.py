@@ -5,6 +5,9 @@ end-to-end parity uses the converged Ewald sum.  The bar: relative l2 error of p
 (over all 3n components) and the relative energy error at most 2 * tol; stage outputs of the
 FP64 path within a few hundred ulps of the oracle (bounded by the polynomial-fit tolerance).
 """
+import os
+import sys
+
 import numpy as np
 import pytest
 
@@ -18,6 +21,8 @@ pe = require_library()
 from oracle import exact  # noqa: E402
 from oracle.alg2 import Alg2  # noqa: E402
 from workloads import nacl_lattice, uniform_alternating, uniform_neutral  # noqa: E402
+
+sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
 
 
 def _rel(a, b):
@@ -209,6 +214,37 @@ def test_full_size_sampled(full_size, tol, prec):
     _check(phi[tg], F[tg], None, ref, tol)
     assert np.isfinite(E)
 
+
+
+# ------------------------------------------------------ long counter arrays (multi-block scan) --
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_long_cell_arrays_multi_block_scan(prec):
+    """More than 64K cell counters (n = 2e4 at grid density 24 with cells of r_c / 4: ~2.5e5 cells) take
+    the multi-block counting-sort scan; phi and F at 256 sampled targets within the accuracy bar."""
+    x, rho, L = uniform_neutral(20_000, seed=3)
+    plan, phi, F, E = _run(x, rho, L, 1e-6, prec, sr_reach=4, grid_density=24.0, autotune=0)
+    q = plan.params
+    assert q.cells[0] * q.cells[1] * q.cells[2] > 4 * 16384
+    tg = np.linspace(0, len(x) - 1, 256).astype(np.int64)
+    ref = exact.pswf_exact(x, rho, L, targets=tg)
+    _check(phi[tg], F[tg], None, ref, 1e-6)
+    assert np.isfinite(E)
+
+
+# ------------------------------------- n = 1e7 (large workload), stored oracle values at 64 targets --
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_large_1e7_against_stored_oracle_values(prec):
+    """n = 1e7 uniform neutral charges at tol 1e-8 and grid density 4, the large configuration the bench
+    times (float-float kernels for 'mixed', float64 for 'fp64'): phi and F at the 64 targets of
+    tests/golden/uniform1e7_seed0.txt (converged PSWF Ewald sum of the oracle, written by
+    tests/golden/make_reference_values.py) within the accuracy bar."""
+    import make_reference_values as stored
+    tg, phi_ref, F_ref, _ = stored.read("uniform1e7")
+    x, rho, L = uniform_neutral(10_000_000, seed=0)
+    plan, phi, F, E = _run(x, rho, L, 1e-8, prec, grid_density=4.0, autotune=0)
+    del plan
+    _check(phi[tg], F[tg], None, (phi_ref, None, None, F_ref), 1e-8)
+    assert np.isfinite(E)
 
 # ------------------------------------------------------------------------ edge cases --
 def test_two_charges():
