@@ -216,6 +216,8 @@ struct ewald_plan_s {
     int* sr_cz = nullptr;      // float-float plans: z cell index of every cell-sorted record
     void* grid_ff = nullptr;   // float-float plans: the interpolation grid as {hi, lo} float pairs
     int4* sr_cols = nullptr;   // real-space columns {dx, dy, dzmax, 0} with box distance < rc
+    int* scan_tmp = nullptr;   // multi-block scan: block sums and offsets of both segments (long arrays only)
+    int scan_nb0 = 0, scan_nb1 = 0;
     int n_cols = 0;
     int sr_rcap = 0;           // bound on the contiguous source ranges of one neighbourhood
     void* scratch = nullptr;
@@ -297,7 +299,7 @@ struct ewald_plan_s {
     }
 
     ~ewald_plan_s() {
-        void* bufs[] = {key_rank, perm, zeroed, tile_off, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, sr_lo, sr_f32, sr_cz, grid_ff, sr_cols, scratch,
+        void* bufs[] = {key_rank, perm, zeroed, tile_off, cell_off, sp_rec, sp_idx, sr_rec, sr_idx, sr_lo, sr_f32, sr_cz, grid_ff, sr_cols, scan_tmp, scratch,
                         pooled_grids ? nullptr : grid_a, pooled_grids ? nullptr : grid_b, pooled_grids ? nullptr : spec,
                         wcoef, dwcoef, p1c, qc, iw, mtab, gcoef, phi_int, f_int, epart, energy_d, x_stage, rho_stage};
         for (void* b : bufs)
@@ -425,6 +427,29 @@ cudaError_t stable_ranks(ewald_plan p, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Counting-sort offsets of the tiles and cells: one block per segment for short arrays; beyond
+// kScanMulti counters the multi-block form (a single block would walk the chunks one after another).
+constexpr int kScanMulti = 4 * pswf::kScanChunk;
+inline int round4(int v) { return (v + 3) & ~3; }   // int4 alignment of the sub-arrays of scan_tmp
+size_t scan_tmp_ints(int nb0, int nb1) { return round4(nb0) + round4(nb1) + round4(nb0 + 1) + round4(nb1 + 1); }
+
+cudaError_t launch_scan(ewald_plan p, cudaStream_t s) {
+    if (!p->scan_tmp) {
+        pswf::k_scan<<<2, 1024, 0, s>>>(p->tile_cnt, p->tile_off, p->ntiles, p->cell_cnt, p->cell_off, p->ncells);
+        return cudaGetLastError();
+    }
+    const int nb0 = p->scan_nb0, nb1 = p->scan_nb1;
+    int* bsum0 = p->scan_tmp;
+    int* bsum1 = bsum0 + round4(nb0);
+    int* boff0 = bsum1 + round4(nb1);
+    int* boff1 = boff0 + round4(nb0 + 1);
+    pswf::k_scan_sums<<<nb0 + nb1, 1024, 0, s>>>(p->tile_cnt, p->ntiles, nb0, p->cell_cnt, p->ncells, bsum0, bsum1);
+    pswf::k_scan<<<2, 1024, 0, s>>>(bsum0, boff0, nb0, bsum1, boff1, nb1);
+    pswf::k_scan_apply<<<nb0 + nb1, 1024, 0, s>>>(p->tile_cnt, p->tile_off, p->ntiles, nb0, p->cell_cnt, p->cell_off,
+                                                  p->ncells, boff0, boff1);
+    return cudaGetLastError();
+}
+
 template <typename real, typename cplx>
 int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, double* f, cudaStream_t s) {
     using pswf::Vec4;
@@ -435,8 +460,7 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     const int tb = 256, nb = (n + tb - 1) / tb;
     pswf::k_prep<std::is_same<real, float>::value><<<nb, tb, 0, s>>>(x, rho, g, p->key_rank, p->tile_cnt, p->cell_cnt, p->status);
     PSWF_CUDA(cudaGetLastError());
-    pswf::k_scan<<<2, 1024, 0, s>>>(p->tile_cnt, p->tile_off, p->ntiles, p->cell_cnt, p->cell_off, p->ncells);
-    PSWF_CUDA(cudaGetLastError());
+    PSWF_CUDA(launch_scan(p, s));
     PSWF_CUDA(stable_ranks(p, s));
     auto* sp_rec = static_cast<Vec4<real>*>(p->sp_rec);
     auto* sr_rec = static_cast<Vec4<real>*>(p->sr_rec);
@@ -550,8 +574,7 @@ int run_pipeline_ff(ewald_plan p, const double* x, const double* rho, double* ph
     const int tb = 256, nb = (n + tb - 1) / tb;
     pswf::k_prep<false><<<nb, tb, 0, s>>>(x, rho, g, p->key_rank, p->tile_cnt, p->cell_cnt, p->status);
     PSWF_CUDA(cudaGetLastError());
-    pswf::k_scan<<<2, 1024, 0, s>>>(p->tile_cnt, p->tile_off, p->ntiles, p->cell_cnt, p->cell_off, p->ncells);
-    PSWF_CUDA(cudaGetLastError());
+    PSWF_CUDA(launch_scan(p, s));
     PSWF_CUDA(stable_ranks(p, s));
     auto* sp_h = static_cast<float4*>(p->sp_rec);
     auto* sp_l = sp_h + nn;
@@ -952,6 +975,15 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
             cudaGetLastError();
             delete p;
             return fail(EWALD_ENOMEM, "device allocation of the real-space columns failed");
+        }
+    }
+    if (std::max(p->ntiles, p->ncells) > kScanMulti) {   // long counter arrays: multi-block scan scratch
+        p->scan_nb0 = (p->ntiles + pswf::kScanChunk - 1) / pswf::kScanChunk;
+        p->scan_nb1 = (p->ncells + pswf::kScanChunk - 1) / pswf::kScanChunk;
+        if (dmalloc(&p->scan_tmp, sizeof(int) * scan_tmp_ints(p->scan_nb0, p->scan_nb1)) != cudaSuccess) {
+            cudaGetLastError();
+            delete p;
+            return fail(EWALD_ENOMEM, "device allocation of the scan scratch failed");
         }
     }
     // batch members (pre != nullptr) get their streams and events only when a batch graph is captured
