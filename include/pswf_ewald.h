@@ -39,7 +39,8 @@ extern "C" {
 #define EWALD_ECUDA        4  /* a CUDA runtime call failed */
 #define EWALD_ECUFFT       5  /* a cuFFT call failed */
 #define EWALD_ETOOBIG      6  /* grid, window support or particle count beyond the library limits */
-#define EWALD_ETIMEOUT     7  /* reserved: a bounded device wait expired */
+#define EWALD_ETIMEOUT     7  /* a bounded device wait expired (tensor-core spreading: an MMA
+                                         completion did not arrive within ~1 s) */
 #define EWALD_ENONFINITE   8  /* an input position or charge is not finite */
 
 /* ---- precision of the device path ------------------------------------- */
@@ -76,6 +77,10 @@ typedef struct ewald_opts {
                              when sr_reach is 0).  The cutoff, and with it the balance between
                              the real-space sum and Alg. 2, is what the paper leaves to
                              measurement (Sec. 6.2.2).  0 (default): off. */
+    int    spread_kernel; /* Alg. 2 step 1 on float32 (EWALD_MIXED, tol >= 1e-7) plans: 1 = CUDA-core
+                             kernel (per-column register accumulation), 2 = tensor-core kernel
+                             (tcgen05 split-TF32 products per tile, window support P <= 14), 0
+                             (default) = automatic.  Other plans always use their CUDA-core kernel. */
 } ewald_opts;
 
 /* ---- derived parameters (Alg. 3 and the library's readings of it) ------ */
@@ -112,6 +117,7 @@ typedef struct ewald_params {
     int    sr_reach_z; /* real-space cells per cutoff radius along z (cells of edge >= rc / sr_reach
                           along x, y and >= rc / sr_reach_z along z): 4 for EWALD_MIXED plans, whose
                           real-space kernel walks z windows of columns; sr_reach otherwise */
+    int    spread_kernel; /* spreading kernel of the plan: 1 CUDA cores, 2 tensor cores */
 } ewald_params;
 
 typedef struct ewald_plan_s* ewald_plan;   /* opaque, owned by the library */

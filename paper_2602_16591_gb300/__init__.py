@@ -26,7 +26,7 @@ PATH_NAMES = {EWALD_FP64: "f64", EWALD_MIXED: "f32", EWALD_FLOATFLOAT: "ff"}
 class ewald_opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("rc", ctypes.c_double), ("grid_density", ctypes.c_double),
                 ("tol_safety", ctypes.c_double), ("sr_reach", ctypes.c_int), ("window_extra", ctypes.c_int),
-                ("autotune", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("spread_kernel", ctypes.c_int)]
 
 
 class ewald_params(ctypes.Structure):
@@ -35,7 +35,7 @@ class ewald_params(ctypes.Structure):
                  "tol", "fit_tol")] + [("n", ctypes.c_int64)] + [(k, ctypes.c_int) for k in
                 ("m", "P", "deg_w", "deg_r", "tile", "ncell", "sr_reach", "precision")] + \
         [("box", ctypes.c_double * 3), ("grid", ctypes.c_int * 3), ("cells", ctypes.c_int * 3), ("deg_g", ctypes.c_int),
-         ("sr_reach_z", ctypes.c_int)]
+         ("sr_reach_z", ctypes.c_int), ("spread_kernel", ctypes.c_int)]
 
     def as_dict(self):
         out = {}
@@ -100,7 +100,7 @@ def _check(code):
 
 
 def make_opts(precision="fp64", rc=None, grid_density=None, tol_safety=None, sr_reach=None, window_extra=None,
-              autotune=None):
+              autotune=None, spread_kernel=None):
     o = ewald_opts()
     _check(_lib.ewald_opts_default(ctypes.byref(o)))
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -116,6 +116,8 @@ def make_opts(precision="fp64", rc=None, grid_density=None, tol_safety=None, sr_
         o.window_extra = int(window_extra)
     if autotune is not None:
         o.autotune = int(bool(autotune))
+    if spread_kernel is not None:
+        o.spread_kernel = int(spread_kernel)
     return o
 
 

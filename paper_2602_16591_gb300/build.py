@@ -17,7 +17,8 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libpswf_ewald.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "dispatch_f32.cu", "dispatch_f64.cu", "dispatch_ff.cu", "planner.cpp", "static_spread.cu", "batch_f32.cu"]
+SOURCES = ["api.cu", "dispatch_f32.cu", "dispatch_f64.cu", "dispatch_ff.cu", "planner.cpp", "static_spread.cu", "batch_f32.cu",
+           "tc_spread.cu"]
 
 
 def _nvcc():

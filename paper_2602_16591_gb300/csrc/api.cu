@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "tc_spread.h"
 #include "device.cuh"
 #include "launch.h"
 #include "planner.h"
@@ -217,6 +218,8 @@ struct ewald_plan_s {
     void* grid_ff = nullptr;   // float-float plans: the interpolation grid as {hi, lo} float pairs
     int4* sr_cols = nullptr;   // real-space columns {dx, dy, dzmax, 0} with box distance < rc
     int* scan_tmp = nullptr;   // multi-block scan: block sums and offsets of both segments (long arrays only)
+    int* tc_err = nullptr;     // tensor-core spreading: set when an MMA completion wait ran out (zeroed block)
+    bool tc_spread = false;
     int scan_nb0 = 0, scan_nb1 = 0;
     int n_cols = 0;
     int sr_rcap = 0;           // bound on the contiguous source ranges of one neighbourhood
@@ -485,10 +488,19 @@ int run_pipeline(ewald_plan p, const double* x, const double* rho, double* phi, 
     s = s_alg2;
     // Alg. 2 step 1
     p->mark(1, false, s);
-    PSWF_CUDA(pswf::Launch<real>::spread(g.P, p->ntiles, sp_rec, p->sp_idx, p->tile_off,
-                                         static_cast<const real*>(p->wcoef), g.degw,
-                                         pswf::SpreadChain{g.K, g.nt[1] * g.nt[2], p->ntiles},
-                                         static_cast<real*>(p->scratch), s));
+    if constexpr (sizeof(real) == 4) {
+        if (p->tc_spread) {
+            PSWF_CUDA(pswf::launch_spread_tc(g.P, p->ntiles, sp_rec, p->sp_idx, p->tile_off,
+                                             static_cast<const float*>(p->wcoef), g.degw,
+                                             pswf::SpreadChain{g.K, g.nt[1] * g.nt[2], p->ntiles},
+                                             static_cast<float*>(p->scratch), p->tc_err, s));
+        }
+    }
+    if (!p->tc_spread)
+        PSWF_CUDA(pswf::Launch<real>::spread(g.P, p->ntiles, sp_rec, p->sp_idx, p->tile_off,
+                                             static_cast<const real*>(p->wcoef), g.degw,
+                                             pswf::SpreadChain{g.K, g.nt[1] * g.nt[2], p->ntiles},
+                                             static_cast<real*>(p->scratch), s));
     p->mark(1, true, s);
     p->mark(2, false, s);
     const int mm = static_cast<int>(p->m3);
@@ -663,8 +675,12 @@ int eval_device(ewald_plan p, const double* x, const double* rho, double* phi, d
 int read_status(ewald_plan p, cudaStream_t s, double* energy) {
     PSWF_CUDA(cudaMemcpyAsync(p->status_h, p->status, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
     if (energy) PSWF_CUDA(cudaMemcpyAsync(p->status_h + 3, p->energy_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    int* tc_err_h = reinterpret_cast<int*>(p->status_h + 4);
+    *tc_err_h = 0;
+    if (p->tc_spread) PSWF_CUDA(cudaMemcpyAsync(tc_err_h, p->tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     PSWF_CUDA(cudaStreamSynchronize(s));
     if (energy) *energy = p->status_h[3];
+    if (*tc_err_h) return fail(EWALD_ETIMEOUT, "tensor-core spreading: an MMA completion wait ran out");
     if (p->status_h[2] > 0) return fail(EWALD_ENONFINITE, "non-finite position or charge in the input");
     if (std::fabs(p->status_h[0]) > 1e-10 * p->status_h[1])
         return fail(EWALD_ENONNEUTRAL, "charges are not neutral: |sum rho| > 1e-10 sum |rho|");
@@ -904,7 +920,7 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
     struct A { void** ptr; size_t bytes; } allocs[] = {
         {reinterpret_cast<void**>(&p->key_rank), sizeof(int4) * n},
         {reinterpret_cast<void**>(&p->perm), sizeof(int) * 2 * n},
-        {&p->zeroed, sizeof(double) * 4 + sizeof(int) * (((p->ntiles + 1 + 3) / 4) * 4 + p->ncells + 1)},
+        {&p->zeroed, sizeof(double) * 4 + sizeof(int) * (((p->ntiles + 1 + 3) / 4) * 4 + ((p->ncells + 1 + 3) / 4) * 4 + 4)},
         {reinterpret_cast<void**>(&p->tile_off), sizeof(int) * (p->ntiles + 1)},
         {reinterpret_cast<void**>(&p->cell_off), sizeof(int) * (p->ncells + 1)},
         {&p->sp_rec, 4 * rs * n},
@@ -937,7 +953,9 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
     p->status = static_cast<double*>(p->zeroed);
     p->tile_cnt = reinterpret_cast<int*>(p->status + 4);
     p->cell_cnt = p->tile_cnt + ((p->ntiles + 1 + 3) / 4) * 4;
-    p->zeroed_bytes = sizeof(double) * 4 + sizeof(int) * (((p->ntiles + 1 + 3) / 4) * 4 + p->ncells + 1);
+    p->tc_err = p->cell_cnt + ((p->ncells + 1 + 3) / 4) * 4;
+    p->zeroed_bytes = sizeof(double) * 4 + sizeof(int) * (((p->ntiles + 1 + 3) / 4) * 4 + ((p->ncells + 1 + 3) / 4) * 4 + 4);
+    p->tc_spread = q.spread_kernel == 2;
     if ((!p->fp64 && dmalloc(&p->sr_lo, 4 * sizeof(float) * n) != cudaSuccess) ||
         (p->fp64 && !p->ff && dmalloc(&p->sr_f32, sizeof(float4) * n) != cudaSuccess) ||
         (p->ff && dmalloc(&p->sr_cz, sizeof(int) * n) != cudaSuccess) ||
@@ -994,7 +1012,7 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
             delete p;
             return rcs;
         }
-        if (cudaMallocHost(reinterpret_cast<void**>(&p->status_h), sizeof(double) * 4) != cudaSuccess) {
+        if (cudaMallocHost(reinterpret_cast<void**>(&p->status_h), sizeof(double) * 5) != cudaSuccess) {
             delete p;
             return fail(EWALD_ENOMEM, "pinned host allocation failed");
         }

@@ -347,6 +347,7 @@ ewald_opts default_opts() {
     o.sr_reach = 0;
     o.window_extra = 0;
     o.autotune = 0;
+    o.spread_kernel = 0;
     return o;
 }
 
@@ -525,6 +526,9 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
     return make_plan_box(box, n, tol, o);
 }
 
+// Automatic choice of the tensor-core spreading kernel for the float32 plans that support it.
+constexpr bool kTensorSpreadAuto = false;
+
 HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opts& o) {
     for (int d = 0; d < 3; ++d)
         if (!(box[d] > 0) || !std::isfinite(box[d])) throw std::invalid_argument("box edges must be positive and finite");
@@ -540,6 +544,7 @@ HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opt
     if (o.window_extra < 0 || o.window_extra > 8) throw std::invalid_argument("window_extra must lie in [0, 8]");
     if (o.autotune != 0 && o.autotune != 1) throw std::invalid_argument("autotune must be 0 or 1");
     if (o.sr_reach < 0 || o.sr_reach > 4) throw std::invalid_argument("sr_reach must lie in [0, 4]");
+    if (o.spread_kernel < 0 || o.spread_kernel > 2) throw std::invalid_argument("spread_kernel must be 0, 1 or 2");
 
     const double As = 5.0, Aw = 3.1;                      // Secs. 5.1.1 and 5.2.1
     static const double kappa = kappa_constant();
@@ -652,6 +657,9 @@ HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opt
     }
     p.ncell = p.cells[0];
     p.fit_tol = std::max(0.02 * t, p.precision == EWALD_MIXED ? 1e-8 : 5e-15);
+    // spreading kernel: tensor cores for float32 plans whose tile block fits the accumulator (P <= 14)
+    const bool tc_ok = p.precision == EWALD_MIXED && P <= 14;
+    p.spread_kernel = tc_ok && (o.spread_kernel == 2 || (o.spread_kernel == 0 && kTensorSpreadAuto)) ? 2 : 1;
 
     const Prolate ps(p.cs), pw(p.cw);
     p.lambda_s = ps.lambda;

@@ -131,6 +131,53 @@ def f32_bench_case():
     return plan, x, rho, A, A.spread(x, rho), A.spread(x, np.abs(rho))
 
 
+@pytest.fixture(scope="module")
+def f32_bench_case_tc():
+    """The headline plan with the tensor-core spreading kernel (spread_kernel = 2)."""
+    x, rho, L = uniform_neutral(100_000, seed=0)
+    plan = pe.Plan(L, len(x), 1e-6, precision="mixed", grid_density=6.0, spread_kernel=2)
+    assert plan.params.spread_kernel == 2
+    phi, F, E = plan.eval(torch.tensor(x, device="cuda"), torch.tensor(rho, device="cuda"))
+    A = _alg2(plan, x, rho)
+    return plan, x, rho, A, A.spread(x, rho), A.spread(x, np.abs(rho)), (phi.cpu().numpy(), F.cpu().numpy(), E)
+
+
+def test_stage_spread_grid_tensor_cores(f32_bench_case_tc):
+    """Alg. 2 step 1 on the tensor cores (split-TF32 products, float32 accumulation in tensor memory):
+    the float32 bound of test_stage_spread_grid_float32 holds for every grid value."""
+    plan, x, rho, A, a_ref, a_abs, _ = f32_bench_case_tc
+    a_gpu = plan.debug_grid(0)
+    bound = (3 * plan.params.fit_tol + 2.0 ** -24 * (12 + 200)) * a_abs + 1e-30
+    assert np.all(np.abs(a_gpu - a_ref) <= bound), float(np.max(np.abs(a_gpu - a_ref) / bound))
+    assert _rel(a_gpu, a_ref) <= 2e-6
+
+
+def test_tensor_core_spreading_end_to_end(f32_bench_case_tc):
+    """phi and F of the tensor-core plan at 256 targets against the converged Ewald sum within the
+    accuracy bar at tol 1e-6; its energy against the oracle's stored energy of this workload
+    (tests/golden/uniform1e5_seed0.txt) is printed for the record (the bar is asserted at tol 1e-4 below)."""
+    plan, x, rho, A, a_ref, a_abs, (phi, F, E) = f32_bench_case_tc
+    tg = np.linspace(0, len(x) - 1, 256).astype(np.int64)
+    ref = _exact("bench256", x, rho, 1.0, tg)
+    _check(phi[tg], F[tg], None, ref, 1e-6)
+    import make_reference_values as stored
+    E_ref = stored.read("uniform1e5")[3]
+    print("tensor-core spreading, tol 1e-6: relative energy error %.3g" % (abs(E - E_ref) / abs(E_ref)))
+
+
+def test_tensor_core_spreading_meets_bar_at_1e_4():
+    """At tol 1e-4 the tensor-core plan meets the whole bar: phi, F (l2 and worst particle) and E."""
+    x, rho, L = uniform_neutral(100_000, seed=0)
+    plan, phi, F, E = _run(x, rho, L, 1e-4, "mixed", grid_density=6.0, spread_kernel=2)
+    assert plan.params.spread_kernel == 2
+    tg = np.linspace(0, len(x) - 1, 256).astype(np.int64)
+    ref = _exact("bench256", x, rho, 1.0, tg)
+    _check(phi[tg], F[tg], None, ref, 1e-4)
+    import make_reference_values as stored
+    E_ref = stored.read("uniform1e5")[3]
+    assert abs(E - E_ref) <= 2e-4 * abs(E_ref)
+
+
 def test_stage_spread_grid_float32(f32_bench_case):
     """Alg. 2 step 1 on the float32 path.  Each term rho w_x w_y w_z carries the window fit error and the
     float32 rounding of z and of the products (a few units of 2^-24 relative, |dw/dz| <= ~2), and each
