@@ -79,8 +79,10 @@ typedef struct ewald_opts {
                              measurement (Sec. 6.2.2).  0 (default): off. */
     int    spread_kernel; /* Alg. 2 step 1 on float32 (EWALD_MIXED, tol >= 1e-7) plans: 1 = CUDA-core
                              kernel (per-column register accumulation), 2 = tensor-core kernel
-                             (tcgen05 split-TF32 products per tile, window support P <= 14), 0
-                             (default) = automatic.  Other plans always use their CUDA-core kernel. */
+                             (tcgen05 split-TF32 products per tile, window support P <= 14; its
+                             float32 accumulation in tensor memory leaves a relative energy error of
+                             ~5e-6), 0 (default) = automatic: tensor cores for tol >= 1e-5, CUDA cores
+                             below.  Other plans always use their CUDA-core kernel. */
 } ewald_opts;
 
 /* ---- derived parameters (Alg. 3 and the library's readings of it) ------ */
@@ -226,6 +228,12 @@ int ewald_profile(ewald_plan plan, int enable);
  * stage over the recorded evaluations into ms[EWALD_NSTAGES] and their number
  * into *count. */
 int ewald_profile_read(ewald_plan plan, double* ms, int* count);
+
+/* Check of the device timeout path (no plan): one warp waits on an mbarrier
+ * that nothing arrives at, with the bounded wait of the tensor-core spreading
+ * (here 2e7 SM clocks, ~10 ms, instead of 2e9).  Returns EWALD_ETIMEOUT when the wait
+ * ran out, as it must, after which the CUDA context stays usable. */
+int ewald_debug_wait_timeout(void);
 
 /* ---- host-side tables (no CUDA call), for tests and tooling ------------- */
 

@@ -77,6 +77,7 @@ def _load():
         "ewald_scale_table": (I, [ctypes.POINTER(ewald_params), P]),
         "ewald_profile": (I, [P, I]),
         "ewald_profile_read": (I, [P, P, ctypes.POINTER(ctypes.c_int)]),
+        "ewald_debug_wait_timeout": (I, []),
         "ewald_spread_static": (I, [ctypes.POINTER(ewald_params), P, P, P, P]),
         "ewald_plan_batch_create": (I, [I, P, P, D, ctypes.POINTER(ewald_opts), ctypes.POINTER(P)]),
         "ewald_eval_batch": (I, [P, P, P, P, P, P, P, P]),

@@ -433,6 +433,7 @@ cudaError_t stable_ranks(ewald_plan p, cudaStream_t s) {
 // Counting-sort offsets of the tiles and cells: one block per segment for short arrays; beyond
 // kScanMulti counters the multi-block form (a single block would walk the chunks one after another).
 constexpr int kScanMulti = 4 * pswf::kScanChunk;
+constexpr int kNumSMs = 152;   // GB300 streaming multiprocessors
 inline int round4(int v) { return (v + 3) & ~3; }   // int4 alignment of the sub-arrays of scan_tmp
 size_t scan_tmp_ints(int nb0, int nb1) { return round4(nb0) + round4(nb1) + round4(nb0 + 1) + round4(nb1 + 1); }
 
@@ -901,10 +902,13 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
     g.rc = q.rc;
     g.self = q.self_coeff;
     p->ntiles = g.nt[0] * g.nt[1] * g.nt[2];
-    // x-chains of the spreading: the largest divisor of the x tile count with K T <= 32
+    // x-chains of the spreading: the largest divisor of the x tile count with K T <= 32 (the tensor-core
+    // kernel, at up to 3 CTAs per SM, also keeps at least one chain per SM: small grids take K = 1)
+    p->tc_spread = q.spread_kernel == 2;
     g.K = 1;
+    const int ntiles_all = g.nt[0] * g.nt[1] * g.nt[2];
     for (int k = 32 / g.T; k >= 1; --k)
-        if (g.nt[0] % k == 0) {
+        if (g.nt[0] % k == 0 && (!p->tc_spread || k == 1 || ntiles_all / k >= kNumSMs)) {
             g.K = k;
             break;
         }
@@ -955,7 +959,6 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
     p->cell_cnt = p->tile_cnt + ((p->ntiles + 1 + 3) / 4) * 4;
     p->tc_err = p->cell_cnt + ((p->ncells + 1 + 3) / 4) * 4;
     p->zeroed_bytes = sizeof(double) * 4 + sizeof(int) * (((p->ntiles + 1 + 3) / 4) * 4 + ((p->ncells + 1 + 3) / 4) * 4 + 4);
-    p->tc_spread = q.spread_kernel == 2;
     if ((!p->fp64 && dmalloc(&p->sr_lo, 4 * sizeof(float) * n) != cudaSuccess) ||
         (p->fp64 && !p->ff && dmalloc(&p->sr_f32, sizeof(float4) * n) != cudaSuccess) ||
         (p->ff && dmalloc(&p->sr_cz, sizeof(int) * n) != cudaSuccess) ||
@@ -1582,6 +1585,18 @@ int ewald_profile_read(ewald_plan plan, double* ms, int* count) {
     }
     if (count) *count = static_cast<int>(plan->prof.size());
     return EWALD_OK;
+}
+
+int ewald_debug_wait_timeout(void) {
+    int* flag = nullptr;
+    int h = 0;
+    if (cudaMalloc(&flag, sizeof(int)) != cudaSuccess) return fail(EWALD_ENOMEM, "device allocation failed");
+    cudaError_t e = pswf::launch_wait_probe(20000000ll, flag, nullptr);   // ~10 ms of SM clocks
+    if (e == cudaSuccess) e = cudaMemcpy(&h, flag, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(flag);
+    if (e != cudaSuccess) return fail(EWALD_ECUDA, cudaGetErrorString(e));
+    return h ? fail(EWALD_ETIMEOUT, "bounded device wait ran out (as intended: nothing arrives on the barrier)")
+             : EWALD_OK;
 }
 
 int ewald_pswf_eval(double c, int nx, const double* x, double* psi, double* dpsi, double* chi, double* lambda0) {

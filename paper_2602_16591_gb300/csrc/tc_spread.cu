@@ -4,7 +4,7 @@
 //     S[(y, z), x] = sum_p A[(y, z), p] B[p, x],   A[(y, z), p] = rho_p w_y(p, y) w_z(p, z),
 //                                                  B[p, x] = w_x(p, x),
 // over the tile's extended block (E = T + P - 1 points per axis; w_d(p, .) is zero outside the P
-// points of particle p's stencil).  The kernel builds A and B in shared memory for 32 particles at a
+// points of particle p's stencil).  The kernel builds A and B in shared memory for 16 particles at a
 // time, and one thread issues tcgen05.mma (kind::tf32, M = 128 rows of (y, z), N = 32 columns of x,
 // K = 8 particles per instruction) accumulating S in tensor memory.  TF32 keeps 10 mantissa bits, so
 // every operand is split into a TF32 head and the float32 remainder and the product is taken as
@@ -122,7 +122,7 @@ __device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
 }
 
 
-constexpr int kTcChunk = 32;   // particles per round of MMAs (the K extent of A and B)
+constexpr int kTcChunk = 16;   // particles per round of MMAs (the K extent of A and B)
 constexpr int kTcN = 32;       // accumulator columns (x), E <= 32
 constexpr int kTcRowBytes = kTcChunk * 4;                // one operand row: kTcChunk float32 values
 constexpr int kTcSBO = (kTcChunk / 4) * 128;             // 8-row groups: kTcChunk / 4 core matrices of 128 B
@@ -173,6 +173,10 @@ __global__ void __launch_bounds__(128 * tc_spread_mblocks(P)) k_spread_tc(
     const int y = row / E, z = row - (row / E) * E;
     const uint32_t lane_addr = tbase + (static_cast<uint32_t>((warp & 3) * 32) << 16) + (warp >> 2) * kTcN;
     constexpr uint32_t idesc = idesc_tf32(128, kTcN);
+    // descriptors of the operand bases (every MMA adds its offset to the 14-bit address field; the
+    // operands end below 256 KB of shared memory, so the field does not overflow)
+    const uint64_t dAhi = smem_desc(smem_addr(Ahi), kTcLBO, kTcSBO), dAlo = smem_desc(smem_addr(Alo), kTcLBO, kTcSBO);
+    const uint64_t dBhi = smem_desc(smem_addr(Bhi), kTcLBO, kTcSBO), dBlo = smem_desc(smem_addr(Blo), kTcLBO, kTcSBO);
     float carry[ET];
 #pragma unroll
     for (int a = 0; a < ET; ++a) carry[a] = 0.f;
@@ -186,39 +190,32 @@ __global__ void __launch_bounds__(128 * tc_spread_mblocks(P)) k_spread_tc(
         const int beg = tile_off[tile], end = tile_off[tile + 1];
         for (int base = beg; base < end && !failed; base += kTcChunk) {
             const int cnt = min(kTcChunk, end - base);
-            // (1) window weights: task (particle j, axis d) per thread; B column j, Wy / Wz row j
+            // (1) zero B and the weight rows (all threads, 16-byte stores), then the window weights:
+            //     task (particle j, axis d) per thread writes the P nonzeros of B column j / Wy, Wz row j
+            for (int i = t; i < (2 * kTcN * kTcChunk + 2 * kTcChunk * EP) / 4; i += NT)
+                reinterpret_cast<float4*>(Bhi)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncthreads();
             if (t < 3 * kTcChunk) {
                 const int j = t / 3, d = t - 3 * j;
-                float w[P];
-                int o = 0;
-                float scale = 1.f;
                 if (j < cnt) {
                     const Vec4<float> r = rec[base + j];
-                    const int pk = idx[base + j].x;
-                    o = (pk >> (8 * d)) & 0xff;
-                    if (d == 1) scale = r.w;
+                    const int o = (idx[base + j].x >> (8 * d)) & 0xff;
+                    float w[P];
                     window_weights<float, P>(sc, degw, d == 0 ? r.x : (d == 1 ? r.y : r.z), w);
-                } else {
+                    if (d == 0) {
 #pragma unroll
-                    for (int a = 0; a < P; ++a) w[a] = 0.f;
-                }
-                if (d == 0) {
-                    for (int x = 0; x < kTcN; ++x) {
-                        Bhi[kmajor(x, j)] = 0.f;
-                        Blo[kmajor(x, j)] = 0.f;
+                        for (int a = 0; a < P; ++a) {
+                            float hi, lo;
+                            split_tf32(w[a], hi, lo);
+                            Bhi[kmajor(o + a, j)] = hi;
+                            Blo[kmajor(o + a, j)] = lo;
+                        }
+                    } else {
+                        float* W = (d == 1 ? Wy : Wz) + j * EP;
+                        const float scale = d == 1 ? r.w : 1.f;
+#pragma unroll
+                        for (int a = 0; a < P; ++a) W[o + a] = w[a] * scale;
                     }
-#pragma unroll
-                    for (int a = 0; a < P; ++a) {
-                        float hi, lo;
-                        split_tf32(w[a], hi, lo);
-                        Bhi[kmajor(o + a, j)] = hi;
-                        Blo[kmajor(o + a, j)] = lo;
-                    }
-                } else {
-                    float* W = (d == 1 ? Wy : Wz) + j * EP;
-                    for (int e = 0; e < EP; ++e) W[e] = 0.f;
-#pragma unroll
-                    for (int a = 0; a < P; ++a) W[o + a] = w[a] * scale;
                 }
             }
             __syncthreads();
@@ -241,17 +238,17 @@ __global__ void __launch_bounds__(128 * tc_spread_mblocks(P)) k_spread_tc(
             // (3) one thread issues the MMAs of the round: D[mb] (+)= A_hi B_hi + A_hi B_lo + A_lo B_hi
             if (t == 0) {
                 tc_fence_after();
-                const uint32_t a_hi = smem_addr(Ahi), a_lo = smem_addr(Alo), b_hi = smem_addr(Bhi), b_lo = smem_addr(Blo);
 #pragma unroll
                 for (int mb = 0; mb < NMB; ++mb) {
 #pragma unroll
                     for (int ks = 0; ks < kTcChunk / 8; ++ks) {   // 8 particles (two core matrices) per MMA
-                        const uint32_t ao = mb * 16 * kTcSBO + ks * 2 * kTcLBO, bo = ks * 2 * kTcLBO;
+                        // operand offsets enter the descriptors' address field (bytes / 16)
+                        const uint64_t ao = (mb * 16 * kTcSBO + ks * 2 * kTcLBO) >> 4, bo = (ks * 2 * kTcLBO) >> 4;
                         const uint32_t d = tbase + mb * kTcN;
                         const uint32_t acc = (base > beg || ks > 0) ? 1u : 0u;
-                        mma_tf32(d, smem_desc(a_hi + ao, kTcLBO, kTcSBO), smem_desc(b_hi + bo, kTcLBO, kTcSBO), idesc, acc);
-                        mma_tf32(d, smem_desc(a_hi + ao, kTcLBO, kTcSBO), smem_desc(b_lo + bo, kTcLBO, kTcSBO), idesc, 1u);
-                        mma_tf32(d, smem_desc(a_lo + ao, kTcLBO, kTcSBO), smem_desc(b_hi + bo, kTcLBO, kTcSBO), idesc, 1u);
+                        mma_tf32(d, dAhi + ao, dBhi + bo, idesc, acc);
+                        mma_tf32(d, dAhi + ao, dBlo + bo, idesc, 1u);
+                        mma_tf32(d, dAlo + ao, dBhi + bo, idesc, 1u);
                     }
                 }
                 mma_commit(&bar);
@@ -305,6 +302,16 @@ cudaError_t spread_tc_p(int ntiles, const Vec4<float>* rec, const int2* idx, con
     return cudaGetLastError();
 }
 
+// The bounded wait on a barrier that nothing arrives at (the timeout path, exercised by a test):
+// flag = 1 when the wait ran out after max_cycles SM clocks.
+__global__ void k_wait_probe(long long max_cycles, int* __restrict__ flag) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    const bool ok = mbar_wait_block(&bar, 0u, max_cycles);
+    if (threadIdx.x == 0) *flag = ok ? 0 : 1;
+}
+
 }  // namespace
 
 bool tc_spread_supports(int P) { return P >= 3 && P <= 14; }
@@ -325,6 +332,11 @@ cudaError_t launch_spread_tc(int P, int ntiles, const Vec4<float>* rec, const in
 #undef PSWF_TC_CASE
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_wait_probe(long long max_cycles, int* flag, cudaStream_t s) {
+    k_wait_probe<<<1, 32, 0, s>>>(max_cycles, flag);
+    return cudaGetLastError();
 }
 
 }  // namespace pswf

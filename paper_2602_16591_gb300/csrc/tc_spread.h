@@ -22,4 +22,8 @@ size_t tc_spread_smem(int P, int degw);
 cudaError_t launch_spread_tc(int P, int ntiles, const Vec4<float>* rec, const int2* idx, const int* tile_off,
                              const float* wcoef, int degw, SpreadChain ch, float* scratch, int* err_flag, cudaStream_t s);
 
+// One warp waits (bounded by max_cycles SM clocks) on an mbarrier that nothing arrives at and sets
+// *flag (device int) to 1 when the wait ran out.
+cudaError_t launch_wait_probe(long long max_cycles, int* flag, cudaStream_t s);
+
 }  // namespace pswf
