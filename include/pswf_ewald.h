@@ -79,10 +79,10 @@ typedef struct ewald_opts {
                              measurement (Sec. 6.2.2).  0 (default): off. */
     int    spread_kernel; /* Alg. 2 step 1 on float32 (EWALD_MIXED, tol >= 1e-7) plans: 1 = CUDA-core
                              kernel (per-column register accumulation), 2 = tensor-core kernel
-                             (tcgen05 split-TF32 products per tile, window support P <= 14; its
-                             float32 accumulation in tensor memory leaves a relative energy error of
-                             ~5e-6), 0 (default) = automatic: tensor cores for tol >= 1e-5, CUDA cores
-                             below.  Other plans always use their CUDA-core kernel. */
+                             (tcgen05 split-TF32 products per tile, window support P <= 14; within
+                             the accuracy bar down to tol 1e-6), 0 (default) = automatic: tensor
+                             cores for tol >= 1e-5, CUDA cores below.  Other plans always use their
+                             CUDA-core kernel. */
 } ewald_opts;
 
 /* ---- derived parameters (Alg. 3 and the library's readings of it) ------ */

@@ -113,6 +113,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Columns 0..19 of this thread's tensor-memory lane (x16 + x4 loads, warp-collective).
+__device__ __forceinline__ void tmem_ld20(uint32_t taddr, float (&v)[20]) {
+    uint32_t r[20];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19])
+                 : "r"(taddr + 16));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 20; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // TF32 head of a float32 value (round to nearest, ties away: cvt.rna.tf32.f32) and its remainder.
 __device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
     uint32_t h;
@@ -137,13 +154,17 @@ __device__ __forceinline__ int kmajor(int row, int k) {
 }
 
 template <int P>
-__global__ void __launch_bounds__(128 * tc_spread_mblocks(P)) k_spread_tc(
+__global__ void __launch_bounds__(128 * tc_spread_mblocks(P), tc_spread_mblocks(P) <= 3 ? 3 : 2) k_spread_tc(
     const Vec4<float>* __restrict__ rec, const int2* __restrict__ idx, const int* __restrict__ tile_off,
     const float* __restrict__ wcoef, int degw, SpreadChain ch, float* __restrict__ scratch, int* __restrict__ err_flag) {
     constexpr int T = kTile32, E = T + P - 1, ET = E - T, NMB = tc_spread_mblocks(P), NT = 128 * NMB;
     constexpr int EP = (E + 3) / 4 * 4, COLS = tc_spread_tmem_cols(P);
     constexpr int ABYTES = 128 * NMB * kTcRowBytes;   // one of A_hi, A_lo
     static_assert(E <= kTcN && E * E <= 128 * NMB, "tile block exceeds the accumulator shape");
+    constexpr int NLD = E <= 20 ? 20 : 32;   // accumulator columns read back per round
+    auto tmem_ld_cols = [](uint32_t taddr, float (&v)[NLD]) {
+        if constexpr (NLD == 20) tmem_ld20(taddr, v); else tmem_ld32(taddr, v);
+    };
     extern __shared__ __align__(1024) unsigned char smem[];
     float* Ahi = reinterpret_cast<float*>(smem);
     float* Alo = reinterpret_cast<float*>(smem + ABYTES);
@@ -188,6 +209,9 @@ __global__ void __launch_bounds__(128 * tc_spread_mblocks(P)) k_spread_tc(
     for (int k = 0; k < ch.K && !failed; ++k) {
         const int tile = (qx * ch.K + k) * ch.nyz + rem;
         const int beg = tile_off[tile], end = tile_off[tile + 1];
+        float tacc[E];
+#pragma unroll
+        for (int a = 0; a < E; ++a) tacc[a] = 0.f;
         for (int base = beg; base < end && !failed; base += kTcChunk) {
             const int cnt = min(kTcChunk, end - base);
             // (1) zero B and the weight rows (all threads, 16-byte stores), then the window weights:
@@ -236,19 +260,26 @@ __global__ void __launch_bounds__(128 * tc_spread_mblocks(P)) k_spread_tc(
             fence_async_smem();   // generic-proxy stores of A and B -> visible to the tensor cores
             __syncthreads();
             // (3) one thread issues the MMAs of the round: D[mb] (+)= A_hi B_hi + A_hi B_lo + A_lo B_hi
+            // Every round starts a fresh accumulator: the two cross terms of each K step first, the
+            // A_hi B_hi products last, so tensor memory accumulates few terms and the large ones last
+            // (its float32 accumulation is not round-to-nearest: summing a whole tile there left a
+            // relative bias of ~5e-7 in the grid); the rounds are added on the CUDA cores.
             if (t == 0) {
                 tc_fence_after();
 #pragma unroll
                 for (int mb = 0; mb < NMB; ++mb) {
+                    const uint32_t d = tbase + mb * kTcN;
 #pragma unroll
                     for (int ks = 0; ks < kTcChunk / 8; ++ks) {   // 8 particles (two core matrices) per MMA
                         // operand offsets enter the descriptors' address field (bytes / 16)
                         const uint64_t ao = (mb * 16 * kTcSBO + ks * 2 * kTcLBO) >> 4, bo = (ks * 2 * kTcLBO) >> 4;
-                        const uint32_t d = tbase + mb * kTcN;
-                        const uint32_t acc = (base > beg || ks > 0) ? 1u : 0u;
-                        mma_tf32(d, dAhi + ao, dBhi + bo, idesc, acc);
+                        mma_tf32(d, dAlo + ao, dBhi + bo, idesc, ks > 0 ? 1u : 0u);
                         mma_tf32(d, dAhi + ao, dBlo + bo, idesc, 1u);
-                        mma_tf32(d, dAlo + ao, dBhi + bo, idesc, 1u);
+                    }
+#pragma unroll
+                    for (int ks = 0; ks < kTcChunk / 8; ++ks) {
+                        const uint64_t ao = (mb * 16 * kTcSBO + ks * 2 * kTcLBO) >> 4, bo = (ks * 2 * kTcLBO) >> 4;
+                        mma_tf32(d, dAhi + ao, dBhi + bo, idesc, 1u);
                     }
                 }
                 mma_commit(&bar);
@@ -256,26 +287,24 @@ __global__ void __launch_bounds__(128 * tc_spread_mblocks(P)) k_spread_tc(
             // (4) the round's MMAs complete before A and B are rebuilt or S is read
             if (!mbar_wait_block(&bar, phase, kTcWaitCycles)) failed = true;
             phase ^= 1u;
+            if (failed) break;
+            // (5) the round's sums into the tile's accumulators (round to nearest)
+            tc_fence_after();
+            float sv[NLD];
+            tmem_ld_cols(lane_addr, sv);
+#pragma unroll
+            for (int a = 0; a < E; ++a) tacc[a] += sv[a];
+            tc_fence_before();   // loads done before the next round's MMAs (ordered by its __syncthreads)
         }
         if (failed) break;
-        // epilogue: S of this tile (+ the planes carried along the chain); heads out, the rest carried on
-        tc_fence_after();
-        float sv[32];
-        if (end > beg) {   // block-uniform; a tile without particles contributes nothing
-            tmem_ld32(lane_addr, sv);
-        } else {
-#pragma unroll
-            for (int a = 0; a < 32; ++a) sv[a] = 0.f;
-        }
+        // epilogue: the tile's sums (+ the planes carried along the chain); heads out, the rest carried on
         if (own) {
             float* out = heads + static_cast<size_t>(tile) * T * E * E;
 #pragma unroll
-            for (int a = 0; a < T; ++a) out[a * E * E + row] = sv[a] + (a < ET ? carry[a] : 0.f);
+            for (int a = 0; a < T; ++a) out[a * E * E + row] = tacc[a] + (a < ET ? carry[a] : 0.f);
 #pragma unroll
-            for (int a = 0; a < ET; ++a) carry[a] = sv[a + T] + (a + T < ET ? carry[a + T] : 0.f);
+            for (int a = 0; a < ET; ++a) carry[a] = tacc[a + T] + (a + T < ET ? carry[a + T] : 0.f);
         }
-        tc_fence_before();
-        __syncthreads();   // S read before the next tile's MMAs overwrite it
     }
     if (!failed && own) {   // the chain's tail: planes that belong to the tiles after the chain
         float* out = tails + static_cast<size_t>(blockIdx.x) * ET * E * E;
