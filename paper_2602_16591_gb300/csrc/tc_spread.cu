@@ -6,12 +6,16 @@
 // over the tile's extended block (E = T + P - 1 points per axis; w_d(p, .) is zero outside the P
 // points of particle p's stencil).  The kernel builds A and B in shared memory for 16 particles at a
 // time, and one thread issues tcgen05.mma (kind::tf32, M = 128 rows of (y, z), N = 32 columns of x,
-// K = 8 particles per instruction) accumulating S in tensor memory.  TF32 keeps 10 mantissa bits, so
-// every operand is split into a TF32 head and the float32 remainder and the product is taken as
+// K = 8 particles per instruction) into tensor memory.  TF32 keeps 10 mantissa bits, so every operand
+// is split into a TF32 head and the float32 remainder and the product is taken as
 // A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped A_lo B_lo term is ~2^-22 relative): float32-level
-// accuracy from three tensor-core products.  The epilogue reads S back (tcgen05.ld), adds the planes
-// carried along the tile's x-chain and writes the same slab layout as k_spread (heads per tile, tails
-// per chain), so k_halo is shared by both kernels.
+// accuracy from three tensor-core products.  Each round of 16 particles starts a fresh accumulator in
+// tensor memory, adds the small cross terms first and the large A_hi B_hi products last, and is read
+// back (tcgen05.ld) and summed on the CUDA cores: the float32 accumulation in tensor memory is not
+// round-to-nearest, and a whole tile summed there left a relative bias of ~5e-7 in the grid (energy
+// errors of ~5e-6); short rounds bring both to the level of the CUDA-core kernel.  The tile's sums
+// plus the planes carried along its x-chain are written in the slab layout of k_spread (heads per
+// tile, tails per chain), so k_halo is shared by both kernels.
 //
 // Synchronisation: MMA completion is signalled by tcgen05.commit on an mbarrier; every wait on it is
 // bounded and its outcome made block-uniform (__syncthreads_or) before it steers control flow.  A wait
