@@ -174,9 +174,11 @@ __global__ void __launch_bounds__(128 * tc_spread_mblocks(P), tc_spread_mblocks(
     float* Alo = reinterpret_cast<float*>(smem + ABYTES);
     float* Bhi = reinterpret_cast<float*>(smem + 2 * ABYTES);
     float* Blo = Bhi + kTcN * kTcChunk;
-    float* Wy = Blo + kTcN * kTcChunk;   // rho_p w_y(p, y), y < EP (zero outside the stencil)
-    float* Wz = Wy + kTcChunk * EP;      // w_z(p, z)
-    float* sc = Wz + kTcChunk * EP;      // window polynomials
+    // window weights of a round, two buffers (the next round's are computed while the MMAs run):
+    // w_x(p, x) for x < kTcN, rho_p w_y(p, y) and w_z(p, z) for y, z < EP, zero outside the stencil
+    constexpr int WROUND = kTcChunk * (kTcN + 2 * EP);
+    float* Wbuf = Blo + kTcN * kTcChunk;
+    float* sc = Wbuf + 2 * WROUND;       // window polynomials
     __shared__ uint64_t bar;
     __shared__ uint32_t tmem_base;
     const int t = threadIdx.x, warp = t >> 5;
@@ -216,38 +218,33 @@ __global__ void __launch_bounds__(128 * tc_spread_mblocks(P), tc_spread_mblocks(
         float tacc[E];
 #pragma unroll
         for (int a = 0; a < E; ++a) tacc[a] = 0.f;
-        for (int base = beg; base < end && !failed; base += kTcChunk) {
-            const int cnt = min(kTcChunk, end - base);
-            // (1) zero B and the weight rows (all threads, 16-byte stores), then the window weights:
-            //     task (particle j, axis d) per thread writes the P nonzeros of B column j / Wy, Wz row j
-            for (int i = t; i < (2 * kTcN * kTcChunk + 2 * kTcChunk * EP) / 4; i += NT)
-                reinterpret_cast<float4*>(Bhi)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-            __syncthreads();
+        // window weights of the round starting at `first` into buffer b: task (particle j, axis d) per
+        // thread writes the whole zero-padded row (16-byte stores, then the P values of the stencil)
+        auto weights = [&](int first, int b) {
             if (t < 3 * kTcChunk) {
-                const int j = t / 3, d = t - 3 * j;
-                if (j < cnt) {
-                    const Vec4<float> r = rec[base + j];
-                    const int o = (idx[base + j].x >> (8 * d)) & 0xff;
+                const int j = t / 3, d = t - 3 * j, len = d == 0 ? kTcN : EP;
+                float* W = Wbuf + b * WROUND + (d == 0 ? j * kTcN : kTcChunk * kTcN + ((d - 1) * kTcChunk + j) * EP);
+                for (int e = 0; e < len; e += 4) *reinterpret_cast<float4*>(W + e) = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (first + j < end) {
+                    const Vec4<float> r = rec[first + j];
+                    const int o = (idx[first + j].x >> (8 * d)) & 0xff;
                     float w[P];
                     window_weights<float, P>(sc, degw, d == 0 ? r.x : (d == 1 ? r.y : r.z), w);
-                    if (d == 0) {
+                    const float scale = d == 1 ? r.w : 1.f;
 #pragma unroll
-                        for (int a = 0; a < P; ++a) {
-                            float hi, lo;
-                            split_tf32(w[a], hi, lo);
-                            Bhi[kmajor(o + a, j)] = hi;
-                            Blo[kmajor(o + a, j)] = lo;
-                        }
-                    } else {
-                        float* W = (d == 1 ? Wy : Wz) + j * EP;
-                        const float scale = d == 1 ? r.w : 1.f;
-#pragma unroll
-                        for (int a = 0; a < P; ++a) W[o + a] = w[a] * scale;
-                    }
+                    for (int a = 0; a < P; ++a) W[o + a] = w[a] * scale;
                 }
             }
-            __syncthreads();
-            // (2) A rows: A[(y, z), p] = rho_p w_y(p, y) w_z(p, z), split into TF32 head and remainder
+        };
+        if (beg < end) weights(beg, 0);
+        __syncthreads();
+        int rb = 0;   // weight buffer of the current round
+        for (int base = beg; base < end && !failed; base += kTcChunk, rb ^= 1) {
+            const float* Wx = Wbuf + rb * WROUND;
+            const float* Wy = Wx + kTcChunk * kTcN;
+            const float* Wz = Wy + kTcChunk * EP;
+            // (1) operands: A[(y, z), p] = rho_p w_y(p, y) w_z(p, z) (row of this thread) and B[x, p] = w_x(p, x)
+            //     (all threads), split into TF32 head and remainder
             if (own) {
 #pragma unroll
                 for (int p0 = 0; p0 < kTcChunk; p0 += 4) {
@@ -261,9 +258,16 @@ __global__ void __launch_bounds__(128 * tc_spread_mblocks(P), tc_spread_mblocks(
                     *reinterpret_cast<float4*>(Alo + kmajor(row, p0)) = make_float4(lo[0], lo[1], lo[2], lo[3]);
                 }
             }
+            for (int e = t; e < kTcN * kTcChunk; e += NT) {
+                const int j = e / kTcN, x = e - j * kTcN;
+                float hi, lo;
+                split_tf32(Wx[j * kTcN + x], hi, lo);
+                Bhi[kmajor(x, j)] = hi;
+                Blo[kmajor(x, j)] = lo;
+            }
             fence_async_smem();   // generic-proxy stores of A and B -> visible to the tensor cores
             __syncthreads();
-            // (3) one thread issues the MMAs of the round: D[mb] (+)= A_hi B_hi + A_hi B_lo + A_lo B_hi
+            // (2) one thread issues the MMAs of the round: D[mb] = A_hi B_hi + A_hi B_lo + A_lo B_hi.
             // Every round starts a fresh accumulator: the two cross terms of each K step first, the
             // A_hi B_hi products last, so tensor memory accumulates few terms and the large ones last
             // (its float32 accumulation is not round-to-nearest: summing a whole tile there left a
@@ -288,7 +292,10 @@ __global__ void __launch_bounds__(128 * tc_spread_mblocks(P), tc_spread_mblocks(
                 }
                 mma_commit(&bar);
             }
-            // (4) the round's MMAs complete before A and B are rebuilt or S is read
+            // (3) while the MMAs run: the next round's window weights into the other buffer
+            if (base + kTcChunk < end) weights(base + kTcChunk, rb ^ 1);
+            // (4) the round's MMAs complete before A and B are rebuilt or S is read (the wait is also the
+            //     barrier that publishes the next round's weights)
             if (!mbar_wait_block(&bar, phase, kTcWaitCycles)) failed = true;
             phase ^= 1u;
             if (failed) break;
@@ -352,7 +359,7 @@ bool tc_spread_supports(int P) { return P >= 3 && P <= 14; }
 size_t tc_spread_smem(int P, int degw) {
     const int E = kTile32 + P - 1, EP = (E + 3) / 4 * 4;
     return 2 * static_cast<size_t>(128) * tc_spread_mblocks(P) * kTcRowBytes + 2 * sizeof(float) * kTcN * kTcChunk +
-           2 * sizeof(float) * kTcChunk * EP + sizeof(float) * P * (degw + 1);
+           2 * sizeof(float) * kTcChunk * (kTcN + 2 * EP) + sizeof(float) * P * (degw + 1);
 }
 
 cudaError_t launch_spread_tc(int P, int ntiles, const Vec4<float>* rec, const int2* idx, const int* tile_off,
