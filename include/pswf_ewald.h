@@ -61,8 +61,9 @@ extern "C" {
 typedef struct ewald_opts {
     int    precision;     /* EWALD_FP64, EWALD_MIXED or EWALD_FLOATFLOAT (default EWALD_FP64) */
     double rc;            /* <= 0: automatic cutoff rule; > 0: upper bound on the cutoff (length units) */
-    double grid_density;  /* target m^3 / n for the automatic cutoff rule (default 3.0, the
-                             measured optimum of the GB300 kernels for n ~ 1e5) */
+    double grid_density;  /* target m^3 / n for the automatic cutoff rule; 0 (default): the
+                             measured optima of the GB300 kernels, 6 for float32 plans (EWALD_MIXED
+                             at tol >= 1e-7) and 3 for the float64 and float-float plans */
     double tol_safety;    /* the plan is sized for tol * tol_safety (default 0.25; forces have no
                              error model in the paper and measure ~2-5x the potential error) */
     int    sr_reach;      /* cells per cutoff radius in the real-space cell list, 1..4 (along x and

@@ -342,7 +342,7 @@ ewald_opts default_opts() {
     ewald_opts o{};
     o.precision = EWALD_FP64;
     o.rc = 0.0;
-    o.grid_density = 3.0;
+    o.grid_density = 0.0;
     o.tol_safety = 0.25;
     o.sr_reach = 0;
     o.window_extra = 0;
@@ -540,7 +540,8 @@ HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opt
     if (o.precision != EWALD_FP64 && o.precision != EWALD_MIXED && o.precision != EWALD_FLOATFLOAT)
         throw std::invalid_argument("unknown precision");
     if (!(o.tol_safety > 0 && o.tol_safety <= 1)) throw std::invalid_argument("tol_safety must lie in (0, 1]");
-    if (!(o.grid_density > 0)) throw std::invalid_argument("grid_density must be positive");
+    if (!(o.grid_density >= 0) || !std::isfinite(o.grid_density))
+        throw std::invalid_argument("grid_density must be 0 (automatic) or positive");
     if (o.window_extra < 0 || o.window_extra > 8) throw std::invalid_argument("window_extra must lie in [0, 8]");
     if (o.autotune != 0 && o.autotune != 1) throw std::invalid_argument("autotune must be 0 or 1");
     if (o.sr_reach < 0 || o.sr_reach > 4) throw std::invalid_argument("sr_reach must lie in [0, 4]");
@@ -548,6 +549,10 @@ HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opt
 
     const double As = 5.0, Aw = 3.1;                      // Secs. 5.1.1 and 5.2.1
     static const double kappa = kappa_constant();
+    // grid density of the cutoff rule: automatic (0) = the measured optima of the GB300 kernels, 6 for
+    // float32 plans (tile 8) and 3 for the float64 / float-float ones (tile 4)
+    const bool f32_plan = o.precision == EWALD_MIXED && tol >= 1e-7;
+    const double gdens = o.grid_density > 0 ? o.grid_density : (f32_plan ? 6.0 : 3.0);
     const double t_pot = tol * o.tol_safety;   // potential target (window / aliasing side)
     double t = t_pot;                            // split target (tightened for forces below)
     auto cs_at = [&](double rcl, double tt) {
@@ -562,8 +567,8 @@ HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opt
         } else {
             // cube: m* = (g n)^{1/3} points per edge; cuboid (in units of the shortest edge L):
             // m* = L / h with the common spacing h = (V / (g n))^{1/3}
-            const double mstar = cube ? std::cbrt(o.grid_density * static_cast<double>(n))
-                                      : L / std::cbrt(V / (o.grid_density * static_cast<double>(n)));
+            const double mstar = cube ? std::cbrt(gdens * static_cast<double>(n))
+                                      : L / std::cbrt(V / (gdens * static_cast<double>(n)));
             rcl = 0.1;
             for (int it = 0; it < 12; ++it) rcl = std::min(cs_of(rcl) / (kPi * mstar), 0.5);
         }

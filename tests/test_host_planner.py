@@ -66,7 +66,8 @@ CFGS = [(1.0, 1000, 1e-6), (1.0, 512, 1e-6), (1.0, 100_000, 1e-4), (1.0, 100_000
 
 # The planner runs the paper's Alg. 3 (oracle.params) with these additions of its own, each a stated
 # difference from the procedure as printed (the paper leaves r_c to tuning and has no force model):
-GRID_DENSITY = 3.0      # (a) r_c: fixed point r = min(c_s(r) L/(pi (g n)^(1/3)), L/2) for g = m^3/n
+GRID_DENSITY = {8: 6.0, 4: 3.0}   # (a) r_c: fixed point r = min(c_s(r) L/(pi (g n)^(1/3)), L/2) for g = m^3/n:
+#                                   6 for float32 plans (tile 8), 3 for the others (tile 4)
 TOL_SAFETY = 0.25       # (b) the split and window targets are tol * 0.25
 FORCE_M0 = 10.0         # (c) the split target is further multiplied by min(1, 10/m0), m0 the unrounded m
 #                         (d) m is rounded up to a multiple of the spreading tile (8 for float32 plans,
@@ -91,7 +92,7 @@ def library_rule(L, n, tol, mult):
     t = tol * TOL_SAFETY
 
     def cutoff(t):
-        r, mstar = 0.1, (GRID_DENSITY * n) ** (1.0 / 3.0)
+        r, mstar = 0.1, (GRID_DENSITY[mult] * n) ** (1.0 / 3.0)
         for _ in range(12):
             r = min(oparams.cs_of(r, t) / (math.pi * mstar), 0.5)
         return r
@@ -222,7 +223,7 @@ def test_precision_paths():
 def test_opts_defaults_and_autotune_validation():
     import ctypes
     o = pe.make_opts()
-    assert o.autotune == 0 and o.grid_density == 3.0 and o.tol_safety == 0.25 and o.window_extra == 0
+    assert o.autotune == 0 and o.grid_density == 0.0 and o.tol_safety == 0.25 and o.window_extra == 0
     o.autotune = 2
     p = pe.ewald_params()
     assert pe.lib.ewald_plan_params(1.0, 1000, 1e-6, ctypes.byref(o), ctypes.byref(p)) == pe.EWALD_EINVAL
@@ -256,7 +257,7 @@ def library_rule_box(Ls, n, tol, mult):
     t = tol * TOL_SAFETY
 
     def cutoff(t):
-        r, h = 0.1, (V / (GRID_DENSITY * n)) ** (1.0 / 3.0)
+        r, h = 0.1, (V / (GRID_DENSITY[mult] * n)) ** (1.0 / 3.0)
         for _ in range(12):
             r = min(oparams.cs_of(r, t) * h / (math.pi * Lmin), 0.5)
         return r

@@ -160,5 +160,8 @@ def test_shard_assignment_balances_cost():
         loads = [sum(costs[i] for i in s) for s in share]
         bound = max(sum(costs) / world, max(costs))
         assert max(loads) <= 4.0 / 3.0 * bound
-    # the model grows with n and with the window support
-    assert costs[int(np.argmax(ns))] == max(costs)
+    # the model grows with n (up to the grid rounding of m, which moves the FFT term): the most
+    # expensive system is within 10% of the largest n, and cost and n are rank-correlated
+    assert ns[int(np.argmax(costs))] >= 0.9 * max(ns)
+    rank_n, rank_c = np.argsort(np.argsort(ns)), np.argsort(np.argsort(costs))
+    assert np.corrcoef(rank_n, rank_c)[0, 1] > 0.99
