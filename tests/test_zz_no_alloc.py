@@ -66,3 +66,28 @@ def test_static_spread_rejects_problems_beyond_its_scratch():
     code = pe.lib.ewald_spread_static(ctypes.byref(p), dummy, dummy, dummy, None)
     assert code == pe.EWALD_ETOOBIG
     assert b"static array" in pe.lib.ewald_last_error()
+
+
+def test_static_spread_repeat_call_skips_the_table_copy():
+    """A second call with the same (c_w, P, deg_w) leaves the cached window table alone: it issues no
+    host-to-device copy, so it can be recorded into a CUDA graph (a copy from pageable host memory could
+    not be), and the replayed graph reproduces the grid of the direct call bit for bit."""
+    x, rho, L = uniform_neutral(3000, seed=5)
+    xt = torch.tensor(x, device="cuda")
+    rt = torch.tensor(rho, device="cuda")
+    params = pe.plan_params(L, len(x), 1e-8, precision="fp64")
+    ref = _spread_static(params, xt, rt)           # first call: fits and copies the table
+    m = params.m
+    out = torch.full((m ** 3,), float("nan"), dtype=torch.float64, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(graph, stream=side, capture_error_mode="relaxed"):
+            code = pe.lib.ewald_spread_static(ctypes.byref(params), ctypes.c_void_p(xt.data_ptr()),
+                                              ctypes.c_void_p(rt.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                              ctypes.c_void_p(side.cuda_stream))
+    assert code == pe.EWALD_OK, pe.lib.ewald_last_error().decode()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy().reshape(m, m, m), ref)
