@@ -81,9 +81,9 @@ typedef struct ewald_opts {
     int    spread_kernel; /* Alg. 2 step 1 on float32 (EWALD_MIXED, tol >= 1e-7) plans: 1 = CUDA-core
                              kernel (per-column register accumulation), 2 = tensor-core kernel
                              (tcgen05 split-TF32 products per tile, window support P <= 14; within
-                             the accuracy bar down to tol 1e-6), 0 (default) = automatic: tensor
-                             cores for tol >= 1e-5, CUDA cores below.  Other plans always use their
-                             CUDA-core kernel. */
+                             the accuracy bar down to tol 1e-6; faster timed alone, 1-2% slower in
+                             the concurrent step, measured), 0 (default) = automatic = CUDA cores.
+                             Other plans always use their CUDA-core kernel. */
 } ewald_opts;
 
 /* ---- derived parameters (Alg. 3 and the library's readings of it) ------ */

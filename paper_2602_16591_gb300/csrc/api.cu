@@ -902,13 +902,14 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
     g.rc = q.rc;
     g.self = q.self_coeff;
     p->ntiles = g.nt[0] * g.nt[1] * g.nt[2];
-    // x-chains of the spreading: the largest divisor of the x tile count with K T <= 32 (the tensor-core
-    // kernel, at up to 3 CTAs per SM, also keeps at least one chain per SM: small grids take K = 1)
+    // x-chains of the spreading: the largest divisor of the x tile count with K T <= 32 that still leaves
+    // one chain per SM (small grids take K = 1: a 3 x 3 x 3-tile grid gets 27 CTAs instead of 9); batch
+    // members (pre != nullptr) keep the longest chains, since one fused launch covers all systems
     p->tc_spread = q.spread_kernel == 2;
     g.K = 1;
     const int ntiles_all = g.nt[0] * g.nt[1] * g.nt[2];
     for (int k = 32 / g.T; k >= 1; --k)
-        if (g.nt[0] % k == 0 && (!p->tc_spread || k == 1 || ntiles_all / k >= kNumSMs)) {
+        if (g.nt[0] % k == 0 && (pre || k == 1 || ntiles_all / k >= kNumSMs)) {
             g.K = k;
             break;
         }

@@ -526,9 +526,6 @@ HostPlan make_plan(double L, int64_t n, double tol, const ewald_opts& o) {
     return make_plan_box(box, n, tol, o);
 }
 
-// Smallest tolerance at which float32 plans take the tensor-core spreading kernel automatically.
-constexpr double kTensorSpreadMinTol = 1e-5;
-
 HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opts& o) {
     for (int d = 0; d < 3; ++d)
         if (!(box[d] > 0) || !std::isfinite(box[d])) throw std::invalid_argument("box edges must be positive and finite");
@@ -662,11 +659,12 @@ HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opt
     }
     p.ncell = p.cells[0];
     p.fit_tol = std::max(0.02 * t, p.precision == EWALD_MIXED ? 1e-8 : 5e-15);
-    // spreading kernel: tensor cores for float32 plans whose tile block fits the accumulator (P <= 14);
-    // automatic from tol 1e-5 up, where they are faster (at 1e-6 the two kernels take the same time and
-    // the CUDA-core kernel leaves the smaller energy error: 0.75e-6 against 1.4e-6 relative, measured)
+    // spreading kernel: tensor cores on request for float32 plans whose tile block fits the accumulator
+    // (P <= 14); automatic = CUDA cores: timed alone the tensor-core kernel is faster at tol >= 1e-5
+    // (53 vs 59 us at n = 1e5, tol 1e-4), but inside the step, concurrent with the real-space sum, the
+    // whole step measured 1-2% slower with it (0.336 vs 0.333 ms at 1e-5, 0.389 vs 0.381 ms at 1e-6)
     const bool tc_ok = p.precision == EWALD_MIXED && P <= 14;
-    p.spread_kernel = tc_ok && (o.spread_kernel == 2 || (o.spread_kernel == 0 && tol >= kTensorSpreadMinTol)) ? 2 : 1;
+    p.spread_kernel = tc_ok && o.spread_kernel == 2 ? 2 : 1;
 
     const Prolate ps(p.cs), pw(p.cw);
     p.lambda_s = ps.lambda;

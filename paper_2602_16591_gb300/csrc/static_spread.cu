@@ -79,9 +79,11 @@ extern "C" int ewald_spread_static(const ewald_params* p, const double* x, const
     const size_t need_status = align256(sizeof(double) * 4);
     const size_t need_rec = align256(sizeof(pswf::Vec4<double>) * n);
     const size_t need_idx = align256(sizeof(int2) * n);
-    int K = 1;   // x-chains of the spreading (as in the plans): largest divisor of nt with K T <= 32
+    // x-chains of the spreading, as in the single-system plans: the largest divisor of nt with K T <= 32
+    // that leaves one chain per SM (152), K = 1 otherwise
+    int K = 1;
     for (int k = 32 / T; k >= 1; --k)
-        if (nt % k == 0) {
+        if (nt % k == 0 && (k == 1 || ntiles / k >= 152)) {
             K = k;
             break;
         }
