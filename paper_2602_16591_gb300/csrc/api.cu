@@ -389,7 +389,7 @@ cudaError_t launch_short_d(ewald_plan p, const pswf::Vec4<real>* sr_rec, const p
     kp.two_over_rc2 = static_cast<real>(2.0 / (g.rc * g.rc));
     kp.rc2f = static_cast<float>(g.rc * g.rc * (1.0 + 1e-4));
     const int ncells = g.ncell[0] * g.ncell[1] * g.ncell[2];
-    const size_t smem = pswf::short_dyn_smem(p->sr_rcap);
+    const size_t smem = sizeof(real) == 4 ? pswf::short_dyn_smem_f32(p->sr_rcap) : pswf::short_dyn_smem(p->sr_rcap);
     const int blocks = (ncells + pswf::kShortWarps - 1) / pswf::kShortWarps;
     // float32 pairs are cheap: one target at a time, full-warp masked pairs over the target's own
     // neighbourhood; float64 pairs: the two-phase (queued) kernel over cells
@@ -1240,7 +1240,7 @@ int setup_fused(ewald_plan p) {
         return fail(EWALD_ECUDA, "fused batch: stream or event creation failed");
     p->bspread_smem = pswf::Launch<float>::spread_smem(P, degw);
     p->binterp_smem = pswf::Launch<float>::interp_smem(P, degw);
-    p->bshort_smem = pswf::short_dyn_smem(rcap);
+    p->bshort_smem = pswf::short_dyn_smem_f32(rcap);
     p->bD = D;
     p->bP = P;
     p->fused = true;

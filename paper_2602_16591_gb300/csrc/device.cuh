@@ -1007,6 +1007,10 @@ constexpr int kShortMaxRanges = 256;   // >= 81 columns x 3 pieces (nc >= 2R sin
 __host__ __device__ constexpr size_t short_dyn_smem(int rcap) {
     return static_cast<size_t>(kShortWarps) * (16u * rcap + 4u * (rcap + 1));
 }
+// float32 kernel (k_short): the ranges, their x-y cell shifts (float4 per piece) and the offsets
+__host__ __device__ constexpr size_t short_dyn_smem_f32(int rcap) {
+    return static_cast<size_t>(kShortWarps) * (32u * rcap + 4u * (rcap + 1));
+}
 
 // Flattens the source ranges of target cell (cx, cy, cz) for one warp: every column (dx, dy, dzmax) of
 // scol contributes its z-run dz in [-dzmax, dzmax], split into contiguous pieces of the z-fastest cell
@@ -1116,8 +1120,9 @@ struct ShortParams {
 // x-y box distance from the target point is below the cutoff contributes the run of z cells that can
 // hold points within the cutoff of the target (its z window, from the target's own position), split
 // into contiguous pieces at the periodic wrap.  Lanes take one column each.  rng[r] = {first particle,
-// first z cell, dz of that cell, ix | iy << 4}, pos[r] = offset of piece r in the candidate stream,
-// pos[nr] = total, returned (warp-uniform).  Columns whose pieces would overflow cap are dropped (the
+// first z cell, dz of that cell, ix | iy << 4}, shf[r] = the piece's x and y cell shifts {hi x, hi y,
+// lo x, lo y}, pos[r] = offset of piece r in the candidate stream, pos[nr] = total, returned
+// (warp-uniform).  Columns whose pieces would overflow cap are dropped (the
 // host sizes cap for the worst case, so none are).
 // v in (-2 n, 2 n) -> [0, n): periodic cell index
 __device__ __forceinline__ int wrap_cells(int v, int n) {
@@ -1135,17 +1140,21 @@ struct CellGridF {   // what target_ranges needs of the cell grid, in registers
 
 __device__ __forceinline__ int target_ranges(const int* __restrict__ cell_off, const CellGridF cg, int cx, int cy,
                                              int cz, float tx, float ty, float tz, float rc2f, int lane, int cap,
-                                             int4* rng, int* pos) {
+                                             int4* rng, int* pos, const float* __restrict__ shx_hi,
+                                             const float* __restrict__ shy_hi, const float* __restrict__ shx_lo,
+                                             const float* __restrict__ shy_lo, float4* shf) {
     const int R = cg.R, Rz = cg.Rz, W = 2 * R + 1;
     const int ncx = cg.ncx, ncy = cg.ncy, nc = cg.nc;
     const float wx = cg.wx, wy = cg.wy, iwz = cg.iwz;
+    const int divW = (65536 + W - 1) / W;   // k / W = (k divW) >> 16 exactly for k < W^2 <= 81
     int nr = 0;
     for (int k0 = 0; k0 < W * W; k0 += 32) {
         const int k = k0 + lane;
         int npc = 0, zlo = 0, zhi = -1, base = 0, dx = 0, dy = 0;
         if (k < W * W) {
-            dx = k / W - R;
-            dy = k % W - R;
+            const int qd = (k * divW) >> 16;
+            dx = qd - R;
+            dy = k - qd * W - R;
             const float gx = dx > 0 ? dx * wx - tx : (dx < 0 ? tx - (dx + 1) * wx : 0.f);
             const float gy = dy > 0 ? dy * wy - ty : (dy < 0 ? ty - (dy + 1) * wy : 0.f);
             const float d2 = gx * gx + gy * gy;
@@ -1174,6 +1183,7 @@ __device__ __forceinline__ int target_ranges(const int* __restrict__ cell_off, c
             if (slot < cap) {
                 const int a = cell_off[base + zw], b = cell_off[base + zw + len];
                 rng[slot] = make_int4(a, zw, d, (dx + R) | ((dy + R) << 4));
+                shf[slot] = make_float4(shx_hi[dx + R], shy_hi[dy + R], shx_lo[dx + R], shy_lo[dy + R]);
                 pos[slot] = b - a;
             }
             ++slot;
@@ -1240,7 +1250,8 @@ __device__ __forceinline__ void k_short_body(int bx, const Vec4<float>* __restri
     const unsigned below = (1u << lane) - 1u;   // lanes under this one
     extern __shared__ __align__(16) unsigned char short_dyn[];
     int4* rng = reinterpret_cast<int4*>(short_dyn) + warp * rcap;
-    int* pos = reinterpret_cast<int*>(reinterpret_cast<int4*>(short_dyn) + kShortWarps * rcap) + warp * (rcap + 1);
+    float4* shf = reinterpret_cast<float4*>(short_dyn) + kShortWarps * rcap + warp * rcap;
+    int* pos = reinterpret_cast<int*>(reinterpret_cast<float4*>(short_dyn) + 2 * kShortWarps * rcap) + warp * (rcap + 1);
     float4* ring = sh_q[warp];
     const int t0 = (bx * kShortWarps + warp) * kShortTPW;
     const CellGridF cg{R, Rz, g.ncell[0], g.ncell[1], g.ncell[2], static_cast<float>(g.cellw[0]),
@@ -1250,7 +1261,8 @@ __device__ __forceinline__ void k_short_body(int bx, const Vec4<float>* __restri
         const Vec4<float> tl = lo[ti];
         const int c = idx[ti].x;   // packed cell coordinates
         const int cx = c & 1023, cy = (c >> 10) & 1023, cz = c >> 20;
-        const int total = target_ranges(cell_off, cg, cx, cy, cz, th.x, th.y, th.z, kp.rc2f, lane, rcap, rng, pos);
+        const int total = target_ranges(cell_off, cg, cx, cy, cz, th.x, th.y, th.z, kp.rc2f, lane, rcap, rng, pos,
+                                        sh_hi[0], sh_hi[1], sh_lo[0], sh_lo[1], shf);
         float ph = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
         // one queued pair per lane: ring[(head + lane) mod ring] for lanes below cnt, zeros elsewhere
         auto evaluate = [&](int head, int cnt) {
@@ -1281,12 +1293,13 @@ __device__ __forceinline__ void k_short_body(int bx, const Vec4<float>* __restri
             if (p < total) {
                 while (pos[r + 1] <= p) ++r;
                 const int4 rg = rng[r];
+                const float4 sf = shf[r];   // the piece's x, y shifts (hi, lo)
                 const int j = rg.x + (p - pos[r]);
                 const Vec4<float> a = rec[j];
                 const Vec4<float> l = lo[j];
-                const int ix = rg.w & 15, iy = rg.w >> 4, iz = rg.z + (__float_as_int(l.w) - rg.y) + Rz;
-                ddx = (th.x - (a.x + sh_hi[0][ix])) + ((tl.x - l.x) - sh_lo[0][ix]);
-                ddy = (th.y - (a.y + sh_hi[1][iy])) + ((tl.y - l.y) - sh_lo[1][iy]);
+                const int iz = rg.z + (__float_as_int(l.w) - rg.y) + Rz;
+                ddx = (th.x - (a.x + sf.x)) + ((tl.x - l.x) - sf.z);
+                ddy = (th.y - (a.y + sf.y)) + ((tl.y - l.y) - sf.w);
                 ddz = (th.z - (a.z + sh_hi[2][iz])) + ((tl.z - l.z) - sh_lo[2][iz]);
                 const float r2 = fmaf(ddx, ddx, fmaf(ddy, ddy, ddz * ddz));
                 in = r2 < kp.rc2 && r2 > 0.f;
