@@ -311,3 +311,22 @@ def test_eval_host_output_arrays_are_checked():
     ro.flags.writeable = False
     with pytest.raises(ValueError):
         pe._out(ro, (7, 3))
+
+
+def test_spread_kernel_choice():
+    """ewald_opts.spread_kernel: 0 (automatic) and 1 give the CUDA-core kernel; 2 gives the tensor-core
+    kernel only to float32 plans whose window support fits it (P <= 14); other values are rejected."""
+    import ctypes
+    for tol in (1e-4, 1e-6):
+        assert pe.plan_params(1.0, 100_000, tol, precision="mixed").spread_kernel == 1
+        assert pe.plan_params(1.0, 100_000, tol, precision="mixed", spread_kernel=1).spread_kernel == 1
+        assert pe.plan_params(1.0, 100_000, tol, precision="mixed", spread_kernel=2).spread_kernel == 2
+    for prec, tol in (("fp64", 1e-6), ("mixed", 1e-10), ("floatfloat", 1e-8)):
+        p = pe.plan_params(1.0, 100_000, tol, precision=prec, spread_kernel=2)
+        assert p.precision != pe.EWALD_MIXED and p.spread_kernel == 1
+    p = pe.plan_params(1.0, 100_000, 1e-6, precision="mixed", spread_kernel=2, window_extra=3)
+    assert p.P == 15 and p.spread_kernel == 1          # beyond the tensor-core kernel's accumulator
+    o = pe.make_opts(precision="mixed")
+    o.spread_kernel = 3
+    q = pe.ewald_params()
+    assert pe.lib.ewald_plan_params(1.0, 1000, 1e-6, ctypes.byref(o), ctypes.byref(q)) == pe.EWALD_EINVAL
