@@ -504,6 +504,46 @@ __device__ __forceinline__ void window_weights(const real* __restrict__ c, int d
     }
 }
 
+// The same Horner sums with the coefficients stored by power: c[k * PP + a] (rows of PP >= P values,
+// 16-byte aligned), so each power costs PP / VW vector loads instead of P scalar ones.  Same
+// operations in the same order as window_weights, hence the same weights bit for bit.
+template <typename real, int P, int PP>
+__device__ __forceinline__ void window_weights_rows(const real* __restrict__ c, int deg, real z, real (&w)[P]) {
+    constexpr int VW = 16 / static_cast<int>(sizeof(real));
+    static_assert(PP % VW == 0 && PP >= P, "coefficient rows are whole 16-byte vectors");
+    using V = typename std::conditional<sizeof(real) == 4, float4, double2>::type;
+    const V* row = reinterpret_cast<const V*>(c + deg * PP);
+#pragma unroll
+    for (int i = 0; i < PP / VW; ++i) {
+        const V t = row[i];
+        if constexpr (sizeof(real) == 4) {
+            if (4 * i < P) w[4 * i] = t.x;
+            if (4 * i + 1 < P) w[4 * i + 1] = t.y;
+            if (4 * i + 2 < P) w[4 * i + 2] = t.z;
+            if (4 * i + 3 < P) w[4 * i + 3] = t.w;
+        } else {
+            if (2 * i < P) w[2 * i] = t.x;
+            if (2 * i + 1 < P) w[2 * i + 1] = t.y;
+        }
+    }
+    for (int k = deg - 1; k >= 0; --k) {
+        row -= PP / VW;
+#pragma unroll
+        for (int i = 0; i < PP / VW; ++i) {
+            const V t = row[i];
+            if constexpr (sizeof(real) == 4) {
+                if (4 * i < P) w[4 * i] = fma(w[4 * i], z, t.x);
+                if (4 * i + 1 < P) w[4 * i + 1] = fma(w[4 * i + 1], z, t.y);
+                if (4 * i + 2 < P) w[4 * i + 2] = fma(w[4 * i + 2], z, t.z);
+                if (4 * i + 3 < P) w[4 * i + 3] = fma(w[4 * i + 3], z, t.w);
+            } else {
+                if (2 * i < P) w[2 * i] = fma(w[2 * i], z, t.x);
+                if (2 * i + 1 < P) w[2 * i + 1] = fma(w[2 * i + 1], z, t.y);
+            }
+        }
+    }
+}
+
 // ---- Alg. 2 step 1: spreading ------------------------------------------------------------------
 // One CTA per tile of T^3 stencil-start bins.  Thread t owns the column (b, c) = (t / E, t % E) of
 // the tile's extended block (E = T + P - 1 points per axis) and keeps its E values along the first
@@ -853,11 +893,13 @@ __device__ __forceinline__ void k_interp_body(int bx, const real* __restrict__ g
     real* sw = reinterpret_cast<real*>(smem_raw);                 // NWARP * NB * 6 * PP
     constexpr int SP = interp_plane<P, E>();
     real* G = sw + NWARP * NB * 6 * PP;                           // E planes of SP (y-major)
-    real* sc = G + E * SP;                                        // P * (degw + 1)
-    real* sd = sc + P * (degw + 1);                               // P * (degw + 1)
-    for (int i = threadIdx.x; i < P * (degw + 1); i += blockDim.x) {
-        sc[i] = wcoef[i];
-        sd[i] = dwcoef[i];
+    // window and derivative coefficients by power, rows of PP (window_weights_rows)
+    real* sc = G + (E * SP + VW - 1) / VW * VW;                   // (degw + 1) * PP
+    real* sd = sc + PP * (degw + 1);                              // (degw + 1) * PP
+    for (int i = threadIdx.x; i < PP * (degw + 1); i += blockDim.x) {
+        const int k = i / PP, a = i - k * PP;
+        sc[i] = a < P ? wcoef[a * (degw + 1) + k] : real(0);
+        sd[i] = a < P ? dwcoef[a * (degw + 1) + k] : real(0);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     stage_block<real, T, E, SP, NWARP>(grid, mx, my, mz, tx, ty, tz, lane, warp, G);
@@ -870,16 +912,24 @@ __device__ __forceinline__ void k_interp_body(int bx, const real* __restrict__ g
             const int j = task / 6, kind = task % 6, d = kind % 3;
             const Vec4<real> r = rec[b0 + j];
             const real z = d == 0 ? r.x : (d == 1 ? r.y : r.z);
+            // kinds 0-2 are w_d, kinds 3-5 are w'_d / alpha_d.  The lanes of a warp hold mixed kinds, so
+            // the coefficient rows and the factor are selected, not branched on (a branch would run both
+            // Horner sums on half the lanes each); w x 1 is exact.
+            const bool deriv = kind >= 3;
+            const real s = deriv ? (d == 0 ? inv_alpha.x : (d == 1 ? inv_alpha.y : inv_alpha.z)) : real(1);
             real w[P];
-            if (kind < 3) {
-                window_weights<real, P>(sc, degw, z, w);
+            window_weights_rows<real, P, PP>(deriv ? sd : sc, degw, z, w);
+            V* out = reinterpret_cast<V*>(ww + (j * 6 + kind) * PP);
 #pragma unroll
-                for (int a = 0; a < P; ++a) ww[(j * 6 + kind) * PP + a] = w[a];
-            } else {
-                window_weights<real, P>(sd, degw, z, w);
-                const real ia = d == 0 ? inv_alpha.x : (d == 1 ? inv_alpha.y : inv_alpha.z);   // 1/alpha_d
+            for (int v = 0; v < PP / VW; ++v) {
+                real t[VW];
 #pragma unroll
-                for (int a = 0; a < P; ++a) ww[(j * 6 + kind) * PP + a] = w[a] * ia;
+                for (int u = 0; u < VW; ++u) t[u] = VW * v + u < P ? w[VW * v + u] * s : real(0);
+                if constexpr (sizeof(real) == 4) {
+                    out[v] = make_float4(t[0], t[1], t[2], t[3]);
+                } else {
+                    out[v] = make_double2(t[0], t[1]);
+                }
             }
         }
         __syncwarp();

@@ -46,7 +46,8 @@ size_t Launch<real_t>::interp_smem(int P, int degw) {
     constexpr int VW = 16 / static_cast<int>(sizeof(real_t));
     const int PP = (P + VW - 1) / VW * VW;   // padded weight rows (k_interp)
     const int SP = E * E + (((P - E * E) % 32) + 32) % 32;   // padded y-plane (k_interp)
-    return sizeof(real_t) * (static_cast<size_t>(E) * SP + 2 * P * (degw + 1) +
+    const size_t block = (static_cast<size_t>(E) * SP + VW - 1) / VW * VW;   // staged block, then coefficient rows
+    return sizeof(real_t) * (block + 2 * static_cast<size_t>(PP) * (degw + 1) +
                              InterpCfg<real_t>::NWARP * InterpCfg<real_t>::NB * 6 * PP);
 }
 
