@@ -77,6 +77,34 @@ def test_bruteforce_lattice_sum(seed):
     assert np.max(np.abs(grad - ref[1])) <= 1e-7 * np.max(np.abs(ref[1]))
 
 
+@pytest.mark.parametrize("seed", [1, 2])
+def test_bruteforce_lattice_sum_with_dipole(seed):
+    """General neutral cells (dipole D = sum_j rho_j x_j != 0): the cubic-shell replica sum is the
+    sum of a macroscopic cube in vacuum, whose depolarisation factor is 1/3 by symmetry, so it exceeds
+    the Ewald (conducting-boundary) potential by the surface term (4 pi/(3V)) D . x_i and the
+    second-moment constant -(2 pi/(3V)) sum_j rho_j |x_j|^2 (the two together do not depend on the
+    origin), the field by (4 pi/(3V)) D, and the energy by (2 pi/(3V)) |D|^2 (a derivation of this
+    library, checked here; dropping the surface term, flipping its sign or halving it misses by 5-90%)."""
+    rng = np.random.default_rng(seed)
+    x = rng.random((5, 3))
+    rho = rng.uniform(-1.0, 1.0, 5)
+    rho -= rho.mean()
+    D = rho @ x
+    V = 1.0
+    ref = exact.pswf_exact(x, rho, 1.0)
+    Ns = (8, 12, 16, 24, 32)
+    sums = [exact.lattice_shell_sum(x, rho, 1.0, N) for N in Ns]
+    phi_shell = _extrapolate([s[0] for s in sums], Ns)
+    grad_shell = _extrapolate([s[1] for s in sums], Ns)
+    phi = phi_shell - 4 * np.pi / (3 * V) * (x @ D) + 2 * np.pi / (3 * V) * np.sum(rho * np.sum(x * x, axis=1))
+    grad = grad_shell - 4 * np.pi / (3 * V) * D
+    assert np.linalg.norm(D) > 0.1
+    assert np.max(np.abs(phi - ref[0])) <= 1e-7 * np.max(np.abs(ref[0]))
+    assert np.max(np.abs(grad - ref[1])) <= 1e-7 * np.max(np.abs(ref[1]))
+    E_shell = 0.5 * float(rho @ phi_shell)
+    assert abs(E_shell - (ref[2] + 2 * np.pi / (3 * V) * float(D @ D))) <= 1e-7 * abs(ref[2])
+
+
 def test_translation_invariance(small_system):
     x, rho, L = small_system
     a = exact.pswf_exact(x, rho, L)
