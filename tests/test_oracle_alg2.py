@@ -91,6 +91,27 @@ def test_error_models_match_measured_split_error():
         assert model / 4 <= err <= model * 4, (m, err, model)
 
 
+def test_split_error_grows_as_sqrt_rc_at_fixed_cs():
+    """Fig. 6 and Prop. 1: with c_s held fixed (c_s = pi r_c m / L = 4 pi, so m = 64, 32, 16 for
+    r_c = L/16, L/8, L/4) and the window error negligible (P = 16), the far-field error grows as
+    sqrt(r_c): the least-squares slope of log(err) on log(r_c) is 1/2 within 0.1, and every error is
+    within [0.7, 1.4] of eq. PSWF_model with A_s = 5 (a model in r_c or without r_c gives slope 1 or 0)."""
+    x, rho, L = uniform_neutral(400, seed=5, dist="normal")
+    ref = exact.pswf_exact(x, rho, L)
+    rcs, errs = [], []
+    for rc, m in ((0.0625, 64), (0.125, 32), (0.25, 16)):
+        cs = math.pi * rc * m / L
+        P = 16
+        out = Alg2(L, m, P, cs, math.pi * P / 2, rc).total(x, rho)
+        err = np.sqrt(np.mean((out[0] - ref[0]) ** 2))
+        model = 5.0 * np.linalg.norm(rho) / math.sqrt(L ** 3) * math.sqrt(rc) * cs ** -0.5 * math.exp(-cs)
+        assert 0.7 <= err / model <= 1.4, (rc, err, model)
+        rcs.append(rc)
+        errs.append(err)
+    slope = np.polyfit(np.log(rcs), np.log(errs), 1)[0]
+    assert abs(slope - 0.5) <= 0.1, slope
+
+
 def test_alias_model_matches_measured_window_error():
     """Fig. 5(a)-style: with a large m the error plateau follows eq. window_err_model (A_w = 3.1)."""
     x, rho, L = uniform_neutral(400, seed=6, dist="normal")
