@@ -154,6 +154,33 @@ def test_plan_rejects_bad_arguments():
     assert ei.value.code == pe.EWALD_ETOOBIG
 
 
+def test_error_strings_and_thread_local_last_error():
+    """Every status code has its own message (unknown codes too), and ewald_last_error() is per
+    thread: a failure on another thread leaves this thread's message as it was."""
+    import threading
+    msgs = [pe.lib.ewald_error_string(c) for c in range(9)]
+    assert all(msgs) and len(set(msgs)) == 9
+    assert pe.lib.ewald_error_string(pe.EWALD_ETIMEOUT) != pe.lib.ewald_error_string(pe.EWALD_ECUDA)
+    assert pe.lib.ewald_error_string(999) and pe.lib.ewald_error_string(-1)
+    with pytest.raises(pe.EwaldError):
+        pe.plan_params(-1.0, 100, 1e-6)
+    mine = pe.lib.ewald_last_error()
+    theirs = {}
+
+    def other():
+        try:
+            pe.plan_params(1.0, 100, 1e-1)
+        except pe.EwaldError:
+            pass
+        theirs["msg"] = pe.lib.ewald_last_error()
+
+    th = threading.Thread(target=other)
+    th.start()
+    th.join()
+    assert theirs["msg"] and theirs["msg"] != mine
+    assert pe.lib.ewald_last_error() == mine
+
+
 @pytest.mark.parametrize("prec,tol", [("mixed", 1e-6), ("fp64", 1e-6), ("fp64", 1e-10), ("fp64", 1e-12)])
 def test_window_fit_error(prec, tol):
     """Piecewise Horner window (Remark in Sec. 4.3) against the exact psi of the oracle."""
