@@ -52,18 +52,28 @@ def evaluate_sharded(evaluate, ns, costs, rank, world, group=None):
     a tuple (phi (n_i,), F (n_i, 3), E) of host arrays.  The gather runs over torch.distributed on the
     host (`group`: a gloo process group, or the default group); with world == 1 no process group is
     needed.  Returns phi (N,), F (N, 3) concatenated in the batch's order and E (nsys,).
+
+    A rank whose evaluate() raises still takes part in the gather, carrying its error instead of
+    results, so every rank raises RuntimeError naming the failed rank (none is left waiting for the
+    collective's timeout); with world == 1 the exception propagates unchanged.
     """
     share = assign(costs, world)
     mine = share[rank]
-    local = {i: r for i, r in zip(mine, evaluate(mine))} if mine else {}
     if world > 1:
         import torch.distributed as dist
+        try:
+            local, err = ({i: r for i, r in zip(mine, evaluate(mine))} if mine else {}), None
+        except Exception as e:   # reported through the gather below
+            local, err = {}, "%s: %s" % (type(e).__name__, e)
         gathered = [None] * world
-        dist.all_gather_object(gathered, local, group=group)
+        dist.all_gather_object(gathered, (local, err), group=group)
     else:
-        gathered = [local]
+        gathered = [({i: r for i, r in zip(mine, evaluate(mine))} if mine else {}, None)]
+    failed = [(r, e) for r, (_, e) in enumerate(gathered) if e is not None]
+    if failed:
+        raise RuntimeError("sharded batch: rank %d failed: %s" % failed[0])
     results = {}
-    for part in gathered:
+    for part, _ in gathered:
         results.update(part)
     if sorted(results) != list(range(len(ns))):
         raise RuntimeError("sharded batch: systems missing after the gather")
@@ -114,5 +124,5 @@ class ShardedBatchPlan:
 
     def eval(self, x, rho):
         """phi (N,), F (N, 3), E (nsys,) of the whole batch on every rank (host arrays)."""
-        local = self.eval_local(x, rho)
-        return evaluate_sharded(lambda idx: local, self.ns, self.costs, self.rank, self.world, self.group)
+        return evaluate_sharded(lambda idx: self.eval_local(x, rho), self.ns, self.costs, self.rank, self.world,
+                                self.group)

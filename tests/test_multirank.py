@@ -165,3 +165,71 @@ def test_shard_assignment_balances_cost():
     assert ns[int(np.argmax(costs))] >= 0.9 * max(ns)
     rank_n, rank_c = np.argsort(np.argsort(ns)), np.argsort(np.argsort(costs))
     assert np.corrcoef(rank_n, rank_c)[0, 1] > 0.99
+
+
+def _edge_worker(rank, world, port, nsys, fail_rank, out):
+    import sys
+    from datetime import timedelta
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    sys.path.insert(0, os.path.join(root, "tests"))
+    from conftest import require_library
+    require_library()
+    from paper_2602_16591_gb300 import shard
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    # a short collective timeout: a rank left waiting would end the test with an error, not hang it
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=timedelta(seconds=60))
+    systems = _small_batch()[:nsys]
+    ns = [len(s[1]) for s in systems]
+    costs = shard.batch_costs([s[2] for s in systems], ns, 1e-6)
+    ev = _oracle_evaluator(systems)
+
+    def evaluate(indices):
+        if rank == fail_rank:
+            raise ValueError("evaluation failed on purpose")
+        return ev(indices)
+    try:
+        phi, F, E = shard.evaluate_sharded(evaluate, ns, costs, rank, world)
+        out[rank] = ("ok", phi.tobytes(), F.tobytes(), E.tobytes(), len(shard.assign(costs, world)[rank]))
+    except RuntimeError as e:
+        out[rank] = ("error", str(e))
+    dist.destroy_process_group()
+
+
+def _run_edge(world, nsys, fail_rank):
+    port = _free_port()
+    mgr = mp.get_context("spawn").Manager()
+    out = mgr.dict()
+    mp.start_processes(_edge_worker, args=(world, port, nsys, fail_rank, out), nprocs=world,
+                       start_method="spawn", join=True)
+    return dict(out)
+
+
+def test_failed_rank_is_reported_to_every_rank():
+    """A rank whose evaluation raises joins the host gather with its error: every rank raises an error
+    naming it, and none waits for the collective's timeout."""
+    import time
+    t0 = time.perf_counter()
+    out = _run_edge(world=2, nsys=4, fail_rank=1)
+    assert time.perf_counter() - t0 < 50
+    for r in range(2):
+        assert out[r][0] == "error"
+        assert "rank 1 failed" in out[r][1] and "evaluation failed on purpose" in out[r][1]
+
+
+def test_more_ranks_than_systems():
+    """Three ranks, two systems: one rank has an empty share and still receives the whole batch's
+    results, equal bit for bit to the single-rank evaluation."""
+    from conftest import require_library
+    require_library()
+    from paper_2602_16591_gb300 import shard
+    systems = _small_batch()[:2]
+    ns = [len(s[1]) for s in systems]
+    costs = shard.batch_costs([s[2] for s in systems], ns, 1e-6)
+    ref = shard.evaluate_sharded(_oracle_evaluator(systems), ns, costs, 0, 1)
+    out = _run_edge(world=3, nsys=2, fail_rank=-1)
+    assert sorted(out[r][4] for r in range(3)) == [0, 1, 1]       # systems per rank
+    for r in range(3):
+        assert out[r][0] == "ok"
+        assert out[r][1] == ref[0].tobytes() and out[r][2] == ref[1].tobytes() and out[r][3] == ref[2].tobytes()
