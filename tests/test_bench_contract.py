@@ -1,5 +1,6 @@
-"""The reference arm of bench.py on the host: one JSON line with the metric, unit and workload of the
-GPU arm, the oracle timed on the host cores, no product library loaded, and silent non-zero ranks."""
+"""Host-side contract of bench.py.  The reference arm prints one JSON line with the metric, unit and
+workload of the GPU arm and the oracle timed on the host cores, loads no product library, and is silent
+on ranks other than 0.  The clock record of the GPU arm is parsed from nvidia-smi samples."""
 import json
 import os
 import subprocess
@@ -47,3 +48,24 @@ def test_reference_arm_other_ranks_exit_without_work():
              {"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, timeout=120)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_clock_summary_parses_nvidia_smi_samples(tmp_path):
+    """The clocks record of a bench line: median SM clock over the samples, the maximum clock, and every
+    throttle reason seen active at least once; malformed or partial lines are skipped."""
+    csv = tmp_path / "clocks.csv"
+    csv.write_text(
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 1980, 2070, 1390.5, 0x0000000000000004, Not Active, Not Active, Not Active, Active\n"
+        "0, 2070\n"
+        "0, [N/A], 2070, 700.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 2070, 2070, 1000.0, 0x0000000000000008, Active, Not Active, Not Active, Not Active\n")
+    cs = bench.ClockSampler(0)
+    cs.path = str(csv)
+    s = cs.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 3}
+    assert not csv.exists()                          # the temporary record is removed
+    empty = tmp_path / "empty.csv"
+    empty.write_text("")
+    cs.path = str(empty)
+    assert cs.summary() is None
