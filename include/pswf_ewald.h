@@ -129,13 +129,20 @@ typedef struct ewald_plan_s* ewald_plan;   /* opaque, owned by the library */
 int ewald_opts_default(ewald_opts* opts);
 
 /* Host only (no CUDA call): run Alg. 3 (Sec. 6.4) for a box of edge L holding
- * n particles at relative tolerance tol and fill *out.  opts may be NULL. */
+ * n particles at relative tolerance tol and fill *out.  opts may be NULL.
+ * Errors: EWALD_EINVAL (NULL out, L <= 0 or not finite, n < 2, tol outside
+ * [1e-13, 1e-2], an option out of its range), EWALD_ETOOBIG (grid or window
+ * support beyond the library limits). */
 int ewald_plan_params(double L, int64_t n, double tol, const ewald_opts* opts,
                       ewald_params* out);
 
 /* Create a plan on the current CUDA device: parameters as ewald_plan_params,
  * PSWF tables, cuFFT plans and a device workspace sized for n particles.
- * On success *out holds the plan; release it with ewald_plan_destroy. */
+ * On success *out holds the plan; release it with ewald_plan_destroy.  On
+ * failure *out is NULL and nothing stays allocated.  Errors: those of
+ * ewald_plan_params, EWALD_ENOMEM (device or pinned host memory),
+ * EWALD_ECUDA (no usable device, a failed launch while autotuning),
+ * EWALD_ECUFFT (cuFFT plan creation). */
 int ewald_plan_create(double L, int64_t n, double tol, const ewald_opts* opts,
                       ewald_plan* out);
 
@@ -150,7 +157,7 @@ int ewald_plan_params_box(const double* L, int64_t n, double tol, const ewald_op
 int ewald_plan_create_box(const double* L, int64_t n, double tol, const ewald_opts* opts,
                           ewald_plan* out);
 
-/* Copy the plan's parameters into *out. */
+/* Copy the plan's parameters into *out.  Host only.  EWALD_EINVAL on NULL. */
 int ewald_plan_query(ewald_plan plan, ewald_params* out);
 
 /* Evaluate on device buffers (Alg. 2 steps 1-5 plus the real-space sum, self

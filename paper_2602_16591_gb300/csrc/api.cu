@@ -869,6 +869,14 @@ int plan_create_impl(const double* box, int64_t n, double tol, const ewald_opts*
         delete p;
         return fail(EWALD_EINVAL, e.what());
     }
+    // a missing device is reported as such, not as the failure of the first allocation
+    int ndev = 0;
+    const cudaError_t de = cudaGetDeviceCount(&ndev);
+    if (de != cudaSuccess || ndev < 1) {
+        cudaGetLastError();
+        delete p;
+        return fail(EWALD_ECUDA, std::string("no CUDA device: ") + (de != cudaSuccess ? cudaGetErrorString(de) : "none found"));
+    }
     const ewald_params& q = p->hp.p;
     p->fp64 = q.precision != EWALD_MIXED;
     p->ff = q.precision == EWALD_FLOATFLOAT;

@@ -1,6 +1,7 @@
 """CPU tests of the C ABI's host side: exported symbols, the planner's PSWF, Alg. 3, fits, tables.
 
-Everything here runs without a GPU (the library's host entry points make no CUDA call).
+Everything here runs without a GPU (the library's host entry points make no CUDA call; plan creation
+is called only to check how it reports a host without a CUDA device).
 """
 import math
 import os
@@ -357,3 +358,20 @@ def test_spread_kernel_choice():
     o.spread_kernel = 3
     q = pe.ewald_params()
     assert pe.lib.ewald_plan_params(1.0, 1000, 1e-6, ctypes.byref(o), ctypes.byref(q)) == pe.EWALD_EINVAL
+
+
+def test_plan_create_without_a_device_reports_it():
+    """On a host without a CUDA device, plan creation fails with EWALD_ECUDA naming the missing device
+    (not as a failed allocation), after the argument checks, and leaves *out NULL."""
+    import ctypes
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    h = ctypes.c_void_p(1)
+    code = pe.lib.ewald_plan_create(ctypes.c_double(1.0), ctypes.c_int64(1000), ctypes.c_double(1e-6), None,
+                                    ctypes.byref(h))
+    assert code == pe.EWALD_ECUDA and b"no CUDA device" in pe.lib.ewald_last_error()
+    assert h.value is None
+    code = pe.lib.ewald_plan_create(ctypes.c_double(-1.0), ctypes.c_int64(1000), ctypes.c_double(1e-6), None,
+                                    ctypes.byref(h))
+    assert code == pe.EWALD_EINVAL
