@@ -50,6 +50,17 @@ def test_nacl_madelung():
     assert np.max(np.abs(F)) <= 1e-11 * M / d ** 2
 
 
+def test_madelung_value_by_benson_series():
+    """The stored rock-salt constant against an independent route: Benson's series
+    M = 12 pi sum_{m, n odd > 0} sech^2((pi/2) sqrt(m^2 + n^2)), which converges like exp(-pi m) and
+    involves no Ewald split, so the NaCl pin above rests on more than a remembered number."""
+    M = float(read_golden("nacl_madelung.txt")[0][1])
+    odd = np.arange(1, 41, 2, dtype=np.float64)
+    mm, nn = np.meshgrid(odd, odd)
+    benson = 12 * np.pi * np.sum(1.0 / np.cosh(0.5 * np.pi * np.sqrt(mm * mm + nn * nn)) ** 2)
+    assert abs(benson - M) <= 1e-12
+
+
 def _extrapolate(vals, Ns, powers=(2, 3, 4)):
     """Least-squares fit v(N) = v_inf + sum_p a_p N^-p over the shell sums; returns v_inf."""
     A = np.array([[1.0] + [float(N) ** -p for p in powers] for N in Ns])
