@@ -3,7 +3,6 @@ import math
 
 import numpy as np
 import pytest
-from scipy.special import lambertw
 
 from oracle import exact, params
 from oracle.alg2 import Alg2
