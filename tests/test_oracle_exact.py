@@ -50,6 +50,22 @@ def test_nacl_madelung():
     assert np.max(np.abs(F)) <= 1e-11 * M / d ** 2
 
 
+def test_stored_values_are_the_oracles():
+    """The stored oracle values of the 1e5 bench workload (tests/golden/uniform1e5_seed0.txt, written by
+    tests/golden/make_reference_values.py) are reproduced by the oracle as it stands at three of their
+    targets: the GPU parity tests that read them compare against the present oracle, not a stale copy."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden"))
+    import make_reference_values as stored
+    tg, phi, F, _ = stored.read("uniform1e5")
+    sel = np.array([0, 131, len(tg) - 1])
+    x, rho, L = uniform_neutral(100_000, seed=0)
+    p, _, _, f = exact.pswf_exact(x, rho, L, targets=tg[sel])
+    assert np.max(np.abs(p - phi[sel])) <= 1e-12 * np.max(np.abs(phi))
+    assert np.max(np.abs(f - F[sel])) <= 1e-12 * np.max(np.abs(F))
+
+
 def test_madelung_value_by_benson_series():
     """The stored rock-salt constant against an independent route: Benson's series
     M = 12 pi sum_{m, n odd > 0} sech^2((pi/2) sqrt(m^2 + n^2)), which converges like exp(-pi m) and
