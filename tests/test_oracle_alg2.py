@@ -111,6 +111,29 @@ def test_split_error_grows_as_sqrt_rc_at_fixed_cs():
     assert abs(slope - 0.5) <= 0.1, slope
 
 
+def test_alg2_scaling_law_and_a_planted_unit_mistake():
+    """eq. phinondim for Alg. 2 itself: scaling the box, the positions and the cutoff by s with the same
+    (m, P, c_s, c_w) divides phi by s and F by s^2 to rounding, since the grid spacing, alpha, the
+    window transform per h and the 1/V of the scaling all carry their units.  Every other cube test of
+    Alg. 2 runs at L = 1, where a dropped 1/V is invisible; planted here, it breaks the law."""
+    x, rho, L = uniform_neutral(300, seed=8)
+    m, P, rc, s = 24, 12, 0.2, 2.5
+    cs, cw = math.pi * rc * m / L, math.pi * P / 2
+    a = Alg2(L, m, P, cs, cw, rc).total(x, rho)
+    b = Alg2(s * L, m, P, cs, cw, s * rc).total(s * x, rho)
+    assert _rel(b[0], a[0] / s) <= 1e-12
+    assert _rel(b[3], a[3] / s ** 2) <= 1e-12
+
+    class NoVolume(Alg2):   # the planted mistake: S(k) without its 1/V
+        def scaling(self):
+            return super().scaling() * float(np.prod(self.Lv))
+
+    a2 = NoVolume(L, m, P, cs, cw, rc).total(x, rho)
+    b2 = NoVolume(s * L, m, P, cs, cw, s * rc).total(s * x, rho)
+    assert _rel(a2[0], a[0]) <= 1e-14                  # invisible at L = 1
+    assert _rel(b2[0], a2[0] / s) > 0.1
+
+
 def test_alias_model_matches_measured_window_error():
     """Fig. 5(a)-style: with a large m the error plateau follows eq. window_err_model (A_w = 3.1)."""
     x, rho, L = uniform_neutral(400, seed=6, dist="normal")
