@@ -132,6 +132,29 @@ def test_bruteforce_lattice_sum_with_dipole(seed):
     assert abs(E_shell - (ref[2] + 2 * np.pi / (3 * V) * float(D @ D))) <= 1e-7 * abs(ref[2])
 
 
+def test_bruteforce_catches_a_flipped_structure_factor_phase(monkeypatch):
+    """A planted mistake in the k-space sum: rho-hat with the sign of its phase flipped (its conjugate).
+    The centrosymmetric NaCl lattice has a real structure factor and does not notice it; the brute-force
+    lattice sum, which shares no code with the k-space sum, does (so does split independence, whose two
+    splits weight the wrong modes differently)."""
+    rng = np.random.default_rng(1)
+    x = rng.random((5, 3))
+    rho = rng.uniform(-1.0, 1.0, 5)
+    rho -= rho.mean()
+    D = rho @ x
+    Ns = (8, 12, 16, 24, 32)
+    sums = [exact.lattice_shell_sum(x, rho, 1.0, N) for N in Ns]
+    phi_bf = _extrapolate([s[0] for s in sums], Ns) - 4 * np.pi / 3 * (x @ D) \
+        + 2 * np.pi / 3 * np.sum(rho * np.sum(x * x, axis=1))
+    good = exact.pswf_exact(x, rho, 1.0)[0]
+    orig = exact.structure_factor
+    monkeypatch.setattr(exact, "structure_factor", lambda *a, **k: np.conj(orig(*a, **k)))
+    bad = exact.pswf_exact(x, rho, 1.0)[0]
+    scale = np.max(np.abs(phi_bf))
+    assert np.max(np.abs(good - phi_bf)) <= 1e-7 * scale
+    assert np.max(np.abs(bad - phi_bf)) > 1e-3 * scale
+
+
 def test_translation_invariance(small_system):
     x, rho, L = small_system
     a = exact.pswf_exact(x, rho, L)
