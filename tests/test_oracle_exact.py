@@ -87,8 +87,8 @@ def _extrapolate(vals, Ns, powers=(2, 3, 4)):
 @pytest.mark.parametrize("seed", [1, 2])
 def test_bruteforce_lattice_sum(seed):
     """Dipole-free neutral cells: the cubic-shell replica sum of 1/r converges to the
-    Ewald potential plus the constant (2 pi/(3V)) sum_j rho_j |x_j - c|^2 (a derivation
-    of this library; no gradient), so phi, forces and energy are pinned together."""
+    Ewald potential minus the constant (2 pi/(3V)) sum_j rho_j |x_j - c|^2 (a derivation
+    of this library; no gradient), so phi and forces are pinned together."""
     rng = np.random.default_rng(seed)
     c = np.full(3, 0.5)
     a = rng.uniform(-0.3, 0.3, (2, 3))
