@@ -265,9 +265,13 @@ int ewald_window_fit(const ewald_params* p, int nz, const double* z, double* w, 
 int ewald_radial_fit(const ewald_params* p, int nr, const double* r, double* R, double* G);
 
 /* The diagonal scaling S(k) of Alg. 2 step 3 on the half spectrum the library
- * uses: S[(ix*m + iy)*(m/2+1) + iz] for k = (kx(ix), ky(iy), iz), where
- * kx(i) = i for i < m/2 and i - m otherwise; S = 0 outside the open ball
- * 0 < |k| < m/2.  S holds m*m*(m/2+1) doubles. */
+ * uses: S[(ix*my + iy)*(mz/2+1) + iz] for k = (kx(ix), ky(iy), iz), where
+ * (mx, my, mz) = p->grid, kx(i) = i for i < mx/2 and i - mx otherwise (ky
+ * alike).  Cubes: S = 0 outside the open ball 0 < |k| < m/2.  Cuboids (Remark
+ * on cuboid domains, Sec. 6.1): S = 0 outside the mollifier's band
+ * 0 < |omega| < c_s / r_c, M-hat from the plan's polynomial of gammahat, as
+ * the scaling kernel evaluates it.  S holds mx*my*(mz/2+1) doubles (HOST).
+ * EWALD_EINVAL on NULL. */
 int ewald_scale_table(const ewald_params* p, double* S);
 
 /* ---- spreading without device allocation -------------------------------

@@ -193,8 +193,8 @@ def radial_fit(params, r):
 
 
 def scale_table(params):
-    m = params.m
-    S = np.empty((m, m, m // 2 + 1))
+    mx, my, mz = (int(v) for v in params.grid)
+    S = np.empty((mx, my, mz // 2 + 1))
     _check(_lib.ewald_scale_table(ctypes.byref(params), _ptr(S)))
     return S
 

@@ -1674,6 +1674,31 @@ int ewald_scale_table(const ewald_params* p, double* S) {
         const pswf::Prolate ps(p->cs), pw(p->cw);
         std::vector<double> iw, mtab;
         pswf::scale_tables(*p, ps, pw, iw, mtab);
+        if (p->deg_g > 0) {
+            // cuboid: the scaling step's formula (k_scale) on the host, every mode inside the
+            // mollifier's band |omega| < c_s / r_c, M-hat from the plan's polynomial of gammahat
+            const std::vector<double> gc = pswf::fit_gamma(ps, p->deg_g, nullptr);
+            const int mx = p->grid[0], my = p->grid[1], mz = p->grid[2], mh = mz / 2 + 1;
+            const double pi = 3.14159265358979323846;
+            const double V = p->box[0] * p->box[1] * p->box[2], ts = (p->rc / p->cs) * (p->rc / p->cs);
+            double w2d[3];
+            for (int d = 0; d < 3; ++d) w2d[d] = (2.0 * pi / p->box[d]) * (2.0 * pi / p->box[d]);
+            for (int ix = 0; ix < mx; ++ix)
+                for (int iy = 0; iy < my; ++iy)
+                    for (int iz = 0; iz < mh; ++iz) {
+                        const int kx = ix < mx / 2 ? ix : ix - mx, ky = iy < my / 2 ? iy : iy - my, kz = iz;
+                        const double w2 = w2d[0] * kx * kx + w2d[1] * ky * ky + w2d[2] * kz * kz, t = w2 * ts;
+                        double s = 0.0;
+                        if (w2 > 0.0 && t < 1.0) {
+                            const double u = 2.0 * t - 1.0;
+                            double gh = gc[p->deg_g];
+                            for (int k = p->deg_g - 1; k >= 0; --k) gh = gh * u + gc[k];
+                            s = 4.0 * pi / V / w2 * gh * iw[ix] * iw[mx + iy] * iw[mx + my + iz];
+                        }
+                        S[(static_cast<size_t>(ix) * my + iy) * mh + iz] = s;
+                    }
+            return EWALD_OK;
+        }
         const int m = p->m, mh = m / 2 + 1, qmax = (m / 2) * (m / 2);
         for (int ix = 0; ix < m; ++ix)
             for (int iy = 0; iy < m; ++iy)

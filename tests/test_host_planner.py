@@ -232,6 +232,30 @@ def test_scale_table_matches_oracle(L, n, tol):
     assert np.max(np.abs(S * D - M)) <= 1e-12 * np.max(M)
 
 
+@pytest.mark.parametrize("box,tol", [((1.0, 1.25, 0.75), 1e-6), ((2.0, 1.0, 1.0), 1e-10)])
+def test_scale_table_matches_oracle_cuboid(box, tol):
+    """Cuboid boxes: the scaling table (per-axis window transforms, M-hat from the plan's gammahat
+    polynomial) against the oracle's S(k) of Alg. 2 in that box, with the plan's per-axis grids: the
+    same retained modes, and S times the window denominator equal to the oracle's M-hat / V within
+    the polynomial fit tolerance."""
+    p = pe.plan_params(box, 20_000, tol)
+    assert p.deg_g > 0
+    mx, my, mz = (int(v) for v in p.grid)
+    S = pe.scale_table(p)
+    A = Alg2(tuple(p.box), tuple(p.grid), p.P, p.cs, p.cw, p.rc)
+    So = A.scaling()[:, :, : mz // 2 + 1]
+    ks = [A.kgrid(d) for d in range(3)]
+    KX, KY, KZ = np.meshgrid(ks[0], ks[1], np.arange(mz // 2 + 1), indexing="ij")
+    t = ((KX / p.box[0]) ** 2 + (KY / p.box[1]) ** 2 + (KZ / p.box[2]) ** 2) * (2 * np.pi * p.rc / p.cs) ** 2
+    clear = np.abs(t - 1.0) > 1e-9                      # modes not on the band edge itself
+    assert np.all(((S != 0) == (So != 0))[clear])
+    ph = [A.window_ft(d) for d in range(3)]
+    D = ((ph[0][:, None, None] * ph[1][None, :, None] * ph[2][None, None, :]) ** 2)[:, :, : mz // 2 + 1]
+    M = So * D
+    both = (S != 0) & (So != 0)
+    assert np.max(np.abs((S * D - M)[both])) <= 2 * p.fit_tol * np.max(M)
+
+
 def test_precision_paths():
     """MIXED below tol 1e-7 runs the float-float kernels; float-float plans size their fits like FP64."""
     for tol in (1e-8, 1e-10, 1e-12):
