@@ -183,7 +183,9 @@ int ewald_check(ewald_plan plan, void* stream);
 /* Test access: copy an internal stage of the last evaluation to HOST memory
  * as float64.  which = 0: the spread grid a_l (m^3, z fastest; Alg. 2 step 1);
  * which = 1: the grid b_l after scaling and the inverse FFT (Alg. 2 step 4).
- * host_out must hold m^3 doubles.  Synchronises the device. */
+ * host_out must hold grid[0]*grid[1]*grid[2] doubles (m^3 for a cube; the
+ * per-axis grid of ewald_params).  Synchronises the device.  EWALD_EINVAL for
+ * a NULL or batch plan, a NULL host_out or another `which`. */
 int ewald_debug_grid(ewald_plan plan, int which, double* host_out);
 
 /* Release a plan (single-system or batch).  NULL is ignored. */
