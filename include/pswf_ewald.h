@@ -207,10 +207,14 @@ void ewald_plan_destroy(ewald_plan plan);
  * offsets[0] = 0 and offsets[b+1] - offsets[b] = n[b]; system b occupies
  * rows offsets[b] .. offsets[b+1]-1 of the DEVICE arrays x (rows of 3),
  * rho, phi and force (phi, force may be NULL).  energy: HOST array of nsys
- * entries or NULL.  The call enqueues every system's pipeline as one CUDA
- * graph on `stream` (captured on the first call and again whenever a buffer
- * pointer changes; the systems' pipelines are independent branches that run
- * concurrently), then synchronises `stream` and reports the first system
+ * entries or NULL.  Batches of EWALD_MIXED (float32) systems that share the
+ * window support P run every stage as one kernel launch over all systems
+ * (batched cuFFT per grid size, the real-space sum on a second stream);
+ * other batches enqueue every system's pipeline as one CUDA graph on
+ * `stream` (captured on the first call and again whenever a buffer pointer
+ * changes; the systems' pipelines are independent branches that run
+ * concurrently).  Either way the call then synchronises `stream` and reports
+ * the first system
  * found non-neutral (EWALD_ENONNEUTRAL) or with non-finite input
  * (EWALD_ENONFINITE); ewald_last_error() names the system.  The batch plan
  * is not reentrant: one call at a time per plan. */
@@ -253,7 +257,9 @@ int ewald_debug_wait_timeout(void);
 int ewald_pswf_eval(double c, int nx, const double* x, double* psi, double* dpsi,
                     double* chi, double* lambda0);
 
-/* Lambert W on branch 0 (z >= -1/e) or -1 (-1/e <= z < 0), Halley iteration. */
+/* Lambert W on branch 0 (z >= -1/e) or -1 (-1/e <= z < 0), Halley iteration.
+ * For another branch, a NaN z or z outside the branch's domain it returns NaN
+ * and sets the message of ewald_last_error(). */
 double ewald_lambertw(int branch, double z);
 
 /* The fitted window polynomials of a plan (Remark on piecewise polynomials in

@@ -280,7 +280,8 @@ double CosQuadrature::operator()(double omega) const {
 // --------------------------------------------------------------- Lambert W --
 double lambert_w(int branch, double z) {
     const double em1 = 0.36787944117144233;   // 1/e
-    if (z < -em1 - 1e-15) throw std::invalid_argument("Lambert W: z < -1/e");
+    if (branch != 0 && branch != -1) throw std::invalid_argument("Lambert W: branch must be 0 or -1");
+    if (!(z >= -em1 - 1e-15)) throw std::invalid_argument("Lambert W: z < -1/e or not a number");
     if (branch == -1 && !(z < 0)) throw std::invalid_argument("Lambert W_{-1}: z must be in [-1/e, 0)");
     double w;
     if (branch == 0) {

@@ -62,6 +62,15 @@ def test_lambertw_lower(z):
     assert abs(pe.lambertw(-1, z) - ref) <= 1e-13 * abs(ref)
 
 
+def test_lambertw_outside_its_domain():
+    """Another branch, a NaN argument or z outside a branch's domain: NaN and a message, never a
+    number from an undefined logarithm."""
+    for branch, z, msg in [(3, 1.0, b"branch"), (0, -1.0, b"-1/e"), (-1, 0.5, b"[-1/e, 0)"),
+                           (0, float("nan"), b"not a number")]:
+        assert math.isnan(pe.lambertw(branch, z))
+        assert msg in pe.lib.ewald_last_error()
+
+
 CFGS = [(1.0, 1000, 1e-6), (1.0, 512, 1e-6), (1.0, 100_000, 1e-4), (1.0, 100_000, 1e-6), (1.0, 100_000, 1e-10),
         (1.0, 100_000, 1e-12), (9.96, 99_000, 1e-6), (1.0, 10_000_000, 1e-8)]
 
