@@ -60,7 +60,8 @@ extern "C" {
 /* ---- options (ewald_opts_default fills the defaults) -------------------- */
 typedef struct ewald_opts {
     int    precision;     /* EWALD_FP64, EWALD_MIXED or EWALD_FLOATFLOAT (default EWALD_FP64) */
-    double rc;            /* <= 0: automatic cutoff rule; > 0: upper bound on the cutoff (length units) */
+    double rc;            /* <= 0: automatic cutoff rule; > 0: upper bound on the cutoff (length units);
+                             NaN: EWALD_EINVAL */
     double grid_density;  /* target m^3 / n for the automatic cutoff rule; 0 (default): the
                              measured optima of the GB300 kernels, 6 for float32 plans (EWALD_MIXED
                              at tol >= 1e-7) and 3 for the float64 and float-float plans */

@@ -104,7 +104,12 @@ def make_opts(precision="fp64", rc=None, grid_density=None, tol_safety=None, sr_
               autotune=None, spread_kernel=None):
     o = ewald_opts()
     _check(_lib.ewald_opts_default(ctypes.byref(o)))
-    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    if isinstance(precision, str):
+        if precision not in PRECISIONS:
+            raise ValueError("precision must be one of %s" % ", ".join(sorted(PRECISIONS)))
+        o.precision = PRECISIONS[precision]
+    else:
+        o.precision = int(precision)
     if rc is not None:
         o.rc = float(rc)
     if grid_density is not None:

@@ -537,6 +537,7 @@ HostPlan make_plan_box(const double* box, int64_t n, double tol, const ewald_opt
     if (!(tol >= 1e-13 && tol <= 1e-2)) throw std::invalid_argument("tol must lie in [1e-13, 1e-2]");
     if (o.precision != EWALD_FP64 && o.precision != EWALD_MIXED && o.precision != EWALD_FLOATFLOAT)
         throw std::invalid_argument("unknown precision");
+    if (std::isnan(o.rc)) throw std::invalid_argument("rc must be a number (<= 0: automatic cutoff)");
     if (!(o.tol_safety > 0 && o.tol_safety <= 1)) throw std::invalid_argument("tol_safety must lie in (0, 1]");
     if (!(o.grid_density >= 0) || !std::isfinite(o.grid_density))
         throw std::invalid_argument("grid_density must be 0 (automatic) or positive");

@@ -288,6 +288,12 @@ def test_opts_defaults_and_autotune_validation():
     o.autotune = 2
     p = pe.ewald_params()
     assert pe.lib.ewald_plan_params(1.0, 1000, 1e-6, ctypes.byref(o), ctypes.byref(p)) == pe.EWALD_EINVAL
+    o = pe.make_opts()
+    o.rc = float("nan")
+    assert pe.lib.ewald_plan_params(1.0, 1000, 1e-6, ctypes.byref(o), ctypes.byref(p)) == pe.EWALD_EINVAL
+    assert b"rc must be a number" in pe.lib.ewald_last_error()
+    with pytest.raises(ValueError, match="precision must be one of"):
+        pe.make_opts(precision="double")
 
 
 def test_batch_arguments_rejected_before_any_device_work():
