@@ -251,6 +251,12 @@ int ewald_profile_read(ewald_plan plan, double* ms, int* count);
 int ewald_debug_wait_timeout(void);
 
 /* ---- host-side tables (no CUDA call), for tests and tooling ------------- */
+/* ewald_window_fit, ewald_radial_fit and ewald_scale_table take the parameters
+ * of ewald_plan_params / ewald_plan_query; values the planner never produces
+ * (window support outside [3, 24], polynomial degrees out of range,
+ * non-positive or non-finite bandlimits, cutoff, box or spacing, grid sizes
+ * outside [4, 1024], m or L other than the x-axis entries of grid and box)
+ * return EWALD_EINVAL before any table is built. */
 
 /* The planner's PSWF (App. B: Legendre expansion, Sturm bisection + inverse
  * iteration): psi_0^c and its derivative at nx points |x| <= 1, plus chi_0 and

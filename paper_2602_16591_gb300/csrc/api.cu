@@ -1608,6 +1608,28 @@ int ewald_debug_wait_timeout(void) {
              : EWALD_OK;
 }
 
+// The host-table entry points take an ewald_params from the caller: everything the planner never
+// produces is rejected before a table is built (a negative degree or window support would size or index
+// the fitted tables out of range).
+static int check_table_params(const ewald_params* p) {
+    if (!p) return fail(EWALD_EINVAL, "NULL parameters");
+    if (p->P < pswf::kPMin || p->P > pswf::kPMax)
+        return fail(EWALD_EINVAL, "window support P must lie in [" + std::to_string(pswf::kPMin) + ", " +
+                                      std::to_string(pswf::kPMax) + "]");
+    if (p->deg_w < 1 || p->deg_w > pswf::kDegWMax || p->deg_r < 1 || p->deg_r > pswf::kDegRMax ||
+        p->deg_g < 0 || p->deg_g > pswf::kDegRMax)
+        return fail(EWALD_EINVAL, "polynomial degree outside the planner's range");
+    if (!(p->cs > 0) || !(p->cw > 0) || !(p->rc > 0) || !(p->L > 0) || !(p->h > 0) || !(p->alpha > 0) ||
+        !std::isfinite(p->cs) || !std::isfinite(p->cw) || !std::isfinite(p->rc) || !std::isfinite(p->L))
+        return fail(EWALD_EINVAL, "bandlimits, cutoff, box edge, spacing and window half-width must be positive");
+    for (int d = 0; d < 3; ++d)
+        if (p->grid[d] < 4 || p->grid[d] > 1024 || !(p->box[d] > 0) || !std::isfinite(p->box[d]))
+            return fail(EWALD_EINVAL, "grid sizes must lie in [4, 1024] and box edges be positive");
+    if (p->m != p->grid[0] || p->L != p->box[0])
+        return fail(EWALD_EINVAL, "m and L must be the x-axis entries of grid and box");
+    return EWALD_OK;
+}
+
 int ewald_pswf_eval(double c, int nx, const double* x, double* psi, double* dpsi, double* chi, double* lambda0) {
     if (nx < 0 || (nx > 0 && !x)) return fail(EWALD_EINVAL, "bad point array");
     try {
@@ -1635,6 +1657,7 @@ double ewald_lambertw(int branch, double z) {
 
 int ewald_window_fit(const ewald_params* p, int nz, const double* z, double* w, double* dw) {
     if (!p || nz < 0 || (nz > 0 && (!z || !w))) return fail(EWALD_EINVAL, "bad argument");
+    if (const int rc = check_table_params(p)) return rc;
     try {
         const pswf::Prolate pw(p->cw);
         const auto wc = pswf::fit_window(pw, p->P, p->deg_w, false, nullptr);
@@ -1653,6 +1676,7 @@ int ewald_window_fit(const ewald_params* p, int nz, const double* z, double* w, 
 
 int ewald_radial_fit(const ewald_params* p, int nr, const double* r, double* R, double* G) {
     if (!p || nr < 0 || (nr > 0 && (!r || !R))) return fail(EWALD_EINVAL, "bad argument");
+    if (const int rc = check_table_params(p)) return rc;
     try {
         const pswf::Prolate ps(p->cs);
         const auto c1 = pswf::fit_radial(ps, p->rc, p->deg_r, 0, nullptr);
@@ -1670,6 +1694,7 @@ int ewald_radial_fit(const ewald_params* p, int nr, const double* r, double* R, 
 
 int ewald_scale_table(const ewald_params* p, double* S) {
     if (!p || !S) return fail(EWALD_EINVAL, "bad argument");
+    if (const int rc = check_table_params(p)) return rc;
     try {
         const pswf::Prolate ps(p->cs), pw(p->cw);
         std::vector<double> iw, mtab;

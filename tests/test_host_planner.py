@@ -265,6 +265,27 @@ def test_scale_table_matches_oracle_cuboid(box, tol):
     assert np.max(np.abs((S * D - M)[both])) <= 2 * p.fit_tol * np.max(M)
 
 
+def test_host_tables_reject_parameters_the_planner_never_makes():
+    """ewald_window_fit, ewald_radial_fit and ewald_scale_table take an ewald_params from the caller:
+    a window support or degree out of range (a negative window degree used to crash the host), a
+    non-positive or NaN bandlimit or cutoff, or a scalar m that is not grid[0] return EWALD_EINVAL."""
+    import ctypes
+    base = pe.plan_params(1.0, 1000, 1e-6)
+    z = np.linspace(-1, 1, 5)
+    r = np.linspace(0.01, 0.1, 5)
+    W, DW, R, G = np.empty(5 * 24), np.empty(5 * 24), np.empty(5), np.empty(5)
+    S = np.empty(base.grid[0] * base.grid[1] * (base.grid[2] // 2 + 1))
+    for field, value in [("P", 0), ("P", 25), ("deg_w", -1), ("deg_w", 500), ("deg_r", -2), ("deg_g", -1),
+                         ("cw", float("nan")), ("cs", -1.0), ("rc", 0.0), ("m", 0), ("alpha", 0.0)]:
+        p = pe.ewald_params()
+        ctypes.memmove(ctypes.byref(p), ctypes.byref(base), ctypes.sizeof(p))
+        setattr(p, field, value)
+        assert pe.lib.ewald_window_fit(ctypes.byref(p), 5, pe._ptr(z), pe._ptr(W), pe._ptr(DW)) == pe.EWALD_EINVAL
+        assert pe.lib.ewald_radial_fit(ctypes.byref(p), 5, pe._ptr(r), pe._ptr(R), pe._ptr(G)) == pe.EWALD_EINVAL
+        assert pe.lib.ewald_scale_table(ctypes.byref(p), pe._ptr(S)) == pe.EWALD_EINVAL, field
+    assert pe.lib.ewald_window_fit(ctypes.byref(base), 5, pe._ptr(z), pe._ptr(W), pe._ptr(DW)) == pe.EWALD_OK
+
+
 def test_precision_paths():
     """MIXED below tol 1e-7 runs the float-float kernels; float-float plans size their fits like FP64."""
     for tol in (1e-8, 1e-10, 1e-12):
