@@ -286,6 +286,34 @@ def test_host_tables_reject_parameters_the_planner_never_makes():
     assert pe.lib.ewald_window_fit(ctypes.byref(base), 5, pe._ptr(z), pe._ptr(W), pe._ptr(DW)) == pe.EWALD_OK
 
 
+def test_null_arguments_are_rejected():
+    """Every entry point that takes a plan, parameters or output pointers returns EWALD_EINVAL on NULL
+    (before any CUDA call); destroying a NULL plan is a no-op."""
+    import ctypes
+    lib = pe.lib
+    buf = np.zeros(16)
+    cnt = ctypes.c_int(0)
+    p = pe.ewald_params()
+    calls = [lambda: lib.ewald_profile(None, 1),
+             lambda: lib.ewald_profile_read(None, pe._ptr(buf), ctypes.byref(cnt)),
+             lambda: lib.ewald_check(None, None),
+             lambda: lib.ewald_debug_grid(None, 0, pe._ptr(buf)),
+             lambda: lib.ewald_plan_query(None, None),
+             lambda: lib.ewald_eval(None, None, None, None, None, None, None),
+             lambda: lib.ewald_eval_host(None, None, None, None, None, None, None),
+             lambda: lib.ewald_eval_batch(None, None, None, None, None, None, None, None),
+             lambda: lib.ewald_plan_params_box(None, 100, ctypes.c_double(1e-6), None, ctypes.byref(p)),
+             lambda: lib.ewald_plan_params(ctypes.c_double(1.0), 100, ctypes.c_double(1e-6), None, None),
+             lambda: lib.ewald_opts_default(None),
+             lambda: lib.ewald_window_fit(None, 0, None, None, None),
+             lambda: lib.ewald_radial_fit(None, 0, None, None, None),
+             lambda: lib.ewald_scale_table(None, None),
+             lambda: lib.ewald_spread_static(None, None, None, None, None)]
+    for k, call in enumerate(calls):
+        assert call() == pe.EWALD_EINVAL, k
+    lib.ewald_plan_destroy(None)
+
+
 def test_precision_paths():
     """MIXED below tol 1e-7 runs the float-float kernels; float-float plans size their fits like FP64."""
     for tol in (1e-8, 1e-10, 1e-12):
