@@ -314,6 +314,28 @@ def test_null_arguments_are_rejected():
     lib.ewald_plan_destroy(None)
 
 
+def test_static_spread_rejects_parameters_before_any_device_work():
+    """ewald_spread_static checks its parameters before any CUDA call (the pointers below are never
+    dereferenced): float32 (tile 8) parameters, a cuboid box, a window support out of range, no
+    particles, and scratch beyond its static array."""
+    import ctypes
+    dummy = ctypes.c_void_p(16)
+
+    def call(p):
+        return pe.lib.ewald_spread_static(ctypes.byref(p), dummy, dummy, dummy, None), pe.lib.ewald_last_error()
+
+    code, msg = call(pe.plan_params(1.0, 1000, 1e-6, precision="mixed"))
+    assert code == pe.EWALD_EINVAL and b"tile 8" in msg
+    code, msg = call(pe.plan_params((1.0, 1.0, 2.0), 1000, 1e-6))
+    assert code == pe.EWALD_EINVAL and b"cubic" in msg
+    for field, value in [("P", 30), ("n", 0), ("deg_w", 0)]:
+        p = pe.plan_params(1.0, 1000, 1e-6)
+        setattr(p, field, value)
+        assert call(p)[0] == pe.EWALD_EINVAL, field
+    code, msg = call(pe.plan_params(1.0, 10_000_000, 1e-8))
+    assert code == pe.EWALD_ETOOBIG and b"static array" in msg
+
+
 def test_precision_paths():
     """MIXED below tol 1e-7 runs the float-float kernels; float-float plans size their fits like FP64."""
     for tol in (1e-8, 1e-10, 1e-12):
